@@ -1,0 +1,735 @@
+// FP64 CPU oracle for the D3Q19 + immersed-boundary blood-flow step.
+//
+// TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the CPU
+// baseline leg of the benchmark load this library.  It shares no code, no
+// header and no table with the CUDA library: every step below is written out
+// plainly, in the order the paper states it, in double precision, without
+// blocking, fusion or reordering.
+//
+// Source: Gusenbauer et al., "A tunable cancer cell filter using magnetic
+// beads: cellular and fluid dynamic simulations" (arXiv:1110.0995).
+//   Sec. 2.1  lattice-Boltzmann equation with an external force term (D3Q19).
+//   Sec. 2.2  immersed-boundary cycle: transmit velocity to IB points,
+//             compute node forces, spread them with an approximate delta
+//             function, advance fluid and points.
+//   Sec. 2.3.1 membrane moduli K^S (stretching), K^B (bending), K^A_l / K^A_g
+//             (local / global area) and K^V (volume).
+//   Sec. 2.3.3 the global area and volume need every node of a cell.
+//   Sec. 2.4  bounce-back walls, obstacle nodes, no inside/outside distinction.
+//
+// The paper prints no formula for f^eq, the forcing term, the delta function or
+// the membrane forces.  The readings used here (standard second-order
+// equilibrium, Guo forcing, halfway bounce-back, trilinear delta, Dupin-style
+// neo-Hookean stretching, dihedral-angle bending energy, homocentric area
+// forces, facet-normal volume forces, massless IB points advected with the
+// interpolated velocity) are each stated at the function that implements them.
+//
+// Layouts: lattice node p = x + nx*(y + ny*z); populations f[i*N + p];
+// vector fields SoA v[d*N + p]; IB node positions / forces AoS x[3*j + d].
+// Compiled with -ffp-contract=off so that no multiply-add is fused.
+
+#include <cmath>
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <vector>
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// D3Q19 velocity set (Sec. 2.1: "D3Q19 (three dimensions with 19 discrete
+// velocities)").  Weights are not printed in the paper; these are the standard
+// isotropic ones (w0 = 1/3, axis 1/18, diagonal 1/36, c_s^2 = 1/3).  Opposite
+// directions come in consecutive pairs (1,2), (3,4), ..., (17,18).
+// ---------------------------------------------------------------------------
+const int Q = 19;
+const int EV[Q][3] = {
+    {0, 0, 0},
+    {1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1},
+    {1, 1, 0}, {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0},
+    {1, 0, 1}, {-1, 0, -1}, {1, 0, -1}, {-1, 0, 1},
+    {0, 1, 1}, {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
+const double WQ[Q] = {
+    1.0 / 3.0,
+    1.0 / 18.0, 1.0 / 18.0, 1.0 / 18.0, 1.0 / 18.0, 1.0 / 18.0, 1.0 / 18.0,
+    1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0,
+    1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
+const int OPP[Q] = {0, 2, 1, 4, 3, 6, 5, 8, 7, 10, 9, 12, 11, 14, 13, 16, 15, 18, 17};
+
+inline double val(double a) { return a; }
+
+// ---------------------------------------------------------------------------
+// Equilibrium (Sec. 2.1: f^eq depends on rho and u; form not printed).
+// Reading: f_i^eq = w_i rho [1 + 3 e.u + 9/2 (e.u)^2 - 3/2 u.u].
+// ---------------------------------------------------------------------------
+template <class R>
+void equilibrium(R rho, const R u[3], R feq[Q]) {
+    R uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    for (int i = 0; i < Q; ++i) {
+        R eu = EV[i][0] * u[0] + EV[i][1] * u[1] + EV[i][2] * u[2];
+        feq[i] = WQ[i] * rho * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * uu);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Forcing term F_i of the LB equation (Sec. 2.1: "F_i is the external force
+// exerted by the immersed objects on the fluid"; scheme not printed).
+// Reading: Guo et al. (2002),
+//   F_i = (1 - 1/(2 tau)) w_i [3 (e_i - u) + 9 (e_i.u) e_i] . g,
+// used together with the velocity u = (sum_i f_i e_i + g/2) / rho.
+// ---------------------------------------------------------------------------
+template <class R>
+void guo_source(double tau, const R u[3], const R g[3], R S[Q]) {
+    double pre = 1.0 - 1.0 / (2.0 * tau);
+    for (int i = 0; i < Q; ++i) {
+        R eu = EV[i][0] * u[0] + EV[i][1] * u[1] + EV[i][2] * u[2];
+        R s = 0.0;
+        for (int d = 0; d < 3; ++d)
+            s = s + (3.0 * (EV[i][d] - u[d]) + 9.0 * eu * EV[i][d]) * g[d];
+        S[i] = pre * WQ[i] * s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Fluid lattice (Sec. 2.1, 2.4)
+// ---------------------------------------------------------------------------
+template <class R>
+struct Fluid {
+    int nx = 0, ny = 0, nz = 0;
+    long n = 0;
+    double tau = 1.0;
+    double G[3] = {0, 0, 0};           // uniform body force density
+    int per[3] = {1, 0, 0};            // periodic axes; others carry halfway walls
+    double uw[2][3] = {{0, 0, 0}, {0, 0, 0}};  // y-low / y-high wall velocity (tests)
+    std::vector<R> f, fn;              // populations, current and next
+    std::vector<R> g;                  // IB force density spread this step
+    std::vector<R> gext;               // optional static extra force density
+    std::vector<uint8_t> solid;        // 1 = obstacle node
+    std::vector<R> rho, u;             // moments of the last collision
+
+    long idx(int x, int y, int z) const { return x + (long)nx * (y + (long)ny * z); }
+};
+
+template <class R>
+void fluid_init(Fluid<R>& F, int nx, int ny, int nz) {
+    F.nx = nx; F.ny = ny; F.nz = nz;
+    F.n = (long)nx * ny * nz;
+    F.f.assign((size_t)Q * F.n, R(0.0));
+    F.fn.assign((size_t)Q * F.n, R(0.0));
+    F.g.assign((size_t)3 * F.n, R(0.0));
+    F.solid.assign((size_t)F.n, 0);
+    F.rho.assign((size_t)F.n, R(1.0));
+    F.u.assign((size_t)3 * F.n, R(0.0));
+    for (int i = 0; i < Q; ++i)
+        for (long p = 0; p < F.n; ++p) F.f[(size_t)i * F.n + p] = WQ[i];
+}
+
+// One LB time step, Sec. 2.1:
+//   f_i(x + e_i, t + 1) = f_i(x, t) - (f_i - f_i^eq)/tau + F_i.
+// Done literally: per fluid node compute rho and u, collide, then move the
+// post-collision value along e_i ("propagation").  A link that ends outside the
+// domain (non-periodic axis) or on an obstacle node is reflected back into the
+// node it came from, reversed (Sec. 2.4: "at the boundary the direction of
+// velocity is inverted"); reading: halfway bounce-back, wall half a link away.
+// A moving y-wall adds Ladd's momentum term -6 w_i rho0 (e_i . u_w), rho0 = 1.
+// The force density at every fluid node is g_IB + g_ext + G: there is no
+// inside/outside distinction (Sec. 2.4).
+template <class R>
+void lb_step(Fluid<R>& F) {
+    const long N = F.n;
+#pragma omp parallel for schedule(static)
+    for (int z = 0; z < F.nz; ++z) {
+        for (int y = 0; y < F.ny; ++y) {
+            for (int x = 0; x < F.nx; ++x) {
+                const long p = F.idx(x, y, z);
+                if (F.solid[p]) {
+                    for (int i = 0; i < Q; ++i) F.fn[(size_t)i * N + p] = F.f[(size_t)i * N + p];
+                    F.rho[p] = 1.0;
+                    for (int d = 0; d < 3; ++d) F.u[(size_t)d * N + p] = 0.0;
+                    continue;
+                }
+                R fl[Q];
+                for (int i = 0; i < Q; ++i) fl[i] = F.f[(size_t)i * N + p];
+                R rho = 0.0;
+                for (int i = 0; i < Q; ++i) rho = rho + fl[i];
+                R mom[3] = {0.0, 0.0, 0.0};
+                for (int i = 0; i < Q; ++i)
+                    for (int d = 0; d < 3; ++d) mom[d] = mom[d] + EV[i][d] * fl[i];
+                R g[3];
+                for (int d = 0; d < 3; ++d) {
+                    g[d] = F.g[(size_t)d * N + p] + F.G[d];
+                    if (!F.gext.empty()) g[d] = g[d] + F.gext[(size_t)d * N + p];
+                }
+                R u[3];
+                for (int d = 0; d < 3; ++d) u[d] = (mom[d] + 0.5 * g[d]) / rho;
+                R feq[Q], S[Q];
+                equilibrium(rho, u, feq);
+                guo_source(F.tau, u, g, S);
+                F.rho[p] = rho;
+                for (int d = 0; d < 3; ++d) F.u[(size_t)d * N + p] = u[d];
+                for (int i = 0; i < Q; ++i) {
+                    R post = fl[i] - (fl[i] - feq[i]) / F.tau + S[i];
+                    int c[3] = {x + EV[i][0], y + EV[i][1], z + EV[i][2]};
+                    const int dim[3] = {F.nx, F.ny, F.nz};
+                    bool blocked = false;
+                    int wall = -1;
+                    for (int d = 0; d < 3; ++d) {
+                        if (c[d] < 0 || c[d] >= dim[d]) {
+                            if (F.per[d]) {
+                                c[d] = (c[d] + dim[d]) % dim[d];
+                            } else {
+                                blocked = true;
+                                if (d == 1 && wall < 0) wall = (c[d] < 0) ? 0 : 1;
+                            }
+                        }
+                    }
+                    if (!blocked && F.solid[F.idx(c[0], c[1], c[2])]) blocked = true;
+                    if (blocked) {
+                        R back = post;
+                        if (wall >= 0) {
+                            double eu = EV[i][0] * F.uw[wall][0] + EV[i][1] * F.uw[wall][1] +
+                                        EV[i][2] * F.uw[wall][2];
+                            back = back - 6.0 * WQ[i] * 1.0 * eu;
+                        }
+                        F.fn[(size_t)OPP[i] * N + p] = back;
+                    } else {
+                        F.fn[(size_t)i * N + F.idx(c[0], c[1], c[2])] = post;
+                    }
+                }
+            }
+        }
+    }
+    F.f.swap(F.fn);
+}
+
+// ---------------------------------------------------------------------------
+// Immersed-boundary delta function (Sec. 2.2, steps 1 and 3: "discrete
+// approximate delta-function"; kernel not printed).  Reading: trilinear,
+// w(x - X) = prod_d (1 - |x_d - X_d|) over the 8 lattice nodes of the cell
+// containing X.  The same weights transmit velocity (step 1) and spread force
+// (step 3).  Nodes outside the domain on a non-periodic axis and obstacle nodes
+// take no force and contribute zero velocity; weights are not renormalised.
+// ---------------------------------------------------------------------------
+template <class R>
+struct Stencil {
+    long node[8];
+    R w[8];
+    bool ok[8];
+};
+
+template <class R>
+void stencil(const Fluid<R>& F, const R X[3], Stencil<R>& s) {
+    const int dim[3] = {F.nx, F.ny, F.nz};
+    long base[3];
+    for (int d = 0; d < 3; ++d) base[d] = (long)std::floor(val(X[d]));
+    for (int c = 0; c < 8; ++c) {
+        long xc[3] = {base[0] + (c & 1), base[1] + ((c >> 1) & 1), base[2] + ((c >> 2) & 1)};
+        R w = 1.0;
+        bool ok = true;
+        long ic[3];
+        for (int d = 0; d < 3; ++d) {
+            R dist = X[d] - (double)xc[d];
+            if (val(dist) < 0) dist = -dist;
+            w = w * (1.0 - dist);
+            long v = xc[d];
+            if (v < 0 || v >= dim[d]) {
+                if (F.per[d]) v = ((v % dim[d]) + dim[d]) % dim[d];
+                else ok = false;
+            }
+            ic[d] = v;
+        }
+        long p = ok ? F.idx((int)ic[0], (int)ic[1], (int)ic[2]) : -1;
+        if (ok && F.solid[p]) ok = false;
+        s.node[c] = p;
+        s.w[c] = w;
+        s.ok[c] = ok;
+    }
+}
+
+template <class R>
+void spread(const Fluid<R>& F, const R* X, const R* Fn, int n, R* g) {
+    for (int j = 0; j < n; ++j) {
+        Stencil<R> s;
+        stencil(F, &X[3 * j], s);
+        for (int c = 0; c < 8; ++c) {
+            if (!s.ok[c]) continue;
+            for (int d = 0; d < 3; ++d) g[(size_t)d * F.n + s.node[c]] = g[(size_t)d * F.n + s.node[c]] + s.w[c] * Fn[3 * j + d];
+        }
+    }
+}
+
+template <class R>
+void interpolate(const Fluid<R>& F, const R* X, int n, const R* u, R* U) {
+    for (int j = 0; j < n; ++j) {
+        Stencil<R> s;
+        stencil(F, &X[3 * j], s);
+        R acc[3] = {0.0, 0.0, 0.0};
+        for (int c = 0; c < 8; ++c) {
+            if (!s.ok[c]) continue;
+            for (int d = 0; d < 3; ++d) acc[d] = acc[d] + s.w[c] * u[(size_t)d * F.n + s.node[c]];
+        }
+        for (int d = 0; d < 3; ++d) U[3 * j + d] = acc[d];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Membrane mechanics (Sec. 2.3.1)
+// ---------------------------------------------------------------------------
+template <class R>
+inline void sub3(const R* a, const R* b, R* o) { o[0] = a[0] - b[0]; o[1] = a[1] - b[1]; o[2] = a[2] - b[2]; }
+template <class R>
+inline void cross3(const R* a, const R* b, R* o) {
+    o[0] = a[1] * b[2] - a[2] * b[1];
+    o[1] = a[2] * b[0] - a[0] * b[2];
+    o[2] = a[0] * b[1] - a[1] * b[0];
+}
+template <class R>
+inline R dot3(const R* a, const R* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+// Edge list of a closed oriented triangle mesh: every undirected edge {a,b}
+// with the triangle (a,b,c) that traverses it as a->b and the triangle (b,a,d)
+// that traverses it as b->a.  Returns false for a mesh that is not a closed
+// oriented 2-manifold.
+struct Topology {
+    int n = 0, nt = 0;
+    std::vector<int> tri;                 // 3 * nt
+    std::vector<int> ea, eb, ec, ed;      // per edge
+};
+
+bool build_topology(const int* tri, int nt, int n, Topology& T) {
+    T.n = n; T.nt = nt;
+    T.tri.assign(tri, tri + 3 * nt);
+    std::map<std::pair<int, int>, int> third;
+    for (int t = 0; t < nt; ++t) {
+        int v[3] = {tri[3 * t], tri[3 * t + 1], tri[3 * t + 2]};
+        for (int k = 0; k < 3; ++k) {
+            if (v[k] < 0 || v[k] >= n) return false;
+            std::pair<int, int> key(v[k], v[(k + 1) % 3]);
+            if (key.first == key.second) return false;
+            if (third.count(key)) return false;   // directed edge used twice
+            third[key] = v[(k + 2) % 3];
+        }
+    }
+    for (auto& kv : third) {
+        int a = kv.first.first, b = kv.first.second;
+        auto rev = third.find(std::make_pair(b, a));
+        if (rev == third.end()) return false;     // open boundary
+        if (a < b) {
+            T.ea.push_back(a); T.eb.push_back(b);
+            T.ec.push_back(kv.second); T.ed.push_back(rev->second);
+        }
+    }
+    return true;
+}
+
+// Dihedral angle at edge (a,b) between triangle (a,b,c) and triangle (b,a,d),
+// signed about the edge direction: theta = atan2((n1 x n2).e_hat, n1.n2).
+template <class R>
+R dihedral(const R* xa, const R* xb, const R* xc, const R* xd) {
+    R e[3], ac[3], ba[3], bd[3], n1[3], n2[3], m[3];
+    sub3(xb, xa, e); sub3(xc, xa, ac); sub3(xa, xb, ba); sub3(xd, xb, bd);
+    cross3(e, ac, n1);
+    cross3(ba, bd, n2);
+    cross3(n1, n2, m);
+    R le = std::sqrt(dot3(e, e));
+    return std::atan2(dot3(m, e) / le, dot3(n1, n2));
+}
+
+template <class R>
+R tri_area(const R* xa, const R* xb, const R* xc) {
+    R ab[3], ac[3], n[3];
+    sub3(xb, xa, ab); sub3(xc, xa, ac); cross3(ab, ac, n);
+    return 0.5 * std::sqrt(dot3(n, n));
+}
+
+// Enclosed volume of a closed outward mesh: V = sum_t x_a . (x_b x x_c) / 6.
+// Surface area: S = sum_t S_t.  (Sec. 2.3.3: both need every node of a cell.)
+template <class R>
+void area_volume(const R* x, const Topology& T, R& S, R& V) {
+    S = 0.0; V = 0.0;
+    for (int t = 0; t < T.nt; ++t) {
+        const R* a = &x[3 * T.tri[3 * t]];
+        const R* b = &x[3 * T.tri[3 * t + 1]];
+        const R* c = &x[3 * T.tri[3 * t + 2]];
+        R bc[3];
+        cross3(b, c, bc);
+        V = V + dot3(a, bc) / 6.0;
+        S = S + tri_area(a, b, c);
+    }
+}
+
+struct Rest {
+    std::vector<double> L0, th0, S0t;
+    double S0 = 0, V0 = 0;
+};
+
+void rest_state(const double* x0, const Topology& T, Rest& r) {
+    size_t ne = T.ea.size();
+    r.L0.resize(ne); r.th0.resize(ne); r.S0t.resize(T.nt);
+    for (size_t e = 0; e < ne; ++e) {
+        double d[3];
+        sub3(&x0[3 * T.eb[e]], &x0[3 * T.ea[e]], d);
+        r.L0[e] = std::sqrt(dot3(d, d));
+        r.th0[e] = dihedral(&x0[3 * T.ea[e]], &x0[3 * T.eb[e]], &x0[3 * T.ec[e]], &x0[3 * T.ed[e]]);
+    }
+    for (int t = 0; t < T.nt; ++t)
+        r.S0t[t] = tri_area(&x0[3 * T.tri[3 * t]], &x0[3 * T.tri[3 * t + 1]], &x0[3 * T.tri[3 * t + 2]]);
+    area_volume(x0, T, r.S0, r.V0);
+}
+
+enum { TERM_STRETCH = 1, TERM_BEND = 2, TERM_AREA_LOCAL = 4, TERM_AREA_GLOBAL = 8, TERM_VOLUME = 16, TERM_ALL = 31 };
+
+// Stretching, K^S (Sec. 2.3.1: nonlinear, "resembles a neo-Hookean
+// behavior"; formula not printed).  Reading (Dupin et al. 2007 neo-Hookean
+// bond): with lambda = L / L0,
+//   T(lambda) = ks * kappa(lambda) * (lambda - 1),
+//   kappa(lambda) = (lambda^(1/2) + lambda^(-5/2)) / (lambda + lambda^(-3)),
+// pulling both ends of a stretched edge together along the edge.
+template <class R>
+void force_stretch(const R* x, const Topology& T, const Rest& r, double ks, R* F) {
+    for (size_t e = 0; e < T.ea.size(); ++e) {
+        int a = T.ea[e], b = T.eb[e];
+        R d[3];
+        sub3(&x[3 * b], &x[3 * a], d);
+        R L = std::sqrt(dot3(d, d));
+        R lam = L / r.L0[e];
+        R sl = std::sqrt(lam);
+        R kappa = (sl + 1.0 / (lam * lam * sl)) / (lam + 1.0 / (lam * lam * lam));
+        R tension = ks * kappa * (lam - 1.0);
+        for (int k = 0; k < 3; ++k) {
+            R fk = tension * d[k] / L;
+            F[3 * a + k] = F[3 * a + k] + fk;
+            F[3 * b + k] = F[3 * b + k] - fk;
+        }
+    }
+}
+
+// Bending, K^B (Sec. 2.3.1: a preferred angle between the two faces sharing
+// an edge; the departure from it gives the force).  Reading: energy
+// E = (kb/2) (theta - theta0)^2 per edge and F = -grad E, distributed to all
+// four points of the two faces (which conserves momentum).  Gradient of the
+// dihedral angle (Bridson et al. 2003): with e = x_b - x_a, l = |e|,
+//   grad_c = -l n1/|n1|^2,  grad_d = -l n2/|n2|^2,
+//   grad_a = -(1 - s_c) grad_c - (1 - s_d) grad_d,
+//   grad_b = -s_c grad_c - s_d grad_d,   s_v = (x_v - x_a).e / l^2.
+template <class R>
+void force_bend(const R* x, const Topology& T, const Rest& r, double kb, R* F) {
+    for (size_t e = 0; e < T.ea.size(); ++e) {
+        int a = T.ea[e], b = T.eb[e], c = T.ec[e], d = T.ed[e];
+        const R *xa = &x[3 * a], *xb = &x[3 * b], *xc = &x[3 * c], *xd = &x[3 * d];
+        R theta = dihedral(xa, xb, xc, xd);
+        R ev[3], ac[3], ad[3], ba[3], bd[3], n1[3], n2[3];
+        sub3(xb, xa, ev); sub3(xc, xa, ac); sub3(xd, xa, ad); sub3(xa, xb, ba); sub3(xd, xb, bd);
+        cross3(ev, ac, n1);
+        cross3(ba, bd, n2);
+        R l2 = dot3(ev, ev);
+        R l = std::sqrt(l2);
+        R n1s = dot3(n1, n1), n2s = dot3(n2, n2);
+        R sc = dot3(ac, ev) / l2, sd = dot3(ad, ev) / l2;
+        R coef = -kb * (theta - r.th0[e]);
+        for (int k = 0; k < 3; ++k) {
+            R gc = -l * n1[k] / n1s;
+            R gd = -l * n2[k] / n2s;
+            R ga = -(1.0 - sc) * gc - (1.0 - sd) * gd;
+            R gb = -sc * gc - sd * gd;
+            F[3 * a + k] = F[3 * a + k] + coef * ga;
+            F[3 * b + k] = F[3 * b + k] + coef * gb;
+            F[3 * c + k] = F[3 * c + k] + coef * gc;
+            F[3 * d + k] = F[3 * d + k] + coef * gd;
+        }
+    }
+}
+
+// Area, K^A_l and K^A_g (Sec. 2.3.1: a force proportional to the change of
+// area that homocentrically shrinks or expands the face, computed per triangle
+// (local) and for the whole cell (global)).  Reading: on triangle t with
+// centroid c_t and w_i = x_i - c_t,
+//   F_i = -k * dA * (2 S_t / sum_j |w_j|^2) * w_i,
+// with dA = (S_t - S0_t)/S0_t (local, k = kal) or (S - S0)/S0 (global, k = kag):
+// along w_i (homocentric), with the virtual work of E = (k/2) dA^2 * S0 under a
+// homocentric scaling of the face.
+template <class R>
+void force_area(const R* x, const Topology& T, const Rest& r, double kal, double kag, R S, int terms, R* F) {
+    for (int t = 0; t < T.nt; ++t) {
+        int v[3] = {T.tri[3 * t], T.tri[3 * t + 1], T.tri[3 * t + 2]};
+        R St = tri_area(&x[3 * v[0]], &x[3 * v[1]], &x[3 * v[2]]);
+        R cen[3];
+        for (int k = 0; k < 3; ++k) cen[k] = (x[3 * v[0] + k] + x[3 * v[1] + k] + x[3 * v[2] + k]) / 3.0;
+        R w[3][3];
+        R ww = 0.0;
+        for (int i = 0; i < 3; ++i) {
+            sub3(&x[3 * v[i]], cen, w[i]);
+            ww = ww + dot3(w[i], w[i]);
+        }
+        R coef = 0.0;
+        if (terms & TERM_AREA_LOCAL) coef = coef - kal * (St - r.S0t[t]) / r.S0t[t];
+        if (terms & TERM_AREA_GLOBAL) coef = coef - kag * (S - r.S0) / r.S0;
+        coef = coef * 2.0 * St / ww;
+        for (int i = 0; i < 3; ++i)
+            for (int k = 0; k < 3; ++k) F[3 * v[i] + k] = F[3 * v[i] + k] + coef * w[i][k];
+    }
+}
+
+// Volume, K^V (Sec. 2.3.1: per facet a force proportional to the change of
+// volume, distributed to the facet's three points).  Reading:
+//   F_i += -kv (V - V0)/V0 * n_t / 6   for each vertex i of facet t,
+// n_t the unnormalised outward normal; on a closed mesh this is exactly
+// -grad of E = (kv/2) (V - V0)^2 / V0.
+template <class R>
+void force_volume(const R* x, const Topology& T, const Rest& r, double kv, R V, R* F) {
+    R coef = -kv * (V - r.V0) / r.V0 / 6.0;
+    for (int t = 0; t < T.nt; ++t) {
+        int v[3] = {T.tri[3 * t], T.tri[3 * t + 1], T.tri[3 * t + 2]};
+        R ab[3], ac[3], n[3];
+        sub3(&x[3 * v[1]], &x[3 * v[0]], ab);
+        sub3(&x[3 * v[2]], &x[3 * v[0]], ac);
+        cross3(ab, ac, n);
+        for (int i = 0; i < 3; ++i)
+            for (int k = 0; k < 3; ++k) F[3 * v[i] + k] = F[3 * v[i] + k] + coef * n[k];
+    }
+}
+
+// All node forces of one cell (Sec. 2.2 step 2), the sum of the selected terms.
+template <class R>
+void membrane_forces(const R* x, const Topology& T, const Rest& r, const double mod[5], int terms, R* F) {
+    for (int j = 0; j < 3 * T.n; ++j) F[j] = 0.0;
+    R S, V;
+    area_volume(x, T, S, V);
+    if (terms & TERM_STRETCH) force_stretch(x, T, r, mod[0], F);
+    if (terms & TERM_BEND) force_bend(x, T, r, mod[1], F);
+    if (terms & (TERM_AREA_LOCAL | TERM_AREA_GLOBAL)) force_area(x, T, r, mod[2], mod[3], S, terms, F);
+    if (terms & TERM_VOLUME) force_volume(x, T, r, mod[4], V, F);
+}
+
+// ---------------------------------------------------------------------------
+// Coupled system (Sec. 2.2, the four-step cycle)
+// ---------------------------------------------------------------------------
+template <class R>
+struct Cell {
+    Topology T;
+    Rest rest;
+    double mod[5];
+    std::vector<double> x0;
+    std::vector<R> x, F, U;
+};
+
+template <class R>
+struct System {
+    Fluid<R> fl;
+    std::vector<Cell<R>> cells;
+    long steps = 0;
+};
+
+// One cycle.  Sec. 2.2 lists: (1) velocity from the grid to the IB points,
+// (2) node forces, (3) spreading with the delta function, (4) fluid and point
+// motion.  Reading (massless IB points; Newton's m and a drag coefficient are
+// not given): the points move with the interpolated velocity of the fluid
+// update of the same cycle,
+//   F^t = F(X^t); g^t = spread(F^t, X^t); fluid update -> u^t;
+//   X^{t+1} = X^t + interp(u^t, X^t).
+template <class R>
+void system_step(System<R>& s) {
+    Fluid<R>& F = s.fl;
+    std::fill(F.g.begin(), F.g.end(), R(0.0));
+    for (auto& c : s.cells) {
+        membrane_forces(c.x.data(), c.T, c.rest, c.mod, TERM_ALL, c.F.data());
+        spread(F, c.x.data(), c.F.data(), c.T.n, F.g.data());
+    }
+    lb_step(F);
+    for (auto& c : s.cells) {
+        interpolate(F, c.x.data(), c.T.n, F.u.data(), c.U.data());
+        for (int j = 0; j < 3 * c.T.n; ++j) c.x[j] = c.x[j] + c.U[j];
+    }
+    s.steps++;
+}
+
+// Obstacles (Sec. 2.4 and 2.5: bead chains fixed in space are boundary
+// nodes).  A lattice node is solid iff it lies inside or on any sphere,
+// |x - c|^2 <= r^2, evaluated in double from the float inputs.
+void rasterise(const float* sph, int ns, int nx, int ny, int nz, uint8_t* solid) {
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                uint8_t s = 0;
+                for (int k = 0; k < ns; ++k) {
+                    double dx = (double)x - (double)sph[4 * k];
+                    double dy = (double)y - (double)sph[4 * k + 1];
+                    double dz = (double)z - (double)sph[4 * k + 2];
+                    double r = (double)sph[4 * k + 3];
+                    double d2 = dx * dx;
+                    d2 = d2 + dy * dy;
+                    d2 = d2 + dz * dz;
+                    if (d2 <= r * r) { s = 1; break; }
+                }
+                solid[x + (long)nx * (y + (long)ny * z)] = s;
+            }
+}
+
+}  // namespace
+
+// ===========================================================================
+// C interface (double precision) used from Python through ctypes.
+// ===========================================================================
+extern "C" {
+
+typedef System<double> OrSys;
+
+int or_version(void) { return 1; }
+
+void or_constants(int* e /*19x3*/, double* w /*19*/, int* opp /*19*/) {
+    for (int i = 0; i < Q; ++i) {
+        for (int d = 0; d < 3; ++d) e[3 * i + d] = EV[i][d];
+        w[i] = WQ[i];
+        opp[i] = OPP[i];
+    }
+}
+
+void or_equilibrium(double rho, const double* u, double* feq) { equilibrium(rho, u, feq); }
+
+void or_guo_source(double tau, const double* u, const double* g, double* S) { guo_source(tau, u, g, S); }
+
+void or_rasterise_spheres(const float* sph, int ns, int nx, int ny, int nz, uint8_t* solid) {
+    rasterise(sph, ns, nx, ny, nz, solid);
+}
+
+void* or_sys_create(int nx, int ny, int nz, double tau, const double* G, const int* per, const double* uw) {
+    if (nx < 1 || ny < 1 || nz < 1 || !(tau > 0.5)) return nullptr;
+    OrSys* s = new OrSys();
+    fluid_init(s->fl, nx, ny, nz);
+    s->fl.tau = tau;
+    for (int d = 0; d < 3; ++d) {
+        s->fl.G[d] = G ? G[d] : 0.0;
+        s->fl.per[d] = per ? per[d] : 0;
+    }
+    if (uw)
+        for (int k = 0; k < 6; ++k) s->fl.uw[k / 3][k % 3] = uw[k];
+    return s;
+}
+
+void or_sys_destroy(void* h) { delete (OrSys*)h; }
+
+void or_sys_set_solid(void* h, const uint8_t* solid) {
+    OrSys* s = (OrSys*)h;
+    std::memcpy(s->fl.solid.data(), solid, (size_t)s->fl.n);
+}
+
+void or_sys_set_extra_force(void* h, const double* g) {
+    OrSys* s = (OrSys*)h;
+    if (!g) { s->fl.gext.clear(); return; }
+    s->fl.gext.assign(g, g + 3 * s->fl.n);
+}
+
+void or_sys_init_equilibrium(void* h, double rho, const double* u) {
+    OrSys* s = (OrSys*)h;
+    double feq[Q];
+    equilibrium(rho, u, feq);
+    for (int i = 0; i < Q; ++i)
+        for (long p = 0; p < s->fl.n; ++p) s->fl.f[(size_t)i * s->fl.n + p] = feq[i];
+    for (long p = 0; p < s->fl.n; ++p) {
+        s->fl.rho[p] = rho;
+        for (int d = 0; d < 3; ++d) s->fl.u[(size_t)d * s->fl.n + p] = s->fl.solid[p] ? 0.0 : u[d];
+    }
+}
+
+void or_sys_get_f(void* h, double* f) {
+    OrSys* s = (OrSys*)h;
+    std::memcpy(f, s->fl.f.data(), sizeof(double) * Q * s->fl.n);
+}
+
+void or_sys_set_f(void* h, const double* f) {
+    OrSys* s = (OrSys*)h;
+    std::memcpy(s->fl.f.data(), f, sizeof(double) * Q * s->fl.n);
+}
+
+// rho and u of the last collision (the velocity the IB points were moved with).
+void or_sys_get_fields(void* h, double* rho, double* u) {
+    OrSys* s = (OrSys*)h;
+    if (rho) std::memcpy(rho, s->fl.rho.data(), sizeof(double) * s->fl.n);
+    if (u) std::memcpy(u, s->fl.u.data(), sizeof(double) * 3 * s->fl.n);
+}
+
+int or_sys_add_mesh(void* h, const double* x0, int n, const int* tri, int nt, const double* mod) {
+    OrSys* s = (OrSys*)h;
+    Cell<double> c;
+    if (!build_topology(tri, nt, n, c.T)) return -1;
+    c.x0.assign(x0, x0 + 3 * n);
+    rest_state(x0, c.T, c.rest);
+    if (!(c.rest.V0 > 0)) return -2;
+    for (int k = 0; k < 5; ++k) c.mod[k] = mod[k];
+    c.x.assign(x0, x0 + 3 * n);
+    c.F.assign(3 * n, 0.0);
+    c.U.assign(3 * n, 0.0);
+    s->cells.push_back(std::move(c));
+    return (int)s->cells.size() - 1;
+}
+
+void or_sys_set_nodes(void* h, int m, const double* x) {
+    OrSys* s = (OrSys*)h;
+    auto& c = s->cells[m];
+    std::memcpy(c.x.data(), x, sizeof(double) * 3 * c.T.n);
+}
+
+void or_sys_get_nodes(void* h, int m, double* x) {
+    OrSys* s = (OrSys*)h;
+    auto& c = s->cells[m];
+    std::memcpy(x, c.x.data(), sizeof(double) * 3 * c.T.n);
+}
+
+// Node forces of the last completed step (the forces spread in it).
+void or_sys_get_forces(void* h, int m, double* F) {
+    OrSys* s = (OrSys*)h;
+    auto& c = s->cells[m];
+    std::memcpy(F, c.F.data(), sizeof(double) * 3 * c.T.n);
+}
+
+void or_sys_step(void* h, int n_steps) {
+    OrSys* s = (OrSys*)h;
+    for (int k = 0; k < n_steps; ++k) system_step(*s);
+}
+
+// Standalone pieces used by the pin tests.
+int or_mesh_area_volume(const double* x, int n, const int* tri, int nt, double* S, double* V) {
+    Topology T;
+    if (!build_topology(tri, nt, n, T)) return -1;
+    area_volume(x, T, *S, *V);
+    return 0;
+}
+
+int or_mesh_edges(const int* tri, int nt, int n, int* edges /*4*E or NULL*/, int* n_edges) {
+    Topology T;
+    if (!build_topology(tri, nt, n, T)) return -1;
+    *n_edges = (int)T.ea.size();
+    if (edges)
+        for (size_t e = 0; e < T.ea.size(); ++e) {
+            edges[4 * e] = T.ea[e]; edges[4 * e + 1] = T.eb[e];
+            edges[4 * e + 2] = T.ec[e]; edges[4 * e + 3] = T.ed[e];
+        }
+    return 0;
+}
+
+int or_mesh_forces(const double* x, const double* x0, int n, const int* tri, int nt, const double* mod, int terms,
+                   double* F) {
+    Topology T;
+    if (!build_topology(tri, nt, n, T)) return -1;
+    Rest r;
+    rest_state(x0, T, r);
+    membrane_forces(x, T, r, mod, terms, F);
+    return 0;
+}
+
+double or_dihedral(const double* xa, const double* xb, const double* xc, const double* xd) {
+    return dihedral(xa, xb, xc, xd);
+}
+
+void or_spread(void* h, const double* X, const double* Fn, int n, double* g) {
+    OrSys* s = (OrSys*)h;
+    spread(s->fl, X, Fn, n, g);
+}
+
+void or_interpolate(void* h, const double* X, int n, const double* u, double* U) {
+    OrSys* s = (OrSys*)h;
+    interpolate(s->fl, X, n, u, U);
+}
+
+}  // extern "C"
