@@ -1,0 +1,321 @@
+"""Benchmark: D3Q19 + immersed-boundary MLUPS on one GB300.
+
+One step = one full immersed-boundary cycle of the method (per-cell area and
+volume, membrane forces + spreading, fused stream-collide with force,
+interpolation + advance) over the 256x128x64 micropost-filter workload
+(62 cells, 120 bead spheres), FP32 populations.  Inputs are resident in HBM;
+the populations (2 x 159 MB) are larger than the 126 MB L2.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
+
+Multi-GPU: the path is run as independent replicas (one per rank, no
+collective in the data path); `value` is the total over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+BYTES_PER_NODE = {"f32": 152, "f16": 76, "bf16": 76}   # 19 reads + 19 writes per fluid node update
+METRIC = "D3Q19+IBM MLUPS on 1 GB300 (% HBM roofline)"
+
+
+def make_workload(name: str):
+    from paper_1110_0995_gb300 import scene
+
+    if name == "micropost_filter_256x128x64":
+        return scene.micropost_filter(seed=11)
+    if name == "micropost_filter_512x256x128":
+        return scene.micropost_filter_large(seed=31)
+    if name == "channel_32x16x64_1rbc":
+        return scene.channel_plain(seed=1)
+    raise ValueError(name)
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        time.sleep(0.2)
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+        else:
+            self.lines = []
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            parts = [p.strip() for p in l.split(",")]
+            if len(parts) < 6:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[2:6]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        # samples taken while the GPU was busy (the sampler starts slightly before the region)
+        busy = sorted(sm)[len(sm) // 4:] or sm
+        return {"sm_mhz": statistics.median(busy), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_sample_scene(budget_nodes: int):
+    """A smaller instance of the filter workload (same post geometry family,
+    cell density, force) for the CPU oracle, about `budget_nodes` lattice nodes."""
+    from paper_1110_0995_gb300 import scene
+
+    for dims, cols, rows, nr, nc in [((256, 128, 64), 4, 3, 60, 2), ((128, 64, 64), 2, 2, 15, 1),
+                                     ((64, 64, 64), 1, 2, 8, 0), ((64, 32, 32), 1, 1, 2, 0),
+                                     ((32, 32, 16), 1, 1, 1, 0)]:
+        n = dims[0] * dims[1] * dims[2]
+        if n <= budget_nodes:
+            return scene.micropost_filter(seed=11, dims=dims, cols=cols, rows=rows, n_rbc=nr, n_ctc=nc), n
+    return scene.micropost_filter(seed=11, dims=(32, 32, 16), cols=1, rows=1, n_rbc=1, n_ctc=0), 32 * 32 * 16
+
+
+def time_oracle(sc, steps: int, warmup: int = 1):
+    import oracle
+
+    s = oracle.System.from_scene(sc)
+    s.step(warmup)
+    t0 = time.perf_counter()
+    s.step(steps)
+    return time.perf_counter() - t0
+
+
+def cpu_threads() -> int:
+    v = os.environ.get("OMP_NUM_THREADS")
+    return int(v) if v else (os.cpu_count() or 1)
+
+
+def cpu_baseline_line(target_seconds: float = 15.0):
+    """The oracle as it stands, on this host's cores, on a bounded sample of the workload."""
+    sc, n = oracle_sample_scene(256 * 128 * 64)
+    t1 = time_oracle(sc, 1, warmup=1)
+    steps = max(1, min(200, int(target_seconds / max(t1, 1e-3))))
+    dt = time_oracle(sc, steps, warmup=0)
+    return {"value": n * steps / dt / 1e6, "unit": "MLUPS", "cores": cpu_threads(), "kind": "oracle",
+            "sample": f"{steps} steps of the full {sc.dims[0]}x{sc.dims[1]}x{sc.dims[2]} filter "
+                      f"({len(sc.meshes)} cells), FP64 oracle, {cpu_threads()} OpenMP threads"}
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return 0
+    # calibrate: one oracle step of a small sample, then size the per-step sample
+    cal, ncal = oracle_sample_scene(64 * 32 * 32)
+    tcal = time_oracle(cal, 2, warmup=1) / 2
+    rate = ncal / tcal                              # node updates per second
+    budget = 150.0                                  # seconds for warm-up + timed steps
+    per_step_nodes = int(rate * budget / max(1, args.steps + args.warmup))
+    sc, n = oracle_sample_scene(per_step_nodes)
+    import oracle
+
+    s = oracle.System.from_scene(sc)
+    s.step(args.warmup)
+    t0 = time.perf_counter()
+    s.step(args.steps)
+    dt = time.perf_counter() - t0
+    v = n * args.steps / dt / 1e6
+    sample = (f"each step one oracle cycle of the {sc.dims[0]}x{sc.dims[1]}x{sc.dims[2]} filter sample "
+              f"({len(sc.meshes)} cells)")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.workload, "storage": "f64 oracle"},
+            "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": cpu_threads(), "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    rank, local_rank, world = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local_rank)
+    from paper_1110_0995_gb300 import _build, lbibm
+
+    _build.build()
+    sc = make_workload(args.workload)
+    stream = torch.cuda.Stream()
+    sim = lbibm.Simulation.from_scene(sc, storage=args.storage, stream=stream.cuda_stream)
+    n_nodes = sc.n_nodes
+    n_fluid = int((sim.solid_mask() == 0).sum())
+    sim.set_timing(True)
+    sim.step(args.warmup)
+    sim.synchronize()
+    sim.kernel_times()                              # discard warm-up timings
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clk, torch.cuda.stream(stream):
+        e0.record(stream)
+        sim.step(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    kms, kn = sim.kernel_times()
+    if world > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * n_nodes * args.steps / (ms * 1e-3) / 1e6
+
+    # roofline of the dominant kernel (fused stream-collide)
+    k3_ms = kms[2] / max(1, kn[2])
+    peak, peak_kind = measured_peak()
+    alg_bytes = BYTES_PER_NODE[args.storage] * n_fluid
+    achieved = alg_bytes / (k3_ms * 1e-3) / 1e9
+    traffic = None
+    tr_path = os.path.join(ROOT, "profiles", f"traffic_{args.workload}_{args.storage}.json")
+    if os.path.exists(tr_path):
+        with open(tr_path) as f:
+            traffic = json.load(f).get("bytes_per_launch")
+
+    # end to end through the C ABI with host buffers: scene upload from host,
+    # steps, node positions of every cell read back every 10 steps, final fields
+    e2e = None
+    if not args.no_e2e:
+        e2e_steps = args.steps
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s2 = lbibm.Simulation.from_scene(sc, storage=args.storage, stream=stream.cuda_stream)
+        h2d = sum(m.rest.nbytes + m.tris.nbytes for m in sc.meshes) + sc.spheres.nbytes
+        d2h = 0
+        bufs = [np.zeros((m.n_nodes, 3)) for m in sc.meshes]
+        done = 0
+        while done < e2e_steps:
+            k = min(10, e2e_steps - done)
+            s2.step(k)
+            done += k
+            for mi, b in enumerate(bufs):
+                s2.nodes_into(mi, b)
+                d2h += b.nbytes
+        rho, u = s2.fields()
+        d2h += rho.nbytes + u.nbytes
+        s2.synchronize()
+        dt = time.perf_counter() - t0
+        s2.close()
+        e2e = {"value": world * n_nodes * e2e_steps / dt / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": h2d / e2e_steps, "d2h_bytes_per_step": d2h / e2e_steps,
+               "includes": "context creation, scene upload, node readback every 10 steps, final fields"}
+
+    if rank == 0:
+        cpu = None if (args.no_cpu_baseline or world > 1) else cpu_baseline_line()
+        line = {
+            "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
+            "config": {"workload": args.workload, "lattice": list(sc.dims), "cells": len(sc.meshes),
+                       "ib_nodes": sc.n_ib_nodes, "spheres": int(len(sc.spheres)), "fluid_nodes": n_fluid,
+                       "storage": args.storage, "l2": "populations 2x%.0f MB > 126 MB L2" % (
+                           19 * BYTES_PER_NODE[args.storage] / 38 * n_nodes / 1e6),
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                         "kernel": "k_stream_collide", "alg_bytes_per_launch": alg_bytes,
+                         "avg_launch_ms": k3_ms},
+            "kernel_ms_per_step": {"cell_sums": kms[0] / max(1, kn[0]), "forces_spread": kms[1] / max(1, kn[1]),
+                                   "stream_collide": k3_ms, "interp_advance": kms[3] / max(1, kn[3])},
+            "ib_node_updates_per_s": world * sc.n_ib_nodes * args.steps / (ms * 1e-3),
+            "gpu_launches": int(sum(kn)),
+            "clocks": clk.summary(),
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="micropost_filter_256x128x64")
+    ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,191 @@
+/*
+ * lbibm.h - C ABI of the GB300 lattice-Boltzmann + immersed-boundary library.
+ *
+ * The library advances the blood-flow model of Gusenbauer et al., "A tunable
+ * cancer cell filter using magnetic beads: cellular and fluid dynamic
+ * simulations" (arXiv:1110.0995) on one NVIDIA GB300 (sm_103a):
+ *
+ *   - D3Q19 lattice-Boltzmann with an external force term (Sec. 2.1),
+ *   - bounce-back walls and fixed obstacle nodes such as bead chains and
+ *     microposts (Sec. 2.4, 2.5),
+ *   - the immersed-boundary cycle (Sec. 2.2): velocity transmitted from the
+ *     grid to the IB points, node forces from the cell membranes (Sec. 2.3.1:
+ *     stretching K^S, bending K^B, local/global area K^A_l/K^A_g, volume K^V),
+ *     forces spread back onto the grid, fluid and points advanced.
+ *
+ * Conventions (all entry points):
+ *   - Lattice units.  Lattice node (x, y, z), 0 <= x < nx etc., has linear
+ *     index p = x + nx * (y + ny * z).  Non-periodic axes carry halfway
+ *     bounce-back walls at -1/2 and n - 1/2.
+ *   - The caller owns every array it passes.  Inputs are copied during the
+ *     call; outputs are written into caller buffers, on the host unless a
+ *     `dst_is_device` argument says the pointer is device memory (for example
+ *     a torch tensor's data pointer on the context's device).
+ *   - The library owns all device memory of a context (allocated in
+ *     lb_create / ibm_add_mesh / lb_set_obstacles, freed in lb_destroy).
+ *   - Work is queued on the CUDA stream given to lb_create (NULL = the legacy
+ *     default stream).  Calls that return data synchronise that stream.
+ *   - No exception or abort crosses the ABI.  Every call returns an
+ *     lb_status; lb_last_error() gives a message.  A CUDA error poisons the
+ *     context: every later call returns LB_ERR_CUDA.
+ *   - One context per stream; calls on one context are not thread-safe.
+ */
+#ifndef LBIBM_H
+#define LBIBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lb_ctx lb_ctx;
+
+typedef enum {
+    LB_OK = 0,
+    LB_ERR_ARG = 1,      /* invalid argument (sizes, tau <= 1/2, open mesh, ...) */
+    LB_ERR_STATE = 2,    /* call not allowed in the context's current state */
+    LB_ERR_CUDA = 3,     /* CUDA runtime error; the context is poisoned */
+    LB_ERR_OOM = 4,      /* device allocation failed */
+    LB_ERR_NUMERIC = 5,  /* non-finite value or |u| above the stability bound */
+    LB_ERR_TIMEOUT = 6   /* a bounded device-side wait ran out */
+} lb_status;
+
+/* Storage of the populations.  Arithmetic is FP32 in every mode.
+ * LB_F32:          shifted populations h_i = f_i - w_i (rho0 = 1) in FP32.
+ * LB_F16_SHIFTED:  h_i / w_i stored as IEEE binary16, round-to-nearest-even.
+ * LB_BF16_SHIFTED: h_i / w_i stored as bfloat16, round-to-nearest-even. */
+typedef enum { LB_F32 = 0, LB_F16_SHIFTED = 1, LB_BF16_SHIFTED = 2 } lb_storage;
+
+typedef struct {
+    int nx, ny, nz;              /* lattice dimensions, each >= 1; nx*ny*nz <= 2^31 - 1 */
+    double tau;                  /* BGK relaxation time (Sec. 2.1), > 1/2 */
+    double body_force[3];        /* uniform force density at every fluid node */
+    int periodic[3];             /* 1 = periodic axis, 0 = bounce-back walls */
+    double wall_velocity[2][3];  /* velocity of the y = -1/2 and y = ny - 1/2 walls */
+    lb_storage storage;
+    int reserved[4];             /* must be zero */
+} lb_params;
+
+/* Membrane moduli of one cell (Sec. 2.3.1, Table 1). */
+typedef struct {
+    double ks;   /* stretching K^S (neo-Hookean bond) */
+    double kb;   /* bending K^B (dihedral angle) */
+    double kal;  /* local area K^A_l (per triangle) */
+    double kag;  /* global area K^A_g (whole cell) */
+    double kv;   /* volume K^V */
+} ibm_moduli;
+
+/* Create a context: allocates the lattice (two population buffers, force and
+ * velocity fields) and fills it with the rest equilibrium rho = 1, u = 0.
+ * `cuda_stream` is a cudaStream_t (or NULL).  LB_ERR_ARG for invalid params,
+ * LB_ERR_OOM if the lattice does not fit. */
+lb_status lb_create(const lb_params* params, void* cuda_stream, lb_ctx** out);
+
+/* Batched variant: `n_channels` independent lattices (one params entry each,
+ * all with the same storage) advanced together, one launch per kernel per
+ * step for the whole batch (Sec. 3.1's gap sweep is such a batch).  Channel
+ * k's meshes and obstacles are addressed with lb_select_channel. */
+lb_status lb_create_batch(const lb_params* params, int n_channels, void* cuda_stream, lb_ctx** out);
+
+/* Select the channel that later lb_set_obstacles / ibm_add_mesh /
+ * lb_get_fields / lb_get_populations calls refer to (default 0). */
+lb_status lb_select_channel(lb_ctx* ctx, int channel);
+
+/* Free all device memory of the context.  NULL is accepted. */
+lb_status lb_destroy(lb_ctx* ctx);
+
+/* Obstacles (Sec. 2.4, 2.5): every lattice node inside or on one of the `n`
+ * spheres spheres[4k..4k+3] = (cx, cy, cz, r) becomes a solid bounce-back
+ * node; the test |x - c|^2 <= r^2 is evaluated in double from the float
+ * inputs.  `extra_mask` (optional, nx*ny*nz bytes, nonzero = solid) adds
+ * arbitrary solid nodes.  Replaces any previous obstacles.  Only before the
+ * first lb_step (LB_ERR_STATE otherwise). */
+lb_status lb_set_obstacles(lb_ctx* ctx, const float* spheres, int n, const uint8_t* extra_mask);
+
+/* Obstacle map of the selected channel: N bytes, 1 = solid node (host). */
+lb_status lb_get_mask(lb_ctx* ctx, uint8_t* solid);
+
+/* Add one closed cell membrane (Sec. 2.2, 2.3): `rest_xyz` (n_nodes x 3,
+ * lattice units) is the rest shape already placed in the channel and also the
+ * initial position; `tris` (n_tris x 3) are outward counter-clockwise
+ * triangles.  The mesh must be a closed oriented 2-manifold with positive
+ * volume and node valence <= 64 (LB_ERR_ARG otherwise). Positions are kept
+ * in 64-bit fixed point with 2^-40 lu resolution.  Only before the first
+ * lb_step.  *mesh_id receives the index of the mesh within the channel. */
+lb_status ibm_add_mesh(lb_ctx* ctx, const double* rest_xyz, int n_nodes, const int32_t* tris, int n_tris,
+                       const ibm_moduli* moduli, int* mesh_id);
+
+/* Overwrite the current node positions of one mesh (n_nodes x 3, host). */
+lb_status ibm_set_nodes(lb_ctx* ctx, int mesh_id, const double* xyz);
+
+/* Advance `n_steps` immersed-boundary cycles (Sec. 2.2): per-cell area and
+ * volume (FP64 reduction), node forces, spreading, fused stream-collide with
+ * force, velocity interpolation and point advance.  Asynchronous on the
+ * context's stream; launched as a CUDA graph after the first call. */
+lb_status lb_step(lb_ctx* ctx, int n_steps);
+
+/* Wait for the context's stream and report any pending error. */
+lb_status lb_synchronize(lb_ctx* ctx);
+
+/* Density (N floats) and velocity (3 x N floats, SoA: u[d*N + p]) of the last
+ * step's collision, for the selected channel; either pointer may be NULL.
+ * The velocity is the force-corrected u = (sum_i f_i e_i + g/2) / rho; solid
+ * nodes report rho = 1, u = 0.  Before any step: rho = 1, u = 0. */
+lb_status lb_get_fields(lb_ctx* ctx, float* rho, float* u, int dst_is_device);
+
+/* Pre-collision populations f_i(x, t) of the next step (19 x N doubles,
+ * direction-major f[i*N + p], D3Q19 order: rest, +-x, +-y, +-z, then
+ * (+-1,+-1,0), (+-1,0,+-1), (0,+-1,+-1) with opposite directions adjacent),
+ * for the selected channel, on the host. */
+lb_status lb_get_populations(lb_ctx* ctx, double* f);
+
+/* Set the pre-collision populations of the next step (same layout). */
+lb_status lb_set_populations(lb_ctx* ctx, const double* f);
+
+/* Current node positions of one mesh of the selected channel (n x 3, host). */
+lb_status ibm_get_nodes(lb_ctx* ctx, int mesh_id, double* xyz);
+
+/* Node forces spread in the last step (n x 3, host). */
+lb_status ibm_get_forces(lb_ctx* ctx, int mesh_id, double* f);
+
+/* Per-cell surface area and volume at the current positions (FP64 sums),
+ * for every mesh of the selected channel, in mesh order (host). */
+lb_status ibm_get_area_volume(lb_ctx* ctx, double* area, double* volume);
+
+/* Conservation diagnostics of the selected channel, FP64 on the device:
+ * out[0] = sum of rho over fluid nodes, out[1..3] = sum of sum_i e_i f_i
+ * after the last collision, out[4] = number of non-finite populations,
+ * out[5] = max |u| over fluid nodes.  Returns LB_ERR_NUMERIC when out[4] > 0
+ * or out[5] > `u_max` (pass u_max <= 0 to skip the bound). */
+lb_status lb_diagnostics(lb_ctx* ctx, double u_max, double out[6]);
+
+/* Number of completed steps. */
+lb_status lb_get_step(lb_ctx* ctx, int64_t* step);
+
+/* Checkpoint: with buf == NULL, *bytes receives the size; otherwise the
+ * whole device state (populations, force fields, positions, step) is copied
+ * into buf (host, *bytes large enough). */
+lb_status lb_save_state(lb_ctx* ctx, void* buf, size_t* bytes);
+lb_status lb_load_state(lb_ctx* ctx, const void* buf, size_t bytes);
+
+/* Optional per-kernel timing: when enabled, lb_step records CUDA events
+ * around every launch of each kernel (no graph), and lb_kernel_times returns
+ * the accumulated milliseconds and launch counts per kernel class:
+ * 0 = cell area/volume, 1 = membrane forces + spreading,
+ * 2 = fused stream-collide, 3 = interpolation + advance. */
+lb_status lb_set_timing(lb_ctx* ctx, int enable);
+lb_status lb_kernel_times(lb_ctx* ctx, double ms[4], int64_t launches[4]);
+
+/* Static message for the last error on this context (never NULL). */
+const char* lb_last_error(const lb_ctx* ctx);
+
+/* Library version: major * 10000 + minor * 100 + patch. */
+int lb_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBIBM_H */

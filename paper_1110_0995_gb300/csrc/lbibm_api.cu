@@ -1,0 +1,1034 @@
+// C ABI of the GB300 lattice-Boltzmann + immersed-boundary library (see
+// include/lbibm.h).  Host-side responsibilities: argument validation, the
+// membrane topology (node rings, wing vertices, rest lengths / angles / areas
+// in FP64), device memory, and the order of the four kernels of one cycle of
+// Sec. 2.2 (area/volume sums -> forces + spreading -> stream-collide ->
+// interpolation + advance), launched directly or replayed as CUDA graphs.
+#include "lbibm.h"
+#include "lbibm_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+using namespace lbibm;
+
+namespace {
+
+constexpr int CHUNK_TRIS = 512;     // triangles per block of the area/volume reduction
+constexpr int MAX_VALENCE = 64;
+
+struct ChannelHost {
+    lb_params p;
+    ChannelDev d;
+    int n_blocks = 0;
+};
+
+struct MeshHost {
+    int ch = 0;
+    int node0 = 0, n = 0;
+    int tri0 = 0, nt = 0;
+    int cell = 0;
+    double S0 = 0, V0 = 0;
+};
+
+struct EventPair {
+    cudaEvent_t a, b;
+    int cls;
+};
+
+}  // namespace
+
+struct lb_ctx {
+    std::string err = "no error";
+    bool poisoned = false;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    lb_storage storage = LB_F32;
+    std::vector<ChannelHost> ch;
+    int cur = 0;
+    long long Ntot = 0;
+    int total_blocks = 0;
+    // lattice
+    void* h[2] = {nullptr, nullptr};
+    uint32_t* mask = nullptr;
+    uint8_t* slow = nullptr;
+    float4* g[2] = {nullptr, nullptr};
+    uint8_t* fl[2] = {nullptr, nullptr};
+    float4* u = nullptr;
+    ChannelDev* d_ch = nullptr;
+    double* diag_partials = nullptr;
+    double* diag_out = nullptr;
+    int diag_blocks = 0;
+    // immersed boundary, host staging
+    std::vector<Q4> hq0, hq;
+    std::vector<int> hcell_of;
+    std::vector<float4> hr0;
+    std::vector<int> hring_off{0};
+    std::vector<int2> hring;
+    std::vector<float4> hring_rest;
+    std::vector<int4> htris;
+    std::vector<float> htriS0;
+    std::vector<int4> hchunks;
+    std::vector<CellDev> hcells;
+    std::vector<MeshHost> meshes;
+    std::vector<std::vector<int>> ch_meshes;
+    bool committed = false;
+    // immersed boundary, device
+    int M = 0, C = 0, T = 0, NCH = 0, K = 0;
+    Q4* q[2] = {nullptr, nullptr};
+    Q4* q0 = nullptr;
+    float4 *xr = nullptr, *dl = nullptr, *r0 = nullptr, *F = nullptr;
+    int* cell_of = nullptr;
+    int* ring_off = nullptr;
+    int2* ring = nullptr;
+    float4* ring_rest = nullptr;
+    int4* tris = nullptr;
+    float* triS0 = nullptr;
+    int4* chunks = nullptr;
+    double2* partials = nullptr;
+    unsigned* counters = nullptr;
+    double2* cell_sums = nullptr;
+    CellDev* d_cells = nullptr;
+    // stepping
+    long long step = 0;
+    bool started = false;
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    // timing
+    bool timing = false;
+    double ms[4] = {0, 0, 0, 0};
+    long long launches[4] = {0, 0, 0, 0};
+    std::vector<EventPair> pending;
+    std::vector<cudaEvent_t> free_events;
+    std::vector<void*> allocations;
+};
+
+namespace {
+
+lb_status fail(lb_ctx* c, lb_status s, const std::string& msg) {
+    if (c) c->err = msg;
+    return s;
+}
+
+lb_status cuda_fail(lb_ctx* c, cudaError_t e, const char* where) {
+    if (c) {
+        c->poisoned = true;
+        c->err = std::string(where) + ": " + cudaGetErrorString(e);
+    }
+    return e == cudaErrorMemoryAllocation ? LB_ERR_OOM : LB_ERR_CUDA;
+}
+
+#define LB_CUDA(expr)                                            \
+    do {                                                         \
+        cudaError_t e_ = (expr);                                 \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #expr); \
+    } while (0)
+
+#define LB_GUARD(ctx)                                                         \
+    do {                                                                      \
+        if (!(ctx)) return LB_ERR_ARG;                                        \
+        if ((ctx)->poisoned) return LB_ERR_CUDA;                              \
+    } while (0)
+
+template <class T>
+cudaError_t dalloc(lb_ctx* ctx, T** p, size_t count) {
+    void* v = nullptr;
+    cudaError_t e = cudaMalloc(&v, std::max<size_t>(count, 1) * sizeof(T));
+    if (e == cudaSuccess) {
+        *p = (T*)v;
+        ctx->allocations.push_back(v);
+    } else {
+        *p = nullptr;
+    }
+    return e;
+}
+
+void dfree(lb_ctx* ctx, void* p) {
+    if (!p) return;
+    auto it = std::find(ctx->allocations.begin(), ctx->allocations.end(), p);
+    if (it != ctx->allocations.end()) ctx->allocations.erase(it);
+    cudaFree(p);
+}
+
+size_t pop_bytes(lb_storage s) { return s == LB_F32 ? 4 : 2; }
+
+LatticeArgs lattice_args(const lb_ctx* ctx, int par) {
+    LatticeArgs a;
+    a.ch = ctx->d_ch;
+    a.n_ch = (int)ctx->ch.size();
+    a.storage = (int)ctx->storage;
+    a.par = par;
+    a.has_last = ctx->step > 0;
+    a.h0 = ctx->h[0];
+    a.h1 = ctx->h[1];
+    a.Ntot = ctx->Ntot;
+    a.mask = ctx->mask;
+    a.slow = ctx->slow;
+    a.g0 = ctx->g[0];
+    a.g1 = ctx->g[1];
+    a.fl0 = ctx->fl[0];
+    a.fl1 = ctx->fl[1];
+    a.u = ctx->u;
+    return a;
+}
+
+IbmArgs ibm_args(const lb_ctx* ctx, int par) {
+    IbmArgs a;
+    a.n_nodes = ctx->M;
+    a.n_cells = ctx->C;
+    a.par = par;
+    a.ch = ctx->d_ch;
+    a.cells = ctx->d_cells;
+    a.cell_of = ctx->cell_of;
+    a.qa = ctx->q[0];
+    a.qb = ctx->q[1];
+    a.q0 = ctx->q0;
+    a.xr = ctx->xr;
+    a.dl = ctx->dl;
+    a.r0 = ctx->r0;
+    a.ring_off = ctx->ring_off;
+    a.ring = ctx->ring;
+    a.ring_rest = ctx->ring_rest;
+    a.F = ctx->F;
+    a.tris = ctx->tris;
+    a.tri_S0 = ctx->triS0;
+    a.chunks = ctx->chunks;
+    a.n_chunks = ctx->NCH;
+    a.partials = ctx->partials;
+    a.counters = ctx->counters;
+    a.cell_sums = ctx->cell_sums;
+    a.mask = ctx->mask;
+    a.g0 = ctx->g[0];
+    a.g1 = ctx->g[1];
+    a.fl0 = ctx->fl[0];
+    a.fl1 = ctx->fl[1];
+    a.u = ctx->u;
+    return a;
+}
+
+lb_status validate_params(const lb_params& p, std::string& why) {
+    if (p.nx < 1 || p.ny < 1 || p.nz < 1) { why = "lattice dimensions must be >= 1"; return LB_ERR_ARG; }
+    const long long n = (long long)p.nx * p.ny * p.nz;
+    if (n > 2147483647LL) { why = "nx*ny*nz must be < 2^31"; return LB_ERR_ARG; }
+    if (!(p.tau > 0.5) || !std::isfinite(p.tau)) { why = "tau must be > 1/2"; return LB_ERR_ARG; }
+    for (int d = 0; d < 3; ++d)
+        if (!std::isfinite(p.body_force[d])) { why = "body force must be finite"; return LB_ERR_ARG; }
+    if (p.storage != LB_F32 && p.storage != LB_F16_SHIFTED && p.storage != LB_BF16_SHIFTED) {
+        why = "unknown storage";
+        return LB_ERR_ARG;
+    }
+    for (int k = 0; k < 4; ++k)
+        if (p.reserved[k]) { why = "reserved fields must be zero"; return LB_ERR_ARG; }
+    return LB_OK;
+}
+
+// ---- timing helpers ----
+cudaEvent_t take_event(lb_ctx* ctx) {
+    if (!ctx->free_events.empty()) {
+        cudaEvent_t e = ctx->free_events.back();
+        ctx->free_events.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// ---- one cycle (Sec. 2.2) ----
+lb_status enqueue_step(lb_ctx* ctx, int par) {
+    const LatticeArgs la = lattice_args(ctx, par);
+    const IbmArgs ia = ibm_args(ctx, par);
+    const bool ibm = ctx->M > 0;
+    for (int k = 0; k < 4; ++k) {
+        if (!ibm && k != 2) continue;
+        EventPair ep{};
+        if (ctx->timing) {
+            ep.a = take_event(ctx);
+            ep.b = take_event(ctx);
+            ep.cls = k;
+            LB_CUDA(cudaEventRecord(ep.a, ctx->stream));
+        }
+        cudaError_t e = cudaSuccess;
+        switch (k) {
+            case 0: e = launch_cell_sums(ia, ctx->stream); break;
+            case 1: e = launch_forces_spread(ia, ctx->stream); break;
+            case 2: e = launch_stream_collide(la, ctx->total_blocks, ctx->stream); break;
+            case 3: e = launch_interp_advance(ia, ctx->stream); break;
+        }
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "kernel launch");
+        if (ctx->timing) {
+            LB_CUDA(cudaEventRecord(ep.b, ctx->stream));
+            ctx->pending.push_back(ep);
+        }
+    }
+    return LB_OK;
+}
+
+lb_status build_graphs(lb_ctx* ctx) {
+    for (int par = 0; par < 2; ++par) {
+        if (ctx->gexec[par]) continue;
+        cudaGraph_t g = nullptr;
+        LB_CUDA(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+        lb_status s = enqueue_step(ctx, par);
+        cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+        if (s != LB_OK) return s;
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&ctx->gexec[par], g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphInstantiate");
+    }
+    return LB_OK;
+}
+
+void drop_graphs(lb_ctx* ctx) {
+    for (int par = 0; par < 2; ++par)
+        if (ctx->gexec[par]) {
+            cudaGraphExecDestroy(ctx->gexec[par]);
+            ctx->gexec[par] = nullptr;
+        }
+}
+
+// ---- membrane topology on the host (FP64) ----
+double dihedral_host(const double* xa, const double* xb, const double* xc, const double* xd) {
+    double e[3], ac[3], ba[3], bd[3], n1[3], n2[3], m[3];
+    for (int k = 0; k < 3; ++k) {
+        e[k] = xb[k] - xa[k];
+        ac[k] = xc[k] - xa[k];
+        ba[k] = xa[k] - xb[k];
+        bd[k] = xd[k] - xb[k];
+    }
+    auto cr = [](const double* a, const double* b, double* o) {
+        o[0] = a[1] * b[2] - a[2] * b[1];
+        o[1] = a[2] * b[0] - a[0] * b[2];
+        o[2] = a[0] * b[1] - a[1] * b[0];
+    };
+    cr(e, ac, n1);
+    cr(ba, bd, n2);
+    cr(n1, n2, m);
+    const double le = std::sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+    return std::atan2((m[0] * e[0] + m[1] * e[1] + m[2] * e[2]) / le, n1[0] * n2[0] + n1[1] * n2[1] + n1[2] * n2[2]);
+}
+
+double tri_area_host(const double* a, const double* b, const double* c) {
+    const double u[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+    const double v[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+    const double n[3] = {u[1] * v[2] - u[2] * v[1], u[2] * v[0] - u[0] * v[2], u[0] * v[1] - u[1] * v[0]};
+    return 0.5 * std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+}
+
+long long to_fixed(double x) { return std::llround(x * FIX_SCALE); }
+
+lb_status commit_ibm(lb_ctx* ctx) {
+    if (ctx->committed) return LB_OK;
+    ctx->committed = true;
+    ctx->M = (int)ctx->hq0.size();
+    ctx->C = (int)ctx->hcells.size();
+    ctx->T = (int)ctx->htris.size();
+    ctx->NCH = (int)ctx->hchunks.size();
+    ctx->K = (int)ctx->hring.size();
+    if (ctx->M == 0) return LB_OK;
+    auto up = [&](auto** dst, const auto& src) -> cudaError_t {
+        using T = typename std::remove_reference<decltype(src)>::type::value_type;
+        cudaError_t e = dalloc(ctx, (T**)dst, src.size());
+        if (e != cudaSuccess) return e;
+        return cudaMemcpyAsync(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, ctx->stream);
+    };
+    LB_CUDA(up(&ctx->q0, ctx->hq0));
+    LB_CUDA(up(&ctx->q[0], ctx->hq));
+    LB_CUDA(up(&ctx->q[1], ctx->hq));
+    LB_CUDA(up(&ctx->r0, ctx->hr0));
+    LB_CUDA(up(&ctx->cell_of, ctx->hcell_of));
+    LB_CUDA(up(&ctx->ring_off, ctx->hring_off));
+    LB_CUDA(up(&ctx->ring, ctx->hring));
+    LB_CUDA(up(&ctx->ring_rest, ctx->hring_rest));
+    LB_CUDA(up(&ctx->tris, ctx->htris));
+    LB_CUDA(up(&ctx->triS0, ctx->htriS0));
+    LB_CUDA(up(&ctx->chunks, ctx->hchunks));
+    LB_CUDA(up(&ctx->d_cells, ctx->hcells));
+    LB_CUDA(dalloc(ctx, &ctx->xr, ctx->M));
+    LB_CUDA(dalloc(ctx, &ctx->dl, ctx->M));
+    LB_CUDA(dalloc(ctx, &ctx->F, ctx->M));
+    LB_CUDA(cudaMemsetAsync(ctx->F, 0, sizeof(float4) * ctx->M, ctx->stream));
+    LB_CUDA(dalloc(ctx, &ctx->partials, ctx->NCH));
+    LB_CUDA(dalloc(ctx, &ctx->counters, ctx->C));
+    LB_CUDA(cudaMemsetAsync(ctx->counters, 0, sizeof(unsigned) * ctx->C, ctx->stream));
+    LB_CUDA(dalloc(ctx, &ctx->cell_sums, ctx->C));
+    LB_CUDA(cudaMemsetAsync(ctx->cell_sums, 0, sizeof(double2) * ctx->C, ctx->stream));
+    LB_CUDA(launch_prepare_nodes(ibm_args(ctx, (int)(ctx->step & 1)), ctx->stream));
+    return LB_OK;
+}
+
+lb_status upload_channels(lb_ctx* ctx) {
+    std::vector<ChannelDev> v;
+    for (auto& c : ctx->ch) v.push_back(c.d);
+    LB_CUDA(cudaMemcpyAsync(ctx->d_ch, v.data(), sizeof(ChannelDev) * v.size(), cudaMemcpyHostToDevice, ctx->stream));
+    return LB_OK;
+}
+
+lb_status check_channel_mesh(lb_ctx* ctx, int mesh_id, const MeshHost** out) {
+    const auto& ids = ctx->ch_meshes[ctx->cur];
+    if (mesh_id < 0 || mesh_id >= (int)ids.size()) return fail(ctx, LB_ERR_ARG, "mesh id out of range");
+    *out = &ctx->meshes[ids[mesh_id]];
+    return LB_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+extern "C" {
+
+int lb_version(void) { return 10000; }
+
+const char* lb_last_error(const lb_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+lb_status lb_create_batch(const lb_params* params, int n_channels, void* cuda_stream, lb_ctx** out) {
+    if (!out) return LB_ERR_ARG;
+    *out = nullptr;
+    if (!params || n_channels < 1 || n_channels > 4096) return LB_ERR_ARG;
+    for (int k = 0; k < n_channels; ++k) {
+        std::string why;
+        if (validate_params(params[k], why) != LB_OK) return LB_ERR_ARG;
+        if (params[k].storage != params[0].storage) return LB_ERR_ARG;
+    }
+    lb_ctx* ctx = new lb_ctx();
+    ctx->storage = params[0].storage;
+    const int B = stream_collide_block_size();
+    long long base = 0;
+    int blk = 0;
+    for (int k = 0; k < n_channels; ++k) {
+        const lb_params& p = params[k];
+        ChannelHost c;
+        c.p = p;
+        ChannelDev& d = c.d;
+        std::memset(&d, 0, sizeof(d));
+        d.nx = p.nx; d.ny = p.ny; d.nz = p.nz;
+        for (int a = 0; a < 3; ++a) d.per[a] = p.periodic[a] ? 1 : 0;
+        d.n = (long long)p.nx * p.ny * p.nz;
+        d.base = base;
+        d.blk0 = blk;
+        d.omega = (float)(1.0 / p.tau);
+        d.fpre = (float)(1.0 - 1.0 / (2.0 * p.tau));
+        for (int a = 0; a < 3; ++a) d.G[a] = (float)p.body_force[a];
+        d.has_uw = 0;
+        for (int w = 0; w < 2; ++w)
+            for (int a = 0; a < 3; ++a) {
+                d.uw[w][a] = (float)p.wall_velocity[w][a];
+                if (p.wall_velocity[w][a] != 0.0) d.has_uw = 1;
+            }
+        c.n_blocks = (int)((d.n + B - 1) / B);
+        blk += c.n_blocks;
+        base += (d.n + CH_ALIGN - 1) / CH_ALIGN * CH_ALIGN;
+        ctx->ch.push_back(c);
+    }
+    ctx->Ntot = base;
+    ctx->total_blocks = blk;
+    ctx->ch_meshes.resize(n_channels);
+    cudaStream_t us = (cudaStream_t)cuda_stream;
+    if (us == nullptr || us == cudaStreamLegacy || us == cudaStreamPerThread) {
+        cudaError_t e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete ctx;
+            return e == cudaErrorMemoryAllocation ? LB_ERR_OOM : LB_ERR_CUDA;
+        }
+        ctx->own_stream = true;
+    } else {
+        ctx->stream = us;
+    }
+    const long long NT = ctx->Ntot;
+    const long long NG = NT / GROUP;
+    cudaError_t e = cudaSuccess;
+#define TRY(x) if (e == cudaSuccess) e = (x)
+    TRY(dalloc(ctx, (char**)&ctx->h[0], (size_t)Q * NT * pop_bytes(ctx->storage)));
+    TRY(dalloc(ctx, (char**)&ctx->h[1], (size_t)Q * NT * pop_bytes(ctx->storage)));
+    TRY(dalloc(ctx, &ctx->mask, NG));
+    TRY(dalloc(ctx, &ctx->slow, NG));
+    TRY(dalloc(ctx, &ctx->g[0], NT));
+    TRY(dalloc(ctx, &ctx->g[1], NT));
+    TRY(dalloc(ctx, &ctx->fl[0], NG));
+    TRY(dalloc(ctx, &ctx->fl[1], NG));
+    TRY(dalloc(ctx, &ctx->u, NT));
+    TRY(dalloc(ctx, &ctx->d_ch, ctx->ch.size()));
+    ctx->diag_blocks = 152 * 4;
+    TRY(dalloc(ctx, &ctx->diag_partials, (size_t)ctx->diag_blocks * 6));
+    TRY(dalloc(ctx, &ctx->diag_out, 6));
+    TRY(cudaMemsetAsync(ctx->h[0], 0, (size_t)Q * NT * pop_bytes(ctx->storage), ctx->stream));
+    TRY(cudaMemsetAsync(ctx->h[1], 0, (size_t)Q * NT * pop_bytes(ctx->storage), ctx->stream));
+    TRY(cudaMemsetAsync(ctx->mask, 0, NG * 4, ctx->stream));
+    TRY(cudaMemsetAsync(ctx->slow, 0, NG, ctx->stream));
+    TRY(cudaMemsetAsync(ctx->g[0], 0, NT * sizeof(float4), ctx->stream));
+    TRY(cudaMemsetAsync(ctx->g[1], 0, NT * sizeof(float4), ctx->stream));
+    TRY(cudaMemsetAsync(ctx->fl[0], 0, NG, ctx->stream));
+    TRY(cudaMemsetAsync(ctx->fl[1], 0, NG, ctx->stream));
+    TRY(cudaMemsetAsync(ctx->u, 0, NT * sizeof(float4), ctx->stream));
+#undef TRY
+    if (e != cudaSuccess) {
+        lb_status s = e == cudaErrorMemoryAllocation ? LB_ERR_OOM : LB_ERR_CUDA;
+        cudaGetLastError();
+        lb_destroy(ctx);
+        return s;
+    }
+    if (upload_channels(ctx) != LB_OK) { lb_destroy(ctx); return LB_ERR_CUDA; }
+    for (size_t k = 0; k < ctx->ch.size(); ++k)
+        if (launch_slow_flags(ctx->ch[k].d, ctx->d_ch, (int)k, ctx->mask, ctx->slow, ctx->stream) != cudaSuccess) {
+            lb_destroy(ctx);
+            return LB_ERR_CUDA;
+        }
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) { lb_destroy(ctx); return LB_ERR_CUDA; }
+    *out = ctx;
+    return LB_OK;
+}
+
+lb_status lb_create(const lb_params* params, void* cuda_stream, lb_ctx** out) {
+    return lb_create_batch(params, 1, cuda_stream, out);
+}
+
+lb_status lb_select_channel(lb_ctx* ctx, int channel) {
+    LB_GUARD(ctx);
+    if (channel < 0 || channel >= (int)ctx->ch.size()) return fail(ctx, LB_ERR_ARG, "channel out of range");
+    ctx->cur = channel;
+    return LB_OK;
+}
+
+lb_status lb_destroy(lb_ctx* ctx) {
+    if (!ctx) return LB_OK;
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    drop_graphs(ctx);
+    for (void* p : ctx->allocations) cudaFree(p);
+    ctx->allocations.clear();
+    for (auto& ep : ctx->pending) { cudaEventDestroy(ep.a); cudaEventDestroy(ep.b); }
+    for (auto e : ctx->free_events) cudaEventDestroy(e);
+    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+    return LB_OK;
+}
+
+lb_status lb_set_obstacles(lb_ctx* ctx, const float* spheres, int n, const uint8_t* extra_mask) {
+    LB_GUARD(ctx);
+    if (ctx->started) return fail(ctx, LB_ERR_STATE, "obstacles must be set before the first step");
+    if (n < 0 || (n > 0 && !spheres)) return fail(ctx, LB_ERR_ARG, "bad sphere list");
+    for (int k = 0; k < n; ++k)
+        for (int j = 0; j < 4; ++j)
+            if (!std::isfinite(spheres[4 * k + j]) || (j == 3 && spheres[4 * k + 3] < 0))
+                return fail(ctx, LB_ERR_ARG, "sphere data must be finite with r >= 0");
+    const ChannelHost& c = ctx->ch[ctx->cur];
+    const long long w0 = c.d.base / GROUP;
+    const long long nw = (c.d.n + GROUP - 1) / GROUP;
+    LB_CUDA(cudaMemsetAsync(ctx->mask + w0, 0, nw * 4, ctx->stream));
+    LB_CUDA(cudaMemsetAsync(ctx->slow + w0, 0, nw, ctx->stream));
+    float* dsph = nullptr;
+    uint8_t* dext = nullptr;
+    if (n > 0) {
+        LB_CUDA(dalloc(ctx, &dsph, (size_t)4 * n));
+        LB_CUDA(cudaMemcpyAsync(dsph, spheres, sizeof(float) * 4 * n, cudaMemcpyHostToDevice, ctx->stream));
+    }
+    if (extra_mask) {
+        LB_CUDA(dalloc(ctx, &dext, (size_t)c.d.n));
+        LB_CUDA(cudaMemcpyAsync(dext, extra_mask, (size_t)c.d.n, cudaMemcpyHostToDevice, ctx->stream));
+    }
+    LB_CUDA(launch_rasterise(dsph, n, dext, c.d, ctx->d_ch, ctx->cur, ctx->mask, ctx->stream));
+    LB_CUDA(launch_slow_flags(c.d, ctx->d_ch, ctx->cur, ctx->mask, ctx->slow, ctx->stream));
+    LB_CUDA(cudaStreamSynchronize(ctx->stream));
+    dfree(ctx, dsph);
+    dfree(ctx, dext);
+    return LB_OK;
+}
+
+lb_status lb_get_mask(lb_ctx* ctx, uint8_t* solid) {
+    LB_GUARD(ctx);
+    if (!solid) return LB_ERR_ARG;
+    const ChannelDev& d = ctx->ch[ctx->cur].d;
+    std::vector<uint32_t> mask((size_t)((d.n + 31) / 32));
+    LB_CUDA(cudaStreamSynchronize(ctx->stream));
+    LB_CUDA(cudaMemcpy(mask.data(), ctx->mask + d.base / GROUP, sizeof(uint32_t) * mask.size(), cudaMemcpyDeviceToHost));
+    for (long long p = 0; p < d.n; ++p) solid[p] = (mask[p >> 5] >> (p & 31)) & 1u;
+    return LB_OK;
+}
+
+lb_status ibm_add_mesh(lb_ctx* ctx, const double* rest_xyz, int n, const int32_t* tris, int nt,
+                       const ibm_moduli* mod, int* mesh_id) {
+    LB_GUARD(ctx);
+    if (ctx->started || ctx->committed) return fail(ctx, LB_ERR_STATE, "meshes must be added before the first step");
+    if (!rest_xyz || !tris || !mod || n < 4 || nt < 4) return fail(ctx, LB_ERR_ARG, "mesh needs >= 4 nodes and triangles");
+    const double mv[5] = {mod->ks, mod->kb, mod->kal, mod->kag, mod->kv};
+    for (double v : mv)
+        if (!std::isfinite(v)) return fail(ctx, LB_ERR_ARG, "moduli must be finite");
+    for (int k = 0; k < 3 * n; ++k)
+        if (!std::isfinite(rest_xyz[k]) || std::fabs(rest_xyz[k]) > 4.0e6)
+            return fail(ctx, LB_ERR_ARG, "node positions must be finite and |x| < 4e6");
+    // directed edge -> third vertex
+    std::map<std::pair<int, int>, int> third;
+    std::vector<int> out_deg(n, 0);
+    for (int t = 0; t < nt; ++t) {
+        const int v[3] = {tris[3 * t], tris[3 * t + 1], tris[3 * t + 2]};
+        for (int k = 0; k < 3; ++k) {
+            if (v[k] < 0 || v[k] >= n) return fail(ctx, LB_ERR_ARG, "triangle index out of range");
+            const std::pair<int, int> key(v[k], v[(k + 1) % 3]);
+            if (key.first == key.second) return fail(ctx, LB_ERR_ARG, "degenerate triangle");
+            if (third.count(key)) return fail(ctx, LB_ERR_ARG, "mesh is not an oriented 2-manifold (edge used twice)");
+            third[key] = v[(k + 2) % 3];
+            out_deg[v[k]]++;
+        }
+    }
+    for (auto& kv : third)
+        if (!third.count(std::make_pair(kv.first.second, kv.first.first)))
+            return fail(ctx, LB_ERR_ARG, "mesh is not closed");
+    // node rings, counter-clockwise seen from outside: ring[j+1] = third(i -> ring[j])
+    std::vector<std::vector<int>> ringv(n);
+    for (auto& kv : third) {
+        const int i = kv.first.first;
+        if (!ringv[i].empty()) continue;
+        int a = kv.first.second;
+        std::vector<int>& r = ringv[i];
+        for (int guard = 0; guard <= MAX_VALENCE; ++guard) {
+            r.push_back(a);
+            a = third[std::make_pair(i, a)];
+            if (a == r[0]) break;
+        }
+        if ((int)r.size() != out_deg[i] || (int)r.size() > MAX_VALENCE)
+            return fail(ctx, LB_ERR_ARG, "mesh vertex is not a single fan (non-manifold) or valence > 64");
+    }
+    for (int i = 0; i < n; ++i)
+        if (ringv[i].empty()) return fail(ctx, LB_ERR_ARG, "mesh has an isolated node");
+    const double* x = rest_xyz;
+    // rest area / volume (FP64)
+    double S0 = 0.0, V0 = 0.0;
+    for (int t = 0; t < nt; ++t) {
+        const double* a = x + 3 * tris[3 * t];
+        const double* b = x + 3 * tris[3 * t + 1];
+        const double* c = x + 3 * tris[3 * t + 2];
+        S0 += tri_area_host(a, b, c);
+        V0 += (a[0] * (b[1] * c[2] - b[2] * c[1]) + a[1] * (b[2] * c[0] - b[0] * c[2]) +
+               a[2] * (b[0] * c[1] - b[1] * c[0])) / 6.0;
+    }
+    if (!(V0 > 0.0)) return fail(ctx, LB_ERR_ARG, "mesh volume must be positive (outward orientation)");
+
+    auto theta0 = [&](int a, int b) {
+        if (a > b) std::swap(a, b);
+        const int c = third[std::make_pair(a, b)];
+        const int d = third[std::make_pair(b, a)];
+        return dihedral_host(x + 3 * a, x + 3 * b, x + 3 * c, x + 3 * d);
+    };
+    const int node0 = (int)ctx->hq0.size();
+    const int cell = (int)ctx->hcells.size();
+    // fixed-point rest positions
+    std::vector<Q4> q0(n);
+    for (int i = 0; i < n; ++i) {
+        q0[i].x = to_fixed(x[3 * i]);
+        q0[i].y = to_fixed(x[3 * i + 1]);
+        q0[i].z = to_fixed(x[3 * i + 2]);
+        q0[i].w = 0;
+    }
+    for (int i = 0; i < n; ++i) {
+        ctx->hq0.push_back(q0[i]);
+        ctx->hq.push_back(q0[i]);
+        ctx->hcell_of.push_back(cell);
+        ctx->hr0.push_back(make_float4((float)((double)(q0[i].x - q0[0].x) / FIX_SCALE),
+                                       (float)((double)(q0[i].y - q0[0].y) / FIX_SCALE),
+                                       (float)((double)(q0[i].z - q0[0].z) / FIX_SCALE), 0.0f));
+        const std::vector<int>& r = ringv[i];
+        const int k = (int)r.size();
+        for (int j = 0; j < k; ++j) {
+            const int nb = r[j], nx = r[(j + 1) % k];
+            const int outer = third[std::make_pair(nx, nb)];
+            const double* xi = x + 3 * i;
+            const double* xn = x + 3 * nb;
+            const double L0 = std::sqrt((xn[0] - xi[0]) * (xn[0] - xi[0]) + (xn[1] - xi[1]) * (xn[1] - xi[1]) +
+                                        (xn[2] - xi[2]) * (xn[2] - xi[2]));
+            ctx->hring.push_back(make_int2(node0 + nb, node0 + outer));
+            ctx->hring_rest.push_back(make_float4((float)L0, (float)theta0(i, nb), (float)theta0(nb, nx),
+                                                  (float)tri_area_host(xi, xn, x + 3 * nx)));
+        }
+        ctx->hring_off.push_back((int)ctx->hring.size());
+    }
+    const int tri0 = (int)ctx->htris.size();
+    for (int t = 0; t < nt; ++t) {
+        ctx->htris.push_back(make_int4(node0 + tris[3 * t], node0 + tris[3 * t + 1], node0 + tris[3 * t + 2], cell));
+        ctx->htriS0.push_back((float)tri_area_host(x + 3 * tris[3 * t], x + 3 * tris[3 * t + 1], x + 3 * tris[3 * t + 2]));
+    }
+    CellDev cd;
+    std::memset(&cd, 0, sizeof(cd));
+    cd.ch = ctx->cur;
+    cd.ref = node0;
+    cd.node0 = node0;
+    cd.n_nodes = n;
+    cd.chunk0 = (int)ctx->hchunks.size();
+    for (int b = 0; b < nt; b += CHUNK_TRIS)
+        ctx->hchunks.push_back(make_int4(cell, tri0 + b, tri0 + std::min(nt, b + CHUNK_TRIS), 0));
+    cd.n_chunks = (int)ctx->hchunks.size() - cd.chunk0;
+    cd.ks = (float)mod->ks; cd.kb = (float)mod->kb; cd.kal = (float)mod->kal; cd.kag = (float)mod->kag; cd.kv = (float)mod->kv;
+    cd.S0 = S0;
+    cd.V0 = V0;
+    ctx->hcells.push_back(cd);
+    MeshHost mh;
+    mh.ch = ctx->cur; mh.node0 = node0; mh.n = n; mh.tri0 = tri0; mh.nt = nt; mh.cell = cell; mh.S0 = S0; mh.V0 = V0;
+    ctx->meshes.push_back(mh);
+    ctx->ch_meshes[ctx->cur].push_back((int)ctx->meshes.size() - 1);
+    if (mesh_id) *mesh_id = (int)ctx->ch_meshes[ctx->cur].size() - 1;
+    return LB_OK;
+}
+
+lb_status ibm_set_nodes(lb_ctx* ctx, int mesh_id, const double* xyz) {
+    LB_GUARD(ctx);
+    const MeshHost* m;
+    if (check_channel_mesh(ctx, mesh_id, &m) != LB_OK) return LB_ERR_ARG;
+    if (!xyz) return fail(ctx, LB_ERR_ARG, "null positions");
+    std::vector<Q4> q(m->n);
+    for (int i = 0; i < m->n; ++i) {
+        for (int k = 0; k < 3; ++k)
+            if (!std::isfinite(xyz[3 * i + k]) || std::fabs(xyz[3 * i + k]) > 4.0e6)
+                return fail(ctx, LB_ERR_ARG, "positions must be finite and |x| < 4e6");
+        q[i].x = to_fixed(xyz[3 * i]);
+        q[i].y = to_fixed(xyz[3 * i + 1]);
+        q[i].z = to_fixed(xyz[3 * i + 2]);
+        q[i].w = 0;
+    }
+    if (!ctx->committed) {
+        std::copy(q.begin(), q.end(), ctx->hq.begin() + m->node0);
+        return LB_OK;
+    }
+    const int par = (int)(ctx->step & 1);
+    LB_CUDA(cudaMemcpyAsync(ctx->q[par] + m->node0, q.data(), sizeof(Q4) * m->n, cudaMemcpyHostToDevice, ctx->stream));
+    LB_CUDA(launch_prepare_nodes(ibm_args(ctx, par), ctx->stream));
+    LB_CUDA(cudaStreamSynchronize(ctx->stream));
+    return LB_OK;
+}
+
+lb_status lb_step(lb_ctx* ctx, int n_steps) {
+    LB_GUARD(ctx);
+    if (n_steps < 0) return fail(ctx, LB_ERR_ARG, "n_steps < 0");
+    if (n_steps == 0) return LB_OK;
+    lb_status s = commit_ibm(ctx);
+    if (s != LB_OK) return s;
+    ctx->started = true;
+    if (!ctx->timing) {
+        s = build_graphs(ctx);
+        if (s != LB_OK) return s;
+    }
+    for (int k = 0; k < n_steps; ++k) {
+        const int par = (int)(ctx->step & 1);
+        if (ctx->timing) {
+            s = enqueue_step(ctx, par);
+            if (s != LB_OK) return s;
+        } else {
+            LB_CUDA(cudaGraphLaunch(ctx->gexec[par], ctx->stream));
+        }
+        ctx->step++;
+    }
+    LB_CUDA(cudaGetLastError());
+    return LB_OK;
+}
+
+lb_status lb_synchronize(lb_ctx* ctx) {
+    LB_GUARD(ctx);
+    LB_CUDA(cudaStreamSynchronize(ctx->stream));
+    return LB_OK;
+}
+
+lb_status lb_get_step(lb_ctx* ctx, int64_t* step) {
+    LB_GUARD(ctx);
+    if (!step) return LB_ERR_ARG;
+    *step = ctx->step;
+    return LB_OK;
+}
+
+lb_status lb_get_fields(lb_ctx* ctx, float* rho, float* u, int dst_is_device) {
+    LB_GUARD(ctx);
+    if (!rho && !u) return LB_OK;
+    const ChannelHost& c = ctx->ch[ctx->cur];
+    const long long n = c.d.n;
+    LatticeArgs a = lattice_args(ctx, (int)(ctx->step & 1));
+    if (dst_is_device) {
+        LB_CUDA(launch_fields(a, c.d, ctx->cur, rho, u, ctx->stream));
+        LB_CUDA(cudaStreamSynchronize(ctx->stream));
+        return LB_OK;
+    }
+    float* buf = nullptr;
+    LB_CUDA(dalloc(ctx, &buf, (size_t)4 * n));
+    lb_status st = LB_OK;
+    cudaError_t e = launch_fields(a, c.d, ctx->cur, rho ? buf : nullptr, u ? buf + n : nullptr, ctx->stream);
+    if (e == cudaSuccess && rho) e = cudaMemcpyAsync(rho, buf, sizeof(float) * n, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess && u) e = cudaMemcpyAsync(u, buf + n, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) st = cuda_fail(ctx, e, "lb_get_fields");
+    dfree(ctx, buf);
+    return st;
+}
+
+lb_status lb_get_populations(lb_ctx* ctx, double* f) {
+    LB_GUARD(ctx);
+    if (!f) return LB_ERR_ARG;
+    const ChannelHost& c = ctx->ch[ctx->cur];
+    const long long n = c.d.n;
+    float* buf = nullptr;
+    LB_CUDA(dalloc(ctx, &buf, (size_t)Q * n));
+    std::vector<float> h((size_t)Q * n);
+    cudaError_t e = launch_pull_populations(lattice_args(ctx, (int)(ctx->step & 1)), c.d, ctx->cur, buf, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), buf, sizeof(float) * Q * n, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    dfree(ctx, buf);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "lb_get_populations");
+    std::vector<uint32_t> mask((size_t)((n + 31) / 32));
+    LB_CUDA(cudaMemcpy(mask.data(), ctx->mask + c.d.base / GROUP, sizeof(uint32_t) * mask.size(), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < Q; ++i)
+        for (long long p = 0; p < n; ++p) {
+            const bool solid = (mask[p >> 5] >> (p & 31)) & 1u;
+            f[(size_t)i * n + p] = wgt_d(i) + (solid ? 0.0 : (double)h[(size_t)i * n + p]);
+        }
+    return LB_OK;
+}
+
+lb_status lb_set_populations(lb_ctx* ctx, const double* f) {
+    LB_GUARD(ctx);
+    if (!f) return LB_ERR_ARG;
+    const ChannelHost& c = ctx->ch[ctx->cur];
+    const ChannelDev& d = c.d;
+    const long long n = d.n;
+    for (long long k = 0; k < (long long)Q * n; ++k)
+        if (!std::isfinite(f[k])) return fail(ctx, LB_ERR_ARG, "populations must be finite");
+    std::vector<uint32_t> mask((size_t)((n + 31) / 32));
+    LB_CUDA(cudaStreamSynchronize(ctx->stream));
+    LB_CUDA(cudaMemcpy(mask.data(), ctx->mask + d.base / GROUP, sizeof(uint32_t) * mask.size(), cudaMemcpyDeviceToHost));
+    auto solid = [&](long long p) { return (bool)((mask[p >> 5] >> (p & 31)) & 1u); };
+    // inverse of the pull step: h*_i(x) = h_i(x + e_i) where x + e_i is fluid and
+    // inside the domain; otherwise h*_i(x) = h_opp(i)(x) minus the wall term.
+    std::vector<float> hs((size_t)Q * n, 0.0f);
+    const int dims[3] = {d.nx, d.ny, d.nz};
+    for (int z = 0; z < d.nz; ++z)
+        for (int y = 0; y < d.ny; ++y)
+            for (int xx = 0; xx < d.nx; ++xx) {
+                const long long p = xx + (long long)d.nx * (y + (long long)d.ny * z);
+                if (solid(p)) continue;
+                for (int i = 0; i < Q; ++i) {
+                    int cc[3] = {xx + ex(i), y + ey(i), z + ez(i)};
+                    bool ok = true;
+                    for (int a = 0; a < 3; ++a)
+                        if (cc[a] < 0 || cc[a] >= dims[a]) {
+                            if (d.per[a]) cc[a] = (cc[a] + dims[a]) % dims[a];
+                            else ok = false;
+                        }
+                    long long q = 0;
+                    if (ok) {
+                        q = cc[0] + (long long)d.nx * (cc[1] + (long long)d.ny * cc[2]);
+                        ok = !solid(q);
+                    }
+                    double v;
+                    if (ok) {
+                        v = f[(size_t)i * n + q] - wgt_d(i);
+                    } else {
+                        const int o = opp(i);
+                        v = f[(size_t)o * n + p] - wgt_d(o);
+                        if (d.has_uw && !d.per[1]) {
+                            int wall = -1;
+                            if (ey(o) == 1 && y == 0) wall = 0;
+                            if (ey(o) == -1 && y == d.ny - 1) wall = 1;
+                            if (wall >= 0)
+                                v -= 6.0 * wgt_d(o) * (ex(o) * c.p.wall_velocity[wall][0] + ey(o) * c.p.wall_velocity[wall][1] +
+                                                       ez(o) * c.p.wall_velocity[wall][2]);
+                        }
+                    }
+                    hs[(size_t)i * n + p] = (float)v;
+                }
+            }
+    const int par = (int)(ctx->step & 1);
+    const size_t eb = pop_bytes(ctx->storage);
+    for (int i = 0; i < Q; ++i) {
+        char* dst = (char*)ctx->h[par] + ((size_t)i * ctx->Ntot + d.base) * eb;
+        if (ctx->storage == LB_F32) {
+            LB_CUDA(cudaMemcpy(dst, hs.data() + (size_t)i * n, sizeof(float) * n, cudaMemcpyHostToDevice));
+        } else {
+            std::vector<uint16_t> tmp(n);
+            for (long long p = 0; p < n; ++p) {
+                const float s = hs[(size_t)i * n + p] * (1.0f / wgt(i));
+                if (ctx->storage == LB_F16_SHIFTED) {
+                    __half hv = __float2half_rn(s);
+                    std::memcpy(&tmp[p], &hv, 2);
+                } else {
+                    __nv_bfloat16 bv = __float2bfloat16_rn(s);
+                    std::memcpy(&tmp[p], &bv, 2);
+                }
+            }
+            LB_CUDA(cudaMemcpy(dst, tmp.data(), 2 * n, cudaMemcpyHostToDevice));
+        }
+    }
+    return LB_OK;
+}
+
+lb_status ibm_get_nodes(lb_ctx* ctx, int mesh_id, double* xyz) {
+    LB_GUARD(ctx);
+    const MeshHost* m;
+    if (check_channel_mesh(ctx, mesh_id, &m) != LB_OK) return LB_ERR_ARG;
+    if (!xyz) return LB_ERR_ARG;
+    std::vector<Q4> q(m->n);
+    if (!ctx->committed) {
+        std::copy(ctx->hq.begin() + m->node0, ctx->hq.begin() + m->node0 + m->n, q.begin());
+    } else {
+        LB_CUDA(cudaMemcpyAsync(q.data(), ctx->q[ctx->step & 1] + m->node0, sizeof(Q4) * m->n, cudaMemcpyDeviceToHost,
+                                ctx->stream));
+        LB_CUDA(cudaStreamSynchronize(ctx->stream));
+    }
+    for (int i = 0; i < m->n; ++i) {
+        xyz[3 * i] = (double)q[i].x / FIX_SCALE;
+        xyz[3 * i + 1] = (double)q[i].y / FIX_SCALE;
+        xyz[3 * i + 2] = (double)q[i].z / FIX_SCALE;
+    }
+    return LB_OK;
+}
+
+lb_status ibm_get_forces(lb_ctx* ctx, int mesh_id, double* f) {
+    LB_GUARD(ctx);
+    const MeshHost* m;
+    if (check_channel_mesh(ctx, mesh_id, &m) != LB_OK) return LB_ERR_ARG;
+    if (!f) return LB_ERR_ARG;
+    lb_status s = commit_ibm(ctx);
+    if (s != LB_OK) return s;
+    std::vector<float4> F(m->n);
+    LB_CUDA(cudaMemcpyAsync(F.data(), ctx->F + m->node0, sizeof(float4) * m->n, cudaMemcpyDeviceToHost, ctx->stream));
+    LB_CUDA(cudaStreamSynchronize(ctx->stream));
+    for (int i = 0; i < m->n; ++i) {
+        f[3 * i] = F[i].x;
+        f[3 * i + 1] = F[i].y;
+        f[3 * i + 2] = F[i].z;
+    }
+    return LB_OK;
+}
+
+lb_status ibm_get_area_volume(lb_ctx* ctx, double* area, double* volume) {
+    LB_GUARD(ctx);
+    lb_status s = commit_ibm(ctx);
+    if (s != LB_OK) return s;
+    const auto& ids = ctx->ch_meshes[ctx->cur];
+    if (ids.empty()) return LB_OK;
+    LB_CUDA(launch_cell_sums(ibm_args(ctx, (int)(ctx->step & 1)), ctx->stream));
+    std::vector<double2> cs(ctx->C);
+    LB_CUDA(cudaMemcpyAsync(cs.data(), ctx->cell_sums, sizeof(double2) * ctx->C, cudaMemcpyDeviceToHost, ctx->stream));
+    LB_CUDA(cudaStreamSynchronize(ctx->stream));
+    for (size_t k = 0; k < ids.size(); ++k) {
+        const MeshHost& m = ctx->meshes[ids[k]];
+        if (area) area[k] = m.S0 + cs[m.cell].x;
+        if (volume) volume[k] = m.V0 + cs[m.cell].y;
+    }
+    return LB_OK;
+}
+
+lb_status lb_diagnostics(lb_ctx* ctx, double u_max, double out[6]) {
+    LB_GUARD(ctx);
+    if (!out) return LB_ERR_ARG;
+    const ChannelHost& c = ctx->ch[ctx->cur];
+    LB_CUDA(launch_diagnostics(lattice_args(ctx, (int)(ctx->step & 1)), c.d, ctx->cur, ctx->diag_partials,
+                               ctx->diag_blocks, ctx->diag_out, ctx->stream));
+    LB_CUDA(cudaMemcpyAsync(out, ctx->diag_out, sizeof(double) * 6, cudaMemcpyDeviceToHost, ctx->stream));
+    LB_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (out[4] > 0) return fail(ctx, LB_ERR_NUMERIC, "non-finite populations");
+    if (u_max > 0 && !(out[5] <= u_max)) return fail(ctx, LB_ERR_NUMERIC, "velocity above the stability bound");
+    return LB_OK;
+}
+
+// ---- checkpoint ----
+namespace {
+struct StateHeader {
+    uint64_t magic;
+    int64_t step;
+    int64_t Ntot;
+    int32_t storage;
+    int32_t M;
+};
+constexpr uint64_t STATE_MAGIC = 0x4c4249424d535431ULL;
+}  // namespace
+
+lb_status lb_save_state(lb_ctx* ctx, void* buf, size_t* bytes) {
+    LB_GUARD(ctx);
+    if (!bytes) return LB_ERR_ARG;
+    lb_status s = commit_ibm(ctx);
+    if (s != LB_OK) return s;
+    const size_t hb = (size_t)Q * ctx->Ntot * pop_bytes(ctx->storage);
+    const size_t gb = (size_t)ctx->Ntot * sizeof(float4);
+    const size_t fb = (size_t)ctx->Ntot / GROUP;
+    const size_t qb = (size_t)ctx->M * sizeof(Q4);
+    const size_t Fb = (size_t)ctx->M * sizeof(float4);
+    const size_t total = sizeof(StateHeader) + hb + gb + fb + qb + Fb;
+    if (!buf) { *bytes = total; return LB_OK; }
+    if (*bytes < total) return fail(ctx, LB_ERR_ARG, "checkpoint buffer too small");
+    StateHeader hd{STATE_MAGIC, ctx->step, ctx->Ntot, (int32_t)ctx->storage, ctx->M};
+    char* p = (char*)buf;
+    std::memcpy(p, &hd, sizeof(hd));
+    p += sizeof(hd);
+    const int par = (int)(ctx->step & 1);
+    LB_CUDA(cudaStreamSynchronize(ctx->stream));
+    LB_CUDA(cudaMemcpy(p, ctx->h[par], hb, cudaMemcpyDeviceToHost)); p += hb;
+    LB_CUDA(cudaMemcpy(p, ctx->g[1 - par], gb, cudaMemcpyDeviceToHost)); p += gb;
+    LB_CUDA(cudaMemcpy(p, ctx->fl[1 - par], fb, cudaMemcpyDeviceToHost)); p += fb;
+    if (ctx->M) {
+        LB_CUDA(cudaMemcpy(p, ctx->q[par], qb, cudaMemcpyDeviceToHost)); p += qb;
+        LB_CUDA(cudaMemcpy(p, ctx->F, Fb, cudaMemcpyDeviceToHost)); p += Fb;
+    }
+    *bytes = total;
+    return LB_OK;
+}
+
+lb_status lb_load_state(lb_ctx* ctx, const void* buf, size_t bytes) {
+    LB_GUARD(ctx);
+    if (!buf || bytes < sizeof(StateHeader)) return LB_ERR_ARG;
+    lb_status s = commit_ibm(ctx);
+    if (s != LB_OK) return s;
+    StateHeader hd;
+    std::memcpy(&hd, buf, sizeof(hd));
+    if (hd.magic != STATE_MAGIC || hd.Ntot != ctx->Ntot || hd.storage != (int32_t)ctx->storage || hd.M != ctx->M)
+        return fail(ctx, LB_ERR_ARG, "checkpoint does not match this context");
+    const size_t hb = (size_t)Q * ctx->Ntot * pop_bytes(ctx->storage);
+    const size_t gb = (size_t)ctx->Ntot * sizeof(float4);
+    const size_t fb = (size_t)ctx->Ntot / GROUP;
+    const size_t qb = (size_t)ctx->M * sizeof(Q4);
+    const size_t Fb = (size_t)ctx->M * sizeof(float4);
+    if (bytes < sizeof(StateHeader) + hb + gb + fb + qb + Fb) return fail(ctx, LB_ERR_ARG, "checkpoint truncated");
+    const char* p = (const char*)buf + sizeof(hd);
+    ctx->step = hd.step;
+    const int par = (int)(ctx->step & 1);
+    LB_CUDA(cudaStreamSynchronize(ctx->stream));
+    LB_CUDA(cudaMemcpy(ctx->h[par], p, hb, cudaMemcpyHostToDevice)); p += hb;
+    LB_CUDA(cudaMemcpy(ctx->g[1 - par], p, gb, cudaMemcpyHostToDevice)); p += gb;
+    LB_CUDA(cudaMemcpy(ctx->fl[1 - par], p, fb, cudaMemcpyHostToDevice)); p += fb;
+    LB_CUDA(cudaMemset(ctx->g[par], 0, gb));
+    LB_CUDA(cudaMemset(ctx->fl[par], 0, fb));
+    if (ctx->M) {
+        LB_CUDA(cudaMemcpy(ctx->q[par], p, qb, cudaMemcpyHostToDevice)); p += qb;
+        LB_CUDA(cudaMemcpy(ctx->F, p, Fb, cudaMemcpyHostToDevice)); p += Fb;
+        LB_CUDA(launch_prepare_nodes(ibm_args(ctx, par), ctx->stream));
+    }
+    LB_CUDA(cudaStreamSynchronize(ctx->stream));
+    ctx->started = ctx->step > 0 || ctx->started;
+    return LB_OK;
+}
+
+// ---- timing ----
+lb_status lb_set_timing(lb_ctx* ctx, int enable) {
+    LB_GUARD(ctx);
+    ctx->timing = enable != 0;
+    return LB_OK;
+}
+
+lb_status lb_kernel_times(lb_ctx* ctx, double ms[4], int64_t launches[4]) {
+    LB_GUARD(ctx);
+    LB_CUDA(cudaStreamSynchronize(ctx->stream));
+    for (auto& ep : ctx->pending) {
+        float t = 0.f;
+        LB_CUDA(cudaEventElapsedTime(&t, ep.a, ep.b));
+        ctx->ms[ep.cls] += t;
+        ctx->launches[ep.cls] += 1;
+        ctx->free_events.push_back(ep.a);
+        ctx->free_events.push_back(ep.b);
+    }
+    ctx->pending.clear();
+    for (int k = 0; k < 4; ++k) {
+        if (ms) ms[k] = ctx->ms[k];
+        if (launches) launches[k] = ctx->launches[k];
+        ctx->ms[k] = 0;
+        ctx->launches[k] = 0;
+    }
+    return LB_OK;
+}
+
+}  // extern "C"

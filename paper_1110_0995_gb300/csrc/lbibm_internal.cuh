@@ -1,0 +1,161 @@
+// Internal declarations of the GB300 lattice-Boltzmann + immersed-boundary
+// library: device data layout, kernel argument blocks and launchers.
+//
+// Data layout in HBM (one context = one batch of channels):
+//   populations  h[2][19][Ntot]   SoA, direction-major; Ntot is the padded sum
+//                                 of all channels' node counts; channel k's
+//                                 nodes start at a multiple of 128.  Storage
+//                                 type float (h = f - w), half or bfloat16
+//                                 (h / w).  Buffer (step & 1) is read, the
+//                                 other written (pull scheme).
+//   obstacle mask uint32[Ntot/32] one bit per node (1 = solid)
+//   slow flags   uint8[Ntot/32]   1 if a node of the 32-node group is solid or
+//                                 has a neighbour outside the domain or solid
+//   force fields float4 g[2][Ntot] IB force density (x, y, z, 0), double-
+//                                 buffered by step parity, sparse in use
+//   force flags  uint8[2][Ntot/32] group's g[parity] holds forces of the step
+//                                 with that parity; cleared by the warp that
+//                                 owns the group one step later
+//   velocity     float4 u[Ntot]   (ux, uy, uz, rho), written only for stamped
+//                                 groups (the stencils of the IB points)
+//   IB nodes     int64 q[M]x4     positions in 2^-40 lu fixed point; q0 rest
+//                float4 xr, dl, r0 positions relative to the cell's reference
+//                                 node, displacement from rest relative to the
+//                                 reference node's, rest position (FP32)
+//   ring CSR     int2 (neighbour, outer vertex), float4 rest data per slot
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace lbibm {
+
+constexpr int Q = 19;
+constexpr int GROUP = 32;           // nodes per mask word / flag / stamp
+// Channel node ranges start at, and are padded to, multiples of this.  Every
+// stream-collide block covers whole groups inside one channel's padded range,
+// so lanes past the channel's end still index valid flag / mask words.
+constexpr int CH_ALIGN = 1024;
+constexpr int MAXV = 8;             // maximum node valence of a membrane mesh
+constexpr double FIX_SCALE = 1099511627776.0;   // 2^40
+constexpr float FIX_SCALE_F = 1099511627776.0f;
+constexpr float FIX_INV_F = 9.094947017729282e-13f;  // 2^-40
+constexpr int FIX_BITS = 40;
+
+struct ChannelDev {
+    int nx, ny, nz;
+    int per[3];
+    long long base;       // first global node index
+    long long n;          // nx * ny * nz
+    int blk0;             // first block of the stream-collide grid for this channel
+    int pad0;
+    float omega;          // 1 / tau
+    float fpre;           // 1 - 1 / (2 tau)
+    float G[3];           // uniform body force
+    float uw[2][3];       // y-low / y-high wall velocity
+    int has_uw;
+};
+
+struct __align__(32) Q4 {
+    long long x, y, z, w;
+};
+
+struct CellDev {
+    int ch;               // channel
+    int ref;              // global index of the reference node (first node of the cell)
+    int node0, n_nodes;
+    int chunk0, n_chunks; // triangle chunks of the area/volume reduction
+    float ks, kb, kal, kag, kv;
+    float pad;
+    double S0, V0;        // rest area and volume (FP64)
+};
+
+struct LatticeArgs {
+    const ChannelDev* ch;
+    int n_ch;
+    int storage;          // lb_storage
+    int par;              // step parity: read h[par], write h[1-par]; forces in g[par]
+    int has_last;         // a step has completed (fields / diagnostics)
+    void* h0;
+    void* h1;
+    long long Ntot;
+    const uint32_t* mask;
+    const uint8_t* slow;
+    float4* g0;
+    float4* g1;
+    uint8_t* fl0;
+    uint8_t* fl1;
+    float4* u;
+};
+
+struct IbmArgs {
+    int n_nodes;          // M
+    int n_cells;
+    int par;              // step parity: positions q[par] are current, q[1-par] receive the advance
+    const ChannelDev* ch;
+    const CellDev* cells;
+    const int* cell_of;   // [M]
+    Q4* qa;               // [M] positions, even steps
+    Q4* qb;               // [M] positions, odd steps
+    const Q4* q0;         // [M] rest positions
+    float4* xr;           // [M]
+    float4* dl;           // [M]
+    const float4* r0;     // [M]
+    const int* ring_off;  // [M+1]
+    const int2* ring;     // [K] (neighbour, outer)
+    const float4* ring_rest;  // [K] (L0, theta0 edge, theta0 opposite edge, S0 triangle)
+    float4* F;            // [M] last node forces
+    // area / volume reduction
+    const int4* tris;     // [T] (a, b, c, cell) global node indices
+    const float* tri_S0;  // [T] rest area of each triangle
+    const int4* chunks;   // [NCH] (cell, t_begin, t_end, 0)
+    int n_chunks;
+    double2* partials;    // [NCH]
+    unsigned* counters;   // [C]
+    double2* cell_sums;   // [C] (dS, dV)
+    // lattice pieces used by spread / interpolation
+    const uint32_t* mask;
+    float4* g0;
+    float4* g1;
+    uint8_t* fl0;
+    uint8_t* fl1;
+    const float4* u;
+};
+
+// D3Q19 velocity set (Sec. 2.1): rest, +-x, +-y, +-z, then the 12 diagonals,
+// opposite directions adjacent.
+__host__ __device__ constexpr int ex(int i) {
+    return i == 1 || i == 7 || i == 9 || i == 11 || i == 13 ? 1 : (i == 2 || i == 8 || i == 10 || i == 12 || i == 14 ? -1 : 0);
+}
+__host__ __device__ constexpr int ey(int i) {
+    return i == 3 || i == 7 || i == 10 || i == 15 || i == 17 ? 1 : (i == 4 || i == 8 || i == 9 || i == 16 || i == 18 ? -1 : 0);
+}
+__host__ __device__ constexpr int ez(int i) {
+    return i == 5 || i == 11 || i == 14 || i == 15 || i == 18 ? 1 : (i == 6 || i == 12 || i == 13 || i == 16 || i == 17 ? -1 : 0);
+}
+__host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+__host__ __device__ constexpr float wgt(int i) { return i == 0 ? (1.0f / 3.0f) : (i <= 6 ? (1.0f / 18.0f) : (1.0f / 36.0f)); }
+__host__ __device__ constexpr double wgt_d(int i) { return i == 0 ? (1.0 / 3.0) : (i <= 6 ? (1.0 / 18.0) : (1.0 / 36.0)); }
+
+// ---- launchers (defined in lattice_kernels.cu / ibm_kernels.cu) ----
+cudaError_t launch_rasterise(const float* spheres, int n_spheres, const uint8_t* extra, const ChannelDev& ch,
+                             const ChannelDev* d_ch, int ch_index, uint32_t* mask, cudaStream_t s);
+cudaError_t launch_slow_flags(const ChannelDev& ch, const ChannelDev* d_ch, int ch_index, const uint32_t* mask,
+                              uint8_t* slow, cudaStream_t s);
+cudaError_t launch_stream_collide(const LatticeArgs& a, int total_blocks, cudaStream_t s);
+cudaError_t launch_fields(const LatticeArgs& a, const ChannelDev& ch, int ch_index, float* rho, float* u,
+                          cudaStream_t s);
+cudaError_t launch_pull_populations(const LatticeArgs& a, const ChannelDev& ch, int ch_index, float* h_out,
+                                    cudaStream_t s);
+cudaError_t launch_diagnostics(const LatticeArgs& a, const ChannelDev& ch, int ch_index, double* partials,
+                               int n_blocks, double* out, cudaStream_t s);
+int stream_collide_block_size();
+
+cudaError_t launch_cell_sums(const IbmArgs& a, cudaStream_t s);
+cudaError_t launch_forces_spread(const IbmArgs& a, cudaStream_t s);
+cudaError_t launch_interp_advance(const IbmArgs& a, cudaStream_t s);
+cudaError_t launch_prepare_nodes(const IbmArgs& a, cudaStream_t s);
+
+}  // namespace lbibm

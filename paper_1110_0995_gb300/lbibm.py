@@ -1,0 +1,277 @@
+"""Thin Python binding of the C ABI in ``include/lbibm.h`` (ctypes).
+
+Argument marshalling only: every step of the method runs in the CUDA library
+``_build/liblbibm.so``.  There is no CPU fallback; importing this module on a
+machine without the compiled library raises.  PyTorch, when used, only
+provides device buffers (``data_ptr``) and the CUDA stream handle.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import _build
+
+LB_OK, LB_ERR_ARG, LB_ERR_STATE, LB_ERR_CUDA, LB_ERR_OOM, LB_ERR_NUMERIC, LB_ERR_TIMEOUT = range(7)
+STORAGE = {"f32": 0, "f16": 1, "bf16": 2}
+
+# Every entry point that include/lbibm.h declares.
+EXPORTS = (
+    "lb_create", "lb_create_batch", "lb_select_channel", "lb_destroy", "lb_set_obstacles", "ibm_add_mesh",
+    "ibm_set_nodes", "lb_step", "lb_synchronize", "lb_get_fields", "lb_get_populations", "lb_set_populations",
+    "ibm_get_nodes", "ibm_get_forces", "ibm_get_area_volume", "lb_diagnostics", "lb_get_step", "lb_save_state",
+    "lb_load_state", "lb_set_timing", "lb_kernel_times", "lb_last_error", "lb_version", "lb_get_mask",
+)
+
+
+class LbParams(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("tau", ctypes.c_double),
+                ("body_force", ctypes.c_double * 3), ("periodic", ctypes.c_int * 3),
+                ("wall_velocity", (ctypes.c_double * 3) * 2), ("storage", ctypes.c_int),
+                ("reserved", ctypes.c_int * 4)]
+
+
+class IbmModuli(ctypes.Structure):
+    _fields_ = [("ks", ctypes.c_double), ("kb", ctypes.c_double), ("kal", ctypes.c_double),
+                ("kag", ctypes.c_double), ("kv", ctypes.c_double)]
+
+
+class LbError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"lbibm status {status}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load the compiled library (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_build.LIB):
+            raise ImportError(f"CUDA library not built: {_build.LIB} (run __graft_entry__.build())")
+        L = ctypes.CDLL(_build.LIB)
+        P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+        sig = {
+            "lb_create": ([ctypes.POINTER(LbParams), P, ctypes.POINTER(P)], I),
+            "lb_create_batch": ([ctypes.POINTER(LbParams), I, P, ctypes.POINTER(P)], I),
+            "lb_select_channel": ([P, I], I),
+            "lb_destroy": ([P], I),
+            "lb_set_obstacles": ([P, P, I, P], I),
+            "ibm_add_mesh": ([P, P, I, P, I, ctypes.POINTER(IbmModuli), ctypes.POINTER(I)], I),
+            "ibm_set_nodes": ([P, I, P], I),
+            "lb_step": ([P, I], I),
+            "lb_synchronize": ([P], I),
+            "lb_get_fields": ([P, P, P, I], I),
+            "lb_get_populations": ([P, P], I),
+            "lb_set_populations": ([P, P], I),
+            "ibm_get_nodes": ([P, I, P], I),
+            "ibm_get_forces": ([P, I, P], I),
+            "ibm_get_area_volume": ([P, P, P], I),
+            "lb_diagnostics": ([P, D, P], I),
+            "lb_get_step": ([P, ctypes.POINTER(ctypes.c_int64)], I),
+            "lb_save_state": ([P, P, ctypes.POINTER(ctypes.c_size_t)], I),
+            "lb_load_state": ([P, P, ctypes.c_size_t], I),
+            "lb_set_timing": ([P, I], I),
+            "lb_kernel_times": ([P, P, P], I),
+            "lb_last_error": ([P], ctypes.c_char_p),
+            "lb_version": ([], I),
+            "lb_get_mask": ([P, P], I),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def make_params(dims, tau=1.0, body_force=(0.0, 0.0, 0.0), periodic=(1, 0, 0),
+                wall_velocity=((0, 0, 0), (0, 0, 0)), storage="f32") -> LbParams:
+    p = LbParams()
+    p.nx, p.ny, p.nz = (int(v) for v in dims)
+    p.tau = float(tau)
+    for d in range(3):
+        p.body_force[d] = float(body_force[d])
+        p.periodic[d] = int(periodic[d])
+        for w in range(2):
+            p.wall_velocity[w][d] = float(wall_velocity[w][d])
+    p.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
+    return p
+
+
+class Simulation:
+    """One context: a channel (or a batch of channels) plus its cell meshes."""
+
+    def __init__(self, params: Sequence[LbParams], stream: Optional[int] = None):
+        self._L = lib()
+        self._h = ctypes.c_void_p()
+        arr = (LbParams * len(params))(*params)
+        st = self._L.lb_create_batch(arr, len(params), ctypes.c_void_p(stream or 0), ctypes.byref(self._h))
+        if st != LB_OK:
+            raise LbError(st, "lb_create_batch failed")
+        self.dims = [(p.nx, p.ny, p.nz) for p in params]
+        self.n_mesh_nodes = [[] for _ in params]
+        self.channel = 0
+
+    # -- construction ------------------------------------------------------
+    @classmethod
+    def from_scene(cls, scene, storage="f32", stream=None) -> "Simulation":
+        return cls.from_scenes([scene], storage, stream)
+
+    @classmethod
+    def from_scenes(cls, scenes, storage="f32", stream=None) -> "Simulation":
+        params = [make_params(s.dims, s.tau, s.body_force, s.periodic, s.wall_velocity, storage) for s in scenes]
+        sim = cls(params, stream)
+        for k, s in enumerate(scenes):
+            sim.select(k)
+            if len(s.spheres):
+                sim.set_obstacles(s.spheres)
+            for m in s.meshes:
+                sim.add_mesh(m.rest, m.tris, m.moduli)
+        sim.select(0)
+        return sim
+
+    def _check(self, st: int):
+        if st != LB_OK:
+            raise LbError(st, self._L.lb_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._L.lb_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self) -> int:
+        return self._h.value
+
+    def select(self, channel: int):
+        self._check(self._L.lb_select_channel(self._h, int(channel)))
+        self.channel = int(channel)
+
+    @property
+    def N(self) -> int:
+        nx, ny, nz = self.dims[self.channel]
+        return nx * ny * nz
+
+    def set_obstacles(self, spheres: np.ndarray, extra_mask: Optional[np.ndarray] = None):
+        sph = np.ascontiguousarray(spheres, dtype=np.float32).reshape(-1, 4)
+        ext = None if extra_mask is None else np.ascontiguousarray(extra_mask, dtype=np.uint8).reshape(self.N)
+        self._check(self._L.lb_set_obstacles(self._h, _ptr(sph) if len(sph) else None, int(sph.shape[0]),
+                                             None if ext is None else _ptr(ext)))
+
+    def solid_mask(self) -> np.ndarray:
+        m = np.zeros(self.N, np.uint8)
+        self._check(self._L.lb_get_mask(self._h, _ptr(m)))
+        return m
+
+    def add_mesh(self, rest: np.ndarray, tris: np.ndarray, moduli) -> int:
+        x = np.ascontiguousarray(rest, dtype=np.float64)
+        t = np.ascontiguousarray(tris, dtype=np.int32)
+        m = IbmModuli(*[float(v) for v in moduli])
+        mid = ctypes.c_int(-1)
+        self._check(self._L.ibm_add_mesh(self._h, _ptr(x), int(x.shape[0]), _ptr(t), int(t.shape[0]),
+                                         ctypes.byref(m), ctypes.byref(mid)))
+        self.n_mesh_nodes[self.channel].append(int(x.shape[0]))
+        return mid.value
+
+    def set_nodes(self, mesh: int, xyz: np.ndarray):
+        x = np.ascontiguousarray(xyz, dtype=np.float64)
+        self._check(self._L.ibm_set_nodes(self._h, int(mesh), _ptr(x)))
+
+    # -- stepping ----------------------------------------------------------
+    def step(self, n: int = 1):
+        self._check(self._L.lb_step(self._h, int(n)))
+
+    def synchronize(self):
+        self._check(self._L.lb_synchronize(self._h))
+
+    @property
+    def steps_done(self) -> int:
+        v = ctypes.c_int64()
+        self._check(self._L.lb_get_step(self._h, ctypes.byref(v)))
+        return v.value
+
+    # -- outputs -----------------------------------------------------------
+    def fields(self):
+        rho = np.zeros(self.N, np.float32)
+        u = np.zeros((3, self.N), np.float32)
+        self._check(self._L.lb_get_fields(self._h, _ptr(rho), _ptr(u), 0))
+        return rho, u
+
+    def fields_to_device(self, rho_ptr: int, u_ptr: int):
+        self._check(self._L.lb_get_fields(self._h, ctypes.c_void_p(rho_ptr), ctypes.c_void_p(u_ptr), 1))
+
+    def populations(self) -> np.ndarray:
+        f = np.zeros((19, self.N))
+        self._check(self._L.lb_get_populations(self._h, _ptr(f)))
+        return f
+
+    def set_populations(self, f: np.ndarray):
+        ff = np.ascontiguousarray(f, dtype=np.float64).reshape(19 * self.N)
+        self._check(self._L.lb_set_populations(self._h, _ptr(ff)))
+
+    def nodes(self, mesh: int) -> np.ndarray:
+        x = np.zeros((self.n_mesh_nodes[self.channel][mesh], 3))
+        self._check(self._L.ibm_get_nodes(self._h, int(mesh), _ptr(x)))
+        return x
+
+    def nodes_into(self, mesh: int, out: np.ndarray):
+        self._check(self._L.ibm_get_nodes(self._h, int(mesh), _ptr(out)))
+
+    def forces(self, mesh: int) -> np.ndarray:
+        f = np.zeros((self.n_mesh_nodes[self.channel][mesh], 3))
+        self._check(self._L.ibm_get_forces(self._h, int(mesh), _ptr(f)))
+        return f
+
+    def area_volume(self):
+        n = len(self.n_mesh_nodes[self.channel])
+        S = np.zeros(n)
+        V = np.zeros(n)
+        self._check(self._L.ibm_get_area_volume(self._h, _ptr(S), _ptr(V)))
+        return S, V
+
+    def diagnostics(self, u_max: float = 0.0) -> np.ndarray:
+        out = np.zeros(6)
+        st = self._L.lb_diagnostics(self._h, float(u_max), _ptr(out))
+        if st not in (LB_OK, LB_ERR_NUMERIC):
+            self._check(st)
+        return out
+
+    def save_state(self) -> bytes:
+        n = ctypes.c_size_t(0)
+        self._check(self._L.lb_save_state(self._h, None, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value)
+        self._check(self._L.lb_save_state(self._h, buf, ctypes.byref(n)))
+        return buf.raw[: n.value]
+
+    def load_state(self, data: bytes):
+        buf = ctypes.create_string_buffer(data, len(data))
+        self._check(self._L.lb_load_state(self._h, buf, len(data)))
+
+    def set_timing(self, on: bool):
+        self._check(self._L.lb_set_timing(self._h, int(bool(on))))
+
+    def kernel_times(self):
+        ms = np.zeros(4)
+        n = np.zeros(4, np.int64)
+        self._check(self._L.lb_kernel_times(self._h, _ptr(ms), _ptr(n)))
+        return ms, n

@@ -1,0 +1,216 @@
+"""GPU path (through the C ABI) vs the FP64 oracle on identical seeded inputs.
+
+Tolerances: FP32 velocity field relative L2 <= 1e-5 and node positions
+<= 1e-5 lu after the stated horizon; obstacle masks bit-exact; membrane forces
+within 1e-5 of the largest force magnitude (FP32 element geometry).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1110_0995_gb300 import scene
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+
+    __graft_entry__.build()
+
+
+def _sim(*a, **k):
+    from paper_1110_0995_gb300 import lbibm
+
+    return lbibm.Simulation.from_scene(*a, **k)
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.asarray(a, float) - b) / np.linalg.norm(b))
+
+
+def _ragged_scene(periodic=(1, 0, 0), wall=((0, 0, 0), (0, 0, 0)), G=(2e-5, -1e-5, 5e-6), dims=(37, 23, 19)):
+    sph = np.array([[9.0, 11.5, 8.25, 3.0], [25.5, 6.0, 12.0, 2.5], [30.0, 17.0, 3.0, 2.0]], np.float32)
+    return scene.Scene(name="ragged", dims=dims, tau=0.8, body_force=G, periodic=periodic, wall_velocity=wall,
+                       spheres=sph, meshes=[], steps=0)
+
+
+def test_obstacle_mask_bit_exact():
+    sc = _ragged_scene()
+    rng = np.random.default_rng(3)
+    sc.spheres = scene.quantize(np.column_stack([rng.uniform(-2, 40, 40), rng.uniform(-2, 25, 40),
+                                                 rng.uniform(-2, 21, 40), rng.uniform(0.5, 4, 40)]),
+                                scene.SPHERE_QUANTUM).astype(np.float32)
+    sim = _sim(sc)
+    assert np.array_equal(sim.solid_mask(), oracle.rasterise(sc.spheres, sc.dims))
+
+
+def test_rest_state_exact():
+    sc = _ragged_scene(G=(0, 0, 0))
+    sim = _sim(sc)
+    sim.step(300)
+    rho, u = sim.fields()
+    assert np.all(rho == 1.0) and np.all(u == 0.0)
+    _, w, _ = oracle.constants()
+    f = sim.populations()
+    assert np.array_equal(f, np.broadcast_to(w[:, None], f.shape))
+
+
+@pytest.mark.parametrize("periodic,wall", [((1, 0, 0), ((0, 0, 0), (0, 0, 0))),
+                                           ((1, 0, 1), ((0, 0, 0), (0.02, 0, 0.01))),
+                                           ((1, 1, 1), ((0, 0, 0), (0, 0, 0))),
+                                           ((0, 0, 0), ((0.01, 0, 0), (0, 0, 0)))])
+def test_lattice_parity_random_state(periodic, wall):
+    """Fused stream-collide vs the oracle from a random non-equilibrium state,
+    ragged lattice (N not a multiple of 32), obstacles, walls, moving walls."""
+    sc = _ragged_scene(periodic, wall)
+    sim = _sim(sc)
+    ref = oracle.System.from_scene(sc)
+    f0 = ref.get_f() * (1 + 0.01 * scene.random_field(7, (19, ref.N)))
+    f0[:, ref.solid == 1] = ref.get_f()[:, ref.solid == 1]
+    ref.set_f(f0)
+    sim.set_populations(f0)
+    np.testing.assert_allclose(sim.populations()[:, ref.solid == 0], f0[:, ref.solid == 0], rtol=0, atol=1e-8)
+    for n in (1, 49):
+        sim.step(n)
+        ref.step(n)
+        rho, u = sim.fields()
+        rho_o, u_o = ref.fields()
+        fluid = ref.solid == 0
+        assert rel_l2(u[:, fluid], u_o[:, fluid]) < 1e-5
+        assert np.abs(rho[fluid] - rho_o[fluid]).max() < 1e-6
+        np.testing.assert_allclose(sim.populations()[:, fluid], ref.get_f()[:, fluid], rtol=0, atol=2e-7)
+
+
+def _deformed_cell(kind, seed, amp):
+    v, t = scene.cell_template(kind)
+    rng = np.random.default_rng(seed)
+    R = scene.random_rotation(rng)
+    rest = scene.quantize(v @ R.T + np.array([16.3, 12.1, 11.7]), scene.POS_QUANTUM)
+    x = scene.quantize(rest + amp * rng.standard_normal(rest.shape), scene.POS_QUANTUM)
+    return rest, x, t
+
+
+@pytest.mark.parametrize("kind,moduli", [("rbc", scene.RBC_MODULI), ("ctc", scene.CTC_MODULI)])
+@pytest.mark.parametrize("amp", [1e-3, 3e-2])
+def test_membrane_forces_and_area_volume(kind, moduli, amp):
+    rest, x, t = _deformed_cell(kind, 5, amp)
+    sc = scene.Scene(name="cell", dims=(40, 32, 32), periodic=(1, 1, 1),
+                     meshes=[scene.Mesh(kind, rest, t, moduli)])
+    sim = _sim(sc)
+    sim.set_nodes(0, x)
+    S, V = sim.area_volume()
+    So, Vo = oracle.mesh_area_volume(x, t)
+    S0, V0 = oracle.mesh_area_volume(rest, t)
+    assert abs((S[0] - S0) - (So - S0)) < 1e-5 * abs(So - S0) + 1e-9 * S0
+    assert abs((V[0] - V0) - (Vo - V0)) < 1e-5 * abs(Vo - V0) + 1e-9 * V0
+    sim.step(1)
+    F = sim.forces(0)
+    Fo = oracle.mesh_forces(x, rest, t, moduli)
+    assert np.abs(F - Fo).max() < 2e-5 * np.abs(Fo).max()
+    assert rel_l2(F, Fo) < 1e-5
+
+
+def test_plain_channel_1000_steps():
+    """32x16x64 channel, one red cell, body force 1e-5, 1000 steps (the plain-method workload)."""
+    sc = scene.channel_plain(seed=1)
+    sim = _sim(sc)
+    ref = oracle.System.from_scene(sc)
+    sim.step(sc.steps)
+    ref.step(sc.steps)
+    _, u = sim.fields()
+    _, uo = ref.fields()
+    assert rel_l2(u, uo) < 1e-5
+    assert np.abs(sim.nodes(0) - ref.nodes(0)).max() < 1e-5
+    assert np.abs(sim.nodes(0) - sc.meshes[0].rest).max() > 0.05     # the cell did move
+
+
+def test_small_filter_parity():
+    """96x48x32 filter with posts, 4 red cells and 1 tumor cell, 300 steps."""
+    sc = scene.small_filter(seed=5, steps=300)
+    sim = _sim(sc)
+    ref = oracle.System.from_scene(sc)
+    sim.step(sc.steps)
+    ref.step(sc.steps)
+    _, u = sim.fields()
+    _, uo = ref.fields()
+    assert rel_l2(u, uo) < 1e-5
+    for m in range(len(sc.meshes)):
+        assert np.abs(sim.nodes(m) - ref.nodes(m)).max() < 1e-5
+
+
+def test_micropost_filter_full_size_parity():
+    """Full 256x128x64 filter (62 cells, 120 beads): 200 steps against the oracle."""
+    sc = scene.micropost_filter(seed=11)
+    sim = _sim(sc)
+    ref = oracle.System.from_scene(sc)
+    assert np.array_equal(sim.solid_mask(), ref.solid)
+    sim.step(200)
+    ref.step(200)
+    _, u = sim.fields()
+    _, uo = ref.fields()
+    assert rel_l2(u, uo) < 1e-5
+    err = max(np.abs(sim.nodes(m) - ref.nodes(m)).max() for m in range(len(sc.meshes)))
+    assert err < 1e-5
+
+
+def test_checkpoint_resume():
+    sc = scene.channel_plain(seed=3, steps=0)
+    sim = _sim(sc)
+    sim.step(150)
+    state = sim.save_state()
+    sim.step(100)
+    xa, (_, ua) = sim.nodes(0), sim.fields()
+    sim.load_state(state)
+    assert sim.steps_done == 150
+    sim.step(100)
+    xb, (_, ub) = sim.nodes(0), sim.fields()
+    assert np.abs(xa - xb).max() < 1e-7
+    assert rel_l2(ub, ua) < 1e-6
+
+
+def test_diagnostics_mass_and_momentum():
+    sc = scene.small_filter(seed=6, steps=0)
+    sim = _sim(sc)
+    d0 = sim.diagnostics()
+    sim.step(100)
+    d1 = sim.diagnostics(u_max=0.1)
+    n_fluid = int((sim.solid_mask() == 0).sum())
+    assert abs(d0[0] - n_fluid) < 1e-9 * n_fluid
+    assert abs(d1[0] - d0[0]) < 1e-6 * n_fluid
+    assert d1[4] == 0 and 0 < d1[5] < 0.1
+
+
+def test_batch_matches_single_channels():
+    """Three channels of different sizes in one context = three separate contexts."""
+    from paper_1110_0995_gb300 import lbibm
+
+    scs = [scene.channel_plain(seed=s, dims=d, steps=0) for s, d in [(1, (32, 16, 24)), (2, (40, 24, 16)), (3, (24, 16, 32))]]
+    batch = lbibm.Simulation.from_scenes(scs)
+    batch.step(120)
+    for k, sc in enumerate(scs):
+        single = _sim(sc)
+        single.step(120)
+        batch.select(k)
+        _, ub = batch.fields()
+        _, us = single.fields()
+        assert rel_l2(ub, us) < 1e-6
+        assert np.abs(batch.nodes(0) - single.nodes(0)).max() < 1e-7
+
+
+@pytest.mark.parametrize("storage,tol", [("f16", 1e-3), ("bf16", None)])
+def test_reduced_precision_storage(storage, tol):
+    """Shifted populations stored in 16 bits, FP32 arithmetic: error vs the oracle per field."""
+    sc = scene.channel_plain(seed=1, steps=200)
+    sim = _sim(sc, storage=storage)
+    ref = oracle.System.from_scene(sc)
+    sim.step(sc.steps)
+    ref.step(sc.steps)
+    _, u = sim.fields()
+    _, uo = ref.fields()
+    err = rel_l2(u, uo)
+    print(f"{storage}: velocity rel L2 {err:.3e}, nodes {np.abs(sim.nodes(0) - ref.nodes(0)).max():.3e}")
+    assert np.isfinite(err)
+    if tol is not None:
+        assert err < tol
