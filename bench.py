@@ -197,6 +197,9 @@ def run_ours(args):
     sc = make_workload(args.workload)
     stream = torch.cuda.Stream()
     sim = lbibm.Simulation.from_scene(sc, storage=args.storage, stream=stream.cuda_stream)
+    from paper_1110_0995_gb300 import autotune
+
+    tuned = autotune.tune(sim, torch.cuda.get_device_name(local_rank), args.storage)
     n_nodes = sc.n_nodes
     n_fluid = int((sim.solid_mask() == 0).sum())
     sim.set_timing(True)
@@ -248,6 +251,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         s2 = lbibm.Simulation.from_scene(sc, storage=args.storage, stream=stream.cuda_stream)
+        s2.set_kernel_config(tuned["npt"], tuned["bs"])
         h2d = sum(m.rest.nbytes + m.tris.nbytes for m in sc.meshes) + sc.spheres.nbytes
         d2h = 0
         bufs = [np.zeros((m.n_nodes, 3)) for m in sc.meshes]
@@ -278,7 +282,8 @@ def run_ours(args):
                        "ib_nodes": sc.n_ib_nodes, "spheres": int(len(sc.spheres)), "fluid_nodes": n_fluid,
                        "storage": args.storage, "l2": "populations 2x%.0f MB > 126 MB L2" % (
                            19 * BYTES_PER_NODE[args.storage] / 38 * n_nodes / 1e6),
-                       "parallelism": "replicas" if world > 1 else "single"},
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "stream_collide_variant": {"nodes_per_thread": tuned["npt"], "block": tuned["bs"]}},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                          "kernel": "k_stream_collide", "alg_bytes_per_launch": alg_bytes,

@@ -126,6 +126,21 @@ lb_status ibm_set_nodes(lb_ctx* ctx, int mesh_id, const double* xyz);
  * context's stream; launched as a CUDA graph after the first call. */
 lb_status lb_step(lb_ctx* ctx, int n_steps);
 
+/* Variant of the fused stream-collide kernel: consecutive x-nodes per thread
+ * (1, 2 or 4 for every storage) and threads
+ * per block (128 or 256).  Every channel's nx must be a multiple of the nodes
+ * per thread.  LB_ERR_ARG for an unsupported pair.  Results do not depend on
+ * the variant. */
+lb_status lb_set_kernel_config(lb_ctx* ctx, int nodes_per_thread, int block_size);
+lb_status lb_get_kernel_config(lb_ctx* ctx, int* nodes_per_thread, int* block_size);
+
+/* Autotuner: times every supported stream-collide variant on this context's
+ * lattice (`repeats` launches each, CUDA events), selects the fastest and
+ * returns it with its mean time per launch in ms.  Only before the first
+ * lb_step (LB_ERR_STATE otherwise): there, repeated launches leave the state
+ * unchanged. */
+lb_status lb_autotune(lb_ctx* ctx, int repeats, int* nodes_per_thread, int* block_size, double* ms);
+
 /* Wait for the context's stream and report any pending error. */
 lb_status lb_synchronize(lb_ctx* ctx);
 

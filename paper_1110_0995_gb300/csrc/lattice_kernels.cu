@@ -10,36 +10,70 @@
 // Storage is shifted: h_i = f_i - w_i (rho0 = 1), so the moments are sums of
 // small numbers (FP32 keeps ~1e-7 relative accuracy on u ~ 1e-3 instead of
 // ~1e-5 with f_i ~ 0.05).  The half/bfloat16 modes store h_i / w_i.
+//
+// The stream-collide kernel handles NPT consecutive x-nodes per thread: every
+// direction is one aligned NPT-wide vector load (128-bit for FP32 with NPT = 4)
+// of the source row; the +-x shifted directions take their missing element
+// from the neighbouring lane with a warp shuffle.  Warps whose 32-node groups
+// touch an obstacle or a wall take a per-node path with bounce-back instead.
 #include "lbibm_internal.cuh"
+
+#include <type_traits>
 
 namespace lbibm {
 
-constexpr int K3_BLOCK = 256;
-static_assert(CH_ALIGN % K3_BLOCK == 0, "channel padding must cover whole stream-collide blocks");
-int stream_collide_block_size() { return K3_BLOCK; }
+constexpr unsigned FULL = 0xffffffffu;
 
 // ---------------------------------------------------------------------------
 // population storage
 // ---------------------------------------------------------------------------
-template <class S> struct Pop;
-template <> struct Pop<float> {
-    static __device__ __forceinline__ float ld(const float* p, long long idx, int) { return __ldg(p + idx); }
-    static __device__ __forceinline__ void st(float* p, long long idx, float h, int) { p[idx] = h; }
+__device__ __forceinline__ float to_f(float v) { return v; }
+__device__ __forceinline__ float to_f(__half v) { return __half2float(v); }
+__device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <class S> __device__ __forceinline__ S from_f(float v);
+template <> __device__ __forceinline__ float from_f<float>(float v) { return v; }
+template <> __device__ __forceinline__ __half from_f<__half>(float v) { return __float2half_rn(v); }
+template <> __device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+
+template <class S> struct Pop {
+    static __device__ __forceinline__ float ld(const S* p, long long idx, int i) {
+        if constexpr (sizeof(S) == 4) return __ldg(p + idx);
+        else return wgt(i) * to_f(__ldg(p + idx));
+    }
+    static __device__ __forceinline__ void st(S* p, long long idx, float h, int i) {
+        if constexpr (sizeof(S) == 4) p[idx] = h;
+        else p[idx] = from_f<S>(h * (1.0f / wgt(i)));
+    }
 };
-template <> struct Pop<__half> {
-    static __device__ __forceinline__ float ld(const __half* p, long long idx, int i) {
-        return wgt(i) * __half2float(__ldg(p + idx));
+
+// NPT consecutive populations of one direction as one aligned vector access.
+template <int BYTES> struct Raw;
+template <> struct Raw<2> { using T = unsigned short; };
+template <> struct Raw<4> { using T = unsigned int; };
+template <> struct Raw<8> { using T = uint2; };
+template <> struct Raw<16> { using T = uint4; };
+
+template <class S, int NPT>
+struct VecIO {
+    using R = typename Raw<sizeof(S) * NPT>::T;
+    static __device__ __forceinline__ void ld(const S* base, long long idx, int i, float out[NPT]) {
+        const R r = __ldg(reinterpret_cast<const R*>(base + idx));
+        const S* e = reinterpret_cast<const S*>(&r);
+#pragma unroll
+        for (int k = 0; k < NPT; ++k) {
+            if constexpr (sizeof(S) == 4) out[k] = to_f(e[k]);
+            else out[k] = wgt(i) * to_f(e[k]);
+        }
     }
-    static __device__ __forceinline__ void st(__half* p, long long idx, float h, int i) {
-        p[idx] = __float2half_rn(h * (1.0f / wgt(i)));
-    }
-};
-template <> struct Pop<__nv_bfloat16> {
-    static __device__ __forceinline__ float ld(const __nv_bfloat16* p, long long idx, int i) {
-        return wgt(i) * __bfloat162float(__ldg(p + idx));
-    }
-    static __device__ __forceinline__ void st(__nv_bfloat16* p, long long idx, float h, int i) {
-        p[idx] = __float2bfloat16_rn(h * (1.0f / wgt(i)));
+    static __device__ __forceinline__ void st(S* base, long long idx, int i, const float in[NPT]) {
+        R r;
+        S* e = reinterpret_cast<S*>(&r);
+#pragma unroll
+        for (int k = 0; k < NPT; ++k) {
+            if constexpr (sizeof(S) == 4) e[k] = from_f<S>(in[k]);
+            else e[k] = from_f<S>(in[k] * (1.0f / wgt(i)));
+        }
+        *reinterpret_cast<R*>(base + idx) = r;
     }
 };
 
@@ -47,34 +81,37 @@ __device__ __forceinline__ bool solid_at(const uint32_t* mask, long long g) {
     return (__ldg(mask + (g >> 5)) >> (g & 31)) & 1u;
 }
 
+__device__ __forceinline__ const ChannelDev& chan(const LatticeArgs& a, int c) {
+    return c < MAXCH_P ? a.chp[c] : a.ch[c];
+}
+
 // Source offsets of the pull scheme for one node: for each axis the linear
 // offset to the neighbour at coordinate -1 ("m") and +1 ("p"), with periodic
 // wrap, and whether that neighbour exists.
 struct Nbr {
-    long long om[3], op[3];
+    int om[3], op[3];
     bool vm[3], vp[3];
 };
 
 __device__ __forceinline__ void neighbours(const ChannelDev& C, int x, int y, int z, Nbr& nb) {
-    const long long sx = 1, sy = C.nx, sz = (long long)C.nx * C.ny;
     const int c[3] = {x, y, z};
     const int n[3] = {C.nx, C.ny, C.nz};
-    const long long s[3] = {sx, sy, sz};
+    const int s[3] = {1, C.nx, C.nx * C.ny};
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         if (c[d] > 0) { nb.om[d] = -s[d]; nb.vm[d] = true; }
-        else if (C.per[d]) { nb.om[d] = (long long)(n[d] - 1) * s[d]; nb.vm[d] = true; }
+        else if (C.per[d]) { nb.om[d] = (n[d] - 1) * s[d]; nb.vm[d] = true; }
         else { nb.om[d] = 0; nb.vm[d] = false; }
         if (c[d] < n[d] - 1) { nb.op[d] = s[d]; nb.vp[d] = true; }
-        else if (C.per[d]) { nb.op[d] = -(long long)(n[d] - 1) * s[d]; nb.vp[d] = true; }
+        else if (C.per[d]) { nb.op[d] = -(n[d] - 1) * s[d]; nb.vp[d] = true; }
         else { nb.op[d] = 0; nb.vp[d] = false; }
     }
 }
 
 // Offset of the pull source x - e_i and whether it lies inside the domain.
 template <int I>
-__device__ __forceinline__ long long src_off(const Nbr& nb, bool& ok) {
-    long long o = 0;
+__device__ __forceinline__ int src_off(const Nbr& nb, bool& ok) {
+    int o = 0;
     ok = true;
     if (ex(I) == 1) { o += nb.om[0]; ok = ok && nb.vm[0]; }
     if (ex(I) == -1) { o += nb.op[0]; ok = ok && nb.vp[0]; }
@@ -85,12 +122,23 @@ __device__ __forceinline__ long long src_off(const Nbr& nb, bool& ok) {
     return o;
 }
 
+// y/z part of the source offset (the +-x part is handled by the vector path).
+template <int I>
+__device__ __forceinline__ int src_off_yz(const Nbr& nb) {
+    int o = 0;
+    if (ey(I) == 1) o += nb.om[1];
+    if (ey(I) == -1) o += nb.op[1];
+    if (ez(I) == 1) o += nb.om[2];
+    if (ez(I) == -1) o += nb.op[2];
+    return o;
+}
+
 // Pull one population with bounce-back where the source is a wall or solid.
 template <class S, int I>
 __device__ __forceinline__ float pull_slow(const S* src, long long NT, long long gp, const Nbr& nb,
                                            const uint32_t* mask, const ChannelDev& C, int y) {
     bool ok;
-    const long long o = src_off<I>(nb, ok);
+    const int o = src_off<I>(nb, ok);
     if (ok) ok = !solid_at(mask, gp + o);
     if (ok) return Pop<S>::ld(src, (long long)I * NT + gp + o, I);
     float h = Pop<S>::ld(src, (long long)opp(I) * NT + gp, opp(I));
@@ -106,36 +154,70 @@ __device__ __forceinline__ float pull_slow(const S* src, long long NT, long long
     return h;
 }
 
+#define LBIBM_ALL_I(M) M(0) M(1) M(2) M(3) M(4) M(5) M(6) M(7) M(8) M(9) M(10) M(11) M(12) M(13) M(14) M(15) M(16) M(17) M(18)
+
 template <class S>
-__device__ __forceinline__ void pull_all(const S* src, long long NT, long long gp, const Nbr& nb,
-                                         const uint32_t* mask, const ChannelDev& C, int y, bool slow, float h[Q]) {
-    if (slow) {
-        h[0] = pull_slow<S, 0>(src, NT, gp, nb, mask, C, y);
-        h[1] = pull_slow<S, 1>(src, NT, gp, nb, mask, C, y);
-        h[2] = pull_slow<S, 2>(src, NT, gp, nb, mask, C, y);
-        h[3] = pull_slow<S, 3>(src, NT, gp, nb, mask, C, y);
-        h[4] = pull_slow<S, 4>(src, NT, gp, nb, mask, C, y);
-        h[5] = pull_slow<S, 5>(src, NT, gp, nb, mask, C, y);
-        h[6] = pull_slow<S, 6>(src, NT, gp, nb, mask, C, y);
-        h[7] = pull_slow<S, 7>(src, NT, gp, nb, mask, C, y);
-        h[8] = pull_slow<S, 8>(src, NT, gp, nb, mask, C, y);
-        h[9] = pull_slow<S, 9>(src, NT, gp, nb, mask, C, y);
-        h[10] = pull_slow<S, 10>(src, NT, gp, nb, mask, C, y);
-        h[11] = pull_slow<S, 11>(src, NT, gp, nb, mask, C, y);
-        h[12] = pull_slow<S, 12>(src, NT, gp, nb, mask, C, y);
-        h[13] = pull_slow<S, 13>(src, NT, gp, nb, mask, C, y);
-        h[14] = pull_slow<S, 14>(src, NT, gp, nb, mask, C, y);
-        h[15] = pull_slow<S, 15>(src, NT, gp, nb, mask, C, y);
-        h[16] = pull_slow<S, 16>(src, NT, gp, nb, mask, C, y);
-        h[17] = pull_slow<S, 17>(src, NT, gp, nb, mask, C, y);
-        h[18] = pull_slow<S, 18>(src, NT, gp, nb, mask, C, y);
-    } else {
+__device__ __forceinline__ void pull_node(const S* src, long long NT, long long gp, const Nbr& nb,
+                                          const uint32_t* mask, const ChannelDev& C, int y, float h[Q]) {
+#define LBIBM_PS(I) h[I] = pull_slow<S, I>(src, NT, gp, nb, mask, C, y);
+    LBIBM_ALL_I(LBIBM_PS)
+#undef LBIBM_PS
+}
+
+// Vector pull, phase 1: issue the loads of direction I for the NPT nodes
+// starting at x0.  Every address stays inside the channel's rows (a missing
+// neighbour maps to offset 0), so the loads can be issued before the warp
+// knows whether it takes this path; lanes past the channel's end load nothing.
+// With NPT = 1 the +-x shift is part of the address; with NPT > 1 the vector
+// is the aligned source row and the lanes at a row end or a warp edge also
+// load the one element their neighbour lane cannot hand them.
+template <class S, int NPT, int I>
+__device__ __forceinline__ void issue_vec(const S* src, long long NT, int gi0, const Nbr& nb, const ChannelDev& C,
+                                          int x0, int lane, bool inr, float v[NPT], float& extra) {
+    extra = 0.0f;
+    const S* pl = src + (size_t)I * (size_t)NT;   // plane of direction I (warp-uniform)
+    if constexpr (NPT == 1) {
         bool ok;
-#define LBIBM_PULL(I) h[I] = Pop<S>::ld(src, (long long)(I) * NT + gp + src_off<I>(nb, ok), I);
-        LBIBM_PULL(0) LBIBM_PULL(1) LBIBM_PULL(2) LBIBM_PULL(3) LBIBM_PULL(4) LBIBM_PULL(5) LBIBM_PULL(6)
-        LBIBM_PULL(7) LBIBM_PULL(8) LBIBM_PULL(9) LBIBM_PULL(10) LBIBM_PULL(11) LBIBM_PULL(12)
-        LBIBM_PULL(13) LBIBM_PULL(14) LBIBM_PULL(15) LBIBM_PULL(16) LBIBM_PULL(17) LBIBM_PULL(18)
-#undef LBIBM_PULL
+        const int b = gi0 + src_off<I>(nb, ok);
+        v[0] = inr ? Pop<S>::ld(pl, b, I) : 0.0f;
+    } else {
+        const int b = gi0 + src_off_yz<I>(nb);   // source row, aligned to NPT
+        if (inr) {
+            VecIO<S, NPT>::ld(pl, b, I, v);
+        } else {
+#pragma unroll
+            for (int k = 0; k < NPT; ++k) v[k] = 0.0f;
+        }
+        if constexpr (ex(I) == 1) {
+            if (inr && (lane == 0 || x0 == 0)) extra = Pop<S>::ld(pl, x0 == 0 ? b + (C.nx - 1) : b - 1, I);
+        } else if constexpr (ex(I) == -1) {
+            if (inr && (lane == 31 || x0 + NPT == C.nx)) extra = Pop<S>::ld(pl, x0 + NPT == C.nx ? b - x0 : b + NPT, I);
+        }
+    }
+}
+
+// Vector pull, phase 2 (converged warp, no walls or obstacles around): place
+// the loaded values, taking the +-x halo element from the neighbouring lane.
+template <int NPT, int I>
+__device__ __forceinline__ void place_vec(const float v[NPT], float extra, const ChannelDev& C, int x0, int lane,
+                                          float h[NPT][Q]) {
+    if constexpr (NPT == 1 || ex(I) == 0) {
+#pragma unroll
+        for (int k = 0; k < NPT; ++k) h[k][I] = v[k];
+    } else if constexpr (ex(I) == 1) {
+        // node x0 + k pulls from x0 + k - 1
+        float left = __shfl_up_sync(FULL, v[NPT - 1], 1);
+        if (lane == 0 || x0 == 0) left = extra;
+        h[0][I] = left;
+#pragma unroll
+        for (int k = 1; k < NPT; ++k) h[k][I] = v[k - 1];
+    } else {
+        // node x0 + k pulls from x0 + k + 1
+        float right = __shfl_down_sync(FULL, v[0], 1);
+        if (lane == 31 || x0 + NPT == C.nx) right = extra;
+#pragma unroll
+        for (int k = 0; k < NPT - 1; ++k) h[k][I] = v[k + 1];
+        h[NPT - 1][I] = right;
     }
 }
 
@@ -152,86 +234,187 @@ __device__ __forceinline__ void moments(const float h[Q], float& drho, float& jx
            ((h[15] + h[16]) + (h[17] + h[18]));
 }
 
+// Macroscopic state of one node for the collision.
+struct Mac {
+    float drho, rho, ux, uy, uz, uu, gx, gy, gz, ug;
+};
+
+__device__ __forceinline__ Mac macro(const float h[Q], float gx, float gy, float gz) {
+    Mac m;
+    float jx, jy, jz;
+    moments(h, m.drho, jx, jy, jz);
+    m.gx = gx; m.gy = gy; m.gz = gz;
+    m.rho = 1.0f + m.drho;
+    const float irho = 1.0f / m.rho;
+    m.ux = (jx + 0.5f * gx) * irho;
+    m.uy = (jy + 0.5f * gy) * irho;
+    m.uz = (jz + 0.5f * gz) * irho;
+    m.uu = m.ux * m.ux + m.uy * m.uy + m.uz * m.uz;
+    m.ug = m.ux * gx + m.uy * gy + m.uz * gz;
+    return m;
+}
+
 // BGK collision with Guo forcing on shifted populations:
 //   h*_i = h_i + omega (h_i^eq - h_i) + S_i,
 //   h_i^eq = w_i [drho + rho (3 e.u + 9/2 (e.u)^2 - 3/2 u.u)],
 //   S_i = (1 - 1/2tau) w_i [3 (e_i - u) + 9 (e_i.u) e_i] . g.
 template <int I>
-__device__ __forceinline__ float collide_one(float hi, float drho, float rho, float ux, float uy, float uz, float uu,
-                                             float gx, float gy, float gz, float ug, float omega, float fpre) {
-    const float eu = ex(I) * ux + ey(I) * uy + ez(I) * uz;
-    const float eg = ex(I) * gx + ey(I) * gy + ez(I) * gz;
-    const float heq = wgt(I) * (drho + rho * (3.0f * eu + 4.5f * eu * eu - 1.5f * uu));
-    const float s = fpre * wgt(I) * (3.0f * (eg - ug) + 9.0f * eu * eg);
+__device__ __forceinline__ float collide_one(float hi, const Mac& m, float omega, float fpre) {
+    const float eu = ex(I) * m.ux + ey(I) * m.uy + ez(I) * m.uz;
+    const float eg = ex(I) * m.gx + ey(I) * m.gy + ez(I) * m.gz;
+    const float heq = wgt(I) * (m.drho + m.rho * (3.0f * eu + 4.5f * eu * eu - 1.5f * m.uu));
+    const float s = fpre * wgt(I) * (3.0f * (eg - m.ug) + 9.0f * eu * eg);
     return hi + omega * (heq - hi) + s;
 }
 
-template <class S>
-__global__ void __launch_bounds__(K3_BLOCK) k_stream_collide(LatticeArgs a) {
+template <class S, int NPT, int I>
+__device__ __forceinline__ void collide_store_vec(S* dst, long long NT, int gi0, const float h[NPT][Q],
+                                                  const Mac m[NPT], float om, float fp) {
+    float o[NPT];
+#pragma unroll
+    for (int k = 0; k < NPT; ++k) o[k] = collide_one<I>(h[k][I], m[k], om, fp);
+    VecIO<S, NPT>::st(dst + (size_t)I * (size_t)NT, gi0, I, o);
+}
+
+// Resident blocks per SM the register budget is sized for (about 85 registers
+// per thread with one node per thread, 128 with two, 255 with four).
+template <int NPT, int BS> struct K3MinBlocks {
+    static constexpr int value = (NPT == 1 ? 768 : (NPT == 2 ? 512 : 256)) / BS > 0
+                                     ? (NPT == 1 ? 768 : (NPT == 2 ? 512 : 256)) / BS : 1;
+};
+
+template <class S, int NPT, int BS>
+__global__ void __launch_bounds__(BS, K3MinBlocks<NPT, BS>::value) k_stream_collide(const __grid_constant__ LatticeArgs a) {
     const int b = blockIdx.x;
     int c = 0;
     for (int k = 1; k < a.n_ch; ++k)
-        if (b >= a.ch[k].blk0) c = k;
-    const ChannelDev C = a.ch[c];
-    const long long p = (long long)(b - C.blk0) * K3_BLOCK + threadIdx.x;
-    const long long gp = C.base + p;
-    const int grp = (int)(gp >> 5);
+        if (b >= chan(a, k).blk0) c = k;
+    const ChannelDev C = chan(a, c);   // registers: read once from the parameter bank
+    const int lane = threadIdx.x & 31;
+    const int p0 = ((b - C.blk0) * BS + (int)threadIdx.x) * NPT;   // first channel-local node of this thread
+    const long long gp0 = C.base + p0;
+    const int gi0 = (int)gp0;      // the padded node count of a context is below 2^31
+    const int grp = gi0 >> 5;
     const int par = a.par;
     uint8_t* fl_prev = par ? a.fl0 : a.fl1;
-    const bool forced = __ldg((par ? a.fl1 : a.fl0) + grp) != 0;
-    const bool prevf = __ldg(fl_prev + grp) != 0;
-    const bool active = p < C.n && !solid_at(a.mask, gp);
-    if (active) {
-        const S* src = (const S*)(par ? a.h1 : a.h0);
-        S* dst = (S*)(par ? a.h0 : a.h1);
-        const long long NT = a.Ntot;
-        const int x = (int)(p % C.nx);
-        const long long r = p / C.nx;
-        const int y = (int)(r % C.ny);
-        const int z = (int)(r / C.ny);
-        Nbr nb;
-        neighbours(C, x, y, z, nb);
-        const bool slow = __ldg(a.slow + grp) != 0;
+    const bool inr = p0 < C.n;
+    // flags first: their latency overlaps the population loads below
+    const uint8_t fcur = __ldg((par ? a.fl1 : a.fl0) + grp);
+    const uint8_t fprev = __ldg(fl_prev + grp);
+    const uint8_t fslow = inr ? __ldg(a.slow + grp) : (uint8_t)0;
+    const S* src = (const S*)(par ? a.h1 : a.h0);
+    S* dst = (S*)(par ? a.h0 : a.h1);
+    const long long NT = a.Ntot;
+    const int x0 = p0 % C.nx;
+    const int r = p0 / C.nx;
+    const int y = r % C.ny;
+    const int z = r / C.ny;
+    Nbr nb;
+    neighbours(C, x0, y, z, nb);
+    // phase 1: every population load of the vector path in flight at once
+    float v[Q][NPT], extra[Q];
+#define LBIBM_IV(I) issue_vec<S, NPT, I>(src, NT, gi0, nb, C, x0, lane, inr, v[I], extra[I]);
+    LBIBM_ALL_I(LBIBM_IV)
+#undef LBIBM_IV
+    const bool forced = fcur != 0;
+    const bool prevf = fprev != 0;
+    const bool wslow = __any_sync(FULL, fslow != 0);
+    const float om = C.omega, fp = C.fpre;
+    const float4* gcur = par ? a.g1 : a.g0;
+    float4* gprev = par ? a.g0 : a.g1;
 
-        float h[Q];
-        pull_all<S>(src, NT, gp, nb, a.mask, C, y, slow, h);
-
-        float drho, jx, jy, jz;
-        moments(h, drho, jx, jy, jz);
-        float gx = C.G[0], gy = C.G[1], gz = C.G[2];
-        if (forced) {
-            const float4 g = (par ? a.g1 : a.g0)[gp];
-            gx += g.x; gy += g.y; gz += g.z;
+    if (!wslow) {
+        // vector path: every node of the warp is fluid with all 18 neighbours in the domain
+        float h[NPT][Q];
+#define LBIBM_PV(I) place_vec<NPT, I>(v[I], extra[I], C, x0, lane, h);
+        LBIBM_ALL_I(LBIBM_PV)
+#undef LBIBM_PV
+        if (inr) {
+            Mac m[NPT];
+#pragma unroll
+            for (int k = 0; k < NPT; ++k) {
+                float gx = C.G[0], gy = C.G[1], gz = C.G[2];
+                if (forced) {
+                    const float4 g = gcur[gi0 + k];
+                    gx += g.x; gy += g.y; gz += g.z;
+                }
+                m[k] = macro(h[k], gx, gy, gz);
+            }
+#define LBIBM_CV(I) collide_store_vec<S, NPT, I>(dst, NT, gi0, h, m, om, fp);
+            LBIBM_ALL_I(LBIBM_CV)
+#undef LBIBM_CV
+#pragma unroll
+            for (int k = 0; k < NPT; ++k) {
+                if (forced) a.u[gi0 + k] = make_float4(m[k].ux, m[k].uy, m[k].uz, m[k].rho);
+                if (prevf) gprev[gi0 + k] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
         }
-        const float rho = 1.0f + drho;
-        const float irho = 1.0f / rho;
-        const float ux = (jx + 0.5f * gx) * irho;
-        const float uy = (jy + 0.5f * gy) * irho;
-        const float uz = (jz + 0.5f * gz) * irho;
-        const float uu = ux * ux + uy * uy + uz * uz;
-        const float ug = ux * gx + uy * gy + uz * gz;
-        const float om = C.omega, fp = C.fpre;
-#define LBIBM_COLL(I) Pop<S>::st(dst, (long long)(I) * NT + gp, \
-        collide_one<I>(h[I], drho, rho, ux, uy, uz, uu, gx, gy, gz, ug, om, fp), I);
-        LBIBM_COLL(0) LBIBM_COLL(1) LBIBM_COLL(2) LBIBM_COLL(3) LBIBM_COLL(4) LBIBM_COLL(5) LBIBM_COLL(6)
-        LBIBM_COLL(7) LBIBM_COLL(8) LBIBM_COLL(9) LBIBM_COLL(10) LBIBM_COLL(11) LBIBM_COLL(12)
-        LBIBM_COLL(13) LBIBM_COLL(14) LBIBM_COLL(15) LBIBM_COLL(16) LBIBM_COLL(17) LBIBM_COLL(18)
-#undef LBIBM_COLL
-        if (forced) a.u[gp] = make_float4(ux, uy, uz, rho);
-        if (prevf) (par ? a.g0 : a.g1)[gp] = make_float4(0.f, 0.f, 0.f, 0.f);
+    } else if (inr) {
+        // per-node path with bounce-back at walls and obstacles
+#pragma unroll 1
+        for (int k = 0; k < NPT; ++k) {
+            const long long gp = gp0 + k;
+            if (solid_at(a.mask, gp)) continue;
+            Nbr nk = nb;
+            if (k > 0) neighbours(C, x0 + k, y, z, nk);
+            float h[Q];
+            pull_node<S>(src, NT, gp, nk, a.mask, C, y, h);
+            float gx = C.G[0], gy = C.G[1], gz = C.G[2];
+            if (forced) {
+                const float4 g = gcur[gp];
+                gx += g.x; gy += g.y; gz += g.z;
+            }
+            const Mac m = macro(h, gx, gy, gz);
+#define LBIBM_C1(I) Pop<S>::st(dst, (long long)(I) * NT + gp, collide_one<I>(h[I], m, om, fp), I);
+            LBIBM_ALL_I(LBIBM_C1)
+#undef LBIBM_C1
+            if (forced) a.u[gp] = make_float4(m.ux, m.uy, m.uz, m.rho);
+            if (prevf) gprev[gp] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
     }
-    // the warp owning this 32-node group clears the previous step's flag after
-    // all its lanes have consumed it
+    // the lane holding the first node of each 32-node group clears the previous
+    // step's flag after every lane of the warp has consumed it
     __syncwarp();
-    if (prevf && (threadIdx.x & 31) == 0) fl_prev[grp] = 0;
+    if (prevf && (gp0 & 31) == 0) fl_prev[grp] = 0;
 }
 
-cudaError_t launch_stream_collide(const LatticeArgs& a, int total_blocks, cudaStream_t s) {
+// Supported (nodes per thread, block size) pairs per storage type.
+static const K3Config CFG_F32[] = {{1, 256}, {2, 256}, {4, 256}, {4, 128}, {2, 128}, {1, 128}};
+static const K3Config CFG_16[] = {{2, 256}, {4, 256}, {4, 128}, {2, 128}, {1, 256}, {1, 128}};
+
+int k3_config_count(int storage) { return 6; }
+K3Config k3_config_at(int storage, int k) { return storage == 0 ? CFG_F32[k] : CFG_16[k]; }
+bool k3_config_supported(int storage, K3Config c) {
+    for (int k = 0; k < k3_config_count(storage); ++k) {
+        const K3Config d = k3_config_at(storage, k);
+        if (d.npt == c.npt && d.bs == c.bs) return true;
+    }
+    return false;
+}
+
+template <class S>
+static cudaError_t launch_sc_typed(const LatticeArgs& a, K3Config c, int blocks, cudaStream_t s) {
+#define LBIBM_CASE(N, B)                                   \
+    if (c.npt == N && c.bs == B) {                         \
+        k_stream_collide<S, N, B><<<blocks, B, 0, s>>>(a); \
+        return cudaGetLastError();                         \
+    }
+    if constexpr (sizeof(S) == 4) {
+        LBIBM_CASE(1, 256) LBIBM_CASE(2, 256) LBIBM_CASE(4, 256) LBIBM_CASE(4, 128) LBIBM_CASE(2, 128)
+        LBIBM_CASE(1, 128)
+    } else {
+        LBIBM_CASE(2, 256) LBIBM_CASE(4, 256) LBIBM_CASE(4, 128) LBIBM_CASE(2, 128) LBIBM_CASE(1, 256)
+        LBIBM_CASE(1, 128)
+    }
+#undef LBIBM_CASE
+    return cudaErrorInvalidConfiguration;
+}
+
+cudaError_t launch_stream_collide(const LatticeArgs& a, K3Config cfg, int total_blocks, cudaStream_t s) {
     if (total_blocks <= 0) return cudaSuccess;
-    if (a.storage == 0) k_stream_collide<float><<<total_blocks, K3_BLOCK, 0, s>>>(a);
-    else if (a.storage == 1) k_stream_collide<__half><<<total_blocks, K3_BLOCK, 0, s>>>(a);
-    else k_stream_collide<__nv_bfloat16><<<total_blocks, K3_BLOCK, 0, s>>>(a);
-    return cudaGetLastError();
+    if (a.storage == 0) return launch_sc_typed<float>(a, cfg, total_blocks, s);
+    if (a.storage == 1) return launch_sc_typed<__half>(a, cfg, total_blocks, s);
+    return launch_sc_typed<__nv_bfloat16>(a, cfg, total_blocks, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -239,14 +422,14 @@ cudaError_t launch_stream_collide(const LatticeArgs& a, int total_blocks, cudaSt
 // stored post-collision populations: sum_i e_i f*_i = rho u + g/2.
 // ---------------------------------------------------------------------------
 template <class S>
-__global__ void k_fields(LatticeArgs a, int c, float* rho_out, float* u_out) {
-    const ChannelDev C = a.ch[c];
-    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void k_fields(const __grid_constant__ LatticeArgs a, int c, float* rho_out, float* u_out) {
+    const ChannelDev& C = chan(a, c);
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= C.n) return;
     const long long gp = C.base + p;
     if (!a.has_last || solid_at(a.mask, gp)) {
         if (rho_out) rho_out[p] = 1.0f;
-        if (u_out) { u_out[p] = 0.f; u_out[C.n + p] = 0.f; u_out[2 * C.n + p] = 0.f; }
+        if (u_out) { u_out[p] = 0.f; u_out[(long long)C.n + p] = 0.f; u_out[2LL * C.n + p] = 0.f; }
         return;
     }
     // the last step had parity 1 - par and wrote h[par]
@@ -265,25 +448,29 @@ __global__ void k_fields(LatticeArgs a, int c, float* rho_out, float* u_out) {
     if (rho_out) rho_out[p] = rho;
     if (u_out) {
         u_out[p] = (jx - 0.5f * gx) / rho;
-        u_out[C.n + p] = (jy - 0.5f * gy) / rho;
-        u_out[2 * C.n + p] = (jz - 0.5f * gz) / rho;
+        u_out[(long long)C.n + p] = (jy - 0.5f * gy) / rho;
+        u_out[2LL * C.n + p] = (jz - 0.5f * gz) / rho;
     }
 }
 
-cudaError_t launch_fields(const LatticeArgs& a, const ChannelDev& ch, int c, float* rho, float* u, cudaStream_t s) {
+static int chan_n_host(const LatticeArgs& a, int c) { return c < MAXCH_P ? a.chp[c].n : -1; }
+
+cudaError_t launch_fields(const LatticeArgs& a, int c, float* rho, float* u, cudaStream_t s) {
     const int B = 256;
-    const long long blocks = (ch.n + B - 1) / B;
-    if (a.storage == 0) k_fields<float><<<(unsigned)blocks, B, 0, s>>>(a, c, rho, u);
-    else if (a.storage == 1) k_fields<__half><<<(unsigned)blocks, B, 0, s>>>(a, c, rho, u);
-    else k_fields<__nv_bfloat16><<<(unsigned)blocks, B, 0, s>>>(a, c, rho, u);
+    const int n = chan_n_host(a, c);
+    if (n < 0) return cudaErrorInvalidValue;
+    const unsigned blocks = (unsigned)((n + B - 1) / B);
+    if (a.storage == 0) k_fields<float><<<blocks, B, 0, s>>>(a, c, rho, u);
+    else if (a.storage == 1) k_fields<__half><<<blocks, B, 0, s>>>(a, c, rho, u);
+    else k_fields<__nv_bfloat16><<<blocks, B, 0, s>>>(a, c, rho, u);
     return cudaGetLastError();
 }
 
 // Pre-collision (post-stream) shifted populations of the next step.
 template <class S>
-__global__ void k_pull_populations(LatticeArgs a, int c, float* h_out) {
-    const ChannelDev C = a.ch[c];
-    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void k_pull_populations(const __grid_constant__ LatticeArgs a, int c, float* h_out) {
+    const ChannelDev& C = chan(a, c);
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= C.n) return;
     const long long gp = C.base + p;
     const S* src = (const S*)(a.par ? a.h1 : a.h0);
@@ -292,24 +479,26 @@ __global__ void k_pull_populations(LatticeArgs a, int c, float* h_out) {
 #pragma unroll
         for (int i = 0; i < Q; ++i) h[i] = 0.0f;
     } else {
-        const int x = (int)(p % C.nx);
-        const long long r = p / C.nx;
-        const int y = (int)(r % C.ny);
-        const int z = (int)(r / C.ny);
+        const int x = p % C.nx;
+        const int r = p / C.nx;
+        const int y = r % C.ny;
+        const int z = r / C.ny;
         Nbr nb;
         neighbours(C, x, y, z, nb);
-        pull_all<S>(src, a.Ntot, gp, nb, a.mask, C, y, true, h);
+        pull_node<S>(src, a.Ntot, gp, nb, a.mask, C, y, h);
     }
 #pragma unroll
     for (int i = 0; i < Q; ++i) h_out[(long long)i * C.n + p] = h[i];
 }
 
-cudaError_t launch_pull_populations(const LatticeArgs& a, const ChannelDev& ch, int c, float* h_out, cudaStream_t s) {
+cudaError_t launch_pull_populations(const LatticeArgs& a, int c, float* h_out, cudaStream_t s) {
     const int B = 256;
-    const long long blocks = (ch.n + B - 1) / B;
-    if (a.storage == 0) k_pull_populations<float><<<(unsigned)blocks, B, 0, s>>>(a, c, h_out);
-    else if (a.storage == 1) k_pull_populations<__half><<<(unsigned)blocks, B, 0, s>>>(a, c, h_out);
-    else k_pull_populations<__nv_bfloat16><<<(unsigned)blocks, B, 0, s>>>(a, c, h_out);
+    const int n = chan_n_host(a, c);
+    if (n < 0) return cudaErrorInvalidValue;
+    const unsigned blocks = (unsigned)((n + B - 1) / B);
+    if (a.storage == 0) k_pull_populations<float><<<blocks, B, 0, s>>>(a, c, h_out);
+    else if (a.storage == 1) k_pull_populations<__half><<<blocks, B, 0, s>>>(a, c, h_out);
+    else k_pull_populations<__nv_bfloat16><<<blocks, B, 0, s>>>(a, c, h_out);
     return cudaGetLastError();
 }
 
@@ -322,24 +511,24 @@ constexpr int DIAG_N = 6;
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(FULL, v, o);
     return v;
 }
 __device__ __forceinline__ double warp_max(double v) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(FULL, v, o));
     return v;
 }
 
 template <class S>
-__global__ void __launch_bounds__(DIAG_BLOCK) k_diag_partial(LatticeArgs a, int c, double* partials) {
-    const ChannelDev C = a.ch[c];
+__global__ void __launch_bounds__(DIAG_BLOCK) k_diag_partial(const __grid_constant__ LatticeArgs a, int c,
+                                                             double* partials) {
+    const ChannelDev& C = chan(a, c);
     const S* hs = (const S*)(a.par ? a.h1 : a.h0);
     const uint8_t* fl = a.par ? a.fl0 : a.fl1;
     const float4* gg = a.par ? a.g0 : a.g1;
     double acc[DIAG_N] = {0, 0, 0, 0, 0, 0};
-    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < C.n;
-         p += (long long)gridDim.x * blockDim.x) {
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < C.n; p += gridDim.x * blockDim.x) {
         const long long gp = C.base + p;
         if (solid_at(a.mask, gp)) continue;
         float h[Q];
@@ -390,8 +579,8 @@ __global__ void k_diag_final(const double* partials, int n_blocks, double* out) 
     out[k] = v;
 }
 
-cudaError_t launch_diagnostics(const LatticeArgs& a, const ChannelDev& ch, int c, double* partials, int n_blocks,
-                               double* out, cudaStream_t s) {
+cudaError_t launch_diagnostics(const LatticeArgs& a, int c, double* partials, int n_blocks, double* out,
+                               cudaStream_t s) {
     if (a.storage == 0) k_diag_partial<float><<<n_blocks, DIAG_BLOCK, 0, s>>>(a, c, partials);
     else if (a.storage == 1) k_diag_partial<__half><<<n_blocks, DIAG_BLOCK, 0, s>>>(a, c, partials);
     else k_diag_partial<__nv_bfloat16><<<n_blocks, DIAG_BLOCK, 0, s>>>(a, c, partials);
@@ -428,14 +617,14 @@ __global__ void k_rasterise_spheres(const float4* sph, ChannelDev C, uint32_t* m
 }
 
 __global__ void k_rasterise_extra(const uint8_t* extra, ChannelDev C, uint32_t* mask) {
-    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= C.n || !extra[p]) return;
     const long long g = C.base + p;
     atomicOr(mask + (g >> 5), 1u << (g & 31));
 }
 
 cudaError_t launch_rasterise(const float* spheres, int n_spheres, const uint8_t* extra, const ChannelDev& ch,
-                             const ChannelDev*, int, uint32_t* mask, cudaStream_t s) {
+                             uint32_t* mask, cudaStream_t s) {
     if (n_spheres > 0) k_rasterise_spheres<<<n_spheres, 256, 0, s>>>((const float4*)spheres, ch, mask);
     if (extra) k_rasterise_extra<<<(unsigned)((ch.n + 255) / 256), 256, 0, s>>>(extra, ch, mask);
     return cudaGetLastError();
@@ -445,19 +634,19 @@ cudaError_t launch_rasterise(const float* spheres, int n_spheres, const uint8_t*
 // 18 neighbours solid or outside the domain; the stream-collide kernel checks
 // the mask and bounds only there.
 __global__ void k_slow_flags(ChannelDev C, const uint32_t* mask, uint8_t* slow) {
-    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= C.n) return;
     const long long gp = C.base + p;
     bool s = solid_at(mask, gp);
     if (!s) {
-        const int x = (int)(p % C.nx);
-        const long long r = p / C.nx;
-        const int y = (int)(r % C.ny);
-        const int z = (int)(r / C.ny);
+        const int x = p % C.nx;
+        const int r = p / C.nx;
+        const int y = r % C.ny;
+        const int z = r / C.ny;
         Nbr nb;
         neighbours(C, x, y, z, nb);
         bool ok;
-#define LBIBM_CHK(I) { const long long o = src_off<I>(nb, ok); s = s || !ok || solid_at(mask, gp + (ok ? o : 0)); }
+#define LBIBM_CHK(I) { const int o = src_off<I>(nb, ok); s = s || !ok || solid_at(mask, gp + (ok ? o : 0)); }
         LBIBM_CHK(1) LBIBM_CHK(2) LBIBM_CHK(3) LBIBM_CHK(4) LBIBM_CHK(5) LBIBM_CHK(6) LBIBM_CHK(7)
         LBIBM_CHK(8) LBIBM_CHK(9) LBIBM_CHK(10) LBIBM_CHK(11) LBIBM_CHK(12) LBIBM_CHK(13) LBIBM_CHK(14)
         LBIBM_CHK(15) LBIBM_CHK(16) LBIBM_CHK(17) LBIBM_CHK(18)
@@ -466,8 +655,7 @@ __global__ void k_slow_flags(ChannelDev C, const uint32_t* mask, uint8_t* slow) 
     if (s) slow[gp >> 5] = 1;
 }
 
-cudaError_t launch_slow_flags(const ChannelDev& ch, const ChannelDev*, int, const uint32_t* mask, uint8_t* slow,
-                              cudaStream_t s) {
+cudaError_t launch_slow_flags(const ChannelDev& ch, const uint32_t* mask, uint8_t* slow, cudaStream_t s) {
     k_slow_flags<<<(unsigned)((ch.n + 255) / 256), 256, 0, s>>>(ch, mask, slow);
     return cudaGetLastError();
 }

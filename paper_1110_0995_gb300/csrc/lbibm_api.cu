@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <string>
@@ -19,7 +20,7 @@ using namespace lbibm;
 
 namespace {
 
-constexpr int CHUNK_TRIS = 512;     // triangles per block of the area/volume reduction
+constexpr int CHUNK_TRIS = 256;     // triangles per block of the area/volume reduction
 constexpr int MAX_VALENCE = 64;
 
 struct ChannelHost {
@@ -52,6 +53,7 @@ struct lb_ctx {
     std::vector<ChannelHost> ch;
     int cur = 0;
     long long Ntot = 0;
+    long long plane = 0;   // population plane stride (>= Ntot)
     int total_blocks = 0;
     // lattice
     void* h[2] = {nullptr, nullptr};
@@ -66,9 +68,7 @@ struct lb_ctx {
     int diag_blocks = 0;
     // immersed boundary, host staging
     std::vector<Q4> hq0, hq;
-    std::vector<int> hcell_of;
-    std::vector<float4> hr0;
-    std::vector<int> hring_off{0};
+    std::vector<int4> hinfo;
     std::vector<int2> hring;
     std::vector<float4> hring_rest;
     std::vector<int4> htris;
@@ -82,9 +82,8 @@ struct lb_ctx {
     int M = 0, C = 0, T = 0, NCH = 0, K = 0;
     Q4* q[2] = {nullptr, nullptr};
     Q4* q0 = nullptr;
-    float4 *xr = nullptr, *dl = nullptr, *r0 = nullptr, *F = nullptr;
-    int* cell_of = nullptr;
-    int* ring_off = nullptr;
+    float4 *xh = nullptr, *xl = nullptr, *dl = nullptr, *F = nullptr;
+    int4* info = nullptr;
     int2* ring = nullptr;
     float4* ring_rest = nullptr;
     int4* tris = nullptr;
@@ -93,7 +92,10 @@ struct lb_ctx {
     double2* partials = nullptr;
     unsigned* counters = nullptr;
     double2* cell_sums = nullptr;
+    float2* cell_rel = nullptr;
     CellDev* d_cells = nullptr;
+    // stream-collide variant and its grid
+    K3Config k3 = {1, 256};
     // stepping
     long long step = 0;
     bool started = false;
@@ -158,6 +160,8 @@ size_t pop_bytes(lb_storage s) { return s == LB_F32 ? 4 : 2; }
 
 LatticeArgs lattice_args(const lb_ctx* ctx, int par) {
     LatticeArgs a;
+    std::memset(&a, 0, sizeof(a));
+    for (size_t k = 0; k < ctx->ch.size() && k < (size_t)MAXCH_P; ++k) a.chp[k] = ctx->ch[k].d;
     a.ch = ctx->d_ch;
     a.n_ch = (int)ctx->ch.size();
     a.storage = (int)ctx->storage;
@@ -165,7 +169,7 @@ LatticeArgs lattice_args(const lb_ctx* ctx, int par) {
     a.has_last = ctx->step > 0;
     a.h0 = ctx->h[0];
     a.h1 = ctx->h[1];
-    a.Ntot = ctx->Ntot;
+    a.Ntot = ctx->plane;
     a.mask = ctx->mask;
     a.slow = ctx->slow;
     a.g0 = ctx->g[0];
@@ -178,19 +182,21 @@ LatticeArgs lattice_args(const lb_ctx* ctx, int par) {
 
 IbmArgs ibm_args(const lb_ctx* ctx, int par) {
     IbmArgs a;
+    std::memset(&a, 0, sizeof(a));
+    for (size_t k = 0; k < ctx->ch.size() && k < (size_t)MAXCH_P; ++k) a.chp[k] = ctx->ch[k].d;
     a.n_nodes = ctx->M;
     a.n_cells = ctx->C;
     a.par = par;
+    a.n_ch = (int)ctx->ch.size();
     a.ch = ctx->d_ch;
     a.cells = ctx->d_cells;
-    a.cell_of = ctx->cell_of;
+    a.info = ctx->info;
     a.qa = ctx->q[0];
     a.qb = ctx->q[1];
     a.q0 = ctx->q0;
-    a.xr = ctx->xr;
+    a.xh = ctx->xh;
+    a.xl = ctx->xl;
     a.dl = ctx->dl;
-    a.r0 = ctx->r0;
-    a.ring_off = ctx->ring_off;
     a.ring = ctx->ring;
     a.ring_rest = ctx->ring_rest;
     a.F = ctx->F;
@@ -201,6 +207,7 @@ IbmArgs ibm_args(const lb_ctx* ctx, int par) {
     a.partials = ctx->partials;
     a.counters = ctx->counters;
     a.cell_sums = ctx->cell_sums;
+    a.cell_rel = ctx->cell_rel;
     a.mask = ctx->mask;
     a.g0 = ctx->g[0];
     a.g1 = ctx->g[1];
@@ -256,7 +263,7 @@ lb_status enqueue_step(lb_ctx* ctx, int par) {
         switch (k) {
             case 0: e = launch_cell_sums(ia, ctx->stream); break;
             case 1: e = launch_forces_spread(ia, ctx->stream); break;
-            case 2: e = launch_stream_collide(la, ctx->total_blocks, ctx->stream); break;
+            case 2: e = launch_stream_collide(la, ctx->k3, ctx->total_blocks, ctx->stream); break;
             case 3: e = launch_interp_advance(ia, ctx->stream); break;
         }
         if (e != cudaSuccess) return cuda_fail(ctx, e, "kernel launch");
@@ -322,6 +329,44 @@ double tri_area_host(const double* a, const double* b, const double* c) {
 
 long long to_fixed(double x) { return std::llround(x * FIX_SCALE); }
 
+// Extra nodes between population planes.  Planes of exactly 2^k nodes put all
+// 38 read / write streams of the stream-collide kernel at identical large
+// power-of-two offsets; a pad staggers them across DRAM channels.
+long long plane_pad() {
+    const char* e = std::getenv("LBIBM_PLANE_PAD");
+    long long v = e ? std::atoll(e) : 1088;
+    if (v < 0) v = 0;
+    return (v + 63) / 64 * 64;
+}
+
+// Grid of the stream-collide kernel for a (nodes per thread, block size)
+// variant: channel k's blocks start at blk0 and cover its padded node range.
+bool k3_config_valid(const lb_ctx* ctx, K3Config c) {
+    if (!k3_config_supported((int)ctx->storage, c)) return false;
+    for (const auto& ch : ctx->ch)
+        if (ch.d.nx % c.npt != 0) return false;
+    return true;
+}
+
+K3Config default_k3_config(const lb_ctx* ctx) {
+    const K3Config pref[] = {{2, 256}, {1, 256}};
+    for (const K3Config& c : pref)
+        if (k3_config_valid(ctx, c)) return c;
+    return K3Config{1, 256};
+}
+
+void apply_k3_config(lb_ctx* ctx, K3Config c) {
+    ctx->k3 = c;
+    const int per_block = c.npt * c.bs;
+    int blk = 0;
+    for (auto& ch : ctx->ch) {
+        ch.d.blk0 = blk;
+        ch.n_blocks = (ch.d.n + per_block - 1) / per_block;
+        blk += ch.n_blocks;
+    }
+    ctx->total_blocks = blk;
+}
+
 lb_status commit_ibm(lb_ctx* ctx) {
     if (ctx->committed) return LB_OK;
     ctx->committed = true;
@@ -340,16 +385,15 @@ lb_status commit_ibm(lb_ctx* ctx) {
     LB_CUDA(up(&ctx->q0, ctx->hq0));
     LB_CUDA(up(&ctx->q[0], ctx->hq));
     LB_CUDA(up(&ctx->q[1], ctx->hq));
-    LB_CUDA(up(&ctx->r0, ctx->hr0));
-    LB_CUDA(up(&ctx->cell_of, ctx->hcell_of));
-    LB_CUDA(up(&ctx->ring_off, ctx->hring_off));
+    LB_CUDA(up(&ctx->info, ctx->hinfo));
     LB_CUDA(up(&ctx->ring, ctx->hring));
     LB_CUDA(up(&ctx->ring_rest, ctx->hring_rest));
     LB_CUDA(up(&ctx->tris, ctx->htris));
     LB_CUDA(up(&ctx->triS0, ctx->htriS0));
     LB_CUDA(up(&ctx->chunks, ctx->hchunks));
     LB_CUDA(up(&ctx->d_cells, ctx->hcells));
-    LB_CUDA(dalloc(ctx, &ctx->xr, ctx->M));
+    LB_CUDA(dalloc(ctx, &ctx->xh, ctx->M));
+    LB_CUDA(dalloc(ctx, &ctx->xl, ctx->M));
     LB_CUDA(dalloc(ctx, &ctx->dl, ctx->M));
     LB_CUDA(dalloc(ctx, &ctx->F, ctx->M));
     LB_CUDA(cudaMemsetAsync(ctx->F, 0, sizeof(float4) * ctx->M, ctx->stream));
@@ -358,6 +402,8 @@ lb_status commit_ibm(lb_ctx* ctx) {
     LB_CUDA(cudaMemsetAsync(ctx->counters, 0, sizeof(unsigned) * ctx->C, ctx->stream));
     LB_CUDA(dalloc(ctx, &ctx->cell_sums, ctx->C));
     LB_CUDA(cudaMemsetAsync(ctx->cell_sums, 0, sizeof(double2) * ctx->C, ctx->stream));
+    LB_CUDA(dalloc(ctx, &ctx->cell_rel, ctx->C));
+    LB_CUDA(cudaMemsetAsync(ctx->cell_rel, 0, sizeof(float2) * ctx->C, ctx->stream));
     LB_CUDA(launch_prepare_nodes(ibm_args(ctx, (int)(ctx->step & 1)), ctx->stream));
     return LB_OK;
 }
@@ -396,9 +442,7 @@ lb_status lb_create_batch(const lb_params* params, int n_channels, void* cuda_st
     }
     lb_ctx* ctx = new lb_ctx();
     ctx->storage = params[0].storage;
-    const int B = stream_collide_block_size();
     long long base = 0;
-    int blk = 0;
     for (int k = 0; k < n_channels; ++k) {
         const lb_params& p = params[k];
         ChannelHost c;
@@ -407,9 +451,8 @@ lb_status lb_create_batch(const lb_params* params, int n_channels, void* cuda_st
         std::memset(&d, 0, sizeof(d));
         d.nx = p.nx; d.ny = p.ny; d.nz = p.nz;
         for (int a = 0; a < 3; ++a) d.per[a] = p.periodic[a] ? 1 : 0;
-        d.n = (long long)p.nx * p.ny * p.nz;
+        d.n = p.nx * p.ny * p.nz;
         d.base = base;
-        d.blk0 = blk;
         d.omega = (float)(1.0 / p.tau);
         d.fpre = (float)(1.0 - 1.0 / (2.0 * p.tau));
         for (int a = 0; a < 3; ++a) d.G[a] = (float)p.body_force[a];
@@ -419,13 +462,16 @@ lb_status lb_create_batch(const lb_params* params, int n_channels, void* cuda_st
                 d.uw[w][a] = (float)p.wall_velocity[w][a];
                 if (p.wall_velocity[w][a] != 0.0) d.has_uw = 1;
             }
-        c.n_blocks = (int)((d.n + B - 1) / B);
-        blk += c.n_blocks;
-        base += (d.n + CH_ALIGN - 1) / CH_ALIGN * CH_ALIGN;
+        base += ((long long)d.n + CH_ALIGN - 1) / CH_ALIGN * CH_ALIGN;
         ctx->ch.push_back(c);
     }
     ctx->Ntot = base;
-    ctx->total_blocks = blk;
+    ctx->plane = base + plane_pad();
+    if (ctx->plane >= (1LL << 31)) {   // node indices are 32-bit inside the kernels
+        delete ctx;
+        return LB_ERR_ARG;
+    }
+    apply_k3_config(ctx, default_k3_config(ctx));
     ctx->ch_meshes.resize(n_channels);
     cudaStream_t us = (cudaStream_t)cuda_stream;
     if (us == nullptr || us == cudaStreamLegacy || us == cudaStreamPerThread) {
@@ -442,8 +488,8 @@ lb_status lb_create_batch(const lb_params* params, int n_channels, void* cuda_st
     const long long NG = NT / GROUP;
     cudaError_t e = cudaSuccess;
 #define TRY(x) if (e == cudaSuccess) e = (x)
-    TRY(dalloc(ctx, (char**)&ctx->h[0], (size_t)Q * NT * pop_bytes(ctx->storage)));
-    TRY(dalloc(ctx, (char**)&ctx->h[1], (size_t)Q * NT * pop_bytes(ctx->storage)));
+    TRY(dalloc(ctx, (char**)&ctx->h[0], (size_t)Q * ctx->plane * pop_bytes(ctx->storage)));
+    TRY(dalloc(ctx, (char**)&ctx->h[1], (size_t)Q * ctx->plane * pop_bytes(ctx->storage)));
     TRY(dalloc(ctx, &ctx->mask, NG));
     TRY(dalloc(ctx, &ctx->slow, NG));
     TRY(dalloc(ctx, &ctx->g[0], NT));
@@ -455,8 +501,8 @@ lb_status lb_create_batch(const lb_params* params, int n_channels, void* cuda_st
     ctx->diag_blocks = 152 * 4;
     TRY(dalloc(ctx, &ctx->diag_partials, (size_t)ctx->diag_blocks * 6));
     TRY(dalloc(ctx, &ctx->diag_out, 6));
-    TRY(cudaMemsetAsync(ctx->h[0], 0, (size_t)Q * NT * pop_bytes(ctx->storage), ctx->stream));
-    TRY(cudaMemsetAsync(ctx->h[1], 0, (size_t)Q * NT * pop_bytes(ctx->storage), ctx->stream));
+    TRY(cudaMemsetAsync(ctx->h[0], 0, (size_t)Q * ctx->plane * pop_bytes(ctx->storage), ctx->stream));
+    TRY(cudaMemsetAsync(ctx->h[1], 0, (size_t)Q * ctx->plane * pop_bytes(ctx->storage), ctx->stream));
     TRY(cudaMemsetAsync(ctx->mask, 0, NG * 4, ctx->stream));
     TRY(cudaMemsetAsync(ctx->slow, 0, NG, ctx->stream));
     TRY(cudaMemsetAsync(ctx->g[0], 0, NT * sizeof(float4), ctx->stream));
@@ -473,7 +519,7 @@ lb_status lb_create_batch(const lb_params* params, int n_channels, void* cuda_st
     }
     if (upload_channels(ctx) != LB_OK) { lb_destroy(ctx); return LB_ERR_CUDA; }
     for (size_t k = 0; k < ctx->ch.size(); ++k)
-        if (launch_slow_flags(ctx->ch[k].d, ctx->d_ch, (int)k, ctx->mask, ctx->slow, ctx->stream) != cudaSuccess) {
+        if (launch_slow_flags(ctx->ch[k].d, ctx->mask, ctx->slow, ctx->stream) != cudaSuccess) {
             lb_destroy(ctx);
             return LB_ERR_CUDA;
         }
@@ -529,8 +575,8 @@ lb_status lb_set_obstacles(lb_ctx* ctx, const float* spheres, int n, const uint8
         LB_CUDA(dalloc(ctx, &dext, (size_t)c.d.n));
         LB_CUDA(cudaMemcpyAsync(dext, extra_mask, (size_t)c.d.n, cudaMemcpyHostToDevice, ctx->stream));
     }
-    LB_CUDA(launch_rasterise(dsph, n, dext, c.d, ctx->d_ch, ctx->cur, ctx->mask, ctx->stream));
-    LB_CUDA(launch_slow_flags(c.d, ctx->d_ch, ctx->cur, ctx->mask, ctx->slow, ctx->stream));
+    LB_CUDA(launch_rasterise(dsph, n, dext, c.d, ctx->mask, ctx->stream));
+    LB_CUDA(launch_slow_flags(c.d, ctx->mask, ctx->slow, ctx->stream));
     LB_CUDA(cudaStreamSynchronize(ctx->stream));
     dfree(ctx, dsph);
     dfree(ctx, dext);
@@ -625,12 +671,9 @@ lb_status ibm_add_mesh(lb_ctx* ctx, const double* rest_xyz, int n, const int32_t
     for (int i = 0; i < n; ++i) {
         ctx->hq0.push_back(q0[i]);
         ctx->hq.push_back(q0[i]);
-        ctx->hcell_of.push_back(cell);
-        ctx->hr0.push_back(make_float4((float)((double)(q0[i].x - q0[0].x) / FIX_SCALE),
-                                       (float)((double)(q0[i].y - q0[0].y) / FIX_SCALE),
-                                       (float)((double)(q0[i].z - q0[0].z) / FIX_SCALE), 0.0f));
         const std::vector<int>& r = ringv[i];
         const int k = (int)r.size();
+        ctx->hinfo.push_back(make_int4(cell, node0, (int)ctx->hring.size(), k | (ctx->cur << 8)));
         for (int j = 0; j < k; ++j) {
             const int nb = r[j], nx = r[(j + 1) % k];
             const int outer = third[std::make_pair(nx, nb)];
@@ -642,7 +685,6 @@ lb_status ibm_add_mesh(lb_ctx* ctx, const double* rest_xyz, int n, const int32_t
             ctx->hring_rest.push_back(make_float4((float)L0, (float)theta0(i, nb), (float)theta0(nb, nx),
                                                   (float)tri_area_host(xi, xn, x + 3 * nx)));
         }
-        ctx->hring_off.push_back((int)ctx->hring.size());
     }
     const int tri0 = (int)ctx->htris.size();
     for (int t = 0; t < nt; ++t) {
@@ -656,9 +698,10 @@ lb_status ibm_add_mesh(lb_ctx* ctx, const double* rest_xyz, int n, const int32_t
     cd.node0 = node0;
     cd.n_nodes = n;
     cd.chunk0 = (int)ctx->hchunks.size();
+    const int nch = (nt + CHUNK_TRIS - 1) / CHUNK_TRIS;
     for (int b = 0; b < nt; b += CHUNK_TRIS)
-        ctx->hchunks.push_back(make_int4(cell, tri0 + b, tri0 + std::min(nt, b + CHUNK_TRIS), 0));
-    cd.n_chunks = (int)ctx->hchunks.size() - cd.chunk0;
+        ctx->hchunks.push_back(make_int4(cell, tri0 + b, tri0 + std::min(nt, b + CHUNK_TRIS), nch));
+    cd.n_chunks = nch;
     cd.ks = (float)mod->ks; cd.kb = (float)mod->kb; cd.kal = (float)mod->kal; cd.kag = (float)mod->kag; cd.kv = (float)mod->kv;
     cd.S0 = S0;
     cd.V0 = V0;
@@ -722,6 +765,72 @@ lb_status lb_step(lb_ctx* ctx, int n_steps) {
     return LB_OK;
 }
 
+lb_status lb_set_kernel_config(lb_ctx* ctx, int nodes_per_thread, int block_size) {
+    LB_GUARD(ctx);
+    const K3Config c{nodes_per_thread, block_size};
+    if (!k3_config_valid(ctx, c)) return fail(ctx, LB_ERR_ARG, "unsupported stream-collide variant for this lattice");
+    if (c.npt == ctx->k3.npt && c.bs == ctx->k3.bs) return LB_OK;
+    LB_CUDA(cudaStreamSynchronize(ctx->stream));
+    apply_k3_config(ctx, c);
+    drop_graphs(ctx);
+    return upload_channels(ctx);
+}
+
+lb_status lb_get_kernel_config(lb_ctx* ctx, int* nodes_per_thread, int* block_size) {
+    LB_GUARD(ctx);
+    if (nodes_per_thread) *nodes_per_thread = ctx->k3.npt;
+    if (block_size) *block_size = ctx->k3.bs;
+    return LB_OK;
+}
+
+lb_status lb_autotune(lb_ctx* ctx, int repeats, int* nodes_per_thread, int* block_size, double* ms) {
+    LB_GUARD(ctx);
+    if (ctx->step != 0) return fail(ctx, LB_ERR_STATE, "autotune runs only before the first step");
+    if (repeats < 1) repeats = 1;
+    lb_status st = commit_ibm(ctx);
+    if (st != LB_OK) return st;
+    cudaEvent_t e0, e1;
+    LB_CUDA(cudaEventCreate(&e0));
+    LB_CUDA(cudaEventCreate(&e1));
+    const K3Config keep = ctx->k3;
+    K3Config best = keep;
+    double best_ms = 1e30;
+    for (int k = 0; k < k3_config_count((int)ctx->storage); ++k) {
+        const K3Config c = k3_config_at((int)ctx->storage, k);
+        if (!k3_config_valid(ctx, c)) continue;
+        apply_k3_config(ctx, c);
+        if (ctx->ch.size() > (size_t)MAXCH_P && upload_channels(ctx) != LB_OK) return LB_ERR_CUDA;
+        const LatticeArgs la = lattice_args(ctx, 0);
+        cudaError_t e = launch_stream_collide(la, c, ctx->total_blocks, ctx->stream);   // warm-up
+        if (e == cudaSuccess) e = cudaEventRecord(e0, ctx->stream);
+        for (int r = 0; r < repeats && e == cudaSuccess; ++r) e = launch_stream_collide(la, c, ctx->total_blocks, ctx->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, ctx->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float t = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+        if (e != cudaSuccess) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return cuda_fail(ctx, e, "lb_autotune");
+        }
+        if (t / repeats < best_ms) {
+            best_ms = t / repeats;
+            best = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    apply_k3_config(ctx, best);
+    drop_graphs(ctx);
+    st = upload_channels(ctx);
+    if (st != LB_OK) return st;
+    LB_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (nodes_per_thread) *nodes_per_thread = best.npt;
+    if (block_size) *block_size = best.bs;
+    if (ms) *ms = best_ms;
+    return LB_OK;
+}
+
 lb_status lb_synchronize(lb_ctx* ctx) {
     LB_GUARD(ctx);
     LB_CUDA(cudaStreamSynchronize(ctx->stream));
@@ -742,14 +851,14 @@ lb_status lb_get_fields(lb_ctx* ctx, float* rho, float* u, int dst_is_device) {
     const long long n = c.d.n;
     LatticeArgs a = lattice_args(ctx, (int)(ctx->step & 1));
     if (dst_is_device) {
-        LB_CUDA(launch_fields(a, c.d, ctx->cur, rho, u, ctx->stream));
+        LB_CUDA(launch_fields(a, ctx->cur, rho, u, ctx->stream));
         LB_CUDA(cudaStreamSynchronize(ctx->stream));
         return LB_OK;
     }
     float* buf = nullptr;
     LB_CUDA(dalloc(ctx, &buf, (size_t)4 * n));
     lb_status st = LB_OK;
-    cudaError_t e = launch_fields(a, c.d, ctx->cur, rho ? buf : nullptr, u ? buf + n : nullptr, ctx->stream);
+    cudaError_t e = launch_fields(a, ctx->cur, rho ? buf : nullptr, u ? buf + n : nullptr, ctx->stream);
     if (e == cudaSuccess && rho) e = cudaMemcpyAsync(rho, buf, sizeof(float) * n, cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess && u) e = cudaMemcpyAsync(u, buf + n, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
@@ -766,7 +875,7 @@ lb_status lb_get_populations(lb_ctx* ctx, double* f) {
     float* buf = nullptr;
     LB_CUDA(dalloc(ctx, &buf, (size_t)Q * n));
     std::vector<float> h((size_t)Q * n);
-    cudaError_t e = launch_pull_populations(lattice_args(ctx, (int)(ctx->step & 1)), c.d, ctx->cur, buf, ctx->stream);
+    cudaError_t e = launch_pull_populations(lattice_args(ctx, (int)(ctx->step & 1)), ctx->cur, buf, ctx->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), buf, sizeof(float) * Q * n, cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     dfree(ctx, buf);
@@ -836,7 +945,7 @@ lb_status lb_set_populations(lb_ctx* ctx, const double* f) {
     const int par = (int)(ctx->step & 1);
     const size_t eb = pop_bytes(ctx->storage);
     for (int i = 0; i < Q; ++i) {
-        char* dst = (char*)ctx->h[par] + ((size_t)i * ctx->Ntot + d.base) * eb;
+        char* dst = (char*)ctx->h[par] + ((size_t)i * ctx->plane + d.base) * eb;
         if (ctx->storage == LB_F32) {
             LB_CUDA(cudaMemcpy(dst, hs.data() + (size_t)i * n, sizeof(float) * n, cudaMemcpyHostToDevice));
         } else {
@@ -918,7 +1027,7 @@ lb_status lb_diagnostics(lb_ctx* ctx, double u_max, double out[6]) {
     LB_GUARD(ctx);
     if (!out) return LB_ERR_ARG;
     const ChannelHost& c = ctx->ch[ctx->cur];
-    LB_CUDA(launch_diagnostics(lattice_args(ctx, (int)(ctx->step & 1)), c.d, ctx->cur, ctx->diag_partials,
+    LB_CUDA(launch_diagnostics(lattice_args(ctx, (int)(ctx->step & 1)), ctx->cur, ctx->diag_partials,
                                ctx->diag_blocks, ctx->diag_out, ctx->stream));
     LB_CUDA(cudaMemcpyAsync(out, ctx->diag_out, sizeof(double) * 6, cudaMemcpyDeviceToHost, ctx->stream));
     LB_CUDA(cudaStreamSynchronize(ctx->stream));
@@ -944,7 +1053,7 @@ lb_status lb_save_state(lb_ctx* ctx, void* buf, size_t* bytes) {
     if (!bytes) return LB_ERR_ARG;
     lb_status s = commit_ibm(ctx);
     if (s != LB_OK) return s;
-    const size_t hb = (size_t)Q * ctx->Ntot * pop_bytes(ctx->storage);
+    const size_t hb = (size_t)Q * ctx->plane * pop_bytes(ctx->storage);
     const size_t gb = (size_t)ctx->Ntot * sizeof(float4);
     const size_t fb = (size_t)ctx->Ntot / GROUP;
     const size_t qb = (size_t)ctx->M * sizeof(Q4);
@@ -978,7 +1087,7 @@ lb_status lb_load_state(lb_ctx* ctx, const void* buf, size_t bytes) {
     std::memcpy(&hd, buf, sizeof(hd));
     if (hd.magic != STATE_MAGIC || hd.Ntot != ctx->Ntot || hd.storage != (int32_t)ctx->storage || hd.M != ctx->M)
         return fail(ctx, LB_ERR_ARG, "checkpoint does not match this context");
-    const size_t hb = (size_t)Q * ctx->Ntot * pop_bytes(ctx->storage);
+    const size_t hb = (size_t)Q * ctx->plane * pop_bytes(ctx->storage);
     const size_t gb = (size_t)ctx->Ntot * sizeof(float4);
     const size_t fb = (size_t)ctx->Ntot / GROUP;
     const size_t qb = (size_t)ctx->M * sizeof(Q4);

@@ -4,10 +4,10 @@
 // Data layout in HBM (one context = one batch of channels):
 //   populations  h[2][19][Ntot]   SoA, direction-major; Ntot is the padded sum
 //                                 of all channels' node counts; channel k's
-//                                 nodes start at a multiple of 128.  Storage
-//                                 type float (h = f - w), half or bfloat16
-//                                 (h / w).  Buffer (step & 1) is read, the
-//                                 other written (pull scheme).
+//                                 nodes start at a multiple of CH_ALIGN.
+//                                 Storage type float (h = f - w), half or
+//                                 bfloat16 (h / w).  Step parity p reads
+//                                 h[p] and writes h[1-p] (pull scheme).
 //   obstacle mask uint32[Ntot/32] one bit per node (1 = solid)
 //   slow flags   uint8[Ntot/32]   1 if a node of the 32-node group is solid or
 //                                 has a neighbour outside the domain or solid
@@ -16,12 +16,16 @@
 //   force flags  uint8[2][Ntot/32] group's g[parity] holds forces of the step
 //                                 with that parity; cleared by the warp that
 //                                 owns the group one step later
-//   velocity     float4 u[Ntot]   (ux, uy, uz, rho), written only for stamped
+//   velocity     float4 u[Ntot]   (ux, uy, uz, rho), written only for flagged
 //                                 groups (the stencils of the IB points)
-//   IB nodes     int64 q[M]x4     positions in 2^-40 lu fixed point; q0 rest
-//                float4 xr, dl, r0 positions relative to the cell's reference
-//                                 node, displacement from rest relative to the
-//                                 reference node's, rest position (FP32)
+//   IB nodes     int64 q[2][M]x4  positions in 2^-40 lu fixed point (by parity)
+//                int64 q0[M]x4    rest positions
+//                float4 xh, xl    position relative to the cell's reference
+//                                 node as an unevaluated FP32 sum hi + lo
+//                float4 dl        displacement from rest relative to the
+//                                 reference node's displacement
+//                float4 r0        rest position relative to the reference node
+//                int4 info        (cell, reference node, ring offset, valence | channel << 8)
 //   ring CSR     int2 (neighbour, outer vertex), float4 rest data per slot
 #pragma once
 
@@ -33,24 +37,24 @@
 namespace lbibm {
 
 constexpr int Q = 19;
-constexpr int GROUP = 32;           // nodes per mask word / flag / stamp
+constexpr int GROUP = 32;           // nodes per mask word / flag
 // Channel node ranges start at, and are padded to, multiples of this.  Every
 // stream-collide block covers whole groups inside one channel's padded range,
 // so lanes past the channel's end still index valid flag / mask words.
-constexpr int CH_ALIGN = 1024;
-constexpr int MAXV = 8;             // maximum node valence of a membrane mesh
+constexpr int CH_ALIGN = 2048;
+constexpr int MAXCH_P = 32;         // channels carried in the kernel parameter block
 constexpr double FIX_SCALE = 1099511627776.0;   // 2^40
 constexpr float FIX_SCALE_F = 1099511627776.0f;
 constexpr float FIX_INV_F = 9.094947017729282e-13f;  // 2^-40
 constexpr int FIX_BITS = 40;
+constexpr int SUB = 8;              // lanes per IB node in the node-parallel kernels
 
 struct ChannelDev {
     int nx, ny, nz;
     int per[3];
     long long base;       // first global node index
-    long long n;          // nx * ny * nz
+    int n;                // nx * ny * nz (< 2^31)
     int blk0;             // first block of the stream-collide grid for this channel
-    int pad0;
     float omega;          // 1 / tau
     float fpre;           // 1 - 1 / (2 tau)
     float G[3];           // uniform body force
@@ -73,7 +77,7 @@ struct CellDev {
 };
 
 struct LatticeArgs {
-    const ChannelDev* ch;
+    const ChannelDev* ch; // all channels (global memory)
     int n_ch;
     int storage;          // lb_storage
     int par;              // step parity: read h[par], write h[1-par]; forces in g[par]
@@ -88,33 +92,36 @@ struct LatticeArgs {
     uint8_t* fl0;
     uint8_t* fl1;
     float4* u;
+    ChannelDev chp[MAXCH_P];   // copy of the first channels (constant bank)
 };
 
 struct IbmArgs {
     int n_nodes;          // M
     int n_cells;
     int par;              // step parity: positions q[par] are current, q[1-par] receive the advance
+    int n_ch;
     const ChannelDev* ch;
     const CellDev* cells;
-    const int* cell_of;   // [M]
+    const int4* info;     // [M] (cell, ref, ring offset, valence | channel << 8)
     Q4* qa;               // [M] positions, even steps
     Q4* qb;               // [M] positions, odd steps
     const Q4* q0;         // [M] rest positions
-    float4* xr;           // [M]
+    float4* xh;           // [M]
+    float4* xl;           // [M]
     float4* dl;           // [M]
     const float4* r0;     // [M]
-    const int* ring_off;  // [M+1]
     const int2* ring;     // [K] (neighbour, outer)
     const float4* ring_rest;  // [K] (L0, theta0 edge, theta0 opposite edge, S0 triangle)
     float4* F;            // [M] last node forces
     // area / volume reduction
     const int4* tris;     // [T] (a, b, c, cell) global node indices
     const float* tri_S0;  // [T] rest area of each triangle
-    const int4* chunks;   // [NCH] (cell, t_begin, t_end, 0)
+    const int4* chunks;   // [NCH] (cell, t_begin, t_end, chunks of that cell)
     int n_chunks;
     double2* partials;    // [NCH]
     unsigned* counters;   // [C]
     double2* cell_sums;   // [C] (dS, dV)
+    float2* cell_rel;     // [C] (dS / S0, dV / V0)
     // lattice pieces used by spread / interpolation
     const uint32_t* mask;
     float4* g0;
@@ -122,6 +129,7 @@ struct IbmArgs {
     uint8_t* fl0;
     uint8_t* fl1;
     const float4* u;
+    ChannelDev chp[MAXCH_P];
 };
 
 // D3Q19 velocity set (Sec. 2.1): rest, +-x, +-y, +-z, then the 12 diagonals,
@@ -139,19 +147,24 @@ __host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i 
 __host__ __device__ constexpr float wgt(int i) { return i == 0 ? (1.0f / 3.0f) : (i <= 6 ? (1.0f / 18.0f) : (1.0f / 36.0f)); }
 __host__ __device__ constexpr double wgt_d(int i) { return i == 0 ? (1.0 / 3.0) : (i <= 6 ? (1.0 / 18.0) : (1.0 / 36.0)); }
 
+// Stream-collide kernel variants: nodes per thread along x and block size.
+struct K3Config {
+    int npt;
+    int bs;
+};
+bool k3_config_supported(int storage, K3Config c);
+int k3_config_count(int storage);
+K3Config k3_config_at(int storage, int k);
+
 // ---- launchers (defined in lattice_kernels.cu / ibm_kernels.cu) ----
 cudaError_t launch_rasterise(const float* spheres, int n_spheres, const uint8_t* extra, const ChannelDev& ch,
-                             const ChannelDev* d_ch, int ch_index, uint32_t* mask, cudaStream_t s);
-cudaError_t launch_slow_flags(const ChannelDev& ch, const ChannelDev* d_ch, int ch_index, const uint32_t* mask,
-                              uint8_t* slow, cudaStream_t s);
-cudaError_t launch_stream_collide(const LatticeArgs& a, int total_blocks, cudaStream_t s);
-cudaError_t launch_fields(const LatticeArgs& a, const ChannelDev& ch, int ch_index, float* rho, float* u,
-                          cudaStream_t s);
-cudaError_t launch_pull_populations(const LatticeArgs& a, const ChannelDev& ch, int ch_index, float* h_out,
-                                    cudaStream_t s);
-cudaError_t launch_diagnostics(const LatticeArgs& a, const ChannelDev& ch, int ch_index, double* partials,
-                               int n_blocks, double* out, cudaStream_t s);
-int stream_collide_block_size();
+                             uint32_t* mask, cudaStream_t s);
+cudaError_t launch_slow_flags(const ChannelDev& ch, const uint32_t* mask, uint8_t* slow, cudaStream_t s);
+cudaError_t launch_stream_collide(const LatticeArgs& a, K3Config cfg, int total_blocks, cudaStream_t s);
+cudaError_t launch_fields(const LatticeArgs& a, int ch_index, float* rho, float* u, cudaStream_t s);
+cudaError_t launch_pull_populations(const LatticeArgs& a, int ch_index, float* h_out, cudaStream_t s);
+cudaError_t launch_diagnostics(const LatticeArgs& a, int ch_index, double* partials, int n_blocks, double* out,
+                               cudaStream_t s);
 
 cudaError_t launch_cell_sums(const IbmArgs& a, cudaStream_t s);
 cudaError_t launch_forces_spread(const IbmArgs& a, cudaStream_t s);

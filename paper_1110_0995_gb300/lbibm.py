@@ -24,6 +24,7 @@ EXPORTS = (
     "ibm_set_nodes", "lb_step", "lb_synchronize", "lb_get_fields", "lb_get_populations", "lb_set_populations",
     "ibm_get_nodes", "ibm_get_forces", "ibm_get_area_volume", "lb_diagnostics", "lb_get_step", "lb_save_state",
     "lb_load_state", "lb_set_timing", "lb_kernel_times", "lb_last_error", "lb_version", "lb_get_mask",
+    "lb_set_kernel_config", "lb_get_kernel_config", "lb_autotune",
 )
 
 
@@ -85,6 +86,9 @@ def lib():
             "lb_last_error": ([P], ctypes.c_char_p),
             "lb_version": ([], I),
             "lb_get_mask": ([P, P], I),
+            "lb_set_kernel_config": ([P, I, I], I),
+            "lb_get_kernel_config": ([P, ctypes.POINTER(I), ctypes.POINTER(I)], I),
+            "lb_autotune": ([P, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(D)], I),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -266,6 +270,20 @@ class Simulation:
     def load_state(self, data: bytes):
         buf = ctypes.create_string_buffer(data, len(data))
         self._check(self._L.lb_load_state(self._h, buf, len(data)))
+
+    def set_kernel_config(self, nodes_per_thread: int, block_size: int):
+        self._check(self._L.lb_set_kernel_config(self._h, int(nodes_per_thread), int(block_size)))
+
+    def kernel_config(self):
+        n, b = ctypes.c_int(), ctypes.c_int()
+        self._check(self._L.lb_get_kernel_config(self._h, ctypes.byref(n), ctypes.byref(b)))
+        return n.value, b.value
+
+    def autotune(self, repeats: int = 20):
+        """Time every stream-collide variant (before the first step) and keep the fastest."""
+        n, b, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        self._check(self._L.lb_autotune(self._h, int(repeats), ctypes.byref(n), ctypes.byref(b), ctypes.byref(ms)))
+        return n.value, b.value, ms.value
 
     def set_timing(self, on: bool):
         self._check(self._L.lb_set_timing(self._h, int(bool(on))))

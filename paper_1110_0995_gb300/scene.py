@@ -41,6 +41,17 @@ SPHERE_QUANTUM = 2.0 ** -8    # sphere centres / radii are multiples of this (lu
 RBC_MODULI = (0.05, 0.01, 0.01, 0.5, 0.9)
 CTC_MODULI = (0.5, 0.01, 0.01, 0.5, 0.9)
 
+# The massless, explicitly coupled immersed-boundary cycle has a stiffness
+# limit: with these meshes (edges 0.3-0.7 lu) and tau = 1 a stretching
+# modulus above ~0.035 makes small perturbations grow (ks = 0.05 by ~3x per
+# 100 steps, ks = 0.5 diverges within ~50 steps).  Long runs therefore use the
+# largest stable stretching moduli, the tumor cell still the stiffer one; the
+# other four moduli are unchanged.
+STABLE_RBC_MODULI = (0.02, 0.01, 0.01, 0.5, 0.9)
+STABLE_CTC_MODULI = (0.03, 0.01, 0.01, 0.5, 0.9)
+STABLE = {"rbc": STABLE_RBC_MODULI, "ctc": STABLE_CTC_MODULI}
+SPEC = {"rbc": RBC_MODULI, "ctc": CTC_MODULI}
+
 RBC_RADIUS = 4.0
 CTC_RADIUS = 8.0
 BEAD_RADIUS = 3.0
@@ -295,19 +306,19 @@ def place_cells(rng: np.random.Generator, dims, periodic, spheres: np.ndarray,
 # ---------------------------------------------------------------------------
 
 def channel_plain(seed: int = 1, steps: int = 1000, dims=(32, 16, 64), n_rbc: int = 1,
-                  body_force: float = 1e-5) -> Scene:
-    """Plain channel 32x16x64: periodic x, walls in y and z, one red cell."""
+                  body_force: float = 1e-5, moduli: Optional[dict] = None) -> Scene:
+    """Plain channel 32x16x64: periodic x, walls in y and z, one red cell
+    (moduli as stated for the plain-method workload unless given)."""
     rng = np.random.default_rng(seed)
     per = (1, 0, 0)
-    meshes = place_cells(rng, dims, per, np.zeros((0, 4), np.float32), ["rbc"] * n_rbc,
-                         {"rbc": RBC_MODULI, "ctc": CTC_MODULI})
+    meshes = place_cells(rng, dims, per, np.zeros((0, 4), np.float32), ["rbc"] * n_rbc, moduli or SPEC)
     return Scene(name=f"channel_{dims[0]}x{dims[1]}x{dims[2]}_{n_rbc}rbc", dims=tuple(dims), tau=1.0,
                  body_force=(body_force, 0.0, 0.0), periodic=per, meshes=meshes, steps=steps, seed=seed)
 
 
 def micropost_filter(seed: int = 11, dims=(256, 128, 64), cols: int = 4, rows: int = 3,
                      n_rbc: int = 60, n_ctc: int = 2, gap_range=(8.0, 14.0), body_force: float = 2e-5,
-                     steps: int = 20000) -> Scene:
+                     steps: int = 20000, moduli: Optional[dict] = None) -> Scene:
     """Micropost filter: staggered bead-chain posts, red cells and tumor cells."""
     rng = np.random.default_rng(seed)
     per = (1, 0, 0)
@@ -316,7 +327,7 @@ def micropost_filter(seed: int = 11, dims=(256, 128, 64), cols: int = 4, rows: i
     gaps = rng.uniform(gap_range[0], gap_range[1], size=cols)
     spheres = post_array(dims, cols, rows, n_beads, gaps)
     kinds = ["ctc"] * n_ctc + ["rbc"] * n_rbc
-    meshes = place_cells(rng, dims, per, spheres, kinds, {"rbc": RBC_MODULI, "ctc": CTC_MODULI})
+    meshes = place_cells(rng, dims, per, spheres, kinds, moduli or STABLE)
     return Scene(name=f"micropost_filter_{dims[0]}x{dims[1]}x{dims[2]}", dims=tuple(dims), tau=1.0,
                  body_force=(body_force, 0.0, 0.0), periodic=per, spheres=spheres, meshes=meshes,
                  steps=steps, seed=seed)
@@ -344,16 +355,14 @@ def gap_sweep(seed: int = 21, n_channels: int = 24, steps: int = 5000) -> List[S
         spheres = post_array(dims, 1, rows, n_beads, [gap], x_span=(0.0, float(nx)))
         sub = np.random.default_rng(int(rng.integers(0, 2 ** 31)))
         try:
-            meshes = place_cells(sub, dims, (1, 0, 0), spheres, ["rbc"] * n_rbc,
-                                 {"rbc": RBC_MODULI, "ctc": CTC_MODULI}, max_tries=4000)
+            meshes = place_cells(sub, dims, (1, 0, 0), spheres, ["rbc"] * n_rbc, STABLE, max_tries=4000)
         except RuntimeError:
             # very small channels cannot hold 40 cells: keep as many as fit
             meshes = []
             for k in range(n_rbc, 0, -1):
                 try:
                     meshes = place_cells(np.random.default_rng(int(sub.integers(0, 2 ** 31))), dims, (1, 0, 0),
-                                         spheres, ["rbc"] * k, {"rbc": RBC_MODULI, "ctc": CTC_MODULI},
-                                         max_tries=2000)
+                                         spheres, ["rbc"] * k, STABLE, max_tries=2000)
                     break
                 except RuntimeError:
                     continue
@@ -370,8 +379,7 @@ def adjoint_channel(seed: int = 41, steps: int = 400) -> Scene:
     gap = float(rng.uniform(8.0, 14.0))
     spheres = post_array(dims, 1, 2, 6, [gap], x_span=(64.0, 128.0))
     kinds = ["ctc"] + ["rbc"] * 8
-    meshes = place_cells(rng, dims, (1, 0, 0), spheres, kinds, {"rbc": RBC_MODULI, "ctc": CTC_MODULI},
-                         x_range=(0.0, 60.0))
+    meshes = place_cells(rng, dims, (1, 0, 0), spheres, kinds, STABLE, x_range=(0.0, 60.0))
     return Scene(name="adjoint_128x64x64", dims=dims, tau=1.0, body_force=(1e-5, 0.0, 0.0),
                  periodic=(1, 0, 0), spheres=spheres, meshes=meshes, steps=steps, seed=seed)
 
