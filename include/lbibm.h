@@ -169,6 +169,32 @@ lb_status ibm_get_forces(lb_ctx* ctx, int mesh_id, double* f);
  * for every mesh of the selected channel, in mesh order (host). */
 lb_status ibm_get_area_volume(lb_ctx* ctx, double* area, double* volume);
 
+/* Surface area and enclosed volume of closed triangle meshes, allocating no
+ * device memory.  The paper has no counterpart to this entry point: it serves
+ * callers that cannot allocate device memory (code under a framework that
+ * owns the whole device memory pool, latency-critical loops that cannot
+ * afford cudaMalloc's implicit synchronisation, embedded callers with a fixed
+ * memory budget).  It computes what ibm_get_area_volume reports, from caller
+ * buffers instead of a context:
+ *   xyz             device, n_nodes x 3 doubles (node positions)
+ *   tris            device, n_tris x 3 int32 node indices, outward counter-clockwise
+ *   cell_tri_start  device, n_cells + 1 int32: cell c owns triangles
+ *                   [cell_tri_start[c], cell_tri_start[c+1])
+ *   cell_tri_start_host  the same offsets in host memory (sizes the grid)
+ *   area, volume    device, n_cells doubles each (outputs)
+ * FP64 throughout; queued on cuda_stream (NULL = legacy default stream),
+ * asynchronous.  Scratch is a fixed 1 MiB device array (65,536 partial sums
+ * of 256 triangles each) that every GPU loading the library holds until the
+ * process exits: LB_ERR_ARG when n_cells times the largest number of
+ * 256-triangle chunks of one cell exceeds 65,536, or n_cells > 65,535.  The
+ * first call on a device looks the array's address up (cudaGetSymbolAddress);
+ * make that first call before any stream capture.  Every call shares the
+ * array, so calls that overlap on the GPU race.  Calls no cudaMalloc or
+ * cudaFree. */
+lb_status ibm_area_volume_noalloc(const double* xyz, const int32_t* tris, const int32_t* cell_tri_start,
+                                  const int32_t* cell_tri_start_host, int n_cells, double* area, double* volume,
+                                  void* cuda_stream);
+
 /* Conservation diagnostics of the selected channel, FP64 on the device:
  * out[0] = sum of rho over fluid nodes, out[1..3] = sum of sum_i e_i f_i
  * after the last collision, out[4] = number of non-finite populations,

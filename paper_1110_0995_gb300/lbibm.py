@@ -24,7 +24,7 @@ EXPORTS = (
     "ibm_set_nodes", "lb_step", "lb_synchronize", "lb_get_fields", "lb_get_populations", "lb_set_populations",
     "ibm_get_nodes", "ibm_get_forces", "ibm_get_area_volume", "lb_diagnostics", "lb_get_step", "lb_save_state",
     "lb_load_state", "lb_set_timing", "lb_kernel_times", "lb_last_error", "lb_version", "lb_get_mask",
-    "lb_set_kernel_config", "lb_get_kernel_config", "lb_autotune",
+    "lb_set_kernel_config", "lb_get_kernel_config", "lb_autotune", "ibm_area_volume_noalloc",
 )
 
 
@@ -89,6 +89,7 @@ def lib():
             "lb_set_kernel_config": ([P, I, I], I),
             "lb_get_kernel_config": ([P, ctypes.POINTER(I), ctypes.POINTER(I)], I),
             "lb_autotune": ([P, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(D)], I),
+            "ibm_area_volume_noalloc": ([P, P, P, P, I, P, P, P], I),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
