@@ -126,11 +126,14 @@ lb_status ibm_set_nodes(lb_ctx* ctx, int mesh_id, const double* xyz);
  * context's stream; launched as a CUDA graph after the first call. */
 lb_status lb_step(lb_ctx* ctx, int n_steps);
 
-/* Variant of the fused stream-collide kernel: consecutive x-nodes per thread
- * (1, 2 or 4 for every storage) and threads
- * per block (128 or 256).  Every channel's nx must be a multiple of the nodes
- * per thread.  LB_ERR_ARG for an unsupported pair.  Results do not depend on
- * the variant. */
+/* Variant of the fused stream-collide kernel.  nodes_per_thread 1, 2 or 4:
+ * consecutive x-nodes per thread (every channel's nx a multiple of it), with
+ * block_size 128 or 256.  nodes_per_thread 0: staged variant (rows copied to
+ * shared memory asynchronously; block_size 256; every channel's row of nx
+ * populations a multiple of 16 bytes and nx <= 512).  nodes_per_thread -1:
+ * pipelined variant (persistent warps, block_size 128 or 256).  The default
+ * is 1 node per thread, 128 threads.  LB_ERR_ARG for an unsupported pair.
+ * Results do not depend on the variant. */
 lb_status lb_set_kernel_config(lb_ctx* ctx, int nodes_per_thread, int block_size);
 lb_status lb_get_kernel_config(lb_ctx* ctx, int* nodes_per_thread, int* block_size);
 

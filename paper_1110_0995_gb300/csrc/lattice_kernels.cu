@@ -18,6 +18,8 @@
 // touch an obstacle or a wall take a per-node path with bounce-back instead.
 #include "lbibm_internal.cuh"
 
+#include <cuda_pipeline.h>
+
 #include <type_traits>
 
 namespace lbibm {
@@ -136,10 +138,10 @@ __device__ __forceinline__ int src_off_yz(const Nbr& nb) {
 // Pull one population with bounce-back where the source is a wall or solid.
 template <class S, int I>
 __device__ __forceinline__ float pull_slow(const S* src, long long NT, long long gp, const Nbr& nb,
-                                           const uint32_t* mask, const ChannelDev& C, int y) {
+                                           const uint32_t* mask, const ChannelDev& C, int y, bool check_solid) {
     bool ok;
     const int o = src_off<I>(nb, ok);
-    if (ok) ok = !solid_at(mask, gp + o);
+    if (ok && check_solid) ok = !solid_at(mask, gp + o);
     if (ok) return Pop<S>::ld(src, (long long)I * NT + gp + o, I);
     float h = Pop<S>::ld(src, (long long)opp(I) * NT + gp, opp(I));
     if (C.has_uw && !C.per[1]) {
@@ -158,8 +160,9 @@ __device__ __forceinline__ float pull_slow(const S* src, long long NT, long long
 
 template <class S>
 __device__ __forceinline__ void pull_node(const S* src, long long NT, long long gp, const Nbr& nb,
-                                          const uint32_t* mask, const ChannelDev& C, int y, float h[Q]) {
-#define LBIBM_PS(I) h[I] = pull_slow<S, I>(src, NT, gp, nb, mask, C, y);
+                                          const uint32_t* mask, const ChannelDev& C, int y, float h[Q],
+                                          bool check_solid = true) {
+#define LBIBM_PS(I) h[I] = pull_slow<S, I>(src, NT, gp, nb, mask, C, y, check_solid);
     LBIBM_ALL_I(LBIBM_PS)
 #undef LBIBM_PS
 }
@@ -267,24 +270,68 @@ __device__ __forceinline__ float collide_one(float hi, const Mac& m, float omega
     return hi + omega * (heq - hi) + s;
 }
 
+// The same collision for the pair of opposite directions (I, I+1), I odd:
+// e_{I+1} = -e_I, so the equilibrium and the source split into a part even in
+// e (shared) and a part odd in e (sign flipped), which halves the arithmetic.
+template <int I>
+__device__ __forceinline__ void collide_pair(float h[Q], const Mac& m, float A1, float om, float fp) {
+    constexpr int J = I + 1;
+    const float w = wgt(I);
+    const float eu = ex(I) * m.ux + ey(I) * m.uy + ez(I) * m.uz;
+    const float eg = ex(I) * m.gx + ey(I) * m.gy + ez(I) * m.gz;
+    const float seq = w * (A1 + 4.5f * m.rho * eu * eu);
+    const float aeq = (3.0f * w) * m.rho * eu;
+    const float ss = (fp * w) * (9.0f * eu * eg - 3.0f * m.ug);
+    const float as = (3.0f * fp * w) * eg;
+    const float hi = h[I], hj = h[J];
+    h[I] = hi + om * ((seq + aeq) - hi) + (ss + as);
+    h[J] = hj + om * ((seq - aeq) - hj) + (ss - as);
+}
+
+// Collide all 19 populations of one node in place (h -> h*).
+__device__ __forceinline__ void collide_all(float h[Q], const Mac& m, float om, float fp) {
+    const float A1 = m.drho - 1.5f * m.rho * m.uu;
+    h[0] = h[0] + om * (wgt(0) * A1 - h[0]) + (fp * wgt(0)) * (-3.0f * m.ug);
+    collide_pair<1>(h, m, A1, om, fp);
+    collide_pair<3>(h, m, A1, om, fp);
+    collide_pair<5>(h, m, A1, om, fp);
+    collide_pair<7>(h, m, A1, om, fp);
+    collide_pair<9>(h, m, A1, om, fp);
+    collide_pair<11>(h, m, A1, om, fp);
+    collide_pair<13>(h, m, A1, om, fp);
+    collide_pair<15>(h, m, A1, om, fp);
+    collide_pair<17>(h, m, A1, om, fp);
+}
+
 template <class S, int NPT, int I>
-__device__ __forceinline__ void collide_store_vec(S* dst, long long NT, int gi0, const float h[NPT][Q],
-                                                  const Mac m[NPT], float om, float fp) {
+__device__ __forceinline__ void store_vec(S* dst, long long NT, int gi0, const float h[NPT][Q]) {
     float o[NPT];
 #pragma unroll
-    for (int k = 0; k < NPT; ++k) o[k] = collide_one<I>(h[k][I], m[k], om, fp);
+    for (int k = 0; k < NPT; ++k) o[k] = h[k][I];
     VecIO<S, NPT>::st(dst + (size_t)I * (size_t)NT, gi0, I, o);
 }
 
-// Resident blocks per SM the register budget is sized for (about 85 registers
-// per thread with one node per thread, 128 with two, 255 with four).
-template <int NPT, int BS> struct K3MinBlocks {
-    static constexpr int value = (NPT == 1 ? 768 : (NPT == 2 ? 512 : 256)) / BS > 0
-                                     ? (NPT == 1 ? 768 : (NPT == 2 ? 512 : 256)) / BS : 1;
+// Resident threads per SM the register budget is sized for.  One node per
+// thread: 1280 threads (48 registers) for FP32 populations, 1024 (64 registers)
+// for 16-bit ones, the fastest of the budgets measured on GB300; two nodes per
+// thread: 768 (80 registers); four: 256 (255 registers).
+#ifndef LBIBM_K3_THREADS1
+#define LBIBM_K3_THREADS1 1280
+#endif
+#ifndef LBIBM_K3_THREADS1_16
+#define LBIBM_K3_THREADS1_16 1024
+#endif
+#ifndef LBIBM_K3_THREADS2
+#define LBIBM_K3_THREADS2 768
+#endif
+template <class S, int NPT, int BS> struct K3MinBlocks {
+    static constexpr int threads = NPT == 1 ? (sizeof(S) == 4 ? LBIBM_K3_THREADS1 : LBIBM_K3_THREADS1_16)
+                                            : (NPT == 2 ? LBIBM_K3_THREADS2 : 256);
+    static constexpr int value = threads / BS > 0 ? threads / BS : 1;
 };
 
 template <class S, int NPT, int BS>
-__global__ void __launch_bounds__(BS, K3MinBlocks<NPT, BS>::value) k_stream_collide(const __grid_constant__ LatticeArgs a) {
+__global__ void __launch_bounds__(BS, K3MinBlocks<S, NPT, BS>::value) k_stream_collide(const __grid_constant__ LatticeArgs a) {
     const int b = blockIdx.x;
     int c = 0;
     for (int k = 1; k < a.n_ch; ++k)
@@ -305,10 +352,10 @@ __global__ void __launch_bounds__(BS, K3MinBlocks<NPT, BS>::value) k_stream_coll
     const S* src = (const S*)(par ? a.h1 : a.h0);
     S* dst = (S*)(par ? a.h0 : a.h1);
     const long long NT = a.Ntot;
-    const int x0 = p0 % C.nx;
-    const int r = p0 / C.nx;
-    const int y = r % C.ny;
-    const int z = r / C.ny;
+    const int r = fdiv(p0, C.dnx);
+    const int x0 = p0 - r * C.nx;
+    const int z = fdiv(r, C.dny);
+    const int y = r - z * C.ny;
     Nbr nb;
     neighbours(C, x0, y, z, nb);
     // phase 1: every population load of the vector path in flight at once
@@ -340,9 +387,11 @@ __global__ void __launch_bounds__(BS, K3MinBlocks<NPT, BS>::value) k_stream_coll
                 }
                 m[k] = macro(h[k], gx, gy, gz);
             }
-#define LBIBM_CV(I) collide_store_vec<S, NPT, I>(dst, NT, gi0, h, m, om, fp);
-            LBIBM_ALL_I(LBIBM_CV)
-#undef LBIBM_CV
+#pragma unroll
+            for (int k = 0; k < NPT; ++k) collide_all(h[k], m[k], om, fp);
+#define LBIBM_SV(I) store_vec<S, NPT, I>(dst, NT, gi0, h);
+            LBIBM_ALL_I(LBIBM_SV)
+#undef LBIBM_SV
 #pragma unroll
             for (int k = 0; k < NPT; ++k) {
                 if (forced) a.u[gi0 + k] = make_float4(m[k].ux, m[k].uy, m[k].uz, m[k].rho);
@@ -351,21 +400,23 @@ __global__ void __launch_bounds__(BS, K3MinBlocks<NPT, BS>::value) k_stream_coll
         }
     } else if (inr) {
         // per-node path with bounce-back at walls and obstacles
+        const bool obst = (fslow & 2) != 0;   // an obstacle node in or next to this group
 #pragma unroll 1
         for (int k = 0; k < NPT; ++k) {
             const long long gp = gp0 + k;
-            if (solid_at(a.mask, gp)) continue;
+            if (obst && solid_at(a.mask, gp)) continue;
             Nbr nk = nb;
             if (k > 0) neighbours(C, x0 + k, y, z, nk);
             float h[Q];
-            pull_node<S>(src, NT, gp, nk, a.mask, C, y, h);
+            pull_node<S>(src, NT, gp, nk, a.mask, C, y, h, obst);
             float gx = C.G[0], gy = C.G[1], gz = C.G[2];
             if (forced) {
                 const float4 g = gcur[gp];
                 gx += g.x; gy += g.y; gz += g.z;
             }
             const Mac m = macro(h, gx, gy, gz);
-#define LBIBM_C1(I) Pop<S>::st(dst, (long long)(I) * NT + gp, collide_one<I>(h[I], m, om, fp), I);
+            collide_all(h, m, om, fp);
+#define LBIBM_C1(I) Pop<S>::st(dst, (long long)(I) * NT + gp, h[I], I);
             LBIBM_ALL_I(LBIBM_C1)
 #undef LBIBM_C1
             if (forced) a.u[gp] = make_float4(m.ux, m.uy, m.uz, m.rho);
@@ -378,11 +429,286 @@ __global__ void __launch_bounds__(BS, K3MinBlocks<NPT, BS>::value) k_stream_coll
     if (prevf && (gp0 & 31) == 0) fl_prev[grp] = 0;
 }
 
-// Supported (nodes per thread, block size) pairs per storage type.
-static const K3Config CFG_F32[] = {{1, 256}, {2, 256}, {4, 256}, {4, 128}, {2, 128}, {1, 128}};
-static const K3Config CFG_16[] = {{2, 256}, {4, 256}, {4, 128}, {2, 128}, {1, 256}, {1, 128}};
+// ---------------------------------------------------------------------------
+// Staged variant: a persistent block walks over groups of whole lattice rows
+// (SG_NODES nodes) of one channel.  For each group it copies, for every
+// direction i, the source rows (y - ey_i, z - ez_i) of plane i into shared
+// memory with asynchronous 16-byte copies, double-buffered so that the copies
+// of the next group are in flight while the current one is computed: the
+// bytes in flight are bounded by shared memory, not by registers.  The +-x
+// shift is an index into the staged row.  Nodes of groups that touch a wall
+// or an obstacle take the per-node path with bounce-back from global memory.
+// ---------------------------------------------------------------------------
+constexpr int SG_THREADS = 256;
 
-int k3_config_count(int storage) { return 6; }
+template <class S>
+__device__ __forceinline__ int staged_channel(const LatticeArgs& a, int g) {
+    int c = 0;
+    for (int k = 1; k < a.n_ch; ++k)
+        if (g >= chan(a, k).sg0) c = k;
+    return c;
+}
+
+template <class S>
+__device__ __forceinline__ void staged_issue(const LatticeArgs& a, const S* src, int g, S* B) {
+    const ChannelDev& C = chan(a, staged_channel<S>(a, g));
+    const int R = C.srows;
+    const int r0 = (g - C.sg0) * R;
+    const int rows = min(R, C.ny * C.nz - r0);
+    const int cpr = C.nx * (int)sizeof(S) / 16;   // 16-byte chunks per row
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int ij = warp; ij < Q * rows; ij += SG_THREADS / 32) {
+        const int i = ij / rows, j = ij - i * rows;
+        const int r = r0 + j;
+        const int z = fdiv(r, C.dny), y = r - z * C.ny;
+        int ys = y - ey(i), zs = z - ez(i);
+        bool ok = true;
+        if (ys < 0 || ys >= C.ny) {
+            if (C.per[1]) ys = (ys + C.ny) % C.ny;
+            else ok = false;
+        }
+        if (zs < 0 || zs >= C.nz) {
+            if (C.per[2]) zs = (zs + C.nz) % C.nz;
+            else ok = false;
+        }
+        if (!ok) continue;   // only wall-adjacent rows pull from here; they take the per-node path
+        const char* g0 = (const char*)(src + (size_t)i * (size_t)a.Ntot + C.base + (long long)(ys + C.ny * zs) * C.nx);
+        char* s0 = (char*)(B + i * SG_NODES + j * C.nx);
+        for (int k = lane; k < cpr; k += 32) __pipeline_memcpy_async(s0 + 16 * k, g0 + 16 * k, 16);
+    }
+}
+
+template <class S>
+__device__ __forceinline__ float sm_pop(const S* B, int idx, int i) {
+    if constexpr (sizeof(S) == 4) return B[idx];
+    else return wgt(i) * to_f(B[idx]);
+}
+
+template <class S>
+__device__ __forceinline__ void staged_compute(const LatticeArgs& a, const S* src, S* dst, int g, const S* B) {
+    const ChannelDev C = chan(a, staged_channel<S>(a, g));
+    const int R = C.srows;
+    const int r0 = (g - C.sg0) * R;
+    const int rows = min(R, C.ny * C.nz - r0);
+    const int nn = rows * C.nx;
+    const int par = a.par;
+    uint8_t* fl_prev = par ? a.fl0 : a.fl1;
+    const uint8_t* fl_cur = par ? a.fl1 : a.fl0;
+    const float4* gcur = par ? a.g1 : a.g0;
+    float4* gprev = par ? a.g0 : a.g1;
+    const float om = C.omega, fp = C.fpre;
+    const long long NT = a.Ntot;
+#pragma unroll 1
+    for (int half = 0; half < SG_NODES / SG_THREADS; ++half) {
+        const int n = threadIdx.x + half * SG_THREADS;
+        const bool inr = n < nn;
+        const int p = r0 * C.nx + n;
+        const long long gp = C.base + p;
+        const int grp = (int)(gp >> 5);
+        bool prevf = false;
+        if (inr) {
+            const bool forced = fl_cur[grp] != 0;
+            prevf = fl_prev[grp] != 0;
+            const bool slow = __ldg(a.slow + grp) != 0;
+            const int j = fdiv(n, C.dnx), x = n - j * C.nx;
+            bool active = true;
+            float h[Q];
+            if (!slow) {
+#define LBIBM_SM(I)                                 \
+    {                                               \
+        int xs = x - ex(I);                         \
+        xs += xs < 0 ? C.nx : 0;                    \
+        xs -= xs >= C.nx ? C.nx : 0;                \
+        h[I] = sm_pop<S>(B, I * SG_NODES + j * C.nx + xs, I); \
+    }
+                LBIBM_ALL_I(LBIBM_SM)
+#undef LBIBM_SM
+            } else if (!solid_at(a.mask, gp)) {
+                const int z = fdiv(r0 + j, C.dny), y = (r0 + j) - z * C.ny;
+                Nbr nb;
+                neighbours(C, x, y, z, nb);
+                pull_node<S>(src, NT, gp, nb, a.mask, C, y, h);
+            } else {
+                active = false;
+            }
+            if (active) {
+                float gx = C.G[0], gy = C.G[1], gz = C.G[2];
+                if (forced) {
+                    const float4 gg = gcur[gp];
+                    gx += gg.x; gy += gg.y; gz += gg.z;
+                }
+                const Mac m = macro(h, gx, gy, gz);
+                collide_all(h, m, om, fp);
+#define LBIBM_C1(I) Pop<S>::st(dst, (long long)(I) * NT + gp, h[I], I);
+                LBIBM_ALL_I(LBIBM_C1)
+#undef LBIBM_C1
+                if (forced) a.u[gp] = make_float4(m.ux, m.uy, m.uz, m.rho);
+                if (prevf) gprev[gp] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+        // the warp holding a 32-node group clears its previous-step flag after use
+        __syncwarp();
+        if (inr && prevf && (gp & 31) == 0) fl_prev[grp] = 0;
+    }
+}
+
+template <class S>
+__global__ void __launch_bounds__(SG_THREADS, 2) k_stream_collide_staged(const __grid_constant__ LatticeArgs a) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    S* B0 = reinterpret_cast<S*>(sm);
+    S* B1 = B0 + Q * SG_NODES;
+    const S* src = (const S*)(a.par ? a.h1 : a.h0);
+    S* dst = (S*)(a.par ? a.h0 : a.h1);
+    int g = blockIdx.x;
+    if (g >= a.n_groups) return;
+    staged_issue<S>(a, src, g, B0);
+    __pipeline_commit();
+    int cur = 0;
+    for (; g < a.n_groups; g += gridDim.x) {
+        const int gn = g + gridDim.x;
+        if (gn < a.n_groups) staged_issue<S>(a, src, gn, cur ? B0 : B1);
+        __pipeline_commit();
+        __pipeline_wait_prior(1);   // the current group's copies have landed
+        __syncthreads();
+        staged_compute<S>(a, src, dst, g, cur ? B1 : B0);
+        __syncthreads();            // every thread is done with this buffer before it is refilled
+        cur ^= 1;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Pipelined variant: a persistent grid of warps walks over 32-node groups
+// (one node per lane).  Each warp issues the 19 loads of its next group before
+// it computes the current one, so loads are in flight continuously instead of
+// only during a load phase; warps whose group touches a wall or an obstacle
+// compute it with the per-node path.
+// ---------------------------------------------------------------------------
+struct PipeNode {
+    long long gp;
+    int c, x, y, z;
+    bool inr;
+    uint8_t fcur, fprev, fslow;
+};
+
+template <class S>
+__device__ __forceinline__ void pipe_issue(const LatticeArgs& a, const S* src, int G, int lane, PipeNode& P,
+                                           float v[Q]) {
+    int c = 0;
+    for (int k = 1; k < a.n_ch; ++k)
+        if (G >= chan(a, k).blk0) c = k;
+    const ChannelDev& C = chan(a, c);
+    const int p = (G - C.blk0) * 32 + lane;
+    P.c = c;
+    P.inr = p < C.n;
+    P.gp = C.base + p;
+    const int gi = (int)P.gp;
+    const int grp = gi >> 5;
+    P.fcur = __ldg((a.par ? a.fl1 : a.fl0) + grp);
+    P.fprev = __ldg((a.par ? a.fl0 : a.fl1) + grp);
+    P.fslow = P.inr ? __ldg(a.slow + grp) : (uint8_t)0;
+    const int r = fdiv(p, C.dnx);
+    P.x = p - r * C.nx;
+    P.z = fdiv(r, C.dny);
+    P.y = r - P.z * C.ny;
+    Nbr nb;
+    neighbours(C, P.x, P.y, P.z, nb);
+    float extra;
+#define LBIBM_IP(I) issue_vec<S, 1, I>(src, a.Ntot, gi, nb, C, P.x, lane, P.inr, &v[I], extra);
+    LBIBM_ALL_I(LBIBM_IP)
+#undef LBIBM_IP
+}
+
+template <class S>
+__device__ __forceinline__ void pipe_process(const LatticeArgs& a, const S* src, S* dst, const PipeNode& P,
+                                             const float v[Q]) {
+    const ChannelDev& C = chan(a, P.c);
+    const bool forced = P.fcur != 0, prevf = P.fprev != 0;
+    const bool wslow = __any_sync(FULL, P.fslow != 0);
+    const long long NT = a.Ntot;
+    const long long gp = P.gp;
+    const float4* gcur = a.par ? a.g1 : a.g0;
+    float4* gprev = a.par ? a.g0 : a.g1;
+    bool active = P.inr;
+    float h[Q];
+    if (!wslow) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) h[i] = v[i];
+    } else if (active) {
+        const bool obst = (P.fslow & 2) != 0;
+        if (obst && solid_at(a.mask, gp)) {
+            active = false;
+        } else {
+            Nbr nb;
+            neighbours(C, P.x, P.y, P.z, nb);
+            pull_node<S>(src, NT, gp, nb, a.mask, C, P.y, h, obst);
+        }
+    }
+    if (active) {
+        float gx = C.G[0], gy = C.G[1], gz = C.G[2];
+        if (forced) {
+            const float4 g = gcur[gp];
+            gx += g.x; gy += g.y; gz += g.z;
+        }
+        const Mac m = macro(h, gx, gy, gz);
+        const float om = C.omega, fp = C.fpre;
+        collide_all(h, m, om, fp);
+#define LBIBM_C1(I) Pop<S>::st(dst, (long long)(I) * NT + gp, h[I], I);
+        LBIBM_ALL_I(LBIBM_C1)
+#undef LBIBM_C1
+        if (forced) a.u[gp] = make_float4(m.ux, m.uy, m.uz, m.rho);
+        if (prevf) gprev[gp] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __syncwarp();
+    if (P.inr && prevf && (gp & 31) == 0) (a.par ? a.fl0 : a.fl1)[gp >> 5] = 0;
+}
+
+template <class S, int BS>
+__global__ void __launch_bounds__(BS, 512 / BS) k_stream_collide_pipe(const __grid_constant__ LatticeArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int n_warps = gridDim.x * (BS / 32);
+    int G = blockIdx.x * (BS / 32) + (threadIdx.x >> 5);
+    if (G >= a.n_groups) return;   // whole warps leave together
+    const S* src = (const S*)(a.par ? a.h1 : a.h0);
+    S* dst = (S*)(a.par ? a.h0 : a.h1);
+    PipeNode P0, P1;
+    float v0[Q], v1[Q];
+    pipe_issue<S>(a, src, G, lane, P0, v0);
+    // ping-pong between two register sets: the next group's loads are issued
+    // before the current group is computed
+    for (;;) {
+        int Gn = G + n_warps;
+        if (Gn < a.n_groups) pipe_issue<S>(a, src, Gn, lane, P1, v1);
+        pipe_process<S>(a, src, dst, P0, v0);
+        if (Gn >= a.n_groups) break;
+        G = Gn;
+        Gn = G + n_warps;
+        if (Gn < a.n_groups) pipe_issue<S>(a, src, Gn, lane, P0, v0);
+        pipe_process<S>(a, src, dst, P1, v1);
+        if (Gn >= a.n_groups) break;
+        G = Gn;
+    }
+}
+
+template <class S>
+static size_t staged_smem() { return 2 * (size_t)Q * SG_NODES * sizeof(S); }
+
+cudaError_t prepare_staged(int storage) {
+    if (storage == 0)
+        return cudaFuncSetAttribute(k_stream_collide_staged<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)staged_smem<float>());
+    if (storage == 1)
+        return cudaFuncSetAttribute(k_stream_collide_staged<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)staged_smem<__half>());
+    return cudaFuncSetAttribute(k_stream_collide_staged<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)staged_smem<__nv_bfloat16>());
+}
+
+// Supported (nodes per thread, block size) pairs per storage type; npt = 0 is
+// the staged variant, npt = -1 the pipelined one.
+static const K3Config CFG_F32[] = {{-1, 128}, {-1, 256}, {0, 256}, {1, 256}, {2, 256}, {4, 256}, {4, 128}, {2, 128}, {1, 128}};
+static const K3Config CFG_16[] = {{-1, 128}, {-1, 256}, {0, 256}, {2, 256}, {4, 256}, {4, 128}, {2, 128}, {1, 256}, {1, 128}};
+
+int k3_config_count(int storage) { return 9; }
 K3Config k3_config_at(int storage, int k) { return storage == 0 ? CFG_F32[k] : CFG_16[k]; }
 bool k3_config_supported(int storage, K3Config c) {
     for (int k = 0; k < k3_config_count(storage); ++k) {
@@ -398,6 +724,15 @@ static cudaError_t launch_sc_typed(const LatticeArgs& a, K3Config c, int blocks,
     if (c.npt == N && c.bs == B) {                         \
         k_stream_collide<S, N, B><<<blocks, B, 0, s>>>(a); \
         return cudaGetLastError();                         \
+    }
+    if (c.npt == 0) {
+        k_stream_collide_staged<S><<<blocks, SG_THREADS, staged_smem<S>(), s>>>(a);
+        return cudaGetLastError();
+    }
+    if (c.npt == -1) {
+        if (c.bs == 128) k_stream_collide_pipe<S, 128><<<blocks, 128, 0, s>>>(a);
+        else k_stream_collide_pipe<S, 256><<<blocks, 256, 0, s>>>(a);
+        return cudaGetLastError();
     }
     if constexpr (sizeof(S) == 4) {
         LBIBM_CASE(1, 256) LBIBM_CASE(2, 256) LBIBM_CASE(4, 256) LBIBM_CASE(4, 128) LBIBM_CASE(2, 128)
@@ -479,10 +814,10 @@ __global__ void k_pull_populations(const __grid_constant__ LatticeArgs a, int c,
 #pragma unroll
         for (int i = 0; i < Q; ++i) h[i] = 0.0f;
     } else {
-        const int x = p % C.nx;
-        const int r = p / C.nx;
-        const int y = r % C.ny;
-        const int z = r / C.ny;
+        const int r = fdiv(p, C.dnx);
+        const int x = p - r * C.nx;
+        const int z = fdiv(r, C.dny);
+        const int y = r - z * C.ny;
         Nbr nb;
         neighbours(C, x, y, z, nb);
         pull_node<S>(src, a.Ntot, gp, nb, a.mask, C, y, h);
@@ -634,25 +969,29 @@ cudaError_t launch_rasterise(const float* spheres, int n_spheres, const uint8_t*
 // 18 neighbours solid or outside the domain; the stream-collide kernel checks
 // the mask and bounds only there.
 __global__ void k_slow_flags(ChannelDev C, const uint32_t* mask, uint8_t* slow) {
+    // one warp covers one 32-node group (channel bases are multiples of 32)
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= C.n) return;
     const long long gp = C.base + p;
-    bool s = solid_at(mask, gp);
-    if (!s) {
-        const int x = p % C.nx;
-        const int r = p / C.nx;
-        const int y = r % C.ny;
-        const int z = r / C.ny;
+    bool wall = false, obst = false;
+    if (p < C.n) obst = solid_at(mask, gp);
+    if (p < C.n && !obst) {
+        const int r = fdiv(p, C.dnx);
+        const int x = p - r * C.nx;
+        const int z = fdiv(r, C.dny);
+        const int y = r - z * C.ny;
         Nbr nb;
         neighbours(C, x, y, z, nb);
         bool ok;
-#define LBIBM_CHK(I) { const int o = src_off<I>(nb, ok); s = s || !ok || solid_at(mask, gp + (ok ? o : 0)); }
+#define LBIBM_CHK(I) { const int o = src_off<I>(nb, ok); wall = wall || !ok; obst = obst || (ok && solid_at(mask, gp + o)); }
         LBIBM_CHK(1) LBIBM_CHK(2) LBIBM_CHK(3) LBIBM_CHK(4) LBIBM_CHK(5) LBIBM_CHK(6) LBIBM_CHK(7)
         LBIBM_CHK(8) LBIBM_CHK(9) LBIBM_CHK(10) LBIBM_CHK(11) LBIBM_CHK(12) LBIBM_CHK(13) LBIBM_CHK(14)
         LBIBM_CHK(15) LBIBM_CHK(16) LBIBM_CHK(17) LBIBM_CHK(18)
 #undef LBIBM_CHK
     }
-    if (s) slow[gp >> 5] = 1;
+    const bool any_wall = __any_sync(FULL, wall), any_obst = __any_sync(FULL, obst);
+    // bit 0: a node of the group has a neighbour outside the domain; bit 1: an
+    // obstacle node in the group or next to it
+    if ((threadIdx.x & 31) == 0 && (any_wall || any_obst)) slow[gp >> 5] = (uint8_t)(any_wall | (any_obst << 1));
 }
 
 cudaError_t launch_slow_flags(const ChannelDev& ch, const uint32_t* mask, uint8_t* slow, cudaStream_t s) {

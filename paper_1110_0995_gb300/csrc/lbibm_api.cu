@@ -55,6 +55,8 @@ struct lb_ctx {
     long long Ntot = 0;
     long long plane = 0;   // population plane stride (>= Ntot)
     int total_blocks = 0;
+    int n_groups = 0;        // row groups of the staged stream-collide variant
+    int sm_count = 152;
     // lattice
     void* h[2] = {nullptr, nullptr};
     uint32_t* mask = nullptr;
@@ -177,6 +179,7 @@ LatticeArgs lattice_args(const lb_ctx* ctx, int par) {
     a.fl0 = ctx->fl[0];
     a.fl1 = ctx->fl[1];
     a.u = ctx->u;
+    a.n_groups = ctx->n_groups;
     return a;
 }
 
@@ -343,13 +346,18 @@ long long plane_pad() {
 // variant: channel k's blocks start at blk0 and cover its padded node range.
 bool k3_config_valid(const lb_ctx* ctx, K3Config c) {
     if (!k3_config_supported((int)ctx->storage, c)) return false;
-    for (const auto& ch : ctx->ch)
-        if (ch.d.nx % c.npt != 0) return false;
+    for (const auto& ch : ctx->ch) {
+        if (c.npt == 0) {
+            if (staged_rows(ch.d.nx, (int)pop_bytes(ctx->storage)) == 0) return false;
+        } else if (c.npt > 0 && ch.d.nx % c.npt != 0) {
+            return false;
+        }
+    }
     return true;
 }
 
 K3Config default_k3_config(const lb_ctx* ctx) {
-    const K3Config pref[] = {{2, 256}, {1, 256}};
+    const K3Config pref[] = {{1, 128}};
     for (const K3Config& c : pref)
         if (k3_config_valid(ctx, c)) return c;
     return K3Config{1, 256};
@@ -357,6 +365,33 @@ K3Config default_k3_config(const lb_ctx* ctx) {
 
 void apply_k3_config(lb_ctx* ctx, K3Config c) {
     ctx->k3 = c;
+    if (c.npt == 0) {
+        // staged: row groups per channel, persistent grid of two blocks per SM
+        int grp = 0;
+        for (auto& ch : ctx->ch) {
+            ch.d.srows = staged_rows(ch.d.nx, (int)pop_bytes(ctx->storage));
+            ch.d.sg0 = grp;
+            ch.d.blk0 = 0;
+            const int rows = ch.d.ny * ch.d.nz;
+            grp += ch.d.srows > 0 ? (rows + ch.d.srows - 1) / ch.d.srows : 0;
+        }
+        ctx->n_groups = grp;
+        ctx->total_blocks = std::min(grp, 2 * ctx->sm_count);
+        return;
+    }
+    if (c.npt == -1) {
+        // pipelined: 32-node groups per channel, persistent grid at full residency
+        int grp = 0;
+        for (auto& ch : ctx->ch) {
+            ch.d.blk0 = grp;
+            grp += (ch.d.n + GROUP - 1) / GROUP;
+        }
+        ctx->n_groups = grp;
+        const int warps_per_block = c.bs / 32;
+        const int needed = (grp + warps_per_block - 1) / warps_per_block;
+        ctx->total_blocks = std::min(needed, ctx->sm_count * (512 / c.bs));
+        return;
+    }
     const int per_block = c.npt * c.bs;
     int blk = 0;
     for (auto& ch : ctx->ch) {
@@ -450,6 +485,8 @@ lb_status lb_create_batch(const lb_params* params, int n_channels, void* cuda_st
         ChannelDev& d = c.d;
         std::memset(&d, 0, sizeof(d));
         d.nx = p.nx; d.ny = p.ny; d.nz = p.nz;
+        d.dnx = make_fastdiv(p.nx);
+        d.dny = make_fastdiv(p.ny);
         for (int a = 0; a < 3; ++a) d.per[a] = p.periodic[a] ? 1 : 0;
         d.n = p.nx * p.ny * p.nz;
         d.base = base;
@@ -467,6 +504,18 @@ lb_status lb_create_batch(const lb_params* params, int n_channels, void* cuda_st
     }
     ctx->Ntot = base;
     ctx->plane = base + plane_pad();
+    {
+        int dev = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess)
+            cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, dev);
+        if (ctx->sm_count <= 0) ctx->sm_count = 152;
+        cudaGetLastError();
+        if (prepare_staged((int)ctx->storage) != cudaSuccess) {
+            cudaGetLastError();
+            delete ctx;
+            return LB_ERR_CUDA;
+        }
+    }
     if (ctx->plane >= (1LL << 31)) {   // node indices are 32-bit inside the kernels
         delete ctx;
         return LB_ERR_ARG;

@@ -49,12 +49,42 @@ constexpr float FIX_INV_F = 9.094947017729282e-13f;  // 2^-40
 constexpr int FIX_BITS = 40;
 constexpr int SUB = 8;              // lanes per IB node in the node-parallel kernels
 
+// Exact division of 31-bit non-negative integers by a fixed divisor d >= 1 via
+// multiply-high (Granlund-Montgomery, round-up variant): with l = ceil(log2 d)
+// and m = ceil(2^(31+l) / d), floor(n / d) = (n * m) >> (31 + l) for n < 2^31.
+struct FastDiv {
+    unsigned m;
+    int s;   // l - 1, or -1 for d == 1
+};
+
+inline FastDiv make_fastdiv(int d) {
+    FastDiv f;
+    if (d <= 1) {
+        f.m = 0;
+        f.s = -1;
+        return f;
+    }
+    int l = 0;
+    while ((1LL << l) < d) ++l;
+    const unsigned long long num = 1ULL << (31 + l);
+    f.m = (unsigned)((num + (unsigned long long)d - 1) / (unsigned long long)d);
+    f.s = l - 1;
+    return f;
+}
+
+__device__ __forceinline__ int fdiv(int n, FastDiv f) {
+    return f.s < 0 ? n : (int)(__umulhi((unsigned)n, f.m) >> f.s);
+}
+
 struct ChannelDev {
     int nx, ny, nz;
+    FastDiv dnx, dny;     // division by nx and by ny
     int per[3];
     long long base;       // first global node index
     int n;                // nx * ny * nz (< 2^31)
     int blk0;             // first block of the stream-collide grid for this channel
+    int sg0;              // first row group of the staged stream-collide variant
+    int srows;            // rows per staged group (0: channel not stageable)
     float omega;          // 1 / tau
     float fpre;           // 1 - 1 / (2 tau)
     float G[3];           // uniform body force
@@ -92,6 +122,7 @@ struct LatticeArgs {
     uint8_t* fl0;
     uint8_t* fl1;
     float4* u;
+    int n_groups;         // row groups of the staged stream-collide variant
     ChannelDev chp[MAXCH_P];   // copy of the first channels (constant bank)
 };
 
@@ -148,10 +179,23 @@ __host__ __device__ constexpr float wgt(int i) { return i == 0 ? (1.0f / 3.0f) :
 __host__ __device__ constexpr double wgt_d(int i) { return i == 0 ? (1.0 / 3.0) : (i <= 6 ? (1.0 / 18.0) : (1.0 / 36.0)); }
 
 // Stream-collide kernel variants: nodes per thread along x and block size.
+// npt = 0 selects the staged variant (rows copied to shared memory with
+// asynchronous copies, persistent grid of bs-thread blocks).
 struct K3Config {
     int npt;
     int bs;
 };
+constexpr int SG_NODES = 512;       // nodes per row group of the staged variant
+// Rows per staged group for a row of nx nodes of `bytes`-byte populations, or 0
+// when the row is not 16-byte copyable or no whole number of rows fills a
+// group with a multiple of 32 nodes.
+__host__ __device__ inline int staged_rows(int nx, int bytes) {
+    if ((nx * bytes) % 16 != 0 || nx > SG_NODES) return 0;
+    int r = SG_NODES / nx;
+    while (r > 0 && (r * nx) % 32 != 0) --r;
+    return r;
+}
+cudaError_t prepare_staged(int storage);
 bool k3_config_supported(int storage, K3Config c);
 int k3_config_count(int storage);
 K3Config k3_config_at(int storage, int k);

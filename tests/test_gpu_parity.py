@@ -83,7 +83,7 @@ def test_lattice_parity_random_state(periodic, wall):
         np.testing.assert_allclose(sim.populations()[:, fluid], ref.get_f()[:, fluid], rtol=0, atol=2e-7)
 
 
-VARIANTS = [(1, 128), (1, 256), (2, 128), (2, 256), (4, 128), (4, 256)]
+VARIANTS = [(-1, 128), (-1, 256), (0, 256), (1, 128), (1, 256), (2, 128), (2, 256), (4, 128), (4, 256)]
 
 
 @pytest.mark.parametrize("npt,bs", VARIANTS)
@@ -107,7 +107,7 @@ def test_lattice_parity_every_kernel_variant(npt, bs):
     np.testing.assert_allclose(sim.populations()[:, fluid], ref.get_f()[:, fluid], rtol=0, atol=2e-7)
 
 
-@pytest.mark.parametrize("npt,bs", [(1, 256), (2, 256), (4, 128)])
+@pytest.mark.parametrize("npt,bs", [(-1, 128), (0, 256), (1, 256), (2, 256), (4, 128)])
 def test_plain_channel_every_kernel_variant(npt, bs):
     sc = scene.channel_plain(seed=1, steps=150)
     sim = _sim(sc)
