@@ -131,6 +131,30 @@ def time_oracle(sc, steps: int, warmup: int = 1):
     return time.perf_counter() - t0
 
 
+def profiled_traffic(workload: str, storage: str, variant):
+    """DRAM bytes per stream-collide launch from the committed ncu summary of
+    this workload, or None when there is none, it is for another variant, or
+    the kernel sources changed since the counters were taken."""
+    import hashlib
+    import re
+
+    path = os.path.join(ROOT, "profiles", f"k_stream_collide_{workload}_{storage}.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m = re.search(r"^dram_bytes_per_launch: (\d+)$", text, re.M)
+    h = re.search(r"^kernel_source_sha256: (.*)$", text, re.M)
+    v = re.search(r"k_stream_collide<\w+, (-?\d+), (\d+)>", text)
+    if not (m and h and v) or (int(v.group(1)), int(v.group(2))) != (variant["npt"], variant["bs"]):
+        return None
+    parts = h.group(1).split()
+    for name, digest in zip(parts[0::2], parts[1::2]):
+        src = os.path.join(ROOT, "paper_1110_0995_gb300", "csrc", name)
+        if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest() != digest:
+            return None
+    return int(m.group(1))
+
+
 def cpu_threads() -> int:
     v = os.environ.get("OMP_NUM_THREADS")
     return int(v) if v else (os.cpu_count() or 1)
@@ -199,10 +223,15 @@ def run_ours(args):
     sim = lbibm.Simulation.from_scene(sc, storage=args.storage, stream=stream.cuda_stream)
     from paper_1110_0995_gb300 import autotune
 
-    tuned = autotune.tune(sim, torch.cuda.get_device_name(local_rank), args.storage)
+    if args.variant:
+        npt, bs = (int(v) for v in args.variant.split(","))
+        sim.set_kernel_config(npt, bs)
+        tuned = {"npt": npt, "bs": bs}
+    else:
+        tuned = autotune.tune(sim, torch.cuda.get_device_name(local_rank), args.storage)
     n_nodes = sc.n_nodes
     n_fluid = int((sim.solid_mask() == 0).sum())
-    sim.set_timing(True)
+    sim.set_timing(True)                            # events around every kernel launch
     sim.step(args.warmup)
     sim.synchronize()
     sim.kernel_times()                              # discard warm-up timings
@@ -224,6 +253,8 @@ def run_ours(args):
     barrier()
     ms = e0.elapsed_time(e1)
     kms, kn = sim.kernel_times()
+    diag = sim.diagnostics()                        # FP64 sums over the final state
+    finite = bool(diag[4] == 0)
     if world > 1:
         import torch.distributed as dist
 
@@ -237,11 +268,7 @@ def run_ours(args):
     peak, peak_kind = measured_peak()
     alg_bytes = BYTES_PER_NODE[args.storage] * n_fluid
     achieved = alg_bytes / (k3_ms * 1e-3) / 1e9
-    traffic = None
-    tr_path = os.path.join(ROOT, "profiles", f"traffic_{args.workload}_{args.storage}.json")
-    if os.path.exists(tr_path):
-        with open(tr_path) as f:
-            traffic = json.load(f).get("bytes_per_launch")
+    traffic = profiled_traffic(args.workload, args.storage, tuned)
 
     # end to end through the C ABI with host buffers: scene upload from host,
     # steps, node positions of every cell read back every 10 steps, final fields
@@ -292,6 +319,8 @@ def run_ours(args):
                                    "stream_collide": k3_ms, "interp_advance": kms[3] / max(1, kn[3])},
             "ib_node_updates_per_s": world * sc.n_ib_nodes * args.steps / (ms * 1e-3),
             "gpu_launches": int(sum(kn)),
+            "state_after_timed_steps": {"finite": finite, "mass_per_fluid_node": diag[0] / n_fluid,
+                                        "max_u": diag[5]},
             "clocks": clk.summary(),
             "cpu_baseline": cpu,
             "e2e": e2e,
@@ -307,11 +336,12 @@ def run_ours(args):
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10000)
+    ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="micropost_filter_256x128x64")
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
+    ap.add_argument("--variant", default="", help="stream-collide variant 'npt,bs' instead of the autotuner")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args(argv)

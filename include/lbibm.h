@@ -214,12 +214,16 @@ lb_status lb_get_step(lb_ctx* ctx, int64_t* step);
 lb_status lb_save_state(lb_ctx* ctx, void* buf, size_t* bytes);
 lb_status lb_load_state(lb_ctx* ctx, const void* buf, size_t bytes);
 
-/* Optional per-kernel timing: when enabled, lb_step records CUDA events
- * around every launch of each kernel (no graph), and lb_kernel_times returns
- * the accumulated milliseconds and launch counts per kernel class:
- * 0 = cell area/volume, 1 = membrane forces + spreading,
- * 2 = fused stream-collide, 3 = interpolation + advance. */
-lb_status lb_set_timing(lb_ctx* ctx, int enable);
+/* Optional per-kernel timing.  Kernel classes: 0 = cell area/volume,
+ * 1 = membrane forces + spreading, 2 = fused stream-collide,
+ * 3 = interpolation + advance.  With kernel_mask != 0 (bit k for class k,
+ * 15 = all) lb_step launches the kernels one by one (no graph) and records a
+ * pair of CUDA events on the context's stream around every launch of a
+ * selected class; 0 returns to graph launches.  LB_ERR_ARG outside 0..15.
+ * lb_kernel_times synchronises the stream and returns, per class, the
+ * accumulated event milliseconds (0 for classes not timed) and the number of
+ * launches enqueued (timed or not) since the previous call, then resets both. */
+lb_status lb_set_timing(lb_ctx* ctx, int kernel_mask);
 lb_status lb_kernel_times(lb_ctx* ctx, double ms[4], int64_t launches[4]);
 
 /* Static message for the last error on this context (never NULL). */

@@ -103,7 +103,7 @@ struct lb_ctx {
     bool started = false;
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     // timing
-    bool timing = false;
+    int timing = 0;          // bit k: record events around kernel class k (no graph)
     double ms[4] = {0, 0, 0, 0};
     long long launches[4] = {0, 0, 0, 0};
     std::vector<EventPair> pending;
@@ -256,7 +256,9 @@ lb_status enqueue_step(lb_ctx* ctx, int par) {
     for (int k = 0; k < 4; ++k) {
         if (!ibm && k != 2) continue;
         EventPair ep{};
-        if (ctx->timing) {
+        const bool timed = (ctx->timing >> k) & 1;
+        ctx->launches[k] += 1;
+        if (timed) {
             ep.a = take_event(ctx);
             ep.b = take_event(ctx);
             ep.cls = k;
@@ -270,7 +272,7 @@ lb_status enqueue_step(lb_ctx* ctx, int par) {
             case 3: e = launch_interp_advance(ia, ctx->stream); break;
         }
         if (e != cudaSuccess) return cuda_fail(ctx, e, "kernel launch");
-        if (ctx->timing) {
+        if (timed) {
             LB_CUDA(cudaEventRecord(ep.b, ctx->stream));
             ctx->pending.push_back(ep);
         }
@@ -807,6 +809,8 @@ lb_status lb_step(lb_ctx* ctx, int n_steps) {
             if (s != LB_OK) return s;
         } else {
             LB_CUDA(cudaGraphLaunch(ctx->gexec[par], ctx->stream));
+            for (int c = 0; c < 4; ++c)
+                if (ctx->M > 0 || c == 2) ctx->launches[c] += 1;
         }
         ctx->step++;
     }
@@ -1162,9 +1166,10 @@ lb_status lb_load_state(lb_ctx* ctx, const void* buf, size_t bytes) {
 }
 
 // ---- timing ----
-lb_status lb_set_timing(lb_ctx* ctx, int enable) {
+lb_status lb_set_timing(lb_ctx* ctx, int kernel_mask) {
     LB_GUARD(ctx);
-    ctx->timing = enable != 0;
+    if (kernel_mask < 0 || kernel_mask > 15) return fail(ctx, LB_ERR_ARG, "timing mask outside 0..15");
+    ctx->timing = kernel_mask;
     return LB_OK;
 }
 
@@ -1175,7 +1180,6 @@ lb_status lb_kernel_times(lb_ctx* ctx, double ms[4], int64_t launches[4]) {
         float t = 0.f;
         LB_CUDA(cudaEventElapsedTime(&t, ep.a, ep.b));
         ctx->ms[ep.cls] += t;
-        ctx->launches[ep.cls] += 1;
         ctx->free_events.push_back(ep.a);
         ctx->free_events.push_back(ep.b);
     }

@@ -286,8 +286,10 @@ class Simulation:
         self._check(self._L.lb_autotune(self._h, int(repeats), ctypes.byref(n), ctypes.byref(b), ctypes.byref(ms)))
         return n.value, b.value, ms.value
 
-    def set_timing(self, on: bool):
-        self._check(self._L.lb_set_timing(self._h, int(bool(on))))
+    def set_timing(self, on=True):
+        """True: time every kernel class; an int: bit mask of classes; False: off."""
+        mask = 15 if on is True else (0 if on is False else int(on))
+        self._check(self._L.lb_set_timing(self._h, mask))
 
     def kernel_times(self):
         ms = np.zeros(4)
