@@ -311,10 +311,46 @@ __device__ __forceinline__ void store_vec(S* dst, long long NT, int gi0, const f
     VecIO<S, NPT>::st(dst + (size_t)I * (size_t)NT, gi0, I, o);
 }
 
+// Link masks of NPT consecutive nodes (one aligned vector load).
+template <int NPT>
+__device__ __forceinline__ void links_ld(const uint32_t* p, uint32_t lk[NPT]) {
+    if constexpr (NPT == 1) {
+        lk[0] = __ldg(p);
+    } else if constexpr (NPT == 2) {
+        const uint2 v = __ldg(reinterpret_cast<const uint2*>(p));
+        lk[0] = v.x; lk[1] = v.y;
+    } else {
+        const uint4 v = __ldg(reinterpret_cast<const uint4*>(p));
+        lk[0] = v.x; lk[1] = v.y; lk[2] = v.z; lk[3] = v.w;
+    }
+}
+
+// Halfway bounce-back (Sec. 2.4) for the links of one node whose bit is set
+// in its link mask: the population pulled along direction i comes back from
+// the node's own post-collision population opp(i); on a moving y-wall Ladd's
+// term 6 w_i rho0 e_i . u_wall is added (rho0 = 1).
+template <class S>
+__device__ __forceinline__ void bounce_back(const S* src, long long NT, int gi, uint32_t lk, const ChannelDev& C,
+                                            int y, float h[Q]) {
+    if (!(lk & ~1u)) return;
+#define LBIBM_BB(I)                                                                  \
+    if (I > 0 && ((lk >> I) & 1u)) {                                                 \
+        float v = Pop<S>::ld(src, (long long)opp(I) * NT + gi, opp(I));              \
+        if (C.has_uw && !C.per[1]) {                                                 \
+            const int wall = (ey(I) == 1 && y == 0) ? 0 : ((ey(I) == -1 && y == C.ny - 1) ? 1 : -1); \
+            if (wall >= 0)                                                           \
+                v += 6.0f * wgt(I) * (ex(I) * C.uw[wall][0] + ey(I) * C.uw[wall][1] + ez(I) * C.uw[wall][2]); \
+        }                                                                            \
+        h[I] = v;                                                                    \
+    }
+    LBIBM_ALL_I(LBIBM_BB)
+#undef LBIBM_BB
+}
+
 // Resident threads per SM the register budget is sized for.  One node per
 // thread: 1280 threads (48 registers) for FP32 populations, 1024 (64 registers)
 // for 16-bit ones, the fastest of the budgets measured on GB300; two nodes per
-// thread: 768 (80 registers); four: 256 (255 registers).
+// thread: 512 (128 registers); four: 256 (255 registers).
 #ifndef LBIBM_K3_THREADS1
 #define LBIBM_K3_THREADS1 1280
 #endif
@@ -322,7 +358,7 @@ __device__ __forceinline__ void store_vec(S* dst, long long NT, int gi0, const f
 #define LBIBM_K3_THREADS1_16 1024
 #endif
 #ifndef LBIBM_K3_THREADS2
-#define LBIBM_K3_THREADS2 768
+#define LBIBM_K3_THREADS2 512
 #endif
 template <class S, int NPT, int BS> struct K3MinBlocks {
     static constexpr int threads = NPT == 1 ? (sizeof(S) == 4 ? LBIBM_K3_THREADS1 : LBIBM_K3_THREADS1_16)
@@ -370,57 +406,56 @@ __global__ void __launch_bounds__(BS, K3MinBlocks<S, NPT, BS>::value) k_stream_c
     const float4* gcur = par ? a.g1 : a.g0;
     float4* gprev = par ? a.g0 : a.g1;
 
-    if (!wslow) {
-        // vector path: every node of the warp is fluid with all 18 neighbours in the domain
-        float h[NPT][Q];
+    // phase 2 (converged warp): place the loaded values
+    float h[NPT][Q];
 #define LBIBM_PV(I) place_vec<NPT, I>(v[I], extra[I], C, x0, lane, h);
-        LBIBM_ALL_I(LBIBM_PV)
+    LBIBM_ALL_I(LBIBM_PV)
 #undef LBIBM_PV
-        if (inr) {
-            Mac m[NPT];
+    // groups at a wall or an obstacle: replace the populations of bounce-back
+    // links by the opposite population of the node itself (halfway bounce-back)
+    uint32_t lk[NPT];
 #pragma unroll
-            for (int k = 0; k < NPT; ++k) {
-                float gx = C.G[0], gy = C.G[1], gz = C.G[2];
-                if (forced) {
-                    const float4 g = gcur[gi0 + k];
-                    gx += g.x; gy += g.y; gz += g.z;
-                }
-                m[k] = macro(h[k], gx, gy, gz);
+    for (int k = 0; k < NPT; ++k) lk[k] = 0u;
+    if (wslow) {
+        if (inr && fslow) links_ld<NPT>(a.links + gi0, lk);
+#pragma unroll
+        for (int k = 0; k < NPT; ++k) bounce_back<S>(src, NT, gi0 + k, lk[k], C, y, h[k]);
+    }
+    if (inr) {
+        Mac m[NPT];
+#pragma unroll
+        for (int k = 0; k < NPT; ++k) {
+            float gx = C.G[0], gy = C.G[1], gz = C.G[2];
+            if (forced) {
+                const float4 g = gcur[gi0 + k];
+                gx += g.x; gy += g.y; gz += g.z;
             }
+            m[k] = macro(h[k], gx, gy, gz);
+        }
 #pragma unroll
-            for (int k = 0; k < NPT; ++k) collide_all(h[k], m[k], om, fp);
+        for (int k = 0; k < NPT; ++k) collide_all(h[k], m[k], om, fp);
+        uint32_t solid = 0u;
+#pragma unroll
+        for (int k = 0; k < NPT; ++k) solid |= lk[k];
+        if (!(solid & 1u)) {
 #define LBIBM_SV(I) store_vec<S, NPT, I>(dst, NT, gi0, h);
             LBIBM_ALL_I(LBIBM_SV)
 #undef LBIBM_SV
+        } else {
+            // a solid node among this thread's nodes: it keeps its populations
 #pragma unroll
             for (int k = 0; k < NPT; ++k) {
-                if (forced) a.u[gi0 + k] = make_float4(m[k].ux, m[k].uy, m[k].uz, m[k].rho);
-                if (prevf) gprev[gi0 + k] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (lk[k] & 1u) continue;
+#define LBIBM_S1(I) Pop<S>::st(dst, (long long)(I) * NT + gi0 + k, h[k][I], I);
+                LBIBM_ALL_I(LBIBM_S1)
+#undef LBIBM_S1
             }
         }
-    } else if (inr) {
-        // per-node path with bounce-back at walls and obstacles
-        const bool obst = (fslow & 2) != 0;   // an obstacle node in or next to this group
-#pragma unroll 1
+#pragma unroll
         for (int k = 0; k < NPT; ++k) {
-            const long long gp = gp0 + k;
-            if (obst && solid_at(a.mask, gp)) continue;
-            Nbr nk = nb;
-            if (k > 0) neighbours(C, x0 + k, y, z, nk);
-            float h[Q];
-            pull_node<S>(src, NT, gp, nk, a.mask, C, y, h, obst);
-            float gx = C.G[0], gy = C.G[1], gz = C.G[2];
-            if (forced) {
-                const float4 g = gcur[gp];
-                gx += g.x; gy += g.y; gz += g.z;
-            }
-            const Mac m = macro(h, gx, gy, gz);
-            collide_all(h, m, om, fp);
-#define LBIBM_C1(I) Pop<S>::st(dst, (long long)(I) * NT + gp, h[I], I);
-            LBIBM_ALL_I(LBIBM_C1)
-#undef LBIBM_C1
-            if (forced) a.u[gp] = make_float4(m.ux, m.uy, m.uz, m.rho);
-            if (prevf) gprev[gp] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (lk[k] & 1u) continue;
+            if (forced) a.u[gi0 + k] = make_float4(m[k].ux, m[k].uy, m[k].uz, m[k].rho);
+            if (prevf) gprev[gi0 + k] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
     }
     // the lane holding the first node of each 32-node group clears the previous
@@ -968,11 +1003,18 @@ cudaError_t launch_rasterise(const float* spheres, int n_spheres, const uint8_t*
 // A 32-node group is "slow" when one of its nodes is solid or has one of the
 // 18 neighbours solid or outside the domain; the stream-collide kernel checks
 // the mask and bounds only there.
-__global__ void k_slow_flags(ChannelDev C, const uint32_t* mask, uint8_t* slow) {
+// Link masks and slow-group flags of one channel.  Link mask of a node: bit i
+// (1..18) set when the pull source x - e_i lies outside the domain on a
+// non-periodic axis or on an obstacle node, i.e. population i is bounced back;
+// bit 0 set when the node itself is solid.  Group flag: bit 0 = a node of the
+// 32-node group has a link leaving the domain, bit 1 = an obstacle node in the
+// group or next to it.
+__global__ void k_slow_flags(ChannelDev C, const uint32_t* mask, uint8_t* slow, uint32_t* links) {
     // one warp covers one 32-node group (channel bases are multiples of 32)
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     const long long gp = C.base + p;
     bool wall = false, obst = false;
+    uint32_t lk = 0u;
     if (p < C.n) obst = solid_at(mask, gp);
     if (p < C.n && !obst) {
         const int r = fdiv(p, C.dnx);
@@ -982,20 +1024,29 @@ __global__ void k_slow_flags(ChannelDev C, const uint32_t* mask, uint8_t* slow) 
         Nbr nb;
         neighbours(C, x, y, z, nb);
         bool ok;
-#define LBIBM_CHK(I) { const int o = src_off<I>(nb, ok); wall = wall || !ok; obst = obst || (ok && solid_at(mask, gp + o)); }
+#define LBIBM_CHK(I)                                        \
+    {                                                       \
+        const int o = src_off<I>(nb, ok);                   \
+        const bool sld = ok && solid_at(mask, gp + o);      \
+        wall = wall || !ok;                                 \
+        obst = obst || sld;                                 \
+        if (!ok || sld) lk |= 1u << I;                      \
+    }
         LBIBM_CHK(1) LBIBM_CHK(2) LBIBM_CHK(3) LBIBM_CHK(4) LBIBM_CHK(5) LBIBM_CHK(6) LBIBM_CHK(7)
         LBIBM_CHK(8) LBIBM_CHK(9) LBIBM_CHK(10) LBIBM_CHK(11) LBIBM_CHK(12) LBIBM_CHK(13) LBIBM_CHK(14)
         LBIBM_CHK(15) LBIBM_CHK(16) LBIBM_CHK(17) LBIBM_CHK(18)
 #undef LBIBM_CHK
+    } else if (p < C.n) {
+        lk = 1u;
     }
+    if (p < C.n) links[gp] = lk;
     const bool any_wall = __any_sync(FULL, wall), any_obst = __any_sync(FULL, obst);
-    // bit 0: a node of the group has a neighbour outside the domain; bit 1: an
-    // obstacle node in the group or next to it
-    if ((threadIdx.x & 31) == 0 && (any_wall || any_obst)) slow[gp >> 5] = (uint8_t)(any_wall | (any_obst << 1));
+    if ((threadIdx.x & 31) == 0) slow[gp >> 5] = (uint8_t)(any_wall | (any_obst << 1));
 }
 
-cudaError_t launch_slow_flags(const ChannelDev& ch, const uint32_t* mask, uint8_t* slow, cudaStream_t s) {
-    k_slow_flags<<<(unsigned)((ch.n + 255) / 256), 256, 0, s>>>(ch, mask, slow);
+cudaError_t launch_slow_flags(const ChannelDev& ch, const uint32_t* mask, uint8_t* slow, uint32_t* links,
+                              cudaStream_t s) {
+    k_slow_flags<<<(unsigned)((ch.n + 255) / 256), 256, 0, s>>>(ch, mask, slow, links);
     return cudaGetLastError();
 }
 

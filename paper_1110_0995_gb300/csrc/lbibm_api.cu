@@ -61,6 +61,7 @@ struct lb_ctx {
     void* h[2] = {nullptr, nullptr};
     uint32_t* mask = nullptr;
     uint8_t* slow = nullptr;
+    uint32_t* links = nullptr;   // bounce-back link mask per node
     float4* g[2] = {nullptr, nullptr};
     uint8_t* fl[2] = {nullptr, nullptr};
     float4* u = nullptr;
@@ -174,6 +175,7 @@ LatticeArgs lattice_args(const lb_ctx* ctx, int par) {
     a.Ntot = ctx->plane;
     a.mask = ctx->mask;
     a.slow = ctx->slow;
+    a.links = ctx->links;
     a.g0 = ctx->g[0];
     a.g1 = ctx->g[1];
     a.fl0 = ctx->fl[0];
@@ -543,6 +545,7 @@ lb_status lb_create_batch(const lb_params* params, int n_channels, void* cuda_st
     TRY(dalloc(ctx, (char**)&ctx->h[1], (size_t)Q * ctx->plane * pop_bytes(ctx->storage)));
     TRY(dalloc(ctx, &ctx->mask, NG));
     TRY(dalloc(ctx, &ctx->slow, NG));
+    TRY(dalloc(ctx, &ctx->links, NT));
     TRY(dalloc(ctx, &ctx->g[0], NT));
     TRY(dalloc(ctx, &ctx->g[1], NT));
     TRY(dalloc(ctx, &ctx->fl[0], NG));
@@ -556,6 +559,7 @@ lb_status lb_create_batch(const lb_params* params, int n_channels, void* cuda_st
     TRY(cudaMemsetAsync(ctx->h[1], 0, (size_t)Q * ctx->plane * pop_bytes(ctx->storage), ctx->stream));
     TRY(cudaMemsetAsync(ctx->mask, 0, NG * 4, ctx->stream));
     TRY(cudaMemsetAsync(ctx->slow, 0, NG, ctx->stream));
+    TRY(cudaMemsetAsync(ctx->links, 0, NT * sizeof(uint32_t), ctx->stream));
     TRY(cudaMemsetAsync(ctx->g[0], 0, NT * sizeof(float4), ctx->stream));
     TRY(cudaMemsetAsync(ctx->g[1], 0, NT * sizeof(float4), ctx->stream));
     TRY(cudaMemsetAsync(ctx->fl[0], 0, NG, ctx->stream));
@@ -570,7 +574,7 @@ lb_status lb_create_batch(const lb_params* params, int n_channels, void* cuda_st
     }
     if (upload_channels(ctx) != LB_OK) { lb_destroy(ctx); return LB_ERR_CUDA; }
     for (size_t k = 0; k < ctx->ch.size(); ++k)
-        if (launch_slow_flags(ctx->ch[k].d, ctx->mask, ctx->slow, ctx->stream) != cudaSuccess) {
+        if (launch_slow_flags(ctx->ch[k].d, ctx->mask, ctx->slow, ctx->links, ctx->stream) != cudaSuccess) {
             lb_destroy(ctx);
             return LB_ERR_CUDA;
         }
@@ -627,7 +631,7 @@ lb_status lb_set_obstacles(lb_ctx* ctx, const float* spheres, int n, const uint8
         LB_CUDA(cudaMemcpyAsync(dext, extra_mask, (size_t)c.d.n, cudaMemcpyHostToDevice, ctx->stream));
     }
     LB_CUDA(launch_rasterise(dsph, n, dext, c.d, ctx->mask, ctx->stream));
-    LB_CUDA(launch_slow_flags(c.d, ctx->mask, ctx->slow, ctx->stream));
+    LB_CUDA(launch_slow_flags(c.d, ctx->mask, ctx->slow, ctx->links, ctx->stream));
     LB_CUDA(cudaStreamSynchronize(ctx->stream));
     dfree(ctx, dsph);
     dfree(ctx, dext);

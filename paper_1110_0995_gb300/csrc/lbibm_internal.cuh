@@ -9,8 +9,12 @@
 //                                 bfloat16 (h / w).  Step parity p reads
 //                                 h[p] and writes h[1-p] (pull scheme).
 //   obstacle mask uint32[Ntot/32] one bit per node (1 = solid)
-//   slow flags   uint8[Ntot/32]   1 if a node of the 32-node group is solid or
-//                                 has a neighbour outside the domain or solid
+//   slow flags   uint8[Ntot/32]   nonzero if a node of the 32-node group is
+//                                 solid or has a link leaving the domain or
+//                                 ending on a solid node (bit 0 wall, bit 1 obstacle)
+//   link masks   uint32[Ntot]     per node: bit i = population i is bounced
+//                                 back, bit 0 = node solid; read only by the
+//                                 warps of slow groups
 //   force fields float4 g[2][Ntot] IB force density (x, y, z, 0), double-
 //                                 buffered by step parity, sparse in use
 //   force flags  uint8[2][Ntot/32] group's g[parity] holds forces of the step
@@ -117,6 +121,7 @@ struct LatticeArgs {
     long long Ntot;
     const uint32_t* mask;
     const uint8_t* slow;
+    const uint32_t* links;  // [Ntot] bounce-back link mask per node (bit 0: solid)
     float4* g0;
     float4* g1;
     uint8_t* fl0;
@@ -203,7 +208,8 @@ K3Config k3_config_at(int storage, int k);
 // ---- launchers (defined in lattice_kernels.cu / ibm_kernels.cu) ----
 cudaError_t launch_rasterise(const float* spheres, int n_spheres, const uint8_t* extra, const ChannelDev& ch,
                              uint32_t* mask, cudaStream_t s);
-cudaError_t launch_slow_flags(const ChannelDev& ch, const uint32_t* mask, uint8_t* slow, cudaStream_t s);
+cudaError_t launch_slow_flags(const ChannelDev& ch, const uint32_t* mask, uint8_t* slow, uint32_t* links,
+                              cudaStream_t s);
 cudaError_t launch_stream_collide(const LatticeArgs& a, K3Config cfg, int total_blocks, cudaStream_t s);
 cudaError_t launch_fields(const LatticeArgs& a, int ch_index, float* rho, float* u, cudaStream_t s);
 cudaError_t launch_pull_populations(const LatticeArgs& a, int ch_index, float* h_out, cudaStream_t s);
