@@ -2,10 +2,12 @@
 //   k_cell_sums      per-cell change of surface area and volume, FP32 per-triangle
 //                    terms accumulated in FP64 (Sec. 2.3.3: the global area and
 //                    volume constraints need every node of a cell)
-//   k_forces_spread  node forces (Sec. 2.3.1: stretching, bending, local/global
-//                    area, volume) gathered from the node's incident elements
-//                    (deterministic, no force atomics), then spread with the
-//                    trilinear delta function (Sec. 2.2 step 3)
+//   k_elements       the same per-triangle pass plus each triangle's area and
+//                    volume force terms, and per edge its stretching and
+//                    bending forces (Sec. 2.3.1), every element evaluated once
+//   k_forces_spread  node forces gathered from the element outputs of the
+//                    node's ring (deterministic order, no force atomics), then
+//                    spread with the trilinear delta function (Sec. 2.2 step 3)
 //   k_interp_advance trilinear velocity interpolation (Sec. 2.2 step 1) and the
 //                    point advance X <- X + U (massless points)
 // The two node kernels give each IB node eight lanes: one ring slot (or one
@@ -17,8 +19,7 @@
 // ~1e-7 relative however far the cell has moved.  Length and area changes use
 // the displacement from rest d (relative to the reference node's), so that
 // |e|^2 - L0^2 = 2 e0.de + de.de keeps its relative accuracy when the change
-// is small.  Every element is evaluated in a canonical vertex order so that
-// all lanes touching it compute bit-identical contributions.
+// is small.
 #include "lbibm_internal.cuh"
 
 namespace lbibm {
@@ -115,10 +116,10 @@ __device__ __forceinline__ float3 stretch_on_a(const NodeE& A, const NodeE& B, f
 }
 
 // Bending: E = (kb/2)(theta - theta0)^2 at edge (a, b) between triangle (a, b, c)
-// and triangle (b, a, d); theta = atan2((n1 x n2).e_hat, n1.n2).  Returns the
-// force on vertex `role` (0..3 = a, b, c, d).
-__device__ __forceinline__ float3 bend_on(const NodeE& A, const NodeE& B, const NodeE& Cc, const NodeE& D, float th0,
-                                          float kb, int role) {
+// and triangle (b, a, d); theta = atan2((n1 x n2).e_hat, n1.n2).  Writes the
+// forces on a, b, c, d (they sum to zero up to rounding).
+__device__ __forceinline__ void bend_all(const NodeE& A, const NodeE& B, const NodeE& Cc, const NodeE& D, float th0,
+                                         float kb, float3 f[4]) {
     const float3 e = edge(A, B);
     const float3 ac = edge(A, Cc);
     const float3 ad = edge(A, D);
@@ -133,10 +134,10 @@ __device__ __forceinline__ float3 bend_on(const NodeE& A, const NodeE& B, const 
     const float3 gd = (-l / dot(n2, n2)) * n2;
     const float sc = dot(ac, e) / l2;
     const float sd = dot(ad, e) / l2;
-    const float3 ga = (-(1.0f - sc)) * gc - (1.0f - sd) * gd;
-    const float3 gb = (-sc) * gc - sd * gd;
-    const float3 g = role == 0 ? ga : (role == 1 ? gb : (role == 2 ? gc : gd));
-    return coef * g;
+    f[0] = coef * ((-(1.0f - sc)) * gc - (1.0f - sd) * gd);
+    f[1] = coef * ((-sc) * gc - sd * gd);
+    f[2] = coef * gc;
+    f[3] = coef * gd;
 }
 
 // Area change of triangle (0, 1, 2) from rest: S_t - S0_t from
@@ -152,23 +153,6 @@ __device__ __forceinline__ float tri_dS(const float3& e1, const float3& e2, cons
     return num / (2.0f * (nn + nn0));
 }
 
-// Area (local + global) and volume forces of triangle (0, 1, 2) on vertex `role`:
-// homocentric area force along w_k = x_k - centroid with magnitude
-// k dA (2 S_t / sum |w|^2); volume force -kv dV/V0 n/6.
-__device__ __forceinline__ float3 tri_on(const NodeE& P0, const NodeE& P1, const NodeE& P2, float S0t, float kal,
-                                         float kag_dS, float kv_dV6, int role) {
-    const float3 e1 = edge(P0, P1), e2 = edge(P0, P2);
-    const float dSt = tri_dS(e1, e2, P1.d - P0.d, P2.d - P0.d, S0t);
-    const float St = S0t + dSt;
-    const float3 third = (1.0f / 3.0f) * (e1 + e2);
-    const float3 w0 = -third, w1 = e1 - third, w2 = e2 - third;
-    const float ww = dot(w0, w0) + dot(w1, w1) + dot(w2, w2);
-    const float coefA = (-kal * dSt / S0t - kag_dS) * 2.0f * St / ww;
-    const float3 n = cross(e1, e2);
-    const float3 w = role == 0 ? w0 : (role == 1 ? w1 : w2);
-    return coefA * w - kv_dV6 * n;
-}
-
 // Volume change of the tetrahedron (reference node, 0, 1, 2) from rest, times 6:
 // (r0 + d0).((r1 + d1) x (r2 + d2)) - r0.(r1 x r2), expanded, r = x - d.
 __device__ __forceinline__ float tri_dV6(const NodeE& P0, const NodeE& P1, const NodeE& P2) {
@@ -179,9 +163,14 @@ __device__ __forceinline__ float tri_dV6(const NodeE& P0, const NodeE& P1, const
 }
 
 // ---------------------------------------------------------------------------
-// R1: per-cell dS, dV (FP64 accumulation), one block per chunk of one cell's
+// Per-cell dS, dV (FP64 accumulation), one block per chunk of one cell's
 // triangles, one triangle per thread; the last block of a cell adds the
-// cell's partials in chunk order (deterministic).
+// cell's partials in chunk order (deterministic).  With FORCES the same pass
+// writes each triangle's area and volume force terms:
+//   area (local + global, homocentric): F_k = (kal dS_t/S0_t + kag dS/S0) a_k,
+//     a_k = -(2 S_t / sum_j |w_j|^2) w_k, w_k = x_k - centroid;
+//   volume: F_k = -kv (dV/V0) n_t / 6, n_t = (x_1 - x_0) x (x_2 - x_0).
+// The cell totals dS/S0 and dV/V0 are applied in the node gather.
 // ---------------------------------------------------------------------------
 constexpr int CS_BLOCK = 256;
 
@@ -191,15 +180,32 @@ __device__ __forceinline__ double warp_sum_d(double v) {
     return v;
 }
 
-__global__ void __launch_bounds__(CS_BLOCK) k_cell_sums(const __grid_constant__ IbmArgs a) {
-    const int4 ck = a.chunks[blockIdx.x];
+template <bool FORCES>
+__device__ __forceinline__ void tri_chunk(const IbmArgs& a, int chunk) {
+    const int4 ck = a.chunks[chunk];
     double s = 0.0, v = 0.0;
     const int t = ck.y + threadIdx.x;
     if (t < ck.z) {
         const int4 tr = a.tris[t];
         const NodeE P0 = load_node(a, tr.x), P1 = load_node(a, tr.y), P2 = load_node(a, tr.z);
-        s = (double)tri_dS(edge(P0, P1), edge(P0, P2), P1.d - P0.d, P2.d - P0.d, a.tri_S0[t]);
+        const float3 e1 = edge(P0, P1), e2 = edge(P0, P2);
+        const float S0t = a.tri_S0[t];
+        const float dSt = tri_dS(e1, e2, P1.d - P0.d, P2.d - P0.d, S0t);
+        s = (double)dSt;
         v = (double)tri_dV6(P0, P1, P2);
+        if constexpr (FORCES) {
+            const float St = S0t + dSt;
+            const float3 third = (1.0f / 3.0f) * (e1 + e2);
+            const float3 w0 = -third, w1 = e1 - third, w2 = e2 - third;
+            const float ww = dot(w0, w0) + dot(w1, w1) + dot(w2, w2);
+            const float c = -2.0f * St / ww;
+            const float sl = a.cells[tr.w].kal * dSt / S0t;
+            a.tA[3 * t] = make_float4(c * w0.x, c * w0.y, c * w0.z, sl);
+            a.tA[3 * t + 1] = make_float4(c * w1.x, c * w1.y, c * w1.z, sl);
+            a.tA[3 * t + 2] = make_float4(c * w2.x, c * w2.y, c * w2.z, sl);
+            const float3 n = cross(e1, e2);
+            a.tN[t] = make_float4(n.x, n.y, n.z, 0.f);
+        }
     }
     __shared__ double sh[2][CS_BLOCK / 32];
     __shared__ bool last;
@@ -211,7 +217,7 @@ __global__ void __launch_bounds__(CS_BLOCK) k_cell_sums(const __grid_constant__ 
     if (threadIdx.x == 0) {
         double S = 0.0, V = 0.0;
         for (int w = 0; w < CS_BLOCK / 32; ++w) { S += sh[0][w]; V += sh[1][w]; }
-        a.partials[blockIdx.x] = make_double2(S, V / 6.0);
+        a.partials[chunk] = make_double2(S, V / 6.0);
         __threadfence();
         const unsigned done = atomicAdd(a.counters + ck.x, 1u);
         last = (done + 1 == (unsigned)ck.w);
@@ -238,9 +244,43 @@ __global__ void __launch_bounds__(CS_BLOCK) k_cell_sums(const __grid_constant__ 
     }
 }
 
+__global__ void __launch_bounds__(CS_BLOCK) k_cell_sums(const __grid_constant__ IbmArgs a) {
+    tri_chunk<false>(a, blockIdx.x);
+}
+
 cudaError_t launch_cell_sums(const IbmArgs& a, cudaStream_t s) {
     if (a.n_chunks <= 0) return cudaSuccess;
     k_cell_sums<<<a.n_chunks, CS_BLOCK, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Element pass: blocks [0, n_chunks) are the triangle chunks above (with their
+// force terms), the blocks after them take one edge per thread: stretching
+// (neo-Hookean bond) and bending of edge (a, b), each evaluated once.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(CS_BLOCK) k_elements(const __grid_constant__ IbmArgs a) {
+    if ((int)blockIdx.x < a.n_chunks) {
+        tri_chunk<true>(a, blockIdx.x);
+        return;
+    }
+    const int e = ((int)blockIdx.x - a.n_chunks) * CS_BLOCK + (int)threadIdx.x;
+    if (e >= a.n_edges) return;
+    const int4 ev = a.edges[e];
+    const float4 r = a.edge_rest[e];   // (L0, theta0, ks, kb)
+    const NodeE A = load_node(a, ev.x), B = load_node(a, ev.y), Cc = load_node(a, ev.z), D = load_node(a, ev.w);
+    const float3 fs = stretch_on_a(A, B, r.x, r.z);
+    a.eS[e] = make_float4(fs.x, fs.y, fs.z, 0.f);
+    float3 fb[4];
+    bend_all(A, B, Cc, D, r.y, r.w, fb);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) a.eB[4 * e + k] = make_float4(fb[k].x, fb[k].y, fb[k].z, 0.f);
+}
+
+cudaError_t launch_elements(const IbmArgs& a, cudaStream_t s) {
+    const int blocks = a.n_chunks + (a.n_edges + CS_BLOCK - 1) / CS_BLOCK;
+    if (blocks <= 0) return cudaSuccess;
+    k_elements<<<blocks, CS_BLOCK, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -276,7 +316,10 @@ __device__ __forceinline__ bool corner(const ChannelDev& C, const Q4& q, int c, 
 }
 
 // ---------------------------------------------------------------------------
-// forces + spreading, eight lanes per IB node
+// node forces + spreading, eight lanes per IB node: each lane gathers the
+// node's share of the elements of some ring slots (incident triangle, edge and
+// opposite edge; fixed order, no atomics), the eight partial sums are added by
+// shuffles, then each lane spreads to one stencil corner.
 // ---------------------------------------------------------------------------
 constexpr int FS_BLOCK = 256;
 
@@ -291,32 +334,20 @@ __global__ void __launch_bounds__(FS_BLOCK) k_forces_spread(const __grid_constan
     const float2 rel = a.cell_rel[cid];
     const float kag_dS = C.kag * rel.x;
     const float kv_dV6 = C.kv * rel.y * (1.0f / 6.0f);
-    const float ks = C.ks, kb = C.kb, kal = C.kal;
-    const NodeE I = load_node(a, i);
 
     float3 F = make_float3(0.f, 0.f, 0.f);
     for (int s = sl; s < k; s += SUB) {
-        const int j = k0 + s;
-        const int2 rg = a.ring[j];
-        const int nc = rg.x;
-        const int nn = a.ring[k0 + (s + 1 == k ? 0 : s + 1)].x;
-        const int np = a.ring[k0 + (s == 0 ? k - 1 : s - 1)].x;
-        const float4 rest = a.ring_rest[j];   // L0(i,cur), theta0(i,cur), theta0(cur,next), S0(i,cur,next)
-        const NodeE Pc = load_node(a, nc), Pn = load_node(a, nn), Pp = load_node(a, np), Po = load_node(a, rg.y);
-
-        // stretching of edge (i, cur)
-        if (i < nc) F = F + stretch_on_a(I, Pc, rest.x, ks);
-        else F = F - stretch_on_a(Pc, I, rest.x, ks);
-        // bending of edge (i, cur): triangle (i, cur, next) and triangle (cur, i, prev)
-        if (i < nc) F = F + bend_on(I, Pc, Pn, Pp, rest.y, kb, 0);
-        else F = F + bend_on(Pc, I, Pp, Pn, rest.y, kb, 1);
-        // bending of the opposite edge (cur, next): triangle (cur, next, i), triangle (next, cur, out)
-        if (nc < nn) F = F + bend_on(Pc, Pn, I, Po, rest.z, kb, 2);
-        else F = F + bend_on(Pn, Pc, Po, I, rest.z, kb, 3);
-        // triangle (i, cur, next), rotated to start at its smallest index
-        if (i < nc && i < nn) F = F + tri_on(I, Pc, Pn, rest.w, kal, kag_dS, kv_dV6, 0);
-        else if (nc < nn) F = F + tri_on(Pc, Pn, I, rest.w, kal, kag_dS, kv_dV6, 2);
-        else F = F + tri_on(Pn, I, Pc, rest.w, kal, kag_dS, kv_dV6, 1);
+        const int4 sr = a.slots[k0 + s];
+        const float4 ta = a.tA[sr.x];
+        const float4 tn = a.tN[sr.w];
+        const float4 es = a.eS[sr.y >> 2];
+        const float4 b1 = a.eB[sr.y];
+        const float4 b2 = a.eB[sr.z];
+        const float sg = (sr.y & 3) == 0 ? 1.0f : -1.0f;   // stretching acts on a, its negative on b
+        const float ca = ta.w + kag_dS;
+        F.x += ((ca * ta.x - kv_dV6 * tn.x) + sg * es.x) + (b1.x + b2.x);
+        F.y += ((ca * ta.y - kv_dV6 * tn.y) + sg * es.y) + (b1.y + b2.y);
+        F.z += ((ca * ta.z - kv_dV6 * tn.z) + sg * es.z) + (b1.z + b2.z);
     }
 #pragma unroll
     for (int o = SUB / 2; o > 0; o >>= 1) {

@@ -72,8 +72,9 @@ struct lb_ctx {
     // immersed boundary, host staging
     std::vector<Q4> hq0, hq;
     std::vector<int4> hinfo;
-    std::vector<int2> hring;
-    std::vector<float4> hring_rest;
+    std::vector<int4> hslots;      // ring CSR: element outputs of each ring slot
+    std::vector<int4> hedges;      // (a, b, c, d)
+    std::vector<float4> hedge_rest;  // (L0, theta0, ks, kb)
     std::vector<int4> htris;
     std::vector<float> htriS0;
     std::vector<int4> hchunks;
@@ -82,13 +83,15 @@ struct lb_ctx {
     std::vector<std::vector<int>> ch_meshes;
     bool committed = false;
     // immersed boundary, device
-    int M = 0, C = 0, T = 0, NCH = 0, K = 0;
+    int M = 0, C = 0, T = 0, NCH = 0, K = 0, E = 0;
     Q4* q[2] = {nullptr, nullptr};
     Q4* q0 = nullptr;
     float4 *xh = nullptr, *xl = nullptr, *dl = nullptr, *F = nullptr;
     int4* info = nullptr;
-    int2* ring = nullptr;
-    float4* ring_rest = nullptr;
+    int4* slots = nullptr;
+    int4* edges = nullptr;
+    float4* edge_rest = nullptr;
+    float4 *eS = nullptr, *eB = nullptr, *tA = nullptr, *tN = nullptr;
     int4* tris = nullptr;
     float* triS0 = nullptr;
     int4* chunks = nullptr;
@@ -202,8 +205,14 @@ IbmArgs ibm_args(const lb_ctx* ctx, int par) {
     a.xh = ctx->xh;
     a.xl = ctx->xl;
     a.dl = ctx->dl;
-    a.ring = ctx->ring;
-    a.ring_rest = ctx->ring_rest;
+    a.slots = ctx->slots;
+    a.edges = ctx->edges;
+    a.edge_rest = ctx->edge_rest;
+    a.n_edges = ctx->E;
+    a.eS = ctx->eS;
+    a.eB = ctx->eB;
+    a.tA = ctx->tA;
+    a.tN = ctx->tN;
     a.F = ctx->F;
     a.tris = ctx->tris;
     a.tri_S0 = ctx->triS0;
@@ -268,7 +277,7 @@ lb_status enqueue_step(lb_ctx* ctx, int par) {
         }
         cudaError_t e = cudaSuccess;
         switch (k) {
-            case 0: e = launch_cell_sums(ia, ctx->stream); break;
+            case 0: e = launch_elements(ia, ctx->stream); break;
             case 1: e = launch_forces_spread(ia, ctx->stream); break;
             case 2: e = launch_stream_collide(la, ctx->k3, ctx->total_blocks, ctx->stream); break;
             case 3: e = launch_interp_advance(ia, ctx->stream); break;
@@ -413,7 +422,8 @@ lb_status commit_ibm(lb_ctx* ctx) {
     ctx->C = (int)ctx->hcells.size();
     ctx->T = (int)ctx->htris.size();
     ctx->NCH = (int)ctx->hchunks.size();
-    ctx->K = (int)ctx->hring.size();
+    ctx->K = (int)ctx->hslots.size();
+    ctx->E = (int)ctx->hedges.size();
     if (ctx->M == 0) return LB_OK;
     auto up = [&](auto** dst, const auto& src) -> cudaError_t {
         using T = typename std::remove_reference<decltype(src)>::type::value_type;
@@ -425,8 +435,13 @@ lb_status commit_ibm(lb_ctx* ctx) {
     LB_CUDA(up(&ctx->q[0], ctx->hq));
     LB_CUDA(up(&ctx->q[1], ctx->hq));
     LB_CUDA(up(&ctx->info, ctx->hinfo));
-    LB_CUDA(up(&ctx->ring, ctx->hring));
-    LB_CUDA(up(&ctx->ring_rest, ctx->hring_rest));
+    LB_CUDA(up(&ctx->slots, ctx->hslots));
+    LB_CUDA(up(&ctx->edges, ctx->hedges));
+    LB_CUDA(up(&ctx->edge_rest, ctx->hedge_rest));
+    LB_CUDA(dalloc(ctx, &ctx->eS, ctx->E));
+    LB_CUDA(dalloc(ctx, &ctx->eB, 4 * (size_t)ctx->E));
+    LB_CUDA(dalloc(ctx, &ctx->tA, 3 * (size_t)ctx->T));
+    LB_CUDA(dalloc(ctx, &ctx->tN, ctx->T));
     LB_CUDA(up(&ctx->tris, ctx->htris));
     LB_CUDA(up(&ctx->triS0, ctx->htriS0));
     LB_CUDA(up(&ctx->chunks, ctx->hchunks));
@@ -723,28 +738,45 @@ lb_status ibm_add_mesh(lb_ctx* ctx, const double* rest_xyz, int n, const int32_t
         q0[i].z = to_fixed(x[3 * i + 2]);
         q0[i].w = 0;
     }
+    // triangles, and for each directed edge u -> v the triangle and position
+    // of u in it; edges (a, b) with a < b in triangle order
+    const int tri0 = (int)ctx->htris.size();
+    std::map<std::pair<int, int>, int> tri_of;    // directed edge -> 3 t + position
+    std::map<std::pair<int, int>, int> edge_of;   // (a, b), a < b -> edge index
+    for (int t = 0; t < nt; ++t) {
+        const int v[3] = {tris[3 * t], tris[3 * t + 1], tris[3 * t + 2]};
+        ctx->htris.push_back(make_int4(node0 + v[0], node0 + v[1], node0 + v[2], cell));
+        ctx->htriS0.push_back((float)tri_area_host(x + 3 * v[0], x + 3 * v[1], x + 3 * v[2]));
+        for (int k = 0; k < 3; ++k) {
+            const int a = v[k], b = v[(k + 1) % 3];
+            tri_of[std::make_pair(a, b)] = 3 * (tri0 + t) + k;
+            if (a < b) {
+                const int c = third[std::make_pair(a, b)], d = third[std::make_pair(b, a)];
+                const double* xa = x + 3 * a;
+                const double* xb = x + 3 * b;
+                const double L0 = std::sqrt((xb[0] - xa[0]) * (xb[0] - xa[0]) + (xb[1] - xa[1]) * (xb[1] - xa[1]) +
+                                            (xb[2] - xa[2]) * (xb[2] - xa[2]));
+                edge_of[std::make_pair(a, b)] = (int)ctx->hedges.size();
+                ctx->hedges.push_back(make_int4(node0 + a, node0 + b, node0 + c, node0 + d));
+                ctx->hedge_rest.push_back(make_float4((float)L0, (float)theta0(a, b), (float)mod->ks, (float)mod->kb));
+            }
+        }
+    }
+    auto edge_id = [&](int u, int v) { return edge_of[std::make_pair(std::min(u, v), std::max(u, v))]; };
     for (int i = 0; i < n; ++i) {
         ctx->hq0.push_back(q0[i]);
         ctx->hq.push_back(q0[i]);
         const std::vector<int>& r = ringv[i];
         const int k = (int)r.size();
-        ctx->hinfo.push_back(make_int4(cell, node0, (int)ctx->hring.size(), k | (ctx->cur << 8)));
+        ctx->hinfo.push_back(make_int4(cell, node0, (int)ctx->hslots.size(), k | (ctx->cur << 8)));
         for (int j = 0; j < k; ++j) {
+            // slot j: triangle (i, nb, nx), edge (i, nb), opposite edge (nb, nx)
             const int nb = r[j], nx = r[(j + 1) % k];
-            const int outer = third[std::make_pair(nx, nb)];
-            const double* xi = x + 3 * i;
-            const double* xn = x + 3 * nb;
-            const double L0 = std::sqrt((xn[0] - xi[0]) * (xn[0] - xi[0]) + (xn[1] - xi[1]) * (xn[1] - xi[1]) +
-                                        (xn[2] - xi[2]) * (xn[2] - xi[2]));
-            ctx->hring.push_back(make_int2(node0 + nb, node0 + outer));
-            ctx->hring_rest.push_back(make_float4((float)L0, (float)theta0(i, nb), (float)theta0(nb, nx),
-                                                  (float)tri_area_host(xi, xn, x + 3 * nx)));
+            const int tk = tri_of[std::make_pair(i, nb)];
+            const int role1 = i < nb ? 0 : 1;    // i is a or b of edge (i, nb)
+            const int role2 = nb < nx ? 2 : 3;   // i is c or d of edge (nb, nx)
+            ctx->hslots.push_back(make_int4(tk, 4 * edge_id(i, nb) + role1, 4 * edge_id(nb, nx) + role2, tk / 3));
         }
-    }
-    const int tri0 = (int)ctx->htris.size();
-    for (int t = 0; t < nt; ++t) {
-        ctx->htris.push_back(make_int4(node0 + tris[3 * t], node0 + tris[3 * t + 1], node0 + tris[3 * t + 2], cell));
-        ctx->htriS0.push_back((float)tri_area_host(x + 3 * tris[3 * t], x + 3 * tris[3 * t + 1], x + 3 * tris[3 * t + 2]));
     }
     CellDev cd;
     std::memset(&cd, 0, sizeof(cd));

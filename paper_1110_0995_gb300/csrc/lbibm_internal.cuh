@@ -30,7 +30,16 @@
 //                                 reference node's displacement
 //                float4 r0        rest position relative to the reference node
 //                int4 info        (cell, reference node, ring offset, valence | channel << 8)
-//   ring CSR     int2 (neighbour, outer vertex), float4 rest data per slot
+//   ring CSR     int4 per slot of a node's ring: where the node's share of the
+//                incident triangle, edge and opposite edge lies in the
+//                element outputs below
+//   edges        int4 (a, b, c, d), a < b: edge (a, b) between triangles
+//                (a, b, c) and (b, a, d); float4 (L0, theta0, ks, kb)
+//   element outputs (rewritten every step, read by the node gather):
+//                float4 eS[E]     stretching force on a (on b: its negative)
+//                float4 eB[4E]    bending force on a, b, c, d
+//                float4 tA[3T]    area direction a_k of vertex k, .w = kal dS_t/S0_t
+//                float4 tN[T]     unnormalised outward normal of the triangle
 #pragma once
 
 #include <cuda_runtime.h>
@@ -146,8 +155,14 @@ struct IbmArgs {
     float4* xl;           // [M]
     float4* dl;           // [M]
     const float4* r0;     // [M]
-    const int2* ring;     // [K] (neighbour, outer)
-    const float4* ring_rest;  // [K] (L0, theta0 edge, theta0 opposite edge, S0 triangle)
+    const int4* slots;    // [K] (3 t + role in t, 4 e + role in e, 4 e' + role in e', t) per ring slot
+    const int4* edges;    // [E] (a, b, c, d)
+    const float4* edge_rest;  // [E] (L0, theta0, ks, kb)
+    int n_edges;
+    float4* eS;           // [E]
+    float4* eB;           // [4E]
+    float4* tA;           // [3T]
+    float4* tN;           // [T]
     float4* F;            // [M] last node forces
     // area / volume reduction
     const int4* tris;     // [T] (a, b, c, cell) global node indices
@@ -217,6 +232,7 @@ cudaError_t launch_diagnostics(const LatticeArgs& a, int ch_index, double* parti
                                cudaStream_t s);
 
 cudaError_t launch_cell_sums(const IbmArgs& a, cudaStream_t s);
+cudaError_t launch_elements(const IbmArgs& a, cudaStream_t s);
 cudaError_t launch_forces_spread(const IbmArgs& a, cudaStream_t s);
 cudaError_t launch_interp_advance(const IbmArgs& a, cudaStream_t s);
 cudaError_t launch_prepare_nodes(const IbmArgs& a, cudaStream_t s);
