@@ -137,6 +137,22 @@ lb_status lb_step(lb_ctx* ctx, int n_steps);
 lb_status lb_set_kernel_config(lb_ctx* ctx, int nodes_per_thread, int block_size);
 lb_status lb_get_kernel_config(lb_ctx* ctx, int* nodes_per_thread, int* block_size);
 
+/* Step schedule.  overlapped = 1: when the context has IB meshes
+ * and the stream-collide variant has one node per thread, each cycle runs the
+ * immersed-boundary kernels on a second, higher-priority stream concurrently
+ * with the stream-collide of every 32-node group that no IB point can reach
+ * in that step, then updates the reachable groups; the results equal the
+ * sequential cycle as long as no IB point moves one lattice unit or more in
+ * one step (a spreading target outside the reachable set is counted and
+ * reported by lb_diagnostics as LB_ERR_NUMERIC).  overlapped = 0 (default):
+ * the four kernels run one after another.  On GB300 the overlapped schedule
+ * is currently slower: the latency-bound IB kernels hold SM slots that the
+ * concurrent stream-collide needs.  Per-kernel timing (lb_set_timing) always
+ * uses the sequential schedule.  lb_get_schedule reports the schedule the
+ * next lb_step will use. */
+lb_status lb_set_schedule(lb_ctx* ctx, int overlapped);
+lb_status lb_get_schedule(lb_ctx* ctx, int* overlapped);
+
 /* Autotuner: times every supported stream-collide variant on this context's
  * lattice (`repeats` launches each, CUDA events), selects the fastest and
  * returns it with its mean time per launch in ms.  Only before the first

@@ -172,7 +172,12 @@ __device__ __forceinline__ float tri_dV6(const NodeE& P0, const NodeE& P1, const
 //   volume: F_k = -kv (dV/V0) n_t / 6, n_t = (x_1 - x_0) x (x_2 - x_0).
 // The cell totals dS/S0 and dV/V0 are applied in the node gather.
 // ---------------------------------------------------------------------------
-constexpr int CS_BLOCK = 256;
+// Block size and register budget of the immersed-boundary kernels: 128
+// threads within 64 registers (8192 per block), so that one such block fits
+// in what a retiring stream-collide block frees on an SM that is full of
+// them (6144 registers plus the 4096 left over; overlapped schedule).
+constexpr int CS_BLOCK = 128;
+constexpr int IB_MIN_BLOCKS = 8;
 
 __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
@@ -184,15 +189,14 @@ template <bool FORCES>
 __device__ __forceinline__ void tri_chunk(const IbmArgs& a, int chunk) {
     const int4 ck = a.chunks[chunk];
     double s = 0.0, v = 0.0;
-    const int t = ck.y + threadIdx.x;
-    if (t < ck.z) {
+    for (int t = ck.y + (int)threadIdx.x; t < ck.z; t += CS_BLOCK) {
         const int4 tr = a.tris[t];
         const NodeE P0 = load_node(a, tr.x), P1 = load_node(a, tr.y), P2 = load_node(a, tr.z);
         const float3 e1 = edge(P0, P1), e2 = edge(P0, P2);
         const float S0t = a.tri_S0[t];
         const float dSt = tri_dS(e1, e2, P1.d - P0.d, P2.d - P0.d, S0t);
-        s = (double)dSt;
-        v = (double)tri_dV6(P0, P1, P2);
+        s += (double)dSt;
+        v += (double)tri_dV6(P0, P1, P2);
         if constexpr (FORCES) {
             const float St = S0t + dSt;
             const float3 third = (1.0f / 3.0f) * (e1 + e2);
@@ -244,7 +248,7 @@ __device__ __forceinline__ void tri_chunk(const IbmArgs& a, int chunk) {
     }
 }
 
-__global__ void __launch_bounds__(CS_BLOCK) k_cell_sums(const __grid_constant__ IbmArgs a) {
+__global__ void __launch_bounds__(CS_BLOCK, IB_MIN_BLOCKS) k_cell_sums(const __grid_constant__ IbmArgs a) {
     tri_chunk<false>(a, blockIdx.x);
 }
 
@@ -259,7 +263,7 @@ cudaError_t launch_cell_sums(const IbmArgs& a, cudaStream_t s) {
 // force terms), the blocks after them take one edge per thread: stretching
 // (neo-Hookean bond) and bending of edge (a, b), each evaluated once.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(CS_BLOCK) k_elements(const __grid_constant__ IbmArgs a) {
+__global__ void __launch_bounds__(CS_BLOCK, IB_MIN_BLOCKS) k_elements(const __grid_constant__ IbmArgs a) {
     if ((int)blockIdx.x < a.n_chunks) {
         tri_chunk<true>(a, blockIdx.x);
         return;
@@ -315,26 +319,110 @@ __device__ __forceinline__ bool corner(const ChannelDev& C, const Q4& q, int c, 
     return ok;
 }
 
+// Stencil set of the overlapped schedule.  A point at X with base node
+// floor(X) = (ix, iy, iz) has its stencil in [ix, ix+1]^3 now and, as long as
+// it moves less than one lattice unit per step, in [ix-1, ix+2]^3 after the
+// next advance.  Lane sl (0..7) of the point marks the 32-node groups of the
+// nodes of that box in the rows (dy, dz) = (c & 3, c >> 2) - 1, c = 2 sl, 2 sl + 1.
+__device__ __forceinline__ void mark_box(const ChannelDev& C, const Q4& q, int sl, uint8_t* map) {
+    const int bx = (int)(q.x >> FIX_BITS), by = (int)(q.y >> FIX_BITS), bz = (int)(q.z >> FIX_BITS);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int c = 2 * sl + h;
+        int y = by + (c & 3) - 1, z = bz + (c >> 2) - 1;
+        if (y < 0 || y >= C.ny) {
+            if (!C.per[1]) continue;
+            y = ((y % C.ny) + C.ny) % C.ny;
+        }
+        if (z < 0 || z >= C.nz) {
+            if (!C.per[2]) continue;
+            z = ((z % C.nz) + C.nz) % C.nz;
+        }
+        const long long row = C.base + (long long)C.nx * (y + (long long)C.ny * z);
+        long long last = -1;
+#pragma unroll
+        for (int dx = -1; dx <= 2; ++dx) {
+            int x = bx + dx;
+            if (x < 0 || x >= C.nx) {
+                if (!C.per[0]) continue;
+                x = ((x % C.nx) + C.nx) % C.nx;
+            }
+            const long long g = (row + x) >> 5;
+            if (g != last) map[g] = 1;
+            last = g;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(128, IB_MIN_BLOCKS) k_mark_stencils(const __grid_constant__ IbmArgs a, uint8_t* map) {
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) / SUB;
+    if (i >= a.n_nodes) return;
+    const int chn = a.info[i].w >> 8;
+    mark_box(chan(a, chn), (a.par ? a.qb : a.qa)[i], threadIdx.x & (SUB - 1), map);
+}
+
+cudaError_t launch_mark_stencils(const IbmArgs& a, uint8_t* map, cudaStream_t s) {
+    if (a.n_nodes <= 0) return cudaSuccess;
+    const long long threads = (long long)a.n_nodes * SUB;
+    k_mark_stencils<<<(unsigned)((threads + 127) / 128), 128, 0, s>>>(a, map);
+    return cudaGetLastError();
+}
+
+// Marked groups of a byte map as a list (order unspecified), one atomic per warp.
+__global__ void __launch_bounds__(128, IB_MIN_BLOCKS) k_compact_groups(const uint8_t* map, int n_groups, int* list, int* count) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool on = g < n_groups && map[g] != 0;
+    const unsigned b = __ballot_sync(0xffffffffu, on);
+    if (!b) return;
+    const int lane = threadIdx.x & 31;
+    int base = 0;
+    if (lane == 0) base = atomicAdd(count, __popc(b));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (on) list[base + __popc(b & ((1u << lane) - 1u))] = g;
+}
+
+cudaError_t launch_compact_groups(const uint8_t* map, int n_groups, int* list, int* count, cudaStream_t s) {
+    if (n_groups <= 0) return cudaSuccess;
+    k_compact_groups<<<(n_groups + 127) / 128, 128, 0, s>>>(map, n_groups, list, count);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // node forces + spreading, eight lanes per IB node: each lane gathers the
 // node's share of the elements of some ring slots (incident triangle, edge and
 // opposite edge; fixed order, no atomics), the eight partial sums are added by
 // shuffles, then each lane spreads to one stencil corner.
 // ---------------------------------------------------------------------------
-constexpr int FS_BLOCK = 256;
+constexpr int FS_BLOCK = 128;
 
-__global__ void __launch_bounds__(FS_BLOCK) k_forces_spread(const __grid_constant__ IbmArgs a) {
+__global__ void __launch_bounds__(FS_BLOCK, IB_MIN_BLOCKS) k_forces_spread(const __grid_constant__ IbmArgs a) {
     const int i = (blockIdx.x * FS_BLOCK + threadIdx.x) / SUB;
     const int sl = threadIdx.x & (SUB - 1);
     if (i >= a.n_nodes) return;   // whole groups of eight lanes leave together
     const unsigned smask = 0xffu << (threadIdx.x & 24);
     const int4 inf = a.info[i];
+    const Q4 qi = (a.par ? a.qb : a.qa)[i];
     const int cid = inf.x, k0 = inf.z, k = inf.w & 0xff, chn = inf.w >> 8;
     const CellDev& C = a.cells[cid];
     const float2 rel = a.cell_rel[cid];
+
+    // this lane's stencil corner (Sec. 2.2 step 3), resolved before the
+    // gather so that the mask load is in flight with it
+    const ChannelDev Ch = chan(a, chn);
+    long long g;
+    float w;
+    bool hit = corner(Ch, qi, sl, g, w);
+    if (hit) hit = !((__ldg(a.mask + (g >> 5)) >> (g & 31)) & 1u);
+    if (a.dcur) {
+        // overlapped schedule: the target must be in this step's stencil set
+        // (it is whenever no point moved a lattice unit in one step), and the
+        // next step's set is marked around the current position
+        if (hit && !__ldg(a.dcur + (g >> 5))) atomicAdd(a.sched_err, 1);
+        mark_box(Ch, qi, sl, a.dmark);
+    }
+
     const float kag_dS = C.kag * rel.x;
     const float kv_dV6 = C.kv * rel.y * (1.0f / 6.0f);
-
     float3 F = make_float3(0.f, 0.f, 0.f);
     for (int s = sl; s < k; s += SUB) {
         const int4 sr = a.slots[k0 + s];
@@ -357,12 +445,7 @@ __global__ void __launch_bounds__(FS_BLOCK) k_forces_spread(const __grid_constan
     }
     if (sl == 0) a.F[i] = make_float4(F.x, F.y, F.z, 0.f);
 
-    // spreading (Sec. 2.2 step 3): g(x) += w(x - X) F, one stencil corner per lane
-    const ChannelDev Ch = chan(a, chn);
-    long long g;
-    float w;
-    bool hit = corner(Ch, (a.par ? a.qb : a.qa)[i], sl, g, w);
-    if (hit) hit = !((__ldg(a.mask + (g >> 5)) >> (g & 31)) & 1u);
+    // spreading: g(x) += w(x - X) F at this lane's corner
     if (hit) atomicAdd((a.par ? a.g1 : a.g0) + g, make_float4(w * F.x, w * F.y, w * F.z, 0.f));
     // flag the 32-node groups that received force: one store per distinct group of this warp
     const long long grp = hit ? (g >> 5) : -1;
@@ -384,7 +467,7 @@ cudaError_t launch_forces_spread(const IbmArgs& a, cudaStream_t s) {
 // node with identical arithmetic, so the relative coordinates of the next step
 // are formed without a second pass.  Obstacle nodes hold u = 0.
 // ---------------------------------------------------------------------------
-constexpr int IA_BLOCK = 256;
+constexpr int IA_BLOCK = 128;
 
 __device__ __forceinline__ void write_rel(const IbmArgs& a, int i, const Q4& q, const Q4& qr, const Q4& q0,
                                           const Q4& q0r) {
@@ -406,7 +489,7 @@ __device__ __forceinline__ float3 corner_u(const IbmArgs& a, const ChannelDev& C
     return make_float3(w * u.x, w * u.y, w * u.z);
 }
 
-__global__ void __launch_bounds__(IA_BLOCK) k_interp_advance(const __grid_constant__ IbmArgs a) {
+__global__ void __launch_bounds__(IA_BLOCK, IB_MIN_BLOCKS) k_interp_advance(const __grid_constant__ IbmArgs a) {
     const int i = (blockIdx.x * IA_BLOCK + threadIdx.x) / SUB;
     const int sl = threadIdx.x & (SUB - 1);
     if (i >= a.n_nodes) return;

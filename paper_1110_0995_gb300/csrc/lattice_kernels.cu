@@ -366,15 +366,15 @@ template <class S, int NPT, int BS> struct K3MinBlocks {
     static constexpr int value = threads / BS > 0 ? threads / BS : 1;
 };
 
-template <class S, int NPT, int BS>
-__global__ void __launch_bounds__(BS, K3MinBlocks<S, NPT, BS>::value) k_stream_collide(const __grid_constant__ LatticeArgs a) {
-    const int b = blockIdx.x;
-    int c = 0;
-    for (int k = 1; k < a.n_ch; ++k)
-        if (b >= chan(a, k).blk0) c = k;
-    const ChannelDev C = chan(a, c);   // registers: read once from the parameter bank
-    const int lane = threadIdx.x & 31;
-    const int p0 = ((b - C.blk0) * BS + (int)threadIdx.x) * NPT;   // first channel-local node of this thread
+// Schedules of one stream-collide launch: every node (SC_ALL); the bulk, i.e.
+// every 32-node group outside the step's stencil set (SC_BULK); or the groups
+// of the stencil set from a list (SC_LIST).  Bulk groups carry no IB force in
+// this step and none in the previous one, so their flag loads are skipped.
+enum : int { SC_ALL = 0, SC_BULK = 1, SC_LIST = 2 };
+
+// One thread's NPT nodes starting at channel-local node p0.
+template <class S, int NPT, int MODE>
+__device__ __forceinline__ void sc_nodes(const LatticeArgs& a, const ChannelDev& C, int p0, int lane) {
     const long long gp0 = C.base + p0;
     const int gi0 = (int)gp0;      // the padded node count of a context is below 2^31
     const int grp = gi0 >> 5;
@@ -382,8 +382,8 @@ __global__ void __launch_bounds__(BS, K3MinBlocks<S, NPT, BS>::value) k_stream_c
     uint8_t* fl_prev = par ? a.fl0 : a.fl1;
     const bool inr = p0 < C.n;
     // flags first: their latency overlaps the population loads below
-    const uint8_t fcur = __ldg((par ? a.fl1 : a.fl0) + grp);
-    const uint8_t fprev = __ldg(fl_prev + grp);
+    const uint8_t fcur = MODE == SC_BULK ? (uint8_t)0 : __ldg((par ? a.fl1 : a.fl0) + grp);
+    const uint8_t fprev = MODE == SC_BULK ? (uint8_t)0 : __ldg(fl_prev + grp);
     const uint8_t fslow = inr ? __ldg(a.slow + grp) : (uint8_t)0;
     const S* src = (const S*)(par ? a.h1 : a.h0);
     S* dst = (S*)(par ? a.h0 : a.h1);
@@ -405,6 +405,9 @@ __global__ void __launch_bounds__(BS, K3MinBlocks<S, NPT, BS>::value) k_stream_c
     const float om = C.omega, fp = C.fpre;
     const float4* gcur = par ? a.g1 : a.g0;
     float4* gprev = par ? a.g0 : a.g1;
+    // stencil groups mostly carry force: load it with the populations
+    float4 gpre = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (MODE == SC_LIST && NPT == 1 && inr) gpre = gcur[gi0];
 
     // phase 2 (converged warp): place the loaded values
     float h[NPT][Q];
@@ -427,7 +430,7 @@ __global__ void __launch_bounds__(BS, K3MinBlocks<S, NPT, BS>::value) k_stream_c
         for (int k = 0; k < NPT; ++k) {
             float gx = C.G[0], gy = C.G[1], gz = C.G[2];
             if (forced) {
-                const float4 g = gcur[gi0 + k];
+                const float4 g = (MODE == SC_LIST && NPT == 1) ? gpre : gcur[gi0 + k];
                 gx += g.x; gy += g.y; gz += g.z;
             }
             m[k] = macro(h[k], gx, gy, gz);
@@ -462,6 +465,63 @@ __global__ void __launch_bounds__(BS, K3MinBlocks<S, NPT, BS>::value) k_stream_c
     // step's flag after every lane of the warp has consumed it
     __syncwarp();
     if (prevf && (gp0 & 31) == 0) fl_prev[grp] = 0;
+}
+
+template <class S, int NPT, int BS>
+__global__ void __launch_bounds__(BS, K3MinBlocks<S, NPT, BS>::value) k_stream_collide(const __grid_constant__ LatticeArgs a) {
+    const int b = blockIdx.x;
+    int c = 0;
+    for (int k = 1; k < a.n_ch; ++k)
+        if (b >= chan(a, k).blk0) c = k;
+    const ChannelDev C = chan(a, c);   // registers: read once from the parameter bank
+    const int lane = threadIdx.x & 31;
+    const int p0 = ((b - C.blk0) * BS + (int)threadIdx.x) * NPT;   // first channel-local node of this thread
+    sc_nodes<S, NPT, SC_ALL>(a, C, p0, lane);
+}
+
+// Bulk of the overlapped schedule (one node per thread; a warp is one group).
+// Launched with dynamic shared memory it does not use, sized so that fewer
+// blocks are resident per SM than registers would allow: the room left over
+// takes the blocks of the immersed-boundary kernels running concurrently.
+template <class S, int BS>
+__global__ void __launch_bounds__(BS, K3MinBlocks<S, 1, BS>::value) k_stream_collide_bulk(const __grid_constant__ LatticeArgs a) {
+    const int b = blockIdx.x;
+    int c = 0;
+    for (int k = 1; k < a.n_ch; ++k)
+        if (b >= chan(a, k).blk0) c = k;
+    const ChannelDev C = chan(a, c);
+    const int lane = threadIdx.x & 31;
+    const int p0 = (b - C.blk0) * BS + (int)threadIdx.x;
+    if (__ldg(a.dmap + ((C.base + p0) >> 5))) return;   // a stencil group: the list launch takes it
+    sc_nodes<S, 1, SC_BULK>(a, C, p0, lane);
+}
+
+// Stencil groups of the overlapped schedule: warp w of the grid takes list
+// entry `first + w`; k_stream_collide_list_rest takes the entries beyond the
+// first grid's warps, if any (a loop, which costs registers, so kept apart).
+template <class S>
+__device__ __forceinline__ void sc_list_entry(const LatticeArgs& a, int li, int lane) {
+    const long long g0 = (long long)__ldg(a.dlist + li) * GROUP;
+    int c = 0;
+    for (int k = 1; k < a.n_ch; ++k)
+        if (g0 >= chan(a, k).base) c = k;
+    const ChannelDev C = chan(a, c);
+    sc_nodes<S, 1, SC_LIST>(a, C, (int)(g0 - C.base) + lane, lane);
+}
+
+template <class S, int BS>
+__global__ void __launch_bounds__(BS, 1024 / BS) k_stream_collide_list(const __grid_constant__ LatticeArgs a) {
+    const int li = (int)(blockIdx.x * BS + threadIdx.x) >> 5;
+    if (li >= __ldg(a.dcount)) return;
+    sc_list_entry<S>(a, li, threadIdx.x & 31);
+}
+
+template <class S, int BS>
+__global__ void __launch_bounds__(BS) k_stream_collide_list_rest(const __grid_constant__ LatticeArgs a, int first) {
+    const int nl = __ldg(a.dcount);
+    const int nw = (int)(gridDim.x * BS) >> 5;
+    for (int li = first + ((int)(blockIdx.x * BS + threadIdx.x) >> 5); li < nl; li += nw)
+        sc_list_entry<S>(a, li, threadIdx.x & 31);
 }
 
 // ---------------------------------------------------------------------------
@@ -778,6 +838,50 @@ static cudaError_t launch_sc_typed(const LatticeArgs& a, K3Config c, int blocks,
     }
 #undef LBIBM_CASE
     return cudaErrorInvalidConfiguration;
+}
+
+template <class S>
+static cudaError_t launch_sc_split(const LatticeArgs& a, int bs, int mode, int blocks, size_t smem, cudaStream_t s) {
+    if (mode == SC_BULK) {
+        if (bs == 128) k_stream_collide_bulk<S, 128><<<blocks, 128, smem, s>>>(a);
+        else k_stream_collide_bulk<S, 256><<<blocks, 256, smem, s>>>(a);
+    } else if (mode == SC_LIST) {
+        if (bs == 128) k_stream_collide_list<S, 128><<<blocks, 128, 0, s>>>(a);
+        else k_stream_collide_list<S, 256><<<blocks, 256, 0, s>>>(a);
+    } else {
+        // entries from `smem` on (the warps of the first list grid)
+        if (bs == 128) k_stream_collide_list_rest<S, 128><<<blocks, 128, 0, s>>>(a, (int)smem);
+        else k_stream_collide_list_rest<S, 256><<<blocks, 256, 0, s>>>(a, (int)smem);
+    }
+    return cudaGetLastError();
+}
+
+template <class S>
+static cudaError_t prepare_bulk_typed(int max_smem) {
+    cudaError_t e = cudaFuncSetAttribute(k_stream_collide_bulk<S, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_stream_collide_bulk<S, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+}
+
+cudaError_t prepare_bulk(int storage, int max_smem) {
+    if (storage == 0) return prepare_bulk_typed<float>(max_smem);
+    if (storage == 1) return prepare_bulk_typed<__half>(max_smem);
+    return prepare_bulk_typed<__nv_bfloat16>(max_smem);
+}
+
+const void* stream_collide_bulk_func(int storage, int bs) {
+    if (storage == 0) return bs == 128 ? (const void*)k_stream_collide_bulk<float, 128> : (const void*)k_stream_collide_bulk<float, 256>;
+    if (storage == 1) return bs == 128 ? (const void*)k_stream_collide_bulk<__half, 128> : (const void*)k_stream_collide_bulk<__half, 256>;
+    return bs == 128 ? (const void*)k_stream_collide_bulk<__nv_bfloat16, 128> : (const void*)k_stream_collide_bulk<__nv_bfloat16, 256>;
+}
+
+cudaError_t launch_stream_collide_split(const LatticeArgs& a, int bs, int mode, int blocks, size_t smem,
+                                        cudaStream_t s) {
+    if (blocks <= 0) return cudaSuccess;
+    if (bs != 128 && bs != 256) return cudaErrorInvalidConfiguration;
+    if (a.storage == 0) return launch_sc_split<float>(a, bs, mode, blocks, smem, s);
+    if (a.storage == 1) return launch_sc_split<__half>(a, bs, mode, blocks, smem, s);
+    return launch_sc_split<__nv_bfloat16>(a, bs, mode, blocks, smem, s);
 }
 
 cudaError_t launch_stream_collide(const LatticeArgs& a, K3Config cfg, int total_blocks, cudaStream_t s) {

@@ -106,6 +106,21 @@ struct lb_ctx {
     long long step = 0;
     bool started = false;
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    // overlapped schedule: the immersed-boundary chain on a second stream of
+    // higher priority, concurrent with the bulk of the stream-collide
+    bool overlap = false;          // chosen by the caller (lb_set_schedule)
+    bool dvalid = false;           // the stencil set of the next step is current
+    cudaStream_t ib_stream = nullptr;
+    cudaEvent_t ev_fork[2] = {nullptr, nullptr}, ev_join[2] = {nullptr, nullptr};
+    cudaEvent_t ev_fork2[2] = {nullptr, nullptr}, ev_join2[2] = {nullptr, nullptr};
+    cudaGraphExec_t gexec_ov[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};   // [parity][leading interpolation]
+    uint8_t* dmap[2] = {nullptr, nullptr};
+    int* dlist[2] = {nullptr, nullptr};
+    int* dcount = nullptr;         // [2]
+    int* sched_err = nullptr;
+    int list_blocks = 0;
+    int bulk_res = 10;             // resident bulk blocks per SM (128 threads)
+    long long smem_per_sm = 0;
     // timing
     int timing = 0;          // bit k: record events around kernel class k (no graph)
     double ms[4] = {0, 0, 0, 0};
@@ -185,10 +200,13 @@ LatticeArgs lattice_args(const lb_ctx* ctx, int par) {
     a.fl1 = ctx->fl[1];
     a.u = ctx->u;
     a.n_groups = ctx->n_groups;
+    a.dmap = ctx->dmap[par];
+    a.dlist = ctx->dlist[par];
+    a.dcount = ctx->dcount ? ctx->dcount + par : nullptr;
     return a;
 }
 
-IbmArgs ibm_args(const lb_ctx* ctx, int par) {
+IbmArgs ibm_args(const lb_ctx* ctx, int par, bool overlapped = false) {
     IbmArgs a;
     std::memset(&a, 0, sizeof(a));
     for (size_t k = 0; k < ctx->ch.size() && k < (size_t)MAXCH_P; ++k) a.chp[k] = ctx->ch[k].d;
@@ -228,6 +246,9 @@ IbmArgs ibm_args(const lb_ctx* ctx, int par) {
     a.fl0 = ctx->fl[0];
     a.fl1 = ctx->fl[1];
     a.u = ctx->u;
+    a.dmark = ctx->dmap[1 - par];
+    a.dcur = overlapped ? ctx->dmap[par] : nullptr;
+    a.sched_err = ctx->sched_err;
     return a;
 }
 
@@ -295,9 +316,12 @@ lb_status build_graphs(lb_ctx* ctx) {
     for (int par = 0; par < 2; ++par) {
         if (ctx->gexec[par]) continue;
         cudaGraph_t g = nullptr;
+        long long saved[4];
+        std::copy(ctx->launches, ctx->launches + 4, saved);   // capture launches nothing
         LB_CUDA(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
         lb_status s = enqueue_step(ctx, par);
         cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+        std::copy(saved, saved + 4, ctx->launches);
         if (s != LB_OK) return s;
         if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamEndCapture");
         e = cudaGraphInstantiate(&ctx->gexec[par], g, 0);
@@ -307,12 +331,131 @@ lb_status build_graphs(lb_ctx* ctx) {
     return LB_OK;
 }
 
-void drop_graphs(lb_ctx* ctx) {
+// One cycle in the overlapped schedule.  Only the 32-node groups of the
+// stencil set D (the groups any IB point can reach within one step, computed
+// during the previous step) depend on this step's IB forces, so
+//   ib stream:   [interpolation + advance of the previous step], elements,
+//                forces + spreading (which also marks the next step's D),
+//                compaction of the next D into a list
+//   main stream: stream-collide of every group outside D
+// run concurrently; after the join the groups of D are updated.  The result is
+// the same as the sequential cycle: D contains every group that receives force
+// or is interpolated, and the spreading kernel counts any target outside D.
+// Unused dynamic shared memory per bulk block that caps the bulk at
+// bulk_res resident 128-thread blocks per SM, keeping 8 KB for the blocks of
+// the immersed-boundary kernels (0 when registers cap it first).
+size_t bulk_smem(const lb_ctx* ctx) {
+    const int res = std::max(1, ctx->bulk_res * 128 / ctx->k3.bs);
+    const long long per_block = (ctx->smem_per_sm - 8192) / res - 1024;
+    return per_block > 0 ? (size_t)per_block : 0;
+}
+
+size_t bulk_smem_max(const lb_ctx* ctx) {
+    const long long per_block = (ctx->smem_per_sm - 8192) - 1024;
+    return per_block > 0 ? (size_t)per_block : 0;
+}
+
+lb_status enqueue_step_overlap(lb_ctx* ctx, int par, bool lead_interp) {
+    const LatticeArgs la = lattice_args(ctx, par);
+    const IbmArgs ia = ibm_args(ctx, par, true);
+    const long long NG = ctx->Ntot / GROUP;
+    cudaStream_t m = ctx->stream, ib = ctx->ib_stream;
+    LB_CUDA(cudaEventRecord(ctx->ev_fork[par], m));
+    LB_CUDA(cudaStreamWaitEvent(ib, ctx->ev_fork[par], 0));
+    LB_CUDA(cudaMemsetAsync(ctx->dmap[1 - par], 0, (size_t)NG, ib));
+    LB_CUDA(cudaMemsetAsync(ctx->dcount + (1 - par), 0, sizeof(int), ib));
+    cudaError_t e = cudaSuccess;
+    if (lead_interp && e == cudaSuccess) e = launch_interp_advance(ibm_args(ctx, 1 - par), ib);
+    if (e == cudaSuccess) e = launch_elements(ia, ib);
+    if (e == cudaSuccess) e = launch_forces_spread(ia, ib);
+    if (e == cudaSuccess) e = launch_compact_groups(ctx->dmap[1 - par], (int)NG, ctx->dlist[1 - par], ctx->dcount + (1 - par), ib);
+    if (e == cudaSuccess) e = launch_stream_collide_split(la, ctx->k3.bs, 1, ctx->total_blocks, bulk_smem(ctx), m);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "kernel launch");
+    LB_CUDA(cudaEventRecord(ctx->ev_join[par], ib));
+    LB_CUDA(cudaStreamWaitEvent(m, ctx->ev_join[par], 0));
+    // stencil groups: one warp per list entry on the main stream; entries
+    // beyond that grid (none on the workloads here) by a looping grid on the
+    // second stream, concurrently
+    const int covered = ctx->list_blocks * ctx->k3.bs / 32;
+    LB_CUDA(cudaEventRecord(ctx->ev_fork2[par], m));
+    LB_CUDA(cudaStreamWaitEvent(ib, ctx->ev_fork2[par], 0));
+    e = launch_stream_collide_split(la, ctx->k3.bs, 3, ctx->sm_count, (size_t)covered, ib);
+    if (e == cudaSuccess) e = launch_stream_collide_split(la, ctx->k3.bs, 2, ctx->list_blocks, 0, m);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "kernel launch");
+    LB_CUDA(cudaEventRecord(ctx->ev_join2[par], ib));
+    LB_CUDA(cudaStreamWaitEvent(m, ctx->ev_join2[par], 0));
+    return LB_OK;
+}
+
+bool use_overlap(const lb_ctx* ctx) {
+    const long long m = ctx->committed ? ctx->M : (long long)ctx->hq0.size();
+    return ctx->overlap && m > 0 && ctx->k3.npt == 1 && ctx->timing == 0 && ctx->ib_stream != nullptr;
+}
+
+lb_status build_graphs_overlap(lb_ctx* ctx) {
     for (int par = 0; par < 2; ++par)
+        for (int lead = 0; lead < 2; ++lead) {
+            if (ctx->gexec_ov[par][lead]) continue;
+            cudaGraph_t g = nullptr;
+            LB_CUDA(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+            lb_status s = enqueue_step_overlap(ctx, par, lead != 0);
+            cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+            if (s != LB_OK) return s;
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamEndCapture");
+            // every kernel but the bulk stream-collide at the highest priority, so
+            // that the immersed-boundary chain takes SM slots as bulk blocks retire
+            int lo = 0, hi = 0;
+            cudaDeviceGetStreamPriorityRange(&lo, &hi);
+            const void* bulk = stream_collide_bulk_func((int)ctx->storage, ctx->k3.bs);
+            size_t nn = 0;
+            cudaGraphGetNodes(g, nullptr, &nn);
+            std::vector<cudaGraphNode_t> nodes(nn);
+            if (nn) cudaGraphGetNodes(g, nodes.data(), &nn);
+            for (cudaGraphNode_t nd : nodes) {
+                cudaGraphNodeType t;
+                if (cudaGraphNodeGetType(nd, &t) != cudaSuccess || t != cudaGraphNodeTypeKernel) continue;
+                cudaKernelNodeParams kp;
+                if (cudaGraphKernelNodeGetParams(nd, &kp) != cudaSuccess) continue;
+                cudaLaunchAttributeValue v;
+                std::memset(&v, 0, sizeof(v));
+                v.priority = kp.func == bulk ? lo : hi;
+                cudaGraphKernelNodeSetAttribute(nd, cudaLaunchAttributePriority, &v);
+            }
+            cudaGetLastError();
+            // node priorities only take effect with this flag
+            e = cudaGraphInstantiateWithFlags(&ctx->gexec_ov[par][lead], g, cudaGraphInstantiateFlagUseNodePriority);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphInstantiate");
+        }
+    return LB_OK;
+}
+
+// Stencil set of the coming step from the current positions (after setup,
+// after positions or a checkpoint were loaded, or after sequential steps).
+lb_status prepare_stencil_set(lb_ctx* ctx) {
+    const int par = (int)(ctx->step & 1);
+    const long long NG = ctx->Ntot / GROUP;
+    LB_CUDA(cudaMemsetAsync(ctx->dmap[par], 0, (size_t)NG, ctx->stream));
+    LB_CUDA(cudaMemsetAsync(ctx->dcount + par, 0, sizeof(int), ctx->stream));
+    LB_CUDA(launch_mark_stencils(ibm_args(ctx, par), ctx->dmap[par], ctx->stream));
+    LB_CUDA(launch_compact_groups(ctx->dmap[par], (int)NG, ctx->dlist[par], ctx->dcount + par, ctx->stream));
+    ctx->launches[1] += 2;
+    ctx->dvalid = true;
+    return LB_OK;
+}
+
+void drop_graphs(lb_ctx* ctx) {
+    for (int par = 0; par < 2; ++par) {
         if (ctx->gexec[par]) {
             cudaGraphExecDestroy(ctx->gexec[par]);
             ctx->gexec[par] = nullptr;
         }
+        for (int lead = 0; lead < 2; ++lead)
+            if (ctx->gexec_ov[par][lead]) {
+                cudaGraphExecDestroy(ctx->gexec_ov[par][lead]);
+                ctx->gexec_ov[par][lead] = nullptr;
+            }
+    }
 }
 
 // ---- membrane topology on the host (FP64) ----
@@ -566,6 +709,12 @@ lb_status lb_create_batch(const lb_params* params, int n_channels, void* cuda_st
     TRY(dalloc(ctx, &ctx->fl[0], NG));
     TRY(dalloc(ctx, &ctx->fl[1], NG));
     TRY(dalloc(ctx, &ctx->u, NT));
+    TRY(dalloc(ctx, &ctx->dmap[0], NG));
+    TRY(dalloc(ctx, &ctx->dmap[1], NG));
+    TRY(dalloc(ctx, &ctx->dlist[0], NG));
+    TRY(dalloc(ctx, &ctx->dlist[1], NG));
+    TRY(dalloc(ctx, &ctx->dcount, 2));
+    TRY(dalloc(ctx, &ctx->sched_err, 1));
     TRY(dalloc(ctx, &ctx->d_ch, ctx->ch.size()));
     ctx->diag_blocks = 152 * 4;
     TRY(dalloc(ctx, &ctx->diag_partials, (size_t)ctx->diag_blocks * 6));
@@ -580,6 +729,30 @@ lb_status lb_create_batch(const lb_params* params, int n_channels, void* cuda_st
     TRY(cudaMemsetAsync(ctx->fl[0], 0, NG, ctx->stream));
     TRY(cudaMemsetAsync(ctx->fl[1], 0, NG, ctx->stream));
     TRY(cudaMemsetAsync(ctx->u, 0, NT * sizeof(float4), ctx->stream));
+    TRY(cudaMemsetAsync(ctx->dmap[0], 0, NG, ctx->stream));
+    TRY(cudaMemsetAsync(ctx->dmap[1], 0, NG, ctx->stream));
+    TRY(cudaMemsetAsync(ctx->dcount, 0, 2 * sizeof(int), ctx->stream));
+    TRY(cudaMemsetAsync(ctx->sched_err, 0, sizeof(int), ctx->stream));
+    {
+        int lo = 0, hi = 0;
+        TRY(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+        TRY(cudaStreamCreateWithPriority(&ctx->ib_stream, cudaStreamNonBlocking, hi));
+        for (int k = 0; k < 2; ++k) {
+            TRY(cudaEventCreateWithFlags(&ctx->ev_fork[k], cudaEventDisableTiming));
+            TRY(cudaEventCreateWithFlags(&ctx->ev_join[k], cudaEventDisableTiming));
+            TRY(cudaEventCreateWithFlags(&ctx->ev_fork2[k], cudaEventDisableTiming));
+            TRY(cudaEventCreateWithFlags(&ctx->ev_join2[k], cudaEventDisableTiming));
+        }
+    }
+    ctx->list_blocks = ctx->sm_count * 16;   // 2 waves of 128-thread blocks at 64 registers
+    {
+        int dev = 0, smem = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        ctx->smem_per_sm = smem;
+        cudaGetLastError();
+        if (smem > 0) TRY(prepare_bulk((int)ctx->storage, (int)bulk_smem_max(ctx)));
+    }
 #undef TRY
     if (e != cudaSuccess) {
         lb_status s = e == cudaErrorMemoryAllocation ? LB_ERR_OOM : LB_ERR_CUDA;
@@ -618,6 +791,16 @@ lb_status lb_destroy(lb_ctx* ctx) {
     for (auto& ep : ctx->pending) { cudaEventDestroy(ep.a); cudaEventDestroy(ep.b); }
     for (auto e : ctx->free_events) cudaEventDestroy(e);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+    if (ctx->ib_stream) {
+        cudaStreamSynchronize(ctx->ib_stream);
+        cudaStreamDestroy(ctx->ib_stream);
+    }
+    for (int k = 0; k < 2; ++k) {
+        if (ctx->ev_fork[k]) cudaEventDestroy(ctx->ev_fork[k]);
+        if (ctx->ev_join[k]) cudaEventDestroy(ctx->ev_join[k]);
+        if (ctx->ev_fork2[k]) cudaEventDestroy(ctx->ev_fork2[k]);
+        if (ctx->ev_join2[k]) cudaEventDestroy(ctx->ev_join2[k]);
+    }
     delete ctx;
     return LB_OK;
 }
@@ -824,6 +1007,7 @@ lb_status ibm_set_nodes(lb_ctx* ctx, int mesh_id, const double* xyz) {
     LB_CUDA(cudaMemcpyAsync(ctx->q[par] + m->node0, q.data(), sizeof(Q4) * m->n, cudaMemcpyHostToDevice, ctx->stream));
     LB_CUDA(launch_prepare_nodes(ibm_args(ctx, par), ctx->stream));
     LB_CUDA(cudaStreamSynchronize(ctx->stream));
+    ctx->dvalid = false;
     return LB_OK;
 }
 
@@ -834,6 +1018,29 @@ lb_status lb_step(lb_ctx* ctx, int n_steps) {
     lb_status s = commit_ibm(ctx);
     if (s != LB_OK) return s;
     ctx->started = true;
+    if (use_overlap(ctx)) {
+        s = build_graphs_overlap(ctx);
+        if (s != LB_OK) return s;
+        if (!ctx->dvalid) {
+            s = prepare_stencil_set(ctx);
+            if (s != LB_OK) return s;
+        }
+        for (int k = 0; k < n_steps; ++k) {
+            const int par = (int)(ctx->step & 1);
+            LB_CUDA(cudaGraphLaunch(ctx->gexec_ov[par][k > 0 ? 1 : 0], ctx->stream));
+            ctx->launches[0] += 1;
+            ctx->launches[1] += 2;
+            ctx->launches[2] += 3;
+            if (k > 0) ctx->launches[3] += 1;
+            ctx->step++;
+        }
+        // interpolation + advance of the last step
+        LB_CUDA(launch_interp_advance(ibm_args(ctx, (int)((ctx->step - 1) & 1)), ctx->stream));
+        ctx->launches[3] += 1;
+        LB_CUDA(cudaGetLastError());
+        return LB_OK;
+    }
+    ctx->dvalid = false;
     if (!ctx->timing) {
         s = build_graphs(ctx);
         if (s != LB_OK) return s;
@@ -863,6 +1070,21 @@ lb_status lb_set_kernel_config(lb_ctx* ctx, int nodes_per_thread, int block_size
     apply_k3_config(ctx, c);
     drop_graphs(ctx);
     return upload_channels(ctx);
+}
+
+lb_status lb_set_schedule(lb_ctx* ctx, int overlapped) {
+    LB_GUARD(ctx);
+    if (overlapped != 0 && overlapped != 1) return fail(ctx, LB_ERR_ARG, "schedule must be 0 or 1");
+    LB_CUDA(cudaStreamSynchronize(ctx->stream));
+    ctx->overlap = overlapped != 0;
+    ctx->dvalid = false;
+    return LB_OK;
+}
+
+lb_status lb_get_schedule(lb_ctx* ctx, int* overlapped) {
+    LB_GUARD(ctx);
+    if (overlapped) *overlapped = use_overlap(ctx) ? 1 : 0;
+    return LB_OK;
 }
 
 lb_status lb_get_kernel_config(lb_ctx* ctx, int* nodes_per_thread, int* block_size) {
@@ -1121,6 +1343,10 @@ lb_status lb_diagnostics(lb_ctx* ctx, double u_max, double out[6]) {
     LB_CUDA(cudaMemcpyAsync(out, ctx->diag_out, sizeof(double) * 6, cudaMemcpyDeviceToHost, ctx->stream));
     LB_CUDA(cudaStreamSynchronize(ctx->stream));
     if (out[4] > 0) return fail(ctx, LB_ERR_NUMERIC, "non-finite populations");
+    int serr = 0;
+    LB_CUDA(cudaMemcpy(&serr, ctx->sched_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (serr > 0)
+        return fail(ctx, LB_ERR_NUMERIC, "an IB point moved a lattice unit or more in one step (overlapped schedule)");
     if (u_max > 0 && !(out[5] <= u_max)) return fail(ctx, LB_ERR_NUMERIC, "velocity above the stability bound");
     return LB_OK;
 }
@@ -1195,6 +1421,7 @@ lb_status lb_load_state(lb_ctx* ctx, const void* buf, size_t bytes) {
         LB_CUDA(cudaMemcpy(ctx->q[par], p, qb, cudaMemcpyHostToDevice)); p += qb;
         LB_CUDA(cudaMemcpy(ctx->F, p, Fb, cudaMemcpyHostToDevice)); p += Fb;
         LB_CUDA(launch_prepare_nodes(ibm_args(ctx, par), ctx->stream));
+        ctx->dvalid = false;
     }
     LB_CUDA(cudaStreamSynchronize(ctx->stream));
     ctx->started = ctx->step > 0 || ctx->started;

@@ -137,6 +137,11 @@ struct LatticeArgs {
     uint8_t* fl1;
     float4* u;
     int n_groups;         // row groups of the staged stream-collide variant
+    // overlapped schedule: the step's stencil set (groups that may hold IB
+    // force or be interpolated) as a byte map and as a list
+    const uint8_t* dmap;
+    const int* dlist;
+    const int* dcount;
     ChannelDev chp[MAXCH_P];   // copy of the first channels (constant bank)
 };
 
@@ -180,6 +185,12 @@ struct IbmArgs {
     uint8_t* fl0;
     uint8_t* fl1;
     const float4* u;
+    // overlapped schedule: map receiving the next step's stencil set, the
+    // current step's set (every spread target must lie in it) and the count
+    // of spread targets found outside it
+    uint8_t* dmark;
+    const uint8_t* dcur;
+    int* sched_err;
     ChannelDev chp[MAXCH_P];
 };
 
@@ -226,6 +237,13 @@ cudaError_t launch_rasterise(const float* spheres, int n_spheres, const uint8_t*
 cudaError_t launch_slow_flags(const ChannelDev& ch, const uint32_t* mask, uint8_t* slow, uint32_t* links,
                               cudaStream_t s);
 cudaError_t launch_stream_collide(const LatticeArgs& a, K3Config cfg, int total_blocks, cudaStream_t s);
+// mode 1: bulk (groups outside a.dmap; `smem` bytes of unused dynamic shared
+// memory per block cap its residency), mode 2: the first (blocks * bs / 32)
+// groups of a.dlist, mode 3: the groups of a.dlist from entry `smem` on
+cudaError_t launch_stream_collide_split(const LatticeArgs& a, int bs, int mode, int blocks, size_t smem,
+                                        cudaStream_t s);
+const void* stream_collide_bulk_func(int storage, int bs);
+cudaError_t prepare_bulk(int storage, int max_smem);   // allow up to max_smem dynamic bytes per bulk block
 cudaError_t launch_fields(const LatticeArgs& a, int ch_index, float* rho, float* u, cudaStream_t s);
 cudaError_t launch_pull_populations(const LatticeArgs& a, int ch_index, float* h_out, cudaStream_t s);
 cudaError_t launch_diagnostics(const LatticeArgs& a, int ch_index, double* partials, int n_blocks, double* out,
@@ -236,5 +254,7 @@ cudaError_t launch_elements(const IbmArgs& a, cudaStream_t s);
 cudaError_t launch_forces_spread(const IbmArgs& a, cudaStream_t s);
 cudaError_t launch_interp_advance(const IbmArgs& a, cudaStream_t s);
 cudaError_t launch_prepare_nodes(const IbmArgs& a, cudaStream_t s);
+cudaError_t launch_mark_stencils(const IbmArgs& a, uint8_t* map, cudaStream_t s);
+cudaError_t launch_compact_groups(const uint8_t* map, int n_groups, int* list, int* count, cudaStream_t s);
 
 }  // namespace lbibm

@@ -23,7 +23,7 @@ EXPORTS = (
     "lb_create", "lb_create_batch", "lb_select_channel", "lb_destroy", "lb_set_obstacles", "ibm_add_mesh",
     "ibm_set_nodes", "lb_step", "lb_synchronize", "lb_get_fields", "lb_get_populations", "lb_set_populations",
     "ibm_get_nodes", "ibm_get_forces", "ibm_get_area_volume", "lb_diagnostics", "lb_get_step", "lb_save_state",
-    "lb_load_state", "lb_set_timing", "lb_kernel_times", "lb_last_error", "lb_version", "lb_get_mask",
+    "lb_load_state", "lb_set_schedule", "lb_get_schedule", "lb_set_timing", "lb_kernel_times", "lb_last_error", "lb_version", "lb_get_mask",
     "lb_set_kernel_config", "lb_get_kernel_config", "lb_autotune", "ibm_area_volume_noalloc",
 )
 
@@ -82,6 +82,8 @@ def lib():
             "lb_save_state": ([P, P, ctypes.POINTER(ctypes.c_size_t)], I),
             "lb_load_state": ([P, P, ctypes.c_size_t], I),
             "lb_set_timing": ([P, I], I),
+            "lb_set_schedule": ([P, I], I),
+            "lb_get_schedule": ([P, P], I),
             "lb_kernel_times": ([P, P, P], I),
             "lb_last_error": ([P], ctypes.c_char_p),
             "lb_version": ([], I),
@@ -285,6 +287,15 @@ class Simulation:
         n, b, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
         self._check(self._L.lb_autotune(self._h, int(repeats), ctypes.byref(n), ctypes.byref(b), ctypes.byref(ms)))
         return n.value, b.value, ms.value
+
+    def set_schedule(self, overlapped: bool):
+        """Overlapped (IB chain concurrent with the bulk stream-collide) or sequential cycle."""
+        self._check(self._L.lb_set_schedule(self._h, int(bool(overlapped))))
+
+    def schedule(self) -> int:
+        v = ctypes.c_int(0)
+        self._check(self._L.lb_get_schedule(self._h, ctypes.byref(v)))
+        return v.value
 
     def set_timing(self, on=True):
         """True: time every kernel class; an int: bit mask of classes; False: off."""

@@ -210,6 +210,31 @@ def test_small_filter_parity():
         assert np.abs(sim.nodes(m) - ref.nodes(m)).max() < 1e-5
 
 
+def test_overlapped_schedule_matches_sequential():
+    """The overlapped cycle (IB chain concurrent with the bulk stream-collide)
+    gives the sequential cycle's result, across several lb_step calls, and
+    against the oracle; the default schedule is the sequential one."""
+    sc = scene.small_filter(seed=5, steps=0)
+    runs = {}
+    for ov in (1, 0):
+        sim = _sim(sc)
+        sim.set_schedule(ov)
+        assert sim.schedule() == ov
+        for n in (1, 60, 2, 37):
+            sim.step(n)
+        d = sim.diagnostics()
+        assert d[4] == 0
+        runs[ov] = (sim.fields()[1], [sim.nodes(m) for m in range(len(sc.meshes))])
+    ref = oracle.System.from_scene(sc)
+    ref.step(100)
+    assert rel_l2(runs[1][0], runs[0][0]) < 1e-6
+    assert rel_l2(runs[1][0], ref.fields()[1]) < 1e-5
+    for m in range(len(sc.meshes)):
+        assert np.abs(runs[1][1][m] - runs[0][1][m]).max() < 1e-6
+        assert np.abs(runs[1][1][m] - ref.nodes(m)).max() < 1e-5
+    assert _sim(sc).schedule() == 0
+
+
 def test_micropost_filter_full_size_parity():
     """Full 256x128x64 filter (62 cells, 120 beads): 200 steps against the oracle."""
     sc = scene.micropost_filter(seed=11)
