@@ -10,16 +10,11 @@
 //                    spread with the trilinear delta function (Sec. 2.2 step 3)
 //   k_interp_advance trilinear velocity interpolation (Sec. 2.2 step 1) and the
 //                    point advance X <- X + U (massless points)
-// The two node kernels give each IB node eight lanes: one ring slot (or one
-// stencil corner) per lane, so every load of a node is in flight at once.
+// The force kernel gives each IB node eight lanes: one ring slot and one
+// stencil corner per lane, so every load of a node is in flight at once.
 //
-// Positions are 64-bit fixed point (2^-40 lu).  Element geometry is FP32: edge
-// vectors come from positions relative to the cell's reference node stored as
-// unevaluated sums hi + lo, so (hi_b - hi_a) + (lo_b - lo_a) is the edge to
-// ~1e-7 relative however far the cell has moved.  Length and area changes use
-// the displacement from rest d (relative to the reference node's), so that
-// |e|^2 - L0^2 = 2 e0.de + de.de keeps its relative accuracy when the change
-// is small.
+// Positions are 64-bit fixed point (2^-40 lu); element geometry is FP32 formed
+// from exact fixed-point differences (see Pt below).
 #include "lbibm_internal.cuh"
 
 namespace lbibm {
@@ -34,40 +29,17 @@ __device__ __forceinline__ float3 cross(float3 a, float3 b) {
     return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
 }
 
-struct NodeE {
-    float3 h, l;   // position relative to the reference node, hi + lo
-    float3 d;      // displacement from rest relative to the reference node's
-};
-
 // ---------------------------------------------------------------------------
-// fixed point <-> FP32 with 32-bit integer and FP32 operations only (64-bit
+// fixed point -> FP32 with 32-bit integer and FP32 operations only (64-bit
 // integer <-> float conversions run on the FP64 pipe, which GB300 keeps small)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float pow2f(int e) { return __int_as_float((e + 127) << 23); }   // 2^e, |e| <= 126
 
-// v * 2^-40 as an unevaluated sum hi + lo (hi holds the top 24 bits of |v|).
-__device__ __forceinline__ void fixed_split(long long v, float& hi, float& lo) {
-    const bool neg = v < 0;
-    const unsigned long long a = neg ? (unsigned long long)(-v) : (unsigned long long)v;
-    float h, l;
-    if (a < (1ull << 24)) {
-        h = __uint2float_rn((unsigned)a);
-        l = 0.0f;
-    } else {
-        const int s = 40 - __clzll((long long)a);            // bits below the top 24
-        const unsigned long long top = a >> s;               // exactly 24 significant bits
-        const unsigned long long rem = a - (top << s);       // < 2^s
-        h = __uint2float_rn((unsigned)top) * pow2f(s);
-        l = s <= 24 ? __uint2float_rn((unsigned)rem) : __uint2float_rn((unsigned)(rem >> (s - 24))) * pow2f(s - 24);
-    }
-    hi = (neg ? -h : h) * FIX_INV_F;
-    lo = (neg ? -l : l) * FIX_INV_F;
-}
-
-__device__ __forceinline__ float fixed_to_float(long long v) {
-    float h, l;
-    fixed_split(v, h, l);
-    return h + l;
+// v * 2^-40, correctly rounded for |v| < 2^44 (16 lu), faithfully up to 2^51:
+// v = hi 2^20 + lo with 0 <= lo < 2^20, both exact in FP32, one rounding.
+__device__ __forceinline__ float fx(long long v) {
+    const int hi = (int)(v >> 20);
+    const int lo = (int)(v & 0xFFFFF);
+    return fmaf((float)hi, 9.5367431640625e-07f, (float)lo * FIX_INV_F);   // 2^-20, 2^-40
 }
 
 // round(u * 2^40) for |u| < 2^15: u * 2^16 = m + f with m integral and |f| <= 1/2
@@ -79,16 +51,39 @@ __device__ __forceinline__ long long float_to_fixed(float u) {
     return ((long long)__float2int_rn(m) << 24) + (long long)__float2int_rn(f);
 }
 
-__device__ __forceinline__ NodeE load_node(const IbmArgs& a, int i) {
-    NodeE n;
-    n.h = f3(a.xh[i]);
-    n.l = f3(a.xl[i]);
-    n.d = f3(a.dl[i]);
-    return n;
+// One IB point for the element terms: fixed-point position q and displacement
+// from rest D = q - q0.  Edge vectors and displacement differences are formed
+// exactly as integer differences and rounded once (fx), so an edge is accurate
+// to FP32 rounding of its own length however far the cell has moved, and
+// |e|^2 - L0^2 = 2 e0.de + de.de keeps its relative accuracy when the change
+// is small.
+struct Pt {
+    long long x, y, z;      // q
+    long long dx, dy, dz;   // D
+};
+
+__device__ __forceinline__ Pt load_pt(const IbmArgs& a, const Q4* qc, int i) {
+    const Q4 q = qc[i], q0 = a.q0[i];
+    Pt p;
+    p.x = q.x; p.y = q.y; p.z = q.z;
+    p.dx = q.x - q0.x; p.dy = q.y - q0.y; p.dz = q.z - q0.z;
+    return p;
 }
 
-// edge vector x_b - x_a
-__device__ __forceinline__ float3 edge(const NodeE& A, const NodeE& B) { return (B.h - A.h) + (B.l - A.l); }
+__device__ __forceinline__ const Q4* cur_q(const IbmArgs& a) { return a.par ? a.qb : a.qa; }
+
+// x_b - x_a
+__device__ __forceinline__ float3 edge(const Pt& A, const Pt& B) {
+    return make_float3(fx(B.x - A.x), fx(B.y - A.y), fx(B.z - A.z));
+}
+// D_b - D_a
+__device__ __forceinline__ float3 ddisp(const Pt& A, const Pt& B) {
+    return make_float3(fx(B.dx - A.dx), fx(B.dy - A.dy), fx(B.dz - A.dz));
+}
+// rest position q0_b - q0_a
+__device__ __forceinline__ float3 rest_edge(const Pt& A, const Pt& B) {
+    return make_float3(fx((B.x - B.dx) - (A.x - A.dx)), fx((B.y - B.dy) - (A.y - A.dy)), fx((B.z - B.dz) - (A.z - A.dz)));
+}
 
 __device__ __forceinline__ const ChannelDev& chan(const IbmArgs& a, int c) {
     return c < MAXCH_P ? a.chp[c] : a.ch[c];
@@ -101,9 +96,9 @@ __device__ __forceinline__ const ChannelDev& chan(const IbmArgs& a, int c) {
 // Stretching (neo-Hookean bond, Dupin et al.): tension ks kappa(lambda)(lambda-1)
 // with kappa = (lambda^1/2 + lambda^-5/2)/(lambda + lambda^-3); returns the force
 // on a (the force on b is its negative).  a < b in global index.
-__device__ __forceinline__ float3 stretch_on_a(const NodeE& A, const NodeE& B, float L0, float ks) {
+__device__ __forceinline__ float3 stretch_on_a(const Pt& A, const Pt& B, float L0, float ks) {
     const float3 d = edge(A, B);
-    const float3 de = B.d - A.d;
+    const float3 de = ddisp(A, B);
     const float3 d0 = d - de;
     const float num = 2.0f * dot(d0, de) + dot(de, de);   // |d|^2 - |d0|^2
     const float L = sqrtf(L0 * L0 + num);
@@ -118,7 +113,7 @@ __device__ __forceinline__ float3 stretch_on_a(const NodeE& A, const NodeE& B, f
 // Bending: E = (kb/2)(theta - theta0)^2 at edge (a, b) between triangle (a, b, c)
 // and triangle (b, a, d); theta = atan2((n1 x n2).e_hat, n1.n2).  Writes the
 // forces on a, b, c, d (they sum to zero up to rounding).
-__device__ __forceinline__ void bend_all(const NodeE& A, const NodeE& B, const NodeE& Cc, const NodeE& D, float th0,
+__device__ __forceinline__ void bend_all(const Pt& A, const Pt& B, const Pt& Cc, const Pt& D, float th0,
                                          float kb, float3 f[4]) {
     const float3 e = edge(A, B);
     const float3 ac = edge(A, Cc);
@@ -153,13 +148,15 @@ __device__ __forceinline__ float tri_dS(const float3& e1, const float3& e2, cons
     return num / (2.0f * (nn + nn0));
 }
 
-// Volume change of the tetrahedron (reference node, 0, 1, 2) from rest, times 6:
-// (r0 + d0).((r1 + d1) x (r2 + d2)) - r0.(r1 x r2), expanded, r = x - d.
-__device__ __forceinline__ float tri_dV6(const NodeE& P0, const NodeE& P1, const NodeE& P2) {
-    const float3 r0 = (P0.h - P0.d) + P0.l, r1 = (P1.h - P1.d) + P1.l, r2 = (P2.h - P2.d) + P2.l;
-    const float3 r1r2 = cross(r1, r2), d1r2 = cross(P1.d, r2), r1d2 = cross(r1, P2.d), d1d2 = cross(P1.d, P2.d);
-    return dot(P0.d, r1r2) + dot(r0, d1r2) + dot(r0, r1d2) + dot(P0.d, d1r2) + dot(P0.d, r1d2) + dot(r0, d1d2) +
-           dot(P0.d, d1d2);
+// Volume change of the tetrahedron (reference node R, 0, 1, 2) from rest, times 6:
+// (r0 + d0).((r1 + d1) x (r2 + d2)) - r0.(r1 x r2), expanded, with r_k the rest
+// position and d_k the displacement of point k relative to R's.
+__device__ __forceinline__ float tri_dV6(const Pt& R, const Pt& P0, const Pt& P1, const Pt& P2) {
+    const float3 r0 = rest_edge(R, P0), r1 = rest_edge(R, P1), r2 = rest_edge(R, P2);
+    const float3 d0 = ddisp(R, P0), d1 = ddisp(R, P1), d2 = ddisp(R, P2);
+    const float3 r1r2 = cross(r1, r2), d1r2 = cross(d1, r2), r1d2 = cross(r1, d2), d1d2 = cross(d1, d2);
+    return dot(d0, r1r2) + dot(r0, d1r2) + dot(r0, r1d2) + dot(d0, d1r2) + dot(d0, r1d2) + dot(r0, d1d2) +
+           dot(d0, d1d2);
 }
 
 // ---------------------------------------------------------------------------
@@ -191,12 +188,14 @@ __device__ __forceinline__ void tri_chunk(const IbmArgs& a, int chunk) {
     double s = 0.0, v = 0.0;
     for (int t = ck.y + (int)threadIdx.x; t < ck.z; t += CS_BLOCK) {
         const int4 tr = a.tris[t];
-        const NodeE P0 = load_node(a, tr.x), P1 = load_node(a, tr.y), P2 = load_node(a, tr.z);
+        const Q4* qc = cur_q(a);
+        const Pt R = load_pt(a, qc, a.cells[tr.w].ref);
+        const Pt P0 = load_pt(a, qc, tr.x), P1 = load_pt(a, qc, tr.y), P2 = load_pt(a, qc, tr.z);
         const float3 e1 = edge(P0, P1), e2 = edge(P0, P2);
         const float S0t = a.tri_S0[t];
-        const float dSt = tri_dS(e1, e2, P1.d - P0.d, P2.d - P0.d, S0t);
+        const float dSt = tri_dS(e1, e2, ddisp(P0, P1), ddisp(P0, P2), S0t);
         s += (double)dSt;
-        v += (double)tri_dV6(P0, P1, P2);
+        v += (double)tri_dV6(R, P0, P1, P2);
         if constexpr (FORCES) {
             const float St = S0t + dSt;
             const float3 third = (1.0f / 3.0f) * (e1 + e2);
@@ -248,7 +247,7 @@ __device__ __forceinline__ void tri_chunk(const IbmArgs& a, int chunk) {
     }
 }
 
-__global__ void __launch_bounds__(CS_BLOCK, IB_MIN_BLOCKS) k_cell_sums(const __grid_constant__ IbmArgs a) {
+__global__ void __launch_bounds__(CS_BLOCK, 6) k_cell_sums(const __grid_constant__ IbmArgs a) {
     tri_chunk<false>(a, blockIdx.x);
 }
 
@@ -263,7 +262,7 @@ cudaError_t launch_cell_sums(const IbmArgs& a, cudaStream_t s) {
 // force terms), the blocks after them take one edge per thread: stretching
 // (neo-Hookean bond) and bending of edge (a, b), each evaluated once.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(CS_BLOCK, IB_MIN_BLOCKS) k_elements(const __grid_constant__ IbmArgs a) {
+__global__ void __launch_bounds__(CS_BLOCK, 6) k_elements(const __grid_constant__ IbmArgs a) {
     if ((int)blockIdx.x < a.n_chunks) {
         tri_chunk<true>(a, blockIdx.x);
         return;
@@ -272,7 +271,8 @@ __global__ void __launch_bounds__(CS_BLOCK, IB_MIN_BLOCKS) k_elements(const __gr
     if (e >= a.n_edges) return;
     const int4 ev = a.edges[e];
     const float4 r = a.edge_rest[e];   // (L0, theta0, ks, kb)
-    const NodeE A = load_node(a, ev.x), B = load_node(a, ev.y), Cc = load_node(a, ev.z), D = load_node(a, ev.w);
+    const Q4* qc = cur_q(a);
+    const Pt A = load_pt(a, qc, ev.x), B = load_pt(a, qc, ev.y), Cc = load_pt(a, qc, ev.z), D = load_pt(a, qc, ev.w);
     const float3 fs = stretch_on_a(A, B, r.x, r.z);
     a.eS[e] = make_float4(fs.x, fs.y, fs.z, 0.f);
     float3 fb[4];
@@ -462,86 +462,43 @@ cudaError_t launch_forces_spread(const IbmArgs& a, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------------------
-// interpolation + advance (Sec. 2.2 steps 1 and 4), eight lanes per IB node
-// (one stencil corner each).  Every node also advances its cell's reference
-// node with identical arithmetic, so the relative coordinates of the next step
-// are formed without a second pass.  Obstacle nodes hold u = 0.
+// interpolation + advance (Sec. 2.2 steps 1 and 4), one thread per IB node:
+// the eight stencil velocities are loaded at once, U = sum w u, and the
+// position advances by the exact fixed-point addition X <- X + U.  Obstacle
+// and out-of-domain stencil nodes contribute nothing.
 // ---------------------------------------------------------------------------
 constexpr int IA_BLOCK = 128;
 
-__device__ __forceinline__ void write_rel(const IbmArgs& a, int i, const Q4& q, const Q4& qr, const Q4& q0,
-                                          const Q4& q0r) {
-    float hx, hy, hz, lx, ly, lz;
-    fixed_split(q.x - qr.x, hx, lx);
-    fixed_split(q.y - qr.y, hy, ly);
-    fixed_split(q.z - qr.z, hz, lz);
-    a.xh[i] = make_float4(hx, hy, hz, 0.f);
-    a.xl[i] = make_float4(lx, ly, lz, 0.f);
-    a.dl[i] = make_float4(fixed_to_float((q.x - q0.x) - (qr.x - q0r.x)), fixed_to_float((q.y - q0.y) - (qr.y - q0r.y)),
-                          fixed_to_float((q.z - q0.z) - (qr.z - q0r.z)), 0.f);
-}
-
-__device__ __forceinline__ float3 corner_u(const IbmArgs& a, const ChannelDev& Ch, const Q4& q, int c) {
-    long long g;
-    float w;
-    if (!corner(Ch, q, c, g, w)) return make_float3(0.f, 0.f, 0.f);
-    const float4 u = a.u[g];
-    return make_float3(w * u.x, w * u.y, w * u.z);
-}
-
 __global__ void __launch_bounds__(IA_BLOCK, IB_MIN_BLOCKS) k_interp_advance(const __grid_constant__ IbmArgs a) {
-    const int i = (blockIdx.x * IA_BLOCK + threadIdx.x) / SUB;
-    const int sl = threadIdx.x & (SUB - 1);
+    const int i = blockIdx.x * IA_BLOCK + threadIdx.x;
     if (i >= a.n_nodes) return;
-    const unsigned smask = 0xffu << (threadIdx.x & 24);
-    const int4 inf = a.info[i];
-    const int ref = inf.y, chn = inf.w >> 8;
+    const int chn = a.info[i].w >> 8;
     const ChannelDev Ch = chan(a, chn);
-    const Q4* qc = a.par ? a.qb : a.qa;
-    const Q4 q = qc[i], qr = qc[ref];
-    float3 U = corner_u(a, Ch, q, sl);
-    float3 Ur = corner_u(a, Ch, qr, sl);
+    const Q4 q = cur_q(a)[i];
+    float4 u[8];
+    float w[8];
 #pragma unroll
-    for (int o = SUB / 2; o > 0; o >>= 1) {
-        U.x += __shfl_xor_sync(smask, U.x, o);
-        U.y += __shfl_xor_sync(smask, U.y, o);
-        U.z += __shfl_xor_sync(smask, U.z, o);
-        Ur.x += __shfl_xor_sync(smask, Ur.x, o);
-        Ur.y += __shfl_xor_sync(smask, Ur.y, o);
-        Ur.z += __shfl_xor_sync(smask, Ur.z, o);
+    for (int c = 0; c < 8; ++c) {
+        long long g;
+        u[c] = corner(Ch, q, c, g, w[c]) ? a.u[g] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    if (sl != 0) return;
-    Q4 qn = q, qrn = qr;
-    qn.x += float_to_fixed(U.x);
-    qn.y += float_to_fixed(U.y);
-    qn.z += float_to_fixed(U.z);
-    qrn.x += float_to_fixed(Ur.x);
-    qrn.y += float_to_fixed(Ur.y);
-    qrn.z += float_to_fixed(Ur.z);
+    float ux = 0.f, uy = 0.f, uz = 0.f;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        ux = fmaf(w[c], u[c].x, ux);
+        uy = fmaf(w[c], u[c].y, uy);
+        uz = fmaf(w[c], u[c].z, uz);
+    }
+    Q4 qn = q;
+    qn.x += float_to_fixed(ux);
+    qn.y += float_to_fixed(uy);
+    qn.z += float_to_fixed(uz);
     (a.par ? a.qa : a.qb)[i] = qn;
-    write_rel(a, i, qn, qrn, a.q0[i], a.q0[ref]);
 }
 
 cudaError_t launch_interp_advance(const IbmArgs& a, cudaStream_t s) {
     if (a.n_nodes <= 0) return cudaSuccess;
-    const long long threads = (long long)a.n_nodes * SUB;
-    k_interp_advance<<<(unsigned)((threads + IA_BLOCK - 1) / IA_BLOCK), IA_BLOCK, 0, s>>>(a);
-    return cudaGetLastError();
-}
-
-// Relative coordinates from the current fixed-point positions (after setup,
-// after positions are overwritten, or after a checkpoint is loaded).
-__global__ void k_prepare_nodes(const __grid_constant__ IbmArgs a) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.n_nodes) return;
-    const int ref = a.info[i].y;
-    const Q4* qc = a.par ? a.qb : a.qa;
-    write_rel(a, i, qc[i], qc[ref], a.q0[i], a.q0[ref]);
-}
-
-cudaError_t launch_prepare_nodes(const IbmArgs& a, cudaStream_t s) {
-    if (a.n_nodes <= 0) return cudaSuccess;
-    k_prepare_nodes<<<(a.n_nodes + 127) / 128, 128, 0, s>>>(a);
+    k_interp_advance<<<(unsigned)((a.n_nodes + IA_BLOCK - 1) / IA_BLOCK), IA_BLOCK, 0, s>>>(a);
     return cudaGetLastError();
 }
 

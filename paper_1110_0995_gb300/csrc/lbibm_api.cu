@@ -86,7 +86,7 @@ struct lb_ctx {
     int M = 0, C = 0, T = 0, NCH = 0, K = 0, E = 0;
     Q4* q[2] = {nullptr, nullptr};
     Q4* q0 = nullptr;
-    float4 *xh = nullptr, *xl = nullptr, *dl = nullptr, *F = nullptr;
+    float4* F = nullptr;
     int4* info = nullptr;
     int4* slots = nullptr;
     int4* edges = nullptr;
@@ -220,9 +220,6 @@ IbmArgs ibm_args(const lb_ctx* ctx, int par, bool overlapped = false) {
     a.qa = ctx->q[0];
     a.qb = ctx->q[1];
     a.q0 = ctx->q0;
-    a.xh = ctx->xh;
-    a.xl = ctx->xl;
-    a.dl = ctx->dl;
     a.slots = ctx->slots;
     a.edges = ctx->edges;
     a.edge_rest = ctx->edge_rest;
@@ -589,9 +586,6 @@ lb_status commit_ibm(lb_ctx* ctx) {
     LB_CUDA(up(&ctx->triS0, ctx->htriS0));
     LB_CUDA(up(&ctx->chunks, ctx->hchunks));
     LB_CUDA(up(&ctx->d_cells, ctx->hcells));
-    LB_CUDA(dalloc(ctx, &ctx->xh, ctx->M));
-    LB_CUDA(dalloc(ctx, &ctx->xl, ctx->M));
-    LB_CUDA(dalloc(ctx, &ctx->dl, ctx->M));
     LB_CUDA(dalloc(ctx, &ctx->F, ctx->M));
     LB_CUDA(cudaMemsetAsync(ctx->F, 0, sizeof(float4) * ctx->M, ctx->stream));
     LB_CUDA(dalloc(ctx, &ctx->partials, ctx->NCH));
@@ -601,7 +595,6 @@ lb_status commit_ibm(lb_ctx* ctx) {
     LB_CUDA(cudaMemsetAsync(ctx->cell_sums, 0, sizeof(double2) * ctx->C, ctx->stream));
     LB_CUDA(dalloc(ctx, &ctx->cell_rel, ctx->C));
     LB_CUDA(cudaMemsetAsync(ctx->cell_rel, 0, sizeof(float2) * ctx->C, ctx->stream));
-    LB_CUDA(launch_prepare_nodes(ibm_args(ctx, (int)(ctx->step & 1)), ctx->stream));
     return LB_OK;
 }
 
@@ -1005,7 +998,6 @@ lb_status ibm_set_nodes(lb_ctx* ctx, int mesh_id, const double* xyz) {
     }
     const int par = (int)(ctx->step & 1);
     LB_CUDA(cudaMemcpyAsync(ctx->q[par] + m->node0, q.data(), sizeof(Q4) * m->n, cudaMemcpyHostToDevice, ctx->stream));
-    LB_CUDA(launch_prepare_nodes(ibm_args(ctx, par), ctx->stream));
     LB_CUDA(cudaStreamSynchronize(ctx->stream));
     ctx->dvalid = false;
     return LB_OK;
@@ -1420,7 +1412,6 @@ lb_status lb_load_state(lb_ctx* ctx, const void* buf, size_t bytes) {
     if (ctx->M) {
         LB_CUDA(cudaMemcpy(ctx->q[par], p, qb, cudaMemcpyHostToDevice)); p += qb;
         LB_CUDA(cudaMemcpy(ctx->F, p, Fb, cudaMemcpyHostToDevice)); p += Fb;
-        LB_CUDA(launch_prepare_nodes(ibm_args(ctx, par), ctx->stream));
         ctx->dvalid = false;
     }
     LB_CUDA(cudaStreamSynchronize(ctx->stream));

@@ -24,11 +24,6 @@
 //                                 groups (the stencils of the IB points)
 //   IB nodes     int64 q[2][M]x4  positions in 2^-40 lu fixed point (by parity)
 //                int64 q0[M]x4    rest positions
-//                float4 xh, xl    position relative to the cell's reference
-//                                 node as an unevaluated FP32 sum hi + lo
-//                float4 dl        displacement from rest relative to the
-//                                 reference node's displacement
-//                float4 r0        rest position relative to the reference node
 //                int4 info        (cell, reference node, ring offset, valence | channel << 8)
 //   ring CSR     int4 per slot of a node's ring: where the node's share of the
 //                incident triangle, edge and opposite edge lies in the
@@ -156,10 +151,6 @@ struct IbmArgs {
     Q4* qa;               // [M] positions, even steps
     Q4* qb;               // [M] positions, odd steps
     const Q4* q0;         // [M] rest positions
-    float4* xh;           // [M]
-    float4* xl;           // [M]
-    float4* dl;           // [M]
-    const float4* r0;     // [M]
     const int4* slots;    // [K] (3 t + role in t, 4 e + role in e, 4 e' + role in e', t) per ring slot
     const int4* edges;    // [E] (a, b, c, d)
     const float4* edge_rest;  // [E] (L0, theta0, ks, kb)
@@ -253,7 +244,6 @@ cudaError_t launch_cell_sums(const IbmArgs& a, cudaStream_t s);
 cudaError_t launch_elements(const IbmArgs& a, cudaStream_t s);
 cudaError_t launch_forces_spread(const IbmArgs& a, cudaStream_t s);
 cudaError_t launch_interp_advance(const IbmArgs& a, cudaStream_t s);
-cudaError_t launch_prepare_nodes(const IbmArgs& a, cudaStream_t s);
 cudaError_t launch_mark_stencils(const IbmArgs& a, uint8_t* map, cudaStream_t s);
 cudaError_t launch_compact_groups(const uint8_t* map, int n_groups, int* list, int* count, cudaStream_t s);
 
