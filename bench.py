@@ -36,14 +36,17 @@ METRIC = "D3Q19+IBM MLUPS on 1 GB300 (% HBM roofline)"
 
 
 def make_workload(name: str):
+    """The channels of a workload (one, or the batched sweep's 24)."""
     from paper_1110_0995_gb300 import scene
 
     if name == "micropost_filter_256x128x64":
-        return scene.micropost_filter(seed=11)
+        return [scene.micropost_filter(seed=11)]
     if name == "micropost_filter_512x256x128":
-        return scene.micropost_filter_large(seed=31)
+        return [scene.micropost_filter_large(seed=31)]
     if name == "channel_32x16x64_1rbc":
-        return scene.channel_plain(seed=1)
+        return [scene.channel_plain(seed=1)]
+    if name == "gap_sweep_24ch":
+        return scene.gap_sweep(seed=21)
     raise ValueError(name)
 
 
@@ -223,9 +226,9 @@ def run_ours(args):
     from paper_1110_0995_gb300 import _build, lbibm
 
     _build.build()
-    sc = make_workload(args.workload)
+    scenes = make_workload(args.workload)
     stream = torch.cuda.Stream()
-    sim = lbibm.Simulation.from_scene(sc, storage=args.storage, stream=stream.cuda_stream)
+    sim = lbibm.Simulation.from_scenes(scenes, storage=args.storage, stream=stream.cuda_stream)
     from paper_1110_0995_gb300 import autotune
 
     if args.variant:
@@ -234,8 +237,14 @@ def run_ours(args):
         tuned = {"npt": npt, "bs": bs}
     else:
         tuned = autotune.tune(sim, torch.cuda.get_device_name(local_rank), args.storage)
-    n_nodes = sc.n_nodes
-    n_fluid = int((sim.solid_mask() == 0).sum())
+    n_nodes = sum(s.n_nodes for s in scenes)
+    n_fluid = 0
+    for k in range(len(scenes)):
+        sim.select(k)
+        n_fluid += int((sim.solid_mask() == 0).sum())
+    sim.select(0)
+    n_cells = sum(len(s.meshes) for s in scenes)
+    n_ib = sum(s.n_ib_nodes for s in scenes)
     sim.step(args.warmup)
     sim.synchronize()
     state = sim.save_state()                        # both timed passes start from this state
@@ -265,7 +274,13 @@ def run_ours(args):
             torch.cuda.synchronize()
         barrier()
         kms, kn = sim.kernel_times()
-        diag = sim.diagnostics()                    # FP64 sums over the final state
+        diag = np.zeros(6)                          # FP64 sums over the final state, all channels
+        for k in range(len(scenes)):
+            sim.select(k)
+            d = sim.diagnostics()
+            diag[:5] += d[:5]
+            diag[5] = max(diag[5], d[5])
+        sim.select(0)
         return e0.elapsed_time(e1), kms, kn, diag, clk
 
     # pass 1: the number reported (graph replay, no instrumentation)
@@ -296,21 +311,24 @@ def run_ours(args):
         e2e_steps = args.steps
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        s2 = lbibm.Simulation.from_scene(sc, storage=args.storage, stream=stream.cuda_stream)
+        s2 = lbibm.Simulation.from_scenes(scenes, storage=args.storage, stream=stream.cuda_stream)
         s2.set_kernel_config(tuned["npt"], tuned["bs"])
-        h2d = sum(m.rest.nbytes + m.tris.nbytes for m in sc.meshes) + sc.spheres.nbytes
+        h2d = sum(m.rest.nbytes + m.tris.nbytes for s in scenes for m in s.meshes) + sum(s.spheres.nbytes for s in scenes)
         d2h = 0
-        bufs = [np.zeros((m.n_nodes, 3)) for m in sc.meshes]
+        bufs = [np.zeros((sum(m.n_nodes for m in s.meshes), 3)) for s in scenes]
         done = 0
         while done < e2e_steps:
             k = min(10, e2e_steps - done)
             s2.step(k)
             done += k
-            for mi, b in enumerate(bufs):
-                s2.nodes_into(mi, b)
+            for c, b in enumerate(bufs):
+                s2.select(c)
+                s2.all_nodes_into(b)
                 d2h += b.nbytes
-        rho, u = s2.fields()
-        d2h += rho.nbytes + u.nbytes
+        for c in range(len(scenes)):
+            s2.select(c)
+            rho, u = s2.fields()
+            d2h += rho.nbytes + u.nbytes
         s2.synchronize()
         dt = time.perf_counter() - t0
         s2.close()
@@ -319,13 +337,15 @@ def run_ours(args):
                "includes": "context creation, scene upload, node readback every 10 steps, final fields"}
 
     if rank == 0:
-        cpu = None if (args.no_cpu_baseline or world > 1) else cpu_baseline_line()
+        cpu = None if (args.no_cpu_baseline or world > 1 or len(scenes) > 1) else cpu_baseline_line()
         line = {
             "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
-            "config": {"workload": args.workload, "lattice": list(sc.dims), "cells": len(sc.meshes),
-                       "ib_nodes": sc.n_ib_nodes, "spheres": int(len(sc.spheres)), "fluid_nodes": n_fluid,
+            "config": {"workload": args.workload,
+                       "lattice": list(scenes[0].dims) if len(scenes) == 1 else [list(s.dims) for s in scenes],
+                       "cells": n_cells, "ib_nodes": n_ib, "spheres": int(sum(len(s.spheres) for s in scenes)),
+                       "fluid_nodes": n_fluid,
                        "storage": args.storage, "l2": "populations 2x%.0f MB > 126 MB L2" % (
                            19 * BYTES_PER_NODE[args.storage] / 38 * n_nodes / 1e6),
                        "parallelism": "replicas" if world > 1 else "single",
@@ -334,9 +354,9 @@ def run_ours(args):
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                          "kernel": "k_stream_collide", "alg_bytes_per_launch": alg_bytes,
                          "avg_launch_ms": k3_ms},
-            "kernel_ms_per_step": {"cell_sums": kms[0] / max(1, kn[0]), "forces_spread": kms[1] / max(1, kn[1]),
+            "kernel_ms_per_step": {"elements": kms[0] / max(1, kn[0]), "forces_spread": kms[1] / max(1, kn[1]),
                                    "stream_collide": k3_ms, "interp_advance": kms[3] / max(1, kn[3])},
-            "ib_node_updates_per_s": world * sc.n_ib_nodes * args.steps / (ms * 1e-3),
+            "ib_node_updates_per_s": world * n_ib * args.steps / (ms * 1e-3),
             "gpu_launches": int(sum(kn)),
             "kernel_timing": {"ms_per_step_with_events": ms_ev / args.steps, "clocks": clk_ev.summary(),
                               "how": "second pass over the same K steps from the same saved state, "

@@ -181,6 +181,13 @@ lb_status lb_set_populations(lb_ctx* ctx, const double* f);
 /* Current node positions of one mesh of the selected channel (n x 3, host). */
 lb_status ibm_get_nodes(lb_ctx* ctx, int mesh_id, double* xyz);
 
+/* Current positions of every mesh of the selected channel, in the order the
+ * meshes were added, concatenated into xyz (sum of their node counts x 3,
+ * host, caller-owned).  One device-to-host transfer per run of adjacent meshes
+ * through a page-locked staging buffer, one wait.  The paper's filter runs
+ * record cell trajectories (Sec. 3); this is that readback. */
+lb_status ibm_get_all_nodes(lb_ctx* ctx, double* xyz);
+
 /* Node forces spread in the last step (n x 3, host). */
 lb_status ibm_get_forces(lb_ctx* ctx, int mesh_id, double* f);
 
@@ -230,7 +237,8 @@ lb_status lb_get_step(lb_ctx* ctx, int64_t* step);
 lb_status lb_save_state(lb_ctx* ctx, void* buf, size_t* bytes);
 lb_status lb_load_state(lb_ctx* ctx, const void* buf, size_t bytes);
 
-/* Optional per-kernel timing.  Kernel classes: 0 = cell area/volume,
+/* Optional per-kernel timing.  Kernel classes: 0 = element pass (cell area /
+ * volume sums and element forces),
  * 1 = membrane forces + spreading, 2 = fused stream-collide,
  * 3 = interpolation + advance.  With kernel_mask != 0 (bit k for class k,
  * 15 = all) lb_step launches the kernels one by one (no graph) and records a

@@ -87,6 +87,7 @@ struct lb_ctx {
     Q4* q[2] = {nullptr, nullptr};
     Q4* q0 = nullptr;
     float4* F = nullptr;
+    Q4* hq_pinned = nullptr;       // page-locked staging of positions for readback [M]
     int4* info = nullptr;
     int4* slots = nullptr;
     int4* edges = nullptr;
@@ -587,6 +588,7 @@ lb_status commit_ibm(lb_ctx* ctx) {
     LB_CUDA(up(&ctx->chunks, ctx->hchunks));
     LB_CUDA(up(&ctx->d_cells, ctx->hcells));
     LB_CUDA(dalloc(ctx, &ctx->F, ctx->M));
+    LB_CUDA(cudaMallocHost((void**)&ctx->hq_pinned, sizeof(Q4) * (size_t)ctx->M));
     LB_CUDA(cudaMemsetAsync(ctx->F, 0, sizeof(float4) * ctx->M, ctx->stream));
     LB_CUDA(dalloc(ctx, &ctx->partials, ctx->NCH));
     LB_CUDA(dalloc(ctx, &ctx->counters, ctx->C));
@@ -780,6 +782,7 @@ lb_status lb_destroy(lb_ctx* ctx) {
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     drop_graphs(ctx);
     for (void* p : ctx->allocations) cudaFree(p);
+    if (ctx->hq_pinned) cudaFreeHost(ctx->hq_pinned);
     ctx->allocations.clear();
     for (auto& ep : ctx->pending) { cudaEventDestroy(ep.a); cudaEventDestroy(ep.b); }
     for (auto e : ctx->free_events) cudaEventDestroy(e);
@@ -1269,25 +1272,57 @@ lb_status lb_set_populations(lb_ctx* ctx, const double* f) {
     return LB_OK;
 }
 
+// Copy node ranges of the current positions into the page-locked staging
+// buffer (adjacent ranges merged into one copy), wait once, convert.
+lb_status read_positions(lb_ctx* ctx, const std::vector<const MeshHost*>& ms, double* xyz) {
+    if (!ctx->committed) {
+        size_t o = 0;
+        for (const MeshHost* m : ms)
+            for (int i = 0; i < m->n; ++i, ++o) {
+                const Q4& q = ctx->hq[m->node0 + i];
+                xyz[3 * o] = (double)q.x / FIX_SCALE;
+                xyz[3 * o + 1] = (double)q.y / FIX_SCALE;
+                xyz[3 * o + 2] = (double)q.z / FIX_SCALE;
+            }
+        return LB_OK;
+    }
+    const Q4* src = ctx->q[ctx->step & 1];
+    size_t k = 0;
+    while (k < ms.size()) {
+        size_t e = k + 1;
+        while (e < ms.size() && ms[e]->node0 == ms[e - 1]->node0 + ms[e - 1]->n) ++e;
+        const int n0 = ms[k]->node0, n1 = ms[e - 1]->node0 + ms[e - 1]->n;
+        LB_CUDA(cudaMemcpyAsync(ctx->hq_pinned + n0, src + n0, sizeof(Q4) * (size_t)(n1 - n0), cudaMemcpyDeviceToHost,
+                                ctx->stream));
+        k = e;
+    }
+    LB_CUDA(cudaStreamSynchronize(ctx->stream));
+    size_t o = 0;
+    for (const MeshHost* m : ms)
+        for (int i = 0; i < m->n; ++i, ++o) {
+            const Q4& q = ctx->hq_pinned[m->node0 + i];
+            xyz[3 * o] = (double)q.x / FIX_SCALE;
+            xyz[3 * o + 1] = (double)q.y / FIX_SCALE;
+            xyz[3 * o + 2] = (double)q.z / FIX_SCALE;
+        }
+    return LB_OK;
+}
+
 lb_status ibm_get_nodes(lb_ctx* ctx, int mesh_id, double* xyz) {
     LB_GUARD(ctx);
     const MeshHost* m;
     if (check_channel_mesh(ctx, mesh_id, &m) != LB_OK) return LB_ERR_ARG;
     if (!xyz) return LB_ERR_ARG;
-    std::vector<Q4> q(m->n);
-    if (!ctx->committed) {
-        std::copy(ctx->hq.begin() + m->node0, ctx->hq.begin() + m->node0 + m->n, q.begin());
-    } else {
-        LB_CUDA(cudaMemcpyAsync(q.data(), ctx->q[ctx->step & 1] + m->node0, sizeof(Q4) * m->n, cudaMemcpyDeviceToHost,
-                                ctx->stream));
-        LB_CUDA(cudaStreamSynchronize(ctx->stream));
-    }
-    for (int i = 0; i < m->n; ++i) {
-        xyz[3 * i] = (double)q[i].x / FIX_SCALE;
-        xyz[3 * i + 1] = (double)q[i].y / FIX_SCALE;
-        xyz[3 * i + 2] = (double)q[i].z / FIX_SCALE;
-    }
-    return LB_OK;
+    return read_positions(ctx, {m}, xyz);
+}
+
+lb_status ibm_get_all_nodes(lb_ctx* ctx, double* xyz) {
+    LB_GUARD(ctx);
+    if (!xyz) return LB_ERR_ARG;
+    std::vector<const MeshHost*> ms;
+    for (int id : ctx->ch_meshes[ctx->cur]) ms.push_back(&ctx->meshes[id]);
+    if (ms.empty()) return LB_OK;
+    return read_positions(ctx, ms, xyz);
 }
 
 lb_status ibm_get_forces(lb_ctx* ctx, int mesh_id, double* f) {

@@ -22,7 +22,7 @@ STORAGE = {"f32": 0, "f16": 1, "bf16": 2}
 EXPORTS = (
     "lb_create", "lb_create_batch", "lb_select_channel", "lb_destroy", "lb_set_obstacles", "ibm_add_mesh",
     "ibm_set_nodes", "lb_step", "lb_synchronize", "lb_get_fields", "lb_get_populations", "lb_set_populations",
-    "ibm_get_nodes", "ibm_get_forces", "ibm_get_area_volume", "lb_diagnostics", "lb_get_step", "lb_save_state",
+    "ibm_get_nodes", "ibm_get_all_nodes", "ibm_get_forces", "ibm_get_area_volume", "lb_diagnostics", "lb_get_step", "lb_save_state",
     "lb_load_state", "lb_set_schedule", "lb_get_schedule", "lb_set_timing", "lb_kernel_times", "lb_last_error", "lb_version", "lb_get_mask",
     "lb_set_kernel_config", "lb_get_kernel_config", "lb_autotune", "ibm_area_volume_noalloc",
 )
@@ -75,6 +75,7 @@ def lib():
             "lb_get_populations": ([P, P], I),
             "lb_set_populations": ([P, P], I),
             "ibm_get_nodes": ([P, I, P], I),
+            "ibm_get_all_nodes": ([P, P], I),
             "ibm_get_forces": ([P, I, P], I),
             "ibm_get_area_volume": ([P, P, P], I),
             "lb_diagnostics": ([P, D, P], I),
@@ -243,6 +244,10 @@ class Simulation:
 
     def nodes_into(self, mesh: int, out: np.ndarray):
         self._check(self._L.ibm_get_nodes(self._h, int(mesh), _ptr(out)))
+
+    def all_nodes_into(self, out: np.ndarray):
+        """Positions of every mesh of the selected channel, concatenated (one transfer)."""
+        self._check(self._L.ibm_get_all_nodes(self._h, _ptr(out)))
 
     def forces(self, mesh: int) -> np.ndarray:
         f = np.zeros((self.n_mesh_nodes[self.channel][mesh], 3))

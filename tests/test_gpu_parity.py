@@ -294,6 +294,42 @@ def test_batch_matches_single_channels():
         assert np.abs(batch.nodes(0) - single.nodes(0)).max() < 1e-7
 
 
+def test_all_nodes_readback():
+    """ibm_get_all_nodes returns the meshes' positions concatenated, before and after stepping."""
+    sc = scene.small_filter(seed=5, steps=0)
+    sim = _sim(sc)
+    n = sum(m.n_nodes for m in sc.meshes)
+    out = np.zeros((n, 3))
+    sim.all_nodes_into(out)
+    assert np.array_equal(out, np.concatenate([m.rest for m in sc.meshes]))
+    sim.step(7)
+    sim.all_nodes_into(out)
+    assert np.array_equal(out, np.concatenate([sim.nodes(m) for m in range(len(sc.meshes))]))
+
+
+def test_gap_sweep_batch_parity():
+    """The 24-channel gap sweep (uneven sizes 64-256 x 32-128 x 32-64, one post row each, 10-40 red cells) in
+    one context, every kernel one launch per step over all channels: 100 steps; the smallest, median and
+    largest channel against the oracle, every channel finite."""
+    from paper_1110_0995_gb300 import lbibm
+
+    scs = scene.gap_sweep(seed=21, steps=100)
+    assert len(scs) == 24
+    sim = lbibm.Simulation.from_scenes(scs)
+    sim.step(100)
+    for k in range(len(scs)):
+        sim.select(k)
+        assert sim.diagnostics()[4] == 0
+    order = np.argsort([s.n_nodes for s in scs])
+    for k in (order[0], order[len(order) // 2], order[-1]):
+        ref = oracle.System.from_scene(scs[k])
+        ref.step(100)
+        sim.select(int(k))
+        assert rel_l2(sim.fields()[1], ref.fields()[1]) < 1e-5
+        for m in range(len(scs[k].meshes)):
+            assert np.abs(sim.nodes(m) - ref.nodes(m)).max() < 1e-5
+
+
 @pytest.mark.parametrize("storage,tol", [("f16", 1e-3), ("bf16", None)])
 def test_reduced_precision_storage(storage, tol):
     """Shifted populations stored in 16 bits, FP32 arithmetic: error vs the oracle per field."""
