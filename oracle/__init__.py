@@ -26,6 +26,9 @@ Parity status per function (what pins it, in ``tests/test_oracle_*.py``):
                                   under homocentric scaling, invariants
 * force_volume                  : finite differences of the volume energy
 * system_step (coupled cycle)   : a cell in uniform flow translates rigidly
+* DiffProblem (differentiable   : dual-number derivatives vs central finite
+  variant, Brinkman beads)        differences; phi = 0 reproduces the plain cycle;
+                                  phi = 1 with alpha = 2 holds u at g / 2
 """
 from __future__ import annotations
 
@@ -93,6 +96,16 @@ def lib():
         L.or_dihedral.argtypes = [P, P, P, P]
         L.or_spread.argtypes = [vp, P, P, i, P]
         L.or_interpolate.argtypes = [vp, P, i, P, P]
+        L.or_diff_create.restype = vp
+        L.or_diff_create.argtypes = [i, i, i, d, P, P, i, P, d, d]
+        L.or_diff_destroy.argtypes = [vp]
+        L.or_diff_add_mesh.restype = i
+        L.or_diff_add_mesh.argtypes = [vp, P, i, P, i, P]
+        L.or_diff_run.restype = d
+        L.or_diff_run.argtypes = [vp, i, i, i, i, P]
+        L.or_diff_state.restype = d
+        L.or_diff_state.argtypes = [vp, i, i, P, P]
+        L.or_diff_phi.argtypes = [vp, P]
         _lib = L
     return _lib
 
@@ -275,3 +288,70 @@ class System:
         U = np.zeros_like(XX)
         lib().or_interpolate(self._h, _p(XX), int(XX.shape[0]), _p(uu), _p(U))
         return U
+
+
+SEED = {"bead": 1, "ks": 2, "kb": 3}
+
+
+class DiffProblem:
+    """The differentiable variant (Brinkman beads, see ``diff_run`` in
+    lbibm_oracle.cpp): J = mean x displacement of the objective cell after T
+    cycles from rest, and forward-mode derivatives of J (FP64 dual numbers)
+    with respect to one bead coordinate, or the objective cell's ks or kb."""
+
+    def __init__(self, dims, tau, body_force, periodic, beads, alpha=2.0, delta=0.5):
+        self.dims = tuple(int(v) for v in dims)
+        self.N = self.dims[0] * self.dims[1] * self.dims[2]
+        self.beads = _f64(beads).reshape(-1, 4).copy()
+        G = _f64(body_force)
+        per = np.ascontiguousarray(periodic, dtype=np.int32)
+        h = lib().or_diff_create(*self.dims, float(tau), _p(G), _p(per), int(self.beads.shape[0]),
+                                 _p(self.beads), float(alpha), float(delta))
+        if not h:
+            raise ValueError("invalid problem")
+        self._h = h
+        self.n_nodes = []
+
+    @classmethod
+    def from_scene(cls, scene, alpha=2.0, delta=0.5, moduli=None) -> "DiffProblem":
+        p = cls(scene.dims, scene.tau, scene.body_force, scene.periodic, np.asarray(scene.spheres, np.float64),
+                alpha, delta)
+        for k, m in enumerate(scene.meshes):
+            p.add_mesh(m.rest, m.tris, m.moduli if moduli is None else moduli[k])
+        return p
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib().or_diff_destroy(h)
+            self._h = None
+
+    def add_mesh(self, x0, tris, moduli) -> int:
+        xx = _f64(x0)
+        tt = np.ascontiguousarray(tris, dtype=np.int32)
+        m = lib().or_diff_add_mesh(self._h, _p(xx), int(xx.shape[0]), _p(tt), int(tt.shape[0]), _p(_f64(moduli)))
+        if m < 0:
+            raise ValueError("mesh rejected")
+        self.n_nodes.append(int(xx.shape[0]))
+        return m
+
+    def run(self, steps: int, obj: int, seed=None):
+        """J, or (J, dJ/dp) for seed = ("bead", 3 k + axis) / ("ks",) / ("kb",)."""
+        if seed is None:
+            return lib().or_diff_run(self._h, int(steps), int(obj), 0, 0, None)
+        dJ = ctypes.c_double()
+        J = lib().or_diff_run(self._h, int(steps), int(obj), SEED[seed[0]], int(seed[1]) if len(seed) > 1 else 0,
+                              ctypes.byref(dJ))
+        return J, dJ.value
+
+    def state(self, steps: int, obj: int = 0):
+        """(J, last velocity field 3 x N, every mesh's final positions concatenated)."""
+        u = np.zeros(3 * self.N)
+        x = np.zeros((sum(self.n_nodes), 3))
+        J = lib().or_diff_state(self._h, int(steps), int(obj), _p(u), _p(x))
+        return J, u.reshape(3, self.N), x
+
+    def phi(self) -> np.ndarray:
+        out = np.zeros(self.N)
+        lib().or_diff_phi(self._h, _p(out))
+        return out

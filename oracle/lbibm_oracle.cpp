@@ -37,6 +37,10 @@
 
 namespace {
 
+using std::atan2;
+using std::sqrt;
+using std::tanh;
+
 // ---------------------------------------------------------------------------
 // D3Q19 velocity set (Sec. 2.1: "D3Q19 (three dimensions with 19 discrete
 // velocities)").  Weights are not printed in the paper; these are the standard
@@ -58,6 +62,46 @@ const double WQ[Q] = {
 const int OPP[Q] = {0, 2, 1, 4, 3, 6, 5, 8, 7, 10, 9, 12, 11, 14, 13, 16, 15, 18, 17};
 
 inline double val(double a) { return a; }
+
+// ---------------------------------------------------------------------------
+// Forward-mode dual number v + d eps (eps^2 = 0): running the simulation with
+// one parameter seeded (d = 1) gives the exact derivative of every quantity
+// with respect to that parameter alongside its value.  Reference gradient for
+// the differentiable variant below; shares nothing with any adjoint.
+// ---------------------------------------------------------------------------
+struct Dual {
+    double v = 0.0, d = 0.0;
+    Dual() = default;
+    Dual(double a) : v(a), d(0.0) {}
+    Dual(double a, double b) : v(a), d(b) {}
+};
+inline double val(const Dual& a) { return a.v; }
+inline Dual operator+(const Dual& a, const Dual& b) { return Dual(a.v + b.v, a.d + b.d); }
+inline Dual operator-(const Dual& a, const Dual& b) { return Dual(a.v - b.v, a.d - b.d); }
+inline Dual operator-(const Dual& a) { return Dual(-a.v, -a.d); }
+inline Dual operator*(const Dual& a, const Dual& b) { return Dual(a.v * b.v, a.d * b.v + a.v * b.d); }
+inline Dual operator/(const Dual& a, const Dual& b) {
+    return Dual(a.v / b.v, (a.d * b.v - a.v * b.d) / (b.v * b.v));
+}
+inline Dual operator+(const Dual& a, double b) { return Dual(a.v + b, a.d); }
+inline Dual operator+(double a, const Dual& b) { return Dual(a + b.v, b.d); }
+inline Dual operator-(const Dual& a, double b) { return Dual(a.v - b, a.d); }
+inline Dual operator-(double a, const Dual& b) { return Dual(a - b.v, -b.d); }
+inline Dual operator*(const Dual& a, double b) { return Dual(a.v * b, a.d * b); }
+inline Dual operator*(double a, const Dual& b) { return Dual(a * b.v, a * b.d); }
+inline Dual operator/(const Dual& a, double b) { return Dual(a.v / b, a.d / b); }
+inline Dual operator/(double a, const Dual& b) { return Dual(a / b.v, -a * b.d / (b.v * b.v)); }
+inline Dual sqrt(const Dual& a) {
+    const double r = std::sqrt(a.v);
+    return Dual(r, a.d / (2.0 * r));
+}
+inline Dual atan2(const Dual& y, const Dual& x) {
+    return Dual(std::atan2(y.v, x.v), (x.v * y.d - y.v * x.d) / (x.v * x.v + y.v * y.v));
+}
+inline Dual tanh(const Dual& a) {
+    const double t = std::tanh(a.v);
+    return Dual(t, (1.0 - t * t) * a.d);
+}
 
 // ---------------------------------------------------------------------------
 // Equilibrium (Sec. 2.1: f^eq depends on rho and u; form not printed).
@@ -332,15 +376,15 @@ R dihedral(const R* xa, const R* xb, const R* xc, const R* xd) {
     cross3(e, ac, n1);
     cross3(ba, bd, n2);
     cross3(n1, n2, m);
-    R le = std::sqrt(dot3(e, e));
-    return std::atan2(dot3(m, e) / le, dot3(n1, n2));
+    R le = sqrt(dot3(e, e));
+    return atan2(dot3(m, e) / le, dot3(n1, n2));
 }
 
 template <class R>
 R tri_area(const R* xa, const R* xb, const R* xc) {
     R ab[3], ac[3], n[3];
     sub3(xb, xa, ab); sub3(xc, xa, ac); cross3(ab, ac, n);
-    return 0.5 * std::sqrt(dot3(n, n));
+    return 0.5 * sqrt(dot3(n, n));
 }
 
 // Enclosed volume of a closed outward mesh: V = sum_t x_a . (x_b x x_c) / 6.
@@ -392,9 +436,9 @@ void force_stretch(const R* x, const Topology& T, const Rest& r, double ks, R* F
         int a = T.ea[e], b = T.eb[e];
         R d[3];
         sub3(&x[3 * b], &x[3 * a], d);
-        R L = std::sqrt(dot3(d, d));
+        R L = sqrt(dot3(d, d));
         R lam = L / r.L0[e];
-        R sl = std::sqrt(lam);
+        R sl = sqrt(lam);
         R kappa = (sl + 1.0 / (lam * lam * sl)) / (lam + 1.0 / (lam * lam * lam));
         R tension = ks * kappa * (lam - 1.0);
         for (int k = 0; k < 3; ++k) {
@@ -424,7 +468,7 @@ void force_bend(const R* x, const Topology& T, const Rest& r, double kb, R* F) {
         cross3(ev, ac, n1);
         cross3(ba, bd, n2);
         R l2 = dot3(ev, ev);
-        R l = std::sqrt(l2);
+        R l = sqrt(l2);
         R n1s = dot3(n1, n1), n2s = dot3(n2, n2);
         R sc = dot3(ac, ev) / l2, sd = dot3(ad, ev) / l2;
         R coef = -kb * (theta - r.th0[e]);
@@ -566,6 +610,185 @@ void rasterise(const float* sph, int ns, int nx, int ny, int nz, uint8_t* solid)
             }
 }
 
+// ---------------------------------------------------------------------------
+// Differentiable variant: the gradient of a filter objective with respect to
+// the bead centres and the objective cell's stretching and bending moduli.
+// A solid bitmask is piecewise constant in a bead centre (its derivative is
+// zero almost everywhere), so here the beads are a smooth solid fraction
+//   phi_k(x) = 1/2 [1 - tanh((|x - c_k| - r_k) / delta)],
+//   phi(x)   = 1 - prod_k (1 - phi_k(x))          (union of the beads),
+// acting as a Brinkman force density g_B = -alpha phi rho u taken implicitly:
+//   u = (sum_i f_i e_i + g / 2) / (rho (1 + alpha phi / 2)),
+//   g_tot = g - alpha phi rho u   in the Guo source.
+// With alpha = 2 a node with phi = 1 leaves the collision with momentum g/2.
+// Walls stay halfway bounce-back; nothing is a bitmask obstacle.
+// Readings (the paper treats beads as bounce-back nodes only): the form of
+// phi, the union, alpha = 2 and delta = 0.5 lu are this variant's constants.
+// Objective: J = mean x-coordinate of the objective cell's nodes after T
+// cycles minus the same at t = 0.
+// ---------------------------------------------------------------------------
+template <class R>
+void brinkman_phi(const Fluid<R>& F, const std::vector<R>& bead, double delta, std::vector<R>& phi) {
+    const int nb = (int)bead.size() / 4;
+    phi.assign((size_t)F.n, R(0.0));
+#pragma omp parallel for schedule(static)
+    for (int z = 0; z < F.nz; ++z)
+        for (int y = 0; y < F.ny; ++y)
+            for (int x = 0; x < F.nx; ++x) {
+                R prod = 1.0;
+                for (int k = 0; k < nb; ++k) {
+                    R dx = (double)x - bead[4 * k], dy = (double)y - bead[4 * k + 1], dz = (double)z - bead[4 * k + 2];
+                    R d2 = dx * dx + dy * dy + dz * dz;
+                    R dist = val(d2) > 0.0 ? sqrt(d2) : R(0.0);
+                    R phik = 0.5 * (1.0 - tanh((dist - bead[4 * k + 3]) / delta));
+                    prod = prod * (1.0 - phik);
+                }
+                phi[F.idx(x, y, z)] = 1.0 - prod;
+            }
+}
+
+// One LB step of the differentiable variant: lb_step with the Brinkman term in
+// place of obstacle nodes.
+template <class R>
+void lb_step_brinkman(Fluid<R>& F, const std::vector<R>& phi, double alpha) {
+    const long N = F.n;
+#pragma omp parallel for schedule(static)
+    for (int z = 0; z < F.nz; ++z) {
+        for (int y = 0; y < F.ny; ++y) {
+            for (int x = 0; x < F.nx; ++x) {
+                const long p = F.idx(x, y, z);
+                R fl[Q];
+                for (int i = 0; i < Q; ++i) fl[i] = F.f[(size_t)i * N + p];
+                R rho = 0.0;
+                for (int i = 0; i < Q; ++i) rho = rho + fl[i];
+                R mom[3] = {0.0, 0.0, 0.0};
+                for (int i = 0; i < Q; ++i)
+                    for (int d = 0; d < 3; ++d) mom[d] = mom[d] + EV[i][d] * fl[i];
+                R g[3];
+                for (int d = 0; d < 3; ++d) g[d] = F.g[(size_t)d * N + p] + F.G[d];
+                R u[3], gt[3];
+                const R den = rho * (1.0 + 0.5 * alpha * phi[p]);
+                for (int d = 0; d < 3; ++d) u[d] = (mom[d] + 0.5 * g[d]) / den;
+                for (int d = 0; d < 3; ++d) gt[d] = g[d] - alpha * phi[p] * rho * u[d];
+                R feq[Q], S[Q];
+                equilibrium(rho, u, feq);
+                guo_source(F.tau, u, gt, S);
+                F.rho[p] = rho;
+                for (int d = 0; d < 3; ++d) F.u[(size_t)d * N + p] = u[d];
+                for (int i = 0; i < Q; ++i) {
+                    R post = fl[i] - (fl[i] - feq[i]) / F.tau + S[i];
+                    int c[3] = {x + EV[i][0], y + EV[i][1], z + EV[i][2]};
+                    const int dim[3] = {F.nx, F.ny, F.nz};
+                    bool blocked = false;
+                    for (int d = 0; d < 3; ++d)
+                        if (c[d] < 0 || c[d] >= dim[d]) {
+                            if (F.per[d]) c[d] = (c[d] + dim[d]) % dim[d];
+                            else blocked = true;
+                        }
+                    if (blocked) F.fn[(size_t)OPP[i] * N + p] = post;
+                    else F.fn[(size_t)i * N + F.idx(c[0], c[1], c[2])] = post;
+                }
+            }
+        }
+    }
+    F.f.swap(F.fn);
+}
+
+struct DiffMesh {
+    std::vector<double> x0;
+    std::vector<int> tri;
+    double mod[5];
+};
+
+struct DiffProblem {
+    int nx, ny, nz;
+    double tau, G[3];
+    int per[3];
+    std::vector<double> beads;   // cx, cy, cz, r per bead
+    double alpha, delta;
+    std::vector<DiffMesh> meshes;
+};
+
+enum { SEED_NONE = 0, SEED_BEAD = 1, SEED_KS = 2, SEED_KB = 3 };
+
+// A parameter value carrying the seed direction (unit tangent) when R is Dual.
+template <class R> R seeded(double v);
+template <> double seeded<double>(double v) { return v; }
+template <> Dual seeded<Dual>(double v) { return Dual(v, 1.0); }
+
+// Run T cycles from rest (f = w) and return J; with R = Dual and one parameter
+// seeded, J.d is dJ / d(parameter).  u_out / x_out (optional, R = double) take
+// the last cycle's velocity and every mesh's final positions.
+template <class R>
+R diff_run(const DiffProblem& P, int steps, int obj, int seed_kind, int seed_index, double* u_out, double* x_out) {
+    Fluid<R> F;
+    fluid_init(F, P.nx, P.ny, P.nz);
+    F.tau = P.tau;
+    for (int d = 0; d < 3; ++d) { F.G[d] = P.G[d]; F.per[d] = P.per[d]; }
+    std::vector<R> bead(P.beads.begin(), P.beads.end());
+    if (seed_kind == SEED_BEAD) bead[4 * (seed_index / 3) + seed_index % 3] = seeded<R>(P.beads[4 * (seed_index / 3) + seed_index % 3]);
+    std::vector<R> phi;
+    brinkman_phi(F, bead, P.delta, phi);
+    struct C {
+        Topology T;
+        Rest rest;
+        double mod[5];
+        std::vector<R> x, Fa, Fs, Fb, Ftot, U;
+        R ks, kb;
+    };
+    std::vector<C> cells(P.meshes.size());
+    for (size_t m = 0; m < P.meshes.size(); ++m) {
+        const DiffMesh& dm = P.meshes[m];
+        C& c = cells[m];
+        const int n = (int)dm.x0.size() / 3;
+        build_topology(dm.tri.data(), (int)dm.tri.size() / 3, n, c.T);
+        rest_state(dm.x0.data(), c.T, c.rest);
+        for (int k = 0; k < 5; ++k) c.mod[k] = dm.mod[k];
+        c.x.assign(dm.x0.begin(), dm.x0.end());
+        c.Fa.assign(3 * n, R(0.0)); c.Fs = c.Fa; c.Fb = c.Fa; c.Ftot = c.Fa; c.U = c.Fa;
+        c.ks = dm.mod[0];
+        c.kb = dm.mod[1];
+        if ((int)m == obj && seed_kind == SEED_KS) c.ks = seeded<R>(dm.mod[0]);
+        if ((int)m == obj && seed_kind == SEED_KB) c.kb = seeded<R>(dm.mod[1]);
+    }
+    for (int t = 0; t < steps; ++t) {
+        std::fill(F.g.begin(), F.g.end(), R(0.0));
+        for (auto& c : cells) {
+            const int n = c.T.n;
+            // area and volume terms with the stated moduli; stretching and
+            // bending are linear in ks and kb: ks * F_stretch(1) + kb * F_bend(1)
+            membrane_forces(c.x.data(), c.T, c.rest, c.mod, TERM_AREA_LOCAL | TERM_AREA_GLOBAL | TERM_VOLUME, c.Fa.data());
+            std::fill(c.Fs.begin(), c.Fs.end(), R(0.0));
+            std::fill(c.Fb.begin(), c.Fb.end(), R(0.0));
+            force_stretch(c.x.data(), c.T, c.rest, 1.0, c.Fs.data());
+            force_bend(c.x.data(), c.T, c.rest, 1.0, c.Fb.data());
+            for (int j = 0; j < 3 * n; ++j) c.Ftot[j] = c.Fa[j] + c.ks * c.Fs[j] + c.kb * c.Fb[j];
+            spread(F, c.x.data(), c.Ftot.data(), n, F.g.data());
+        }
+        lb_step_brinkman(F, phi, P.alpha);
+        for (auto& c : cells) {
+            interpolate(F, c.x.data(), c.T.n, F.u.data(), c.U.data());
+            for (int j = 0; j < 3 * c.T.n; ++j) c.x[j] = c.x[j] + c.U[j];
+        }
+    }
+    if (u_out)
+        for (size_t k = 0; k < F.u.size(); ++k) u_out[k] = val(F.u[k]);
+    if (x_out) {
+        size_t o = 0;
+        for (auto& c : cells)
+            for (auto& v : c.x) x_out[o++] = val(v);
+    }
+    const C& co = cells[obj];
+    const int n = co.T.n;
+    R mx = 0.0;
+    double mx0 = 0.0;
+    for (int j = 0; j < n; ++j) {
+        mx = mx + co.x[3 * j];
+        mx0 += P.meshes[obj].x0[3 * j];
+    }
+    return mx / (double)n - mx0 / (double)n;
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -686,6 +909,63 @@ void or_sys_get_forces(void* h, int m, double* F) {
 void or_sys_step(void* h, int n_steps) {
     OrSys* s = (OrSys*)h;
     for (int k = 0; k < n_steps; ++k) system_step(*s);
+}
+
+// Differentiable variant (see diff_run).
+void* or_diff_create(int nx, int ny, int nz, double tau, const double* G, const int* per, int nb, const double* beads,
+                     double alpha, double delta) {
+    if (nx < 1 || ny < 1 || nz < 1 || !(tau > 0.5) || nb < 0) return nullptr;
+    DiffProblem* P = new DiffProblem();
+    P->nx = nx; P->ny = ny; P->nz = nz; P->tau = tau;
+    for (int d = 0; d < 3; ++d) { P->G[d] = G[d]; P->per[d] = per[d]; }
+    P->beads.assign(beads, beads + 4 * nb);
+    P->alpha = alpha;
+    P->delta = delta;
+    return P;
+}
+
+void or_diff_destroy(void* h) { delete (DiffProblem*)h; }
+
+int or_diff_add_mesh(void* h, const double* x0, int n, const int* tri, int nt, const double* mod) {
+    DiffProblem* P = (DiffProblem*)h;
+    Topology T;
+    if (!build_topology(tri, nt, n, T)) return -1;
+    DiffMesh m;
+    m.x0.assign(x0, x0 + 3 * n);
+    m.tri.assign(tri, tri + 3 * nt);
+    for (int k = 0; k < 5; ++k) m.mod[k] = mod[k];
+    P->meshes.push_back(std::move(m));
+    return (int)P->meshes.size() - 1;
+}
+
+// J after `steps` cycles; with seed_kind != 0 also dJ/d(parameter) in *dJ:
+// seed_kind 1 = bead coordinate seed_index (3 k + axis), 2 = ks, 3 = kb of mesh obj.
+double or_diff_run(void* h, int steps, int obj, int seed_kind, int seed_index, double* dJ) {
+    DiffProblem* P = (DiffProblem*)h;
+    if (seed_kind == SEED_NONE) {
+        if (dJ) *dJ = 0.0;
+        return diff_run<double>(*P, steps, obj, SEED_NONE, 0, nullptr, nullptr);
+    }
+    Dual J = diff_run<Dual>(*P, steps, obj, seed_kind, seed_index, nullptr, nullptr);
+    if (dJ) *dJ = J.d;
+    return J.v;
+}
+
+// Final velocity field (3 x N) and positions of every mesh (concatenated) after `steps` cycles.
+double or_diff_state(void* h, int steps, int obj, double* u, double* x) {
+    DiffProblem* P = (DiffProblem*)h;
+    return diff_run<double>(*P, steps, obj, SEED_NONE, 0, u, x);
+}
+
+// The solid fraction field (N) of the variant.
+void or_diff_phi(void* h, double* phi) {
+    DiffProblem* P = (DiffProblem*)h;
+    Fluid<double> F;
+    F.nx = P->nx; F.ny = P->ny; F.nz = P->nz;
+    F.n = (long)P->nx * P->ny * P->nz;
+    std::vector<double> ph;
+    brinkman_phi(F, P->beads, P->delta, ph);
+    std::memcpy(phi, ph.data(), sizeof(double) * F.n);
 }
 
 // Standalone pieces used by the pin tests.
