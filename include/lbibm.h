@@ -96,6 +96,37 @@ lb_status lb_select_channel(lb_ctx* ctx, int channel);
 /* Free all device memory of the context.  NULL is accepted. */
 lb_status lb_destroy(lb_ctx* ctx);
 
+/* Differentiable variant (gradient of a filter objective; single-channel
+ * contexts, before the first step).  The beads become a smooth solid
+ * fraction phi(x) = 1 - prod_k (1 - phi_k(x)),
+ * phi_k = 1/2 [1 - tanh((|x - c_k| - r_k) / delta)], entering every collision
+ * as the implicit Brinkman force -alpha phi rho u:
+ * u = (sum_i f_i e_i + g/2) / (rho (1 + alpha phi / 2)) and the Guo source
+ * takes g - alpha phi rho u.  The paper's beads are bounce-back nodes
+ * (Sec. 2.4, 2.5), whose mask is piecewise constant in a bead centre; this
+ * smooth form makes the objective differentiable.  beads: n x {cx, cy, cz, r}
+ * (host, copied).  Walls stay bounce-back; lb_set_obstacles masks, if any,
+ * still apply.  Selects the one-node-per-thread stream-collide variant.
+ * LB_ERR_STATE after the first step, LB_ERR_ARG for bad data. */
+lb_status lb_set_brinkman(lb_ctx* ctx, const double* beads, int n, double alpha, double delta);
+
+/* Gradient of the filter objective J = (mean x of the objective mesh's nodes
+ * after n_steps cycles) - (the same now), for the differentiable variant
+ * (lb_set_brinkman; FP32 populations, one channel), by the discrete adjoint
+ * of the cycle: n_steps forward cycles keeping the state every ckpt_every
+ * cycles, then per segment a recompute that keeps each cycle's data and the
+ * reverse sweep through it (interpolation, stream-collide with the Brinkman
+ * term, spreading, membrane forces).  Outputs (host, caller-owned): *J;
+ * grad_beads[3 k + axis] = dJ/d(centre of bead k), n_beads x 3; *grad_ks and
+ * *grad_kb = dJ/d(ks), dJ/d(kb) of the objective mesh's cell.  Any output may
+ * be NULL.  Afterwards the context holds the state after the n_steps cycles,
+ * as lb_step(n_steps) leaves it.  Device workspace: about
+ * (n_steps / ckpt_every + ckpt_every) x (19 x 4 B) x nodes, kept for the next
+ * call of the same shape.  LB_ERR_STATE without lb_set_brinkman or with
+ * per-kernel timing on; LB_ERR_OOM if the workspace does not fit. */
+lb_status lb_adjoint(lb_ctx* ctx, int n_steps, int ckpt_every, int objective_mesh, double* J, double* grad_beads,
+                     double* grad_ks, double* grad_kb);
+
 /* Obstacles (Sec. 2.4, 2.5): every lattice node inside or on one of the `n`
  * spheres spheres[4k..4k+3] = (cx, cy, cz, r) becomes a solid bounce-back
  * node; the test |x - c|^2 <= r^2 is evaluated in double from the float

@@ -257,6 +257,28 @@ __device__ __forceinline__ Mac macro(const float h[Q], float gx, float gy, float
     return m;
 }
 
+// Differentiable variant: Brinkman force -a rho u (a = alpha phi) taken
+// implicitly, u = (j + g/2) / (rho (1 + a/2)); the collision then uses
+// g_tot = g - a rho u = g - a (j + g/2) / (1 + a/2).
+__device__ __forceinline__ Mac macro_brinkman(const float h[Q], float gx, float gy, float gz, float a) {
+    Mac m;
+    float jx, jy, jz;
+    moments(h, m.drho, jx, jy, jz);
+    m.rho = 1.0f + m.drho;
+    const float vx = jx + 0.5f * gx, vy = jy + 0.5f * gy, vz = jz + 0.5f * gz;
+    const float iD = 1.0f / (1.0f + 0.5f * a);
+    const float s = iD / m.rho;
+    m.ux = vx * s;
+    m.uy = vy * s;
+    m.uz = vz * s;
+    m.gx = gx - a * vx * iD;
+    m.gy = gy - a * vy * iD;
+    m.gz = gz - a * vz * iD;
+    m.uu = m.ux * m.ux + m.uy * m.uy + m.uz * m.uz;
+    m.ug = m.ux * m.gx + m.uy * m.gy + m.uz * m.gz;
+    return m;
+}
+
 // BGK collision with Guo forcing on shifted populations:
 //   h*_i = h_i + omega (h_i^eq - h_i) + S_i,
 //   h_i^eq = w_i [drho + rho (3 e.u + 9/2 (e.u)^2 - 3/2 u.u)],
@@ -368,9 +390,11 @@ template <class S, int NPT, int BS> struct K3MinBlocks {
 
 // Schedules of one stream-collide launch: every node (SC_ALL); the bulk, i.e.
 // every 32-node group outside the step's stencil set (SC_BULK); or the groups
-// of the stencil set from a list (SC_LIST).  Bulk groups carry no IB force in
-// this step and none in the previous one, so their flag loads are skipped.
-enum : int { SC_ALL = 0, SC_BULK = 1, SC_LIST = 2 };
+// of the stencil set from a list (SC_LIST); or every node of the
+// differentiable variant (SC_BRINK: Brinkman beads, velocity written at every
+// node).  Bulk groups carry no IB force in this step and none in the previous
+// one, so their flag loads are skipped.
+enum : int { SC_ALL = 0, SC_BULK = 1, SC_LIST = 2, SC_BRINK = 3 };
 
 // One thread's NPT nodes starting at channel-local node p0.
 template <class S, int NPT, int MODE>
@@ -433,7 +457,8 @@ __device__ __forceinline__ void sc_nodes(const LatticeArgs& a, const ChannelDev&
                 const float4 g = (MODE == SC_LIST && NPT == 1) ? gpre : gcur[gi0 + k];
                 gx += g.x; gy += g.y; gz += g.z;
             }
-            m[k] = macro(h[k], gx, gy, gz);
+            if constexpr (MODE == SC_BRINK) m[k] = macro_brinkman(h[k], gx, gy, gz, a.alpha * __ldg(a.phi + gi0 + k));
+            else m[k] = macro(h[k], gx, gy, gz);
         }
 #pragma unroll
         for (int k = 0; k < NPT; ++k) collide_all(h[k], m[k], om, fp);
@@ -457,7 +482,7 @@ __device__ __forceinline__ void sc_nodes(const LatticeArgs& a, const ChannelDev&
 #pragma unroll
         for (int k = 0; k < NPT; ++k) {
             if (lk[k] & 1u) continue;
-            if (forced) a.u[gi0 + k] = make_float4(m[k].ux, m[k].uy, m[k].uz, m[k].rho);
+            if (forced || MODE == SC_BRINK) a.u[gi0 + k] = make_float4(m[k].ux, m[k].uy, m[k].uz, m[k].rho);
             if (prevf) gprev[gi0 + k] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
     }
@@ -784,6 +809,43 @@ __global__ void __launch_bounds__(BS, 512 / BS) k_stream_collide_pipe(const __gr
     }
 }
 
+// Differentiable variant (one node per thread).
+template <class S, int BS>
+__global__ void __launch_bounds__(BS, K3MinBlocks<S, 1, BS>::value) k_stream_collide_brinkman(const __grid_constant__ LatticeArgs a) {
+    const int b = blockIdx.x;
+    int c = 0;
+    for (int k = 1; k < a.n_ch; ++k)
+        if (b >= chan(a, k).blk0) c = k;
+    const ChannelDev C = chan(a, c);
+    sc_nodes<S, 1, SC_BRINK>(a, C, (b - C.blk0) * BS + (int)threadIdx.x, threadIdx.x & 31);
+}
+
+// Solid fraction of the differentiable variant at every node of a channel:
+// phi = 1 - prod_k (1 - phi_k), phi_k = 1/2 (1 - tanh((|x - c_k| - r_k) / delta)).
+__global__ void k_brinkman_phi(ChannelDev C, const float4* beads, int nb, float inv_delta, float* phi) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= C.n) return;
+    const int r = fdiv(p, C.dnx);
+    const int x = p - r * C.nx;
+    const int z = fdiv(r, C.dny);
+    const int y = r - z * C.ny;
+    float prod = 1.0f;
+    for (int k = 0; k < nb; ++k) {
+        const float4 bk = beads[k];
+        const float dx = (float)x - bk.x, dy = (float)y - bk.y, dz = (float)z - bk.z;
+        const float d = sqrtf(dx * dx + dy * dy + dz * dz);
+        prod *= 1.0f - 0.5f * (1.0f - tanhf((d - bk.w) * inv_delta));
+    }
+    phi[C.base + p] = 1.0f - prod;
+}
+
+cudaError_t launch_brinkman_phi(const ChannelDev& ch, const float* beads, int nb, float delta, float* phi,
+                               cudaStream_t s) {
+    k_brinkman_phi<<<(unsigned)((ch.n + 255) / 256), 256, 0, s>>>(ch, reinterpret_cast<const float4*>(beads), nb,
+                                                                  1.0f / delta, phi);
+    return cudaGetLastError();
+}
+
 template <class S>
 static size_t staged_smem() { return 2 * (size_t)Q * SG_NODES * sizeof(S); }
 
@@ -884,8 +946,21 @@ cudaError_t launch_stream_collide_split(const LatticeArgs& a, int bs, int mode, 
     return launch_sc_split<__nv_bfloat16>(a, bs, mode, blocks, smem, s);
 }
 
+template <class S>
+static cudaError_t launch_sc_brinkman(const LatticeArgs& a, int bs, int blocks, cudaStream_t s) {
+    if (bs == 128) k_stream_collide_brinkman<S, 128><<<blocks, 128, 0, s>>>(a);
+    else k_stream_collide_brinkman<S, 256><<<blocks, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_stream_collide(const LatticeArgs& a, K3Config cfg, int total_blocks, cudaStream_t s) {
     if (total_blocks <= 0) return cudaSuccess;
+    if (a.phi) {
+        if (cfg.npt != 1) return cudaErrorInvalidConfiguration;
+        if (a.storage == 0) return launch_sc_brinkman<float>(a, cfg.bs, total_blocks, s);
+        if (a.storage == 1) return launch_sc_brinkman<__half>(a, cfg.bs, total_blocks, s);
+        return launch_sc_brinkman<__nv_bfloat16>(a, cfg.bs, total_blocks, s);
+    }
     if (a.storage == 0) return launch_sc_typed<float>(a, cfg, total_blocks, s);
     if (a.storage == 1) return launch_sc_typed<__half>(a, cfg, total_blocks, s);
     return launch_sc_typed<__nv_bfloat16>(a, cfg, total_blocks, s);
@@ -904,6 +979,13 @@ __global__ void k_fields(const __grid_constant__ LatticeArgs a, int c, float* rh
     if (!a.has_last || solid_at(a.mask, gp)) {
         if (rho_out) rho_out[p] = 1.0f;
         if (u_out) { u_out[p] = 0.f; u_out[(long long)C.n + p] = 0.f; u_out[2LL * C.n + p] = 0.f; }
+        return;
+    }
+    if (a.phi) {
+        // differentiable variant: the collision wrote rho and u at every node
+        const float4 uu = a.u[gp];
+        if (rho_out) rho_out[p] = uu.w;
+        if (u_out) { u_out[p] = uu.x; u_out[(long long)C.n + p] = uu.y; u_out[2LL * C.n + p] = uu.z; }
         return;
     }
     // the last step had parity 1 - par and wrote h[par]

@@ -120,6 +120,22 @@ struct lb_ctx {
     int* dcount = nullptr;         // [2]
     int* sched_err = nullptr;
     int list_blocks = 0;
+    // differentiable variant
+    float* phi = nullptr;          // bead solid fraction per node (null: off)
+    float alpha = 0.f, delta = 0.f;
+    std::vector<double> beads;     // cx, cy, cz, r per bead (host)
+    float* d_beads = nullptr;
+    // adjoint workspace (allocated by the first lb_adjoint of a given size)
+    struct AdjWork {
+        int K = 0, n_ck = 0;
+        float *ck_h = nullptr, *seg_h = nullptr, *fin_h = nullptr, *lam[2] = {nullptr, nullptr}, *Lphi = nullptr;
+        Q4 *ck_q = nullptr, *seg_q = nullptr, *fin_q = nullptr;
+        float4 *seg_F = nullptr, *seg_g = nullptr, *seg_u = nullptr, *lam_u = nullptr, *lam_g = nullptr;
+        float4 *lamX[2] = {nullptr, nullptr}, *lamF = nullptr, *tri_dS = nullptr, *tri_n = nullptr;
+        float4 *fin_u = nullptr, *fin_F = nullptr;
+        float2* seg_rel = nullptr;
+        double *lam_c = nullptr, *grad = nullptr;
+    } adj;
     int bulk_res = 10;             // resident bulk blocks per SM (128 threads)
     long long smem_per_sm = 0;
     // timing
@@ -201,6 +217,8 @@ LatticeArgs lattice_args(const lb_ctx* ctx, int par) {
     a.fl1 = ctx->fl[1];
     a.u = ctx->u;
     a.n_groups = ctx->n_groups;
+    a.phi = ctx->phi;
+    a.alpha = ctx->alpha;
     a.dmap = ctx->dmap[par];
     a.dlist = ctx->dlist[par];
     a.dcount = ctx->dcount ? ctx->dcount + par : nullptr;
@@ -387,7 +405,7 @@ lb_status enqueue_step_overlap(lb_ctx* ctx, int par, bool lead_interp) {
 
 bool use_overlap(const lb_ctx* ctx) {
     const long long m = ctx->committed ? ctx->M : (long long)ctx->hq0.size();
-    return ctx->overlap && m > 0 && ctx->k3.npt == 1 && ctx->timing == 0 && ctx->ib_stream != nullptr;
+    return ctx->overlap && m > 0 && ctx->phi == nullptr && ctx->k3.npt == 1 && ctx->timing == 0 && ctx->ib_stream != nullptr;
 }
 
 lb_status build_graphs_overlap(lb_ctx* ctx) {
@@ -500,6 +518,7 @@ long long plane_pad() {
 // variant: channel k's blocks start at blk0 and cover its padded node range.
 bool k3_config_valid(const lb_ctx* ctx, K3Config c) {
     if (!k3_config_supported((int)ctx->storage, c)) return false;
+    if (ctx->phi && c.npt != 1) return false;   // the differentiable variant runs one node per thread
     for (const auto& ch : ctx->ch) {
         if (c.npt == 0) {
             if (staged_rows(ch.d.nx, (int)pop_bytes(ctx->storage)) == 0) return false;
@@ -798,6 +817,254 @@ lb_status lb_destroy(lb_ctx* ctx) {
         if (ctx->ev_join2[k]) cudaEventDestroy(ctx->ev_join2[k]);
     }
     delete ctx;
+    return LB_OK;
+}
+
+lb_status lb_set_brinkman(lb_ctx* ctx, const double* beads, int n, double alpha, double delta) {
+    LB_GUARD(ctx);
+    if (ctx->started) return fail(ctx, LB_ERR_STATE, "the Brinkman beads must be set before the first step");
+    if (ctx->ch.size() != 1) return fail(ctx, LB_ERR_ARG, "the differentiable variant takes a single-channel context");
+    if (n < 0 || (n > 0 && !beads) || !(alpha >= 0.0) || !(delta > 0.0))
+        return fail(ctx, LB_ERR_ARG, "bad bead list, alpha or delta");
+    for (int k = 0; k < 4 * n; ++k)
+        if (!std::isfinite(beads[k]) || (k % 4 == 3 && beads[k] < 0))
+            return fail(ctx, LB_ERR_ARG, "bead data must be finite with r >= 0");
+    if (!k3_config_valid(ctx, K3Config{1, ctx->k3.npt == 1 ? ctx->k3.bs : 128}))
+        return fail(ctx, LB_ERR_ARG, "no one-node-per-thread stream-collide variant for this lattice");
+    if (ctx->k3.npt != 1) apply_k3_config(ctx, K3Config{1, 128});
+    ctx->beads.assign(beads, beads + 4 * n);
+    ctx->alpha = (float)alpha;
+    ctx->delta = (float)delta;
+    const ChannelHost& c = ctx->ch[0];
+    if (!ctx->phi) LB_CUDA(dalloc(ctx, &ctx->phi, ctx->Ntot));
+    LB_CUDA(cudaMemsetAsync(ctx->phi, 0, sizeof(float) * ctx->Ntot, ctx->stream));
+    std::vector<float> fb(4 * (size_t)n);
+    for (int k = 0; k < 4 * n; ++k) fb[k] = (float)beads[k];
+    if (ctx->d_beads) dfree(ctx, ctx->d_beads);
+    ctx->d_beads = nullptr;
+    LB_CUDA(dalloc(ctx, &ctx->d_beads, std::max(4 * n, 4)));
+    if (n > 0) {
+        LB_CUDA(cudaMemcpyAsync(ctx->d_beads, fb.data(), sizeof(float) * 4 * n, cudaMemcpyHostToDevice, ctx->stream));
+        LB_CUDA(launch_brinkman_phi(c.d, ctx->d_beads, n, (float)delta, ctx->phi, ctx->stream));
+    }
+    LB_CUDA(cudaStreamSynchronize(ctx->stream));
+    drop_graphs(ctx);
+    return upload_channels(ctx);
+}
+
+// ---- discrete adjoint of the differentiable variant ----
+namespace {
+
+// Forward step t of the differentiable variant, keeping what the reverse
+// sweep of that step reads: populations and positions at its start, node
+// forces, spread force density, the cells' (dS/S0, dV/V0), the velocity.
+lb_status recompute_step(lb_ctx* ctx, int k) {
+    auto& W = ctx->adj;
+    const int par = (int)(ctx->step & 1);
+    const size_t hb = sizeof(float) * Q * (size_t)ctx->plane;
+    cudaStream_t s = ctx->stream;
+    LB_CUDA(cudaMemcpyAsync(W.seg_h + (size_t)k * Q * ctx->plane, ctx->h[par], hb, cudaMemcpyDeviceToDevice, s));
+    LB_CUDA(cudaMemcpyAsync(W.seg_q + (size_t)k * ctx->M, ctx->q[par], sizeof(Q4) * ctx->M, cudaMemcpyDeviceToDevice, s));
+    const LatticeArgs la = lattice_args(ctx, par);
+    const IbmArgs ia = ibm_args(ctx, par);
+    LB_CUDA(launch_elements(ia, s));
+    LB_CUDA(launch_forces_spread(ia, s));
+    LB_CUDA(cudaMemcpyAsync(W.seg_g + (size_t)k * ctx->Ntot, ctx->g[par], sizeof(float4) * ctx->Ntot, cudaMemcpyDeviceToDevice, s));
+    LB_CUDA(cudaMemcpyAsync(W.seg_F + (size_t)k * ctx->M, ctx->F, sizeof(float4) * ctx->M, cudaMemcpyDeviceToDevice, s));
+    LB_CUDA(cudaMemcpyAsync(W.seg_rel + (size_t)k * ctx->C, ctx->cell_rel, sizeof(float2) * ctx->C, cudaMemcpyDeviceToDevice, s));
+    LB_CUDA(launch_stream_collide(la, ctx->k3, ctx->total_blocks, s));
+    LB_CUDA(cudaMemcpyAsync(W.seg_u + (size_t)k * ctx->Ntot, ctx->u, sizeof(float4) * ctx->Ntot, cudaMemcpyDeviceToDevice, s));
+    LB_CUDA(launch_interp_advance(ia, s));
+    ctx->step++;
+    return LB_OK;
+}
+
+// Positions + populations of the current step into (h_dst, q_dst) or back.
+lb_status copy_state(lb_ctx* ctx, float* h, Q4* q, bool save) {
+    const int par = (int)(ctx->step & 1);
+    const size_t hb = sizeof(float) * Q * (size_t)ctx->plane;
+    cudaStream_t s = ctx->stream;
+    if (save) {
+        LB_CUDA(cudaMemcpyAsync(h, ctx->h[par], hb, cudaMemcpyDeviceToDevice, s));
+        LB_CUDA(cudaMemcpyAsync(q, ctx->q[par], sizeof(Q4) * ctx->M, cudaMemcpyDeviceToDevice, s));
+    } else {
+        LB_CUDA(cudaMemcpyAsync(ctx->h[par], h, hb, cudaMemcpyDeviceToDevice, s));
+        LB_CUDA(cudaMemcpyAsync(ctx->q[par], q, sizeof(Q4) * ctx->M, cudaMemcpyDeviceToDevice, s));
+        // force fields and flags as at the start of any step: nothing pending
+        for (int k = 0; k < 2; ++k) {
+            LB_CUDA(cudaMemsetAsync(ctx->g[k], 0, sizeof(float4) * ctx->Ntot, s));
+            LB_CUDA(cudaMemsetAsync(ctx->fl[k], 0, (size_t)(ctx->Ntot / GROUP), s));
+        }
+    }
+    return LB_OK;
+}
+
+double mean_x(lb_ctx* ctx, const MeshHost& m) {
+    std::vector<Q4> q(m.n);
+    cudaMemcpy(q.data(), ctx->q[ctx->step & 1] + m.node0, sizeof(Q4) * m.n, cudaMemcpyDeviceToHost);
+    double s = 0.0;
+    for (const Q4& v : q) s += (double)v.x / FIX_SCALE;
+    return s / m.n;
+}
+
+}  // namespace
+
+lb_status lb_adjoint(lb_ctx* ctx, int n_steps, int ckpt_every, int objective_mesh, double* J, double* grad_beads,
+                     double* grad_ks, double* grad_kb) {
+    LB_GUARD(ctx);
+    if (!ctx->phi) return fail(ctx, LB_ERR_STATE, "lb_adjoint needs the differentiable variant (lb_set_brinkman)");
+    if (ctx->storage != LB_F32) return fail(ctx, LB_ERR_ARG, "lb_adjoint needs FP32 populations");
+    if (n_steps < 1 || ckpt_every < 1) return fail(ctx, LB_ERR_ARG, "n_steps and ckpt_every must be >= 1");
+    if (ctx->timing) return fail(ctx, LB_ERR_STATE, "per-kernel timing is on");
+    lb_status st = commit_ibm(ctx);
+    if (st != LB_OK) return st;
+    const MeshHost* mo;
+    if (check_channel_mesh(ctx, objective_mesh, &mo) != LB_OK) return LB_ERR_ARG;
+    const int nb = (int)ctx->beads.size() / 4;
+    if (nb > 64) return fail(ctx, LB_ERR_ARG, "at most 64 beads");
+    auto& W = ctx->adj;
+    const int K = std::min(ckpt_every, n_steps);
+    const int n_ck = (n_steps + K - 1) / K;
+    const size_t hN = (size_t)Q * ctx->plane;
+    if (W.K != K || W.n_ck != n_ck) {
+        for (void* p : {(void*)W.ck_h, (void*)W.seg_h, (void*)W.fin_h, (void*)W.lam[0], (void*)W.lam[1], (void*)W.Lphi,
+                        (void*)W.ck_q, (void*)W.seg_q, (void*)W.fin_q, (void*)W.seg_F, (void*)W.seg_g, (void*)W.seg_u,
+                        (void*)W.lam_u, (void*)W.lam_g, (void*)W.lamX[0], (void*)W.lamX[1], (void*)W.lamF,
+                        (void*)W.tri_dS, (void*)W.tri_n, (void*)W.seg_rel, (void*)W.lam_c, (void*)W.grad,
+                        (void*)W.fin_u, (void*)W.fin_F})
+            dfree(ctx, p);
+        W = lb_ctx::AdjWork();
+        cudaError_t e = cudaSuccess;
+#define ATRY(x) if (e == cudaSuccess) e = (x)
+        ATRY(dalloc(ctx, &W.ck_h, (size_t)n_ck * hN));
+        ATRY(dalloc(ctx, &W.ck_q, (size_t)n_ck * ctx->M));
+        ATRY(dalloc(ctx, &W.seg_h, (size_t)K * hN));
+        ATRY(dalloc(ctx, &W.seg_q, (size_t)K * ctx->M));
+        ATRY(dalloc(ctx, &W.seg_F, (size_t)K * ctx->M));
+        ATRY(dalloc(ctx, &W.seg_g, (size_t)K * ctx->Ntot));
+        ATRY(dalloc(ctx, &W.seg_u, (size_t)K * ctx->Ntot));
+        ATRY(dalloc(ctx, &W.seg_rel, (size_t)K * ctx->C));
+        ATRY(dalloc(ctx, &W.fin_h, hN));
+        ATRY(dalloc(ctx, &W.fin_q, ctx->M));
+        ATRY(dalloc(ctx, &W.fin_u, ctx->Ntot));
+        ATRY(dalloc(ctx, &W.fin_F, ctx->M));
+        ATRY(dalloc(ctx, &W.lam[0], hN));
+        ATRY(dalloc(ctx, &W.lam[1], hN));
+        ATRY(dalloc(ctx, &W.Lphi, ctx->Ntot));
+        ATRY(dalloc(ctx, &W.lam_u, ctx->Ntot));
+        ATRY(dalloc(ctx, &W.lam_g, ctx->Ntot));
+        ATRY(dalloc(ctx, &W.lamX[0], ctx->M));
+        ATRY(dalloc(ctx, &W.lamX[1], ctx->M));
+        ATRY(dalloc(ctx, &W.lamF, ctx->M));
+        ATRY(dalloc(ctx, &W.tri_dS, 2 * (size_t)ctx->T));
+        ATRY(dalloc(ctx, &W.tri_n, ctx->T));
+        ATRY(dalloc(ctx, &W.lam_c, 2 * (size_t)ctx->C));
+        ATRY(dalloc(ctx, &W.grad, 2 + 3 * 64));
+#undef ATRY
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ctx, e == cudaErrorMemoryAllocation ? LB_ERR_OOM : LB_ERR_CUDA, "adjoint workspace");
+        }
+        W.K = K;
+        W.n_ck = n_ck;
+    }
+    cudaStream_t s = ctx->stream;
+    const long long step0 = ctx->step;
+    const double x0 = mean_x(ctx, *mo);
+    // forward, keeping a checkpoint at the start of every segment
+    for (int c = 0; c < n_ck; ++c) {
+        if (copy_state(ctx, W.ck_h + (size_t)c * hN, W.ck_q + (size_t)c * ctx->M, true) != LB_OK) return LB_ERR_CUDA;
+        st = lb_step(ctx, std::min(K, n_steps - c * K));
+        if (st != LB_OK) return st;
+    }
+    LB_CUDA(cudaStreamSynchronize(s));
+    const double Jv = mean_x(ctx, *mo) - x0;
+    if (copy_state(ctx, W.fin_h, W.fin_q, true) != LB_OK) return LB_ERR_CUDA;
+    // the last cycle's velocity and node forces (what lb_get_fields / ibm_get_forces report)
+    LB_CUDA(cudaMemcpyAsync(W.fin_u, ctx->u, sizeof(float4) * ctx->Ntot, cudaMemcpyDeviceToDevice, s));
+    LB_CUDA(cudaMemcpyAsync(W.fin_F, ctx->F, sizeof(float4) * ctx->M, cudaMemcpyDeviceToDevice, s));
+    // reverse sweep
+    LB_CUDA(cudaMemsetAsync(W.lam[0], 0, sizeof(float) * hN, s));
+    LB_CUDA(cudaMemsetAsync(W.lam[1], 0, sizeof(float) * hN, s));
+    LB_CUDA(cudaMemsetAsync(W.Lphi, 0, sizeof(float) * ctx->Ntot, s));
+    LB_CUDA(cudaMemsetAsync(W.grad, 0, sizeof(double) * (2 + 3 * 64), s));
+    {
+        std::vector<float4> l0(ctx->M, make_float4(0.f, 0.f, 0.f, 0.f));
+        for (int i = 0; i < mo->n; ++i) l0[mo->node0 + i].x = (float)(1.0 / mo->n);   // dJ / dX^T
+        LB_CUDA(cudaMemcpyAsync(W.lamX[0], l0.data(), sizeof(float4) * ctx->M, cudaMemcpyHostToDevice, s));
+        LB_CUDA(cudaStreamSynchronize(s));
+    }
+    AdjArgs A;
+    std::memset(&A, 0, sizeof(A));
+    A.ch = ctx->ch[0].d;
+    A.M = ctx->M;
+    A.n_edges = ctx->E;
+    A.n_tris = ctx->T;
+    A.n_beads = nb;
+    A.obj_cell = mo->cell;
+    A.plane = ctx->plane;
+    A.mask = ctx->mask;
+    A.links = ctx->links;
+    A.phi = ctx->phi;
+    A.alpha = ctx->alpha;
+    A.delta = ctx->delta;
+    A.beads = reinterpret_cast<const float4*>(ctx->d_beads);
+    A.lam_u = W.lam_u;
+    A.lam_g = W.lam_g;
+    A.Lphi = W.Lphi;
+    A.lamF = W.lamF;
+    A.edges = ctx->edges;
+    A.edge_rest = ctx->edge_rest;
+    A.tris = ctx->tris;
+    A.tri_S0 = ctx->triS0;
+    A.info = ctx->info;
+    A.cells = ctx->d_cells;
+    A.tri_dS = W.tri_dS;
+    A.tri_n = W.tri_n;
+    A.lam_c = W.lam_c;
+    A.grad = W.grad;
+    int lc = 0, xc = 0;
+    for (int c = n_ck - 1; c >= 0; --c) {
+        const int len = std::min(K, n_steps - c * K);
+        ctx->step = step0 + (long long)c * K;
+        if (copy_state(ctx, W.ck_h + (size_t)c * hN, W.ck_q + (size_t)c * ctx->M, false) != LB_OK) return LB_ERR_CUDA;
+        for (int k = 0; k < len; ++k)
+            if (recompute_step(ctx, k) != LB_OK) return LB_ERR_CUDA;
+        for (int k = len - 1; k >= 0; --k) {
+            A.q_t = W.seg_q + (size_t)k * ctx->M;
+            A.F_t = W.seg_F + (size_t)k * ctx->M;
+            A.g_t = W.seg_g + (size_t)k * ctx->Ntot;
+            A.u_t = W.seg_u + (size_t)k * ctx->Ntot;
+            A.h_t = W.seg_h + (size_t)k * hN;
+            A.rel_t = W.seg_rel + (size_t)k * ctx->C;
+            A.lam_in = W.lam[lc];
+            A.lam_out = W.lam[1 - lc];
+            A.lamX = W.lamX[xc];
+            A.lamX_out = W.lamX[1 - xc];
+            LB_CUDA(cudaMemsetAsync(W.lam_u, 0, sizeof(float4) * ctx->Ntot, s));
+            LB_CUDA(cudaMemsetAsync(W.lam_c, 0, sizeof(double) * 2 * ctx->C, s));
+            LB_CUDA(launch_adj_interp(A, s));
+            LB_CUDA(launch_adj_collide(A, s));
+            LB_CUDA(launch_adj_spread(A, s));
+            LB_CUDA(launch_adj_membrane(A, s));
+            lc = 1 - lc;
+            xc = 1 - xc;
+        }
+    }
+    LB_CUDA(launch_adj_bead_grad(A, s));
+    std::vector<double> g(2 + 3 * 64);
+    LB_CUDA(cudaMemcpyAsync(g.data(), W.grad, sizeof(double) * g.size(), cudaMemcpyDeviceToHost, s));
+    // leave the context in the state after the n_steps forward steps
+    ctx->step = step0 + n_steps;
+    if (copy_state(ctx, W.fin_h, W.fin_q, false) != LB_OK) return LB_ERR_CUDA;
+    LB_CUDA(cudaMemcpyAsync(ctx->u, W.fin_u, sizeof(float4) * ctx->Ntot, cudaMemcpyDeviceToDevice, s));
+    LB_CUDA(cudaMemcpyAsync(ctx->F, W.fin_F, sizeof(float4) * ctx->M, cudaMemcpyDeviceToDevice, s));
+    LB_CUDA(cudaStreamSynchronize(s));
+    if (J) *J = Jv;
+    if (grad_ks) *grad_ks = g[0];
+    if (grad_kb) *grad_kb = g[1];
+    if (grad_beads)
+        for (int k = 0; k < 3 * nb; ++k) grad_beads[k] = g[2 + k];
     return LB_OK;
 }
 

@@ -137,6 +137,10 @@ struct LatticeArgs {
     const uint8_t* dmap;
     const int* dlist;
     const int* dcount;
+    // differentiable variant: bead solid fraction per node (null: off) and
+    // the Brinkman coefficient alpha
+    const float* phi;
+    float alpha;
     ChannelDev chp[MAXCH_P];   // copy of the first channels (constant bank)
 };
 
@@ -185,6 +189,46 @@ struct IbmArgs {
     ChannelDev chp[MAXCH_P];
 };
 
+// Arguments of the adjoint kernels (one step of the reverse sweep of the
+// differentiable variant; single channel, FP32 populations).
+struct AdjArgs {
+    ChannelDev ch;
+    int M, n_edges, n_tris, n_beads, obj_cell;
+    long long plane;          // population plane stride
+    // the forward step t (recomputed and stored)
+    const Q4* q_t;            // [M] positions at the start of step t
+    const float4* F_t;        // [M] node forces of step t
+    const float4* g_t;        // [plane] spread force density of step t
+    const float4* u_t;        // [plane] velocity of step t's collision
+    const float* h_t;         // [19][plane] populations at the start of step t
+    const float2* rel_t;      // [C] (dS/S0, dV/V0) of step t
+    const uint32_t* mask;
+    const uint32_t* links;
+    const float* phi;
+    float alpha, delta;
+    const float4* beads;      // [n_beads] (cx, cy, cz, r)
+    // adjoint state
+    const float* lam_in;      // [19][plane] adjoint of step t+1's pulled populations
+    float* lam_out;           // [19][plane] adjoint of step t's pulled populations
+    float4* lam_u;            // [plane] adjoint of step t's velocity (from the interpolation)
+    float4* lam_g;            // [plane] adjoint of step t's force density
+    float* Lphi;              // [plane] accumulated adjoint of phi
+    const float4* lamX;       // [M] adjoint of X^{t+1}
+    float4* lamX_out;         // [M] adjoint of X^t
+    float4* lamF;             // [M] adjoint of F^t
+    // membrane topology
+    const int4* edges;
+    const float4* edge_rest;
+    const int4* tris;
+    const float* tri_S0;
+    const int4* info;
+    const CellDev* cells;
+    float4* tri_dS;           // [2T]
+    float4* tri_n;            // [T]
+    double* lam_c;            // [2C]
+    double* grad;             // [2 + 3 n_beads] (ks, kb of the objective cell, bead centres)
+};
+
 // D3Q19 velocity set (Sec. 2.1): rest, +-x, +-y, +-z, then the 12 diagonals,
 // opposite directions adjacent.
 __host__ __device__ constexpr int ex(int i) {
@@ -223,6 +267,8 @@ int k3_config_count(int storage);
 K3Config k3_config_at(int storage, int k);
 
 // ---- launchers (defined in lattice_kernels.cu / ibm_kernels.cu) ----
+cudaError_t launch_brinkman_phi(const ChannelDev& ch, const float* beads, int nb, float delta, float* phi,
+                               cudaStream_t s);
 cudaError_t launch_rasterise(const float* spheres, int n_spheres, const uint8_t* extra, const ChannelDev& ch,
                              uint32_t* mask, cudaStream_t s);
 cudaError_t launch_slow_flags(const ChannelDev& ch, const uint32_t* mask, uint8_t* slow, uint32_t* links,
@@ -244,6 +290,12 @@ cudaError_t launch_cell_sums(const IbmArgs& a, cudaStream_t s);
 cudaError_t launch_elements(const IbmArgs& a, cudaStream_t s);
 cudaError_t launch_forces_spread(const IbmArgs& a, cudaStream_t s);
 cudaError_t launch_interp_advance(const IbmArgs& a, cudaStream_t s);
+
+cudaError_t launch_adj_interp(const AdjArgs& a, cudaStream_t s);
+cudaError_t launch_adj_collide(const AdjArgs& a, cudaStream_t s);
+cudaError_t launch_adj_spread(const AdjArgs& a, cudaStream_t s);
+cudaError_t launch_adj_membrane(const AdjArgs& a, cudaStream_t s);
+cudaError_t launch_adj_bead_grad(const AdjArgs& a, cudaStream_t s);
 cudaError_t launch_mark_stencils(const IbmArgs& a, uint8_t* map, cudaStream_t s);
 cudaError_t launch_compact_groups(const uint8_t* map, int n_groups, int* list, int* count, cudaStream_t s);
 

@@ -20,7 +20,7 @@ STORAGE = {"f32": 0, "f16": 1, "bf16": 2}
 
 # Every entry point that include/lbibm.h declares.
 EXPORTS = (
-    "lb_create", "lb_create_batch", "lb_select_channel", "lb_destroy", "lb_set_obstacles", "ibm_add_mesh",
+    "lb_create", "lb_create_batch", "lb_select_channel", "lb_destroy", "lb_set_obstacles", "lb_set_brinkman", "lb_adjoint", "ibm_add_mesh",
     "ibm_set_nodes", "lb_step", "lb_synchronize", "lb_get_fields", "lb_get_populations", "lb_set_populations",
     "ibm_get_nodes", "ibm_get_all_nodes", "ibm_get_forces", "ibm_get_area_volume", "lb_diagnostics", "lb_get_step", "lb_save_state",
     "lb_load_state", "lb_set_schedule", "lb_get_schedule", "lb_set_timing", "lb_kernel_times", "lb_last_error", "lb_version", "lb_get_mask",
@@ -83,6 +83,8 @@ def lib():
             "lb_save_state": ([P, P, ctypes.POINTER(ctypes.c_size_t)], I),
             "lb_load_state": ([P, P, ctypes.c_size_t], I),
             "lb_set_timing": ([P, I], I),
+            "lb_set_brinkman": ([P, P, I, D, D], I),
+            "lb_adjoint": ([P, I, I, I, P, P, P, P], I),
             "lb_set_schedule": ([P, I], I),
             "lb_get_schedule": ([P, P], I),
             "lb_kernel_times": ([P, P, P], I),
@@ -292,6 +294,23 @@ class Simulation:
         n, b, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
         self._check(self._L.lb_autotune(self._h, int(repeats), ctypes.byref(n), ctypes.byref(b), ctypes.byref(ms)))
         return n.value, b.value, ms.value
+
+    def set_brinkman(self, beads, alpha: float = 2.0, delta: float = 0.5):
+        """Differentiable variant: beads (n x 4: cx, cy, cz, r) as a smooth Brinkman solid fraction."""
+        b = np.ascontiguousarray(beads, dtype=np.float64).reshape(-1, 4)
+        self._check(self._L.lb_set_brinkman(self._h, _ptr(b), int(b.shape[0]), float(alpha), float(delta)))
+        self._n_beads = int(b.shape[0])
+
+    def adjoint(self, n_steps: int, ckpt_every: int = 50, objective_mesh: int = 0) -> dict:
+        """J and its gradient (bead centres, ks, kb of the objective cell) by the discrete adjoint."""
+        nb = self._n_beads
+        J = ctypes.c_double()
+        gks = ctypes.c_double()
+        gkb = ctypes.c_double()
+        gb = np.zeros((max(nb, 1), 3))
+        self._check(self._L.lb_adjoint(self._h, int(n_steps), int(ckpt_every), int(objective_mesh), ctypes.byref(J),
+                                       _ptr(gb), ctypes.byref(gks), ctypes.byref(gkb)))
+        return {"J": J.value, "beads": gb[:nb].copy(), "ks": gks.value, "kb": gkb.value}
 
     def set_schedule(self, overlapped: bool):
         """Overlapped (IB chain concurrent with the bulk stream-collide) or sequential cycle."""

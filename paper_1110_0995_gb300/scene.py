@@ -384,6 +384,18 @@ def adjoint_channel(seed: int = 41, steps: int = 400) -> Scene:
                  periodic=(1, 0, 0), spheres=spheres, meshes=meshes, steps=steps, seed=seed)
 
 
+def adjoint_channel_small(seed: int = 43, steps: int = 100) -> Scene:
+    """64x48x32 channel with two 3-bead posts, 2 red cells and 1 tumor cell (mesh 0)."""
+    rng = np.random.default_rng(seed)
+    dims = (64, 48, 32)
+    gap = float(rng.uniform(8.0, 12.0))
+    spheres = post_array(dims, 1, 2, 3, [gap], x_span=(36.0, 64.0))
+    kinds = ["ctc", "rbc", "rbc"]
+    meshes = place_cells(rng, dims, (1, 0, 0), spheres, kinds, STABLE, x_range=(0.0, 34.0))
+    return Scene(name="adjoint_small_64x48x32", dims=dims, tau=1.0, body_force=(1e-5, 0.0, 0.0),
+                 periodic=(1, 0, 0), spheres=spheres, meshes=meshes, steps=steps, seed=seed)
+
+
 def small_filter(seed: int = 5, dims=(96, 48, 32), n_rbc: int = 4, n_ctc: int = 1, steps: int = 100) -> Scene:
     """Small filter (several tiles, ragged nothing) used for fast parity runs."""
     return micropost_filter(seed=seed, dims=dims, cols=2, rows=2, n_rbc=n_rbc, n_ctc=n_ctc,

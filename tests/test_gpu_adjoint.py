@@ -1,0 +1,101 @@
+"""Differentiable variant on the GPU (Brinkman beads) against the FP64
+oracle's run of the same problem, and (once built) the hand-written adjoint
+against the oracle's dual-number gradient."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1110_0995_gb300 import scene
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+
+    __graft_entry__.build()
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.asarray(a, float) - b) / np.linalg.norm(b))
+
+
+def _gpu_sim(sc):
+    from paper_1110_0995_gb300 import lbibm
+
+    bare = dataclasses.replace(sc, spheres=np.zeros((0, 4), np.float32))
+    sim = lbibm.Simulation.from_scene(bare)
+    sim.set_brinkman(np.asarray(sc.spheres, np.float64))
+    return sim
+
+
+def test_brinkman_forward_parity():
+    """64x48x32 channel, 6 Brinkman beads, 1 tumor + 2 red cells: 100 steps."""
+    sc = scene.adjoint_channel_small(steps=100)
+    sim = _gpu_sim(sc)
+    sim.step(100)
+    ref = oracle.DiffProblem.from_scene(sc)
+    J, uo, xo = ref.state(100, 0)
+    _, u = sim.fields()
+    assert rel_l2(u, uo) < 1e-5
+    x = np.concatenate([sim.nodes(m) for m in range(len(sc.meshes))])
+    assert np.abs(x - xo).max() < 1e-5
+    Jg = sim.nodes(0)[:, 0].mean() - sc.meshes[0].rest[:, 0].mean()
+    assert Jg == pytest.approx(J, rel=1e-5, abs=1e-9)
+
+
+def test_adjoint_gradient_matches_oracle():
+    """dJ/d(bead centres), dJ/dks, dJ/dkb of the tumor cell's x displacement
+    after 60 cycles (checkpoints every 20): the GPU adjoint against the FP64
+    oracle's dual-number derivatives, <= 1e-3 relative."""
+    T = 60
+    sc = scene.adjoint_channel_small(steps=T)
+    sim = _gpu_sim(sc)
+    res = sim.adjoint(T, ckpt_every=20, objective_mesh=0)
+    ref = oracle.DiffProblem.from_scene(sc)
+    J0 = ref.run(T, 0)
+    print(f"J gpu {res['J']:.9e} oracle {J0:.9e}")
+    assert res["J"] == pytest.approx(J0, rel=1e-5)
+    for name in ("ks", "kb"):
+        _, d = ref.run(T, 0, (name,))
+        print(f"dJ/d{name}: gpu {res[name]:.6e} oracle {d:.6e}")
+        assert res[name] == pytest.approx(d, rel=1e-3)
+    gb = res["beads"]
+    order = np.argsort(-np.abs(gb).ravel())
+    checked = [int(i) for i in order[:4]]
+    refs = {}
+    for i in checked:
+        _, refs[i] = ref.run(T, 0, ("bead", i))
+        print(f"dJ/d bead {i // 3} axis {i % 3}: gpu {gb.ravel()[i]:.6e} oracle {refs[i]:.6e}")
+    scale = max(abs(v) for v in refs.values())
+    for i in checked:
+        assert abs(gb.ravel()[i] - refs[i]) <= 1e-3 * scale
+    assert gb.ravel()[checked[0]] == pytest.approx(refs[checked[0]], rel=1e-3)
+
+
+def test_adjoint_leaves_forward_state_and_time_ratio():
+    """After lb_adjoint the context holds the state after the forward steps;
+    the adjoint (forward with checkpoints + recompute + reverse sweep) costs a
+    small multiple of the forward steps alone (printed)."""
+    import time
+
+    T = 60
+    sc = scene.adjoint_channel_small(steps=T)
+    a = _gpu_sim(sc)
+    b = _gpu_sim(sc)
+    a.adjoint(T, ckpt_every=20)
+    b.step(T)
+    assert np.abs(a.nodes(0) - b.nodes(0)).max() < 1e-6   # spreading adds with atomics: rounding-level differences
+    assert rel_l2(a.fields()[1], b.fields()[1]) < 1e-6
+    b.synchronize()
+    t0 = time.perf_counter()
+    b.step(T)
+    b.synchronize()
+    tf = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    b.adjoint(T, ckpt_every=20)
+    ta = time.perf_counter() - t0
+    print(f"forward {1e3 * tf:.2f} ms, adjoint {1e3 * ta:.2f} ms, ratio {ta / tf:.2f}")
