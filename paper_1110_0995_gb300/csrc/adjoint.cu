@@ -7,8 +7,10 @@
 //   membrane forces          F = F(X; ks, kb, ...)
 // each as a vector-Jacobian product written out by hand.  The adjoint of the
 // pull is a gather from the neighbours (the push, read backwards).  Element
-// Jacobians are taken column by column in forward mode (a float dual number
-// per input coordinate), so no second derivative is derived by hand.
+// Jacobians are taken in forward mode (float dual numbers), so no second
+// derivative is derived by hand: for the energy-derived edge forces one
+// evaluation along the adjoint (symmetric Jacobian), for the triangle forces
+// (the homocentric area force is not a gradient) one per input coordinate.
 // Populations are FP32 (shifted storage h = f - w; the shift is a constant).
 #include "lbibm_internal.cuh"
 
@@ -164,121 +166,6 @@ __global__ void k_adj_spread(const __grid_constant__ AdjArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// (B2) stream-collide, reversed, one node per thread.  Gathers the adjoint of
-// this step's output h'(x) from the adjoint of the next step's pulled
-// populations (lam_in): the next step pulled h'_k(x) at x + e_k, or at x
-// itself as direction opp(k) when that link bounces back.  Then the
-// vector-Jacobian product of the collision with respect to the pulled
-// populations (lam_out), the force density (lam_g) and the solid fraction
-// (accumulated into Lphi).
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ int nb_off(const ChannelDev& C, int x, int y, int z, int dx, int dy, int dz, bool& ok) {
-    ok = true;
-    int xs = x + dx, ys = y + dy, zs = z + dz;
-    if (xs < 0 || xs >= C.nx) { if (C.per[0]) xs = (xs + C.nx) % C.nx; else ok = false; }
-    if (ys < 0 || ys >= C.ny) { if (C.per[1]) ys = (ys + C.ny) % C.ny; else ok = false; }
-    if (zs < 0 || zs >= C.nz) { if (C.per[2]) zs = (zs + C.nz) % C.nz; else ok = false; }
-    return ok ? (xs - x) + C.nx * ((ys - y) + C.ny * (zs - z)) : 0;
-}
-
-__global__ void __launch_bounds__(128) k_adj_collide(const __grid_constant__ AdjArgs a) {
-    const ChannelDev& C = a.ch;
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= C.n) return;
-    const long long gp = C.base + p;
-    if ((__ldg(a.mask + (gp >> 5)) >> (gp & 31)) & 1u) return;   // bitmask obstacle nodes do not update
-    const int r = fdiv(p, C.dnx);
-    const int x = p - r * C.nx;
-    const int z = fdiv(r, C.dny);
-    const int y = r - z * C.ny;
-    const long long NT = a.plane;
-    const uint32_t lk = __ldg(a.links + gp);
-    float f[Q], lh[Q];
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        // pulled population (forward): from x - e_i, or bounced back
-        bool ok;
-        const int o = nb_off(C, x, y, z, -ex(i), -ey(i), -ez(i), ok);
-        if ((lk >> i) & 1u) ok = false;
-        float v = ok ? __ldg(a.h_t + (long long)i * NT + gp + o) : __ldg(a.h_t + (long long)opp(i) * NT + gp);
-        if (!ok && C.has_uw && !C.per[1]) {
-            const int wall = (ey(i) == 1 && y == 0) ? 0 : ((ey(i) == -1 && y == C.ny - 1) ? 1 : -1);
-            if (wall >= 0) v += 6.0f * wgt(i) * (ex(i) * C.uw[wall][0] + ey(i) * C.uw[wall][1] + ez(i) * C.uw[wall][2]);
-        }
-        f[i] = v;
-        // adjoint of this node's output h'_i: the next step pulled it at x + e_i,
-        // unless that link bounces (bit opp(i) of this node's mask)
-        bool ok2;
-        const int o2 = nb_off(C, x, y, z, ex(i), ey(i), ez(i), ok2);
-        if ((lk >> opp(i)) & 1u) ok2 = false;
-        lh[i] = ok2 ? __ldg(a.lam_in + (long long)i * NT + gp + o2) : __ldg(a.lam_in + (long long)opp(i) * NT + gp);
-    }
-    // forward quantities (shifted populations: rho = 1 + sum h)
-    float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        drho += f[i];
-        jx += ex(i) * f[i]; jy += ey(i) * f[i]; jz += ez(i) * f[i];
-    }
-    const float rho = 1.0f + drho;
-    const float4 gs = a.g_t[gp];
-    const float gx = gs.x + C.G[0], gy = gs.y + C.G[1], gz = gs.z + C.G[2];
-    const float phi = a.phi ? __ldg(a.phi + gp) : 0.f;
-    const float al = a.alpha * phi;
-    const float D = 1.0f + 0.5f * al;
-    const float vx = jx + 0.5f * gx, vy = jy + 0.5f * gy, vz = jz + 0.5f * gz;
-    const float ux = vx / (rho * D), uy = vy / (rho * D), uz = vz / (rho * D);
-    const float tx = gx - al * vx / D, ty = gy - al * vy / D, tz = gz - al * vz / D;   // g_tot
-    const float uu = ux * ux + uy * uy + uz * uz;
-    const float om = C.omega, fp = C.fpre;   // omega = 1/tau, fp = 1 - omega/2
-    // sums over the outputs h'_i = (1 - om) f_i + om feq_i(rho, u) + S_i(u, g_tot)
-    float lrho = 0.f, lux = 0.f, luy = 0.f, luz = 0.f, ltx = 0.f, lty = 0.f, ltz = 0.f;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        const float L = lh[i];
-        const float w = wgt(i);
-        const float eu = ex(i) * ux + ey(i) * uy + ez(i) * uz;
-        const float et = ex(i) * tx + ey(i) * ty + ez(i) * tz;
-        // d feq_i / d rho = w (1 + 3 eu + 4.5 eu^2 - 1.5 uu)
-        lrho += L * om * w * (1.0f + 3.0f * eu + 4.5f * eu * eu - 1.5f * uu);
-        // d feq_i / d u = w rho (3 e + 9 eu e - 3 u);  d S_i / d u = fp w (-3 t + 9 et e)
-        const float a1 = om * w * rho * (3.0f + 9.0f * eu) + fp * w * 9.0f * et;
-        const float a2 = -3.0f * om * w * rho;
-        const float a3 = -3.0f * fp * w;
-        lux += L * (a1 * ex(i) + a2 * ux + a3 * tx);
-        luy += L * (a1 * ey(i) + a2 * uy + a3 * ty);
-        luz += L * (a1 * ez(i) + a2 * uz + a3 * tz);
-        // d S_i / d g_tot = fp w (3 (e - u) + 9 eu e)
-        const float b1 = fp * w * (3.0f + 9.0f * eu);
-        const float b2 = -3.0f * fp * w;
-        ltx += L * (b1 * ex(i) + b2 * ux);
-        lty += L * (b1 * ey(i) + b2 * uy);
-        ltz += L * (b1 * ez(i) + b2 * uz);
-    }
-    // the interpolation's use of u
-    const float4 lu = a.lam_u[gp];
-    lux += lu.x; luy += lu.y; luz += lu.z;
-    // u = v / (rho D), g_tot = g - al v / D, v = j + g/2
-    const float irD = 1.0f / (rho * D);
-    const float lvx = lux * irD - ltx * al / D, lvy = luy * irD - lty * al / D, lvz = luz * irD - ltz * al / D;
-    lrho -= (lux * ux + luy * uy + luz * uz) / rho;
-    const float lgx = 0.5f * lvx + ltx, lgy = 0.5f * lvy + lty, lgz = 0.5f * lvz + ltz;
-    // pulled populations: direct (1 - om), through rho (1) and j (e_i)
-    float* lo = a.lam_out;
-#pragma unroll
-    for (int i = 0; i < Q; ++i)
-        lo[(long long)i * NT + gp] = (1.0f - om) * lh[i] + lrho + ex(i) * lvx + ey(i) * lvy + ez(i) * lvz;
-    a.lam_g[gp] = make_float4(lgx, lgy, lgz, 0.f);
-    if (a.phi) {
-        // d u / d phi = -(alpha/2) v / (rho D^2);  d g_tot / d phi = -alpha v / D^2
-        const float iD2 = 1.0f / (D * D);
-        const float lphi = -0.5f * a.alpha * (lux * vx + luy * vy + luz * vz) * iD2 / rho -
-                           a.alpha * (ltx * vx + lty * vy + ltz * vz) * iD2;
-        a.Lphi[gp] += lphi;
-    }
-}
-
-// ---------------------------------------------------------------------------
 // (B4) edges: stretching + bending, reversed.  Positions relative to vertex a
 // (the forces depend on differences only, so the column of a is minus the sum
 // of the others).  9 forward-mode columns per edge.
@@ -314,7 +201,14 @@ __device__ __forceinline__ void edge_forces(const V3& xb, const V3& xc, const V3
     fb[3] = coef * gd;
 }
 
-__global__ void k_adj_edges(const __grid_constant__ AdjArgs a) {
+// Stretching and bending forces are minus the gradients of energies
+// (E = L0 int T(lambda) dlambda per bond, E = kb/2 (theta - theta0)^2 per
+// edge), so their Jacobian with respect to the four vertices is symmetric
+// (minus the Hessian) and the vector-Jacobian product with lamF is the
+// Jacobian-vector product along lamF: one forward-mode evaluation per edge,
+// seeded with the adjoint itself (relative to vertex a, the seeds are
+// lamF_v - lamF_a).
+__global__ void __launch_bounds__(128) k_adj_edges(const __grid_constant__ AdjArgs a) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     double gks = 0.0, gkb = 0.0;
     if (e < a.n_edges) {
@@ -322,31 +216,22 @@ __global__ void k_adj_edges(const __grid_constant__ AdjArgs a) {
         const float4 er = a.edge_rest[e];   // (L0, theta0, ks, kb)
         const Q4 qa = a.q_t[ev.x], qb = a.q_t[ev.y], qc = a.q_t[ev.z], qd = a.q_t[ev.w];
         const float4 la = a.lamF[ev.x], lb = a.lamF[ev.y], lc = a.lamF[ev.z], ld = a.lamF[ev.w];
-        const V3 xb0 = rel(qa, qb), xc0 = rel(qa, qc), xd0 = rel(qa, qd);
-        float acc[3][3];
-#pragma unroll 1
-        for (int col = 0; col < 9; ++col) {
-            V3 xb = xb0, xc = xc0, xd = xd0;
-            const int v = col / 3, k = col % 3;
-            if (v == 0) seed(xb, k);
-            else if (v == 1) seed(xc, k);
-            else seed(xd, k);
-            V3 fs[2], fb[4];
-            edge_forces<false>(xb, xc, xd, er.x, er.y, er.z, er.w, fs, fb);
-            acc[v][k] = tdot(fs[0], la) + tdot(fs[1], lb) + tdot(fb[0], la) + tdot(fb[1], lb) + tdot(fb[2], lc) +
-                        tdot(fb[3], ld);
-            if (col == 0 && a.info[ev.x].x == a.obj_cell) {
-                // parameter gradients (values are linear in ks and kb)
-                if (er.z != 0.f) gks = (double)((vdot(fs[0], la) + vdot(fs[1], lb)) / er.z);
-                if (er.w != 0.f)
-                    gkb = (double)((vdot(fb[0], la) + vdot(fb[1], lb) + vdot(fb[2], lc) + vdot(fb[3], ld)) / er.w);
-            }
+        V3 xb = rel(qa, qb), xc = rel(qa, qc), xd = rel(qa, qd);
+        xb.x.d = lb.x - la.x; xb.y.d = lb.y - la.y; xb.z.d = lb.z - la.z;
+        xc.x.d = lc.x - la.x; xc.y.d = lc.y - la.y; xc.z.d = lc.z - la.z;
+        xd.x.d = ld.x - la.x; xd.y.d = ld.y - la.y; xd.z.d = ld.z - la.z;
+        V3 fs[2], fb[4];
+        edge_forces<false>(xb, xc, xd, er.x, er.y, er.z, er.w, fs, fb);
+        atomic_add3(a.lamX_out + ev.x, fs[0].x.d + fb[0].x.d, fs[0].y.d + fb[0].y.d, fs[0].z.d + fb[0].z.d);
+        atomic_add3(a.lamX_out + ev.y, fs[1].x.d + fb[1].x.d, fs[1].y.d + fb[1].y.d, fs[1].z.d + fb[1].z.d);
+        atomic_add3(a.lamX_out + ev.z, fb[2].x.d, fb[2].y.d, fb[2].z.d);
+        atomic_add3(a.lamX_out + ev.w, fb[3].x.d, fb[3].y.d, fb[3].z.d);
+        if (a.info[ev.x].x == a.obj_cell) {
+            // parameter gradients (the forces are linear in ks and kb)
+            if (er.z != 0.f) gks = (double)((vdot(fs[0], la) + vdot(fs[1], lb)) / er.z);
+            if (er.w != 0.f)
+                gkb = (double)((vdot(fb[0], la) + vdot(fb[1], lb) + vdot(fb[2], lc) + vdot(fb[3], ld)) / er.w);
         }
-        atomic_add3(a.lamX_out + ev.y, acc[0][0], acc[0][1], acc[0][2]);
-        atomic_add3(a.lamX_out + ev.z, acc[1][0], acc[1][1], acc[1][2]);
-        atomic_add3(a.lamX_out + ev.w, acc[2][0], acc[2][1], acc[2][2]);
-        atomic_add3(a.lamX_out + ev.x, -(acc[0][0] + acc[1][0] + acc[2][0]), -(acc[0][1] + acc[1][1] + acc[2][1]),
-                    -(acc[0][2] + acc[1][2] + acc[2][2]));
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -382,45 +267,60 @@ __device__ __forceinline__ void tri_forces(const V3& xb, const V3& xc, float S0t
     f[2] = ca * av[2] - mk(c2) * n;
 }
 
-__global__ void k_adj_tris(const __grid_constant__ AdjArgs a) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= a.n_tris) return;
-    const int4 tr = a.tris[t];
-    const CellDev& C = a.cells[tr.w];
-    const float2 rel_sv = a.rel_t[tr.w];   // (dS/S0, dV/V0) of this step
-    const float c1 = C.kag * rel_sv.x, c2 = C.kv * rel_sv.y / 6.0f;
-    const Q4 qa = a.q_t[tr.x], qb = a.q_t[tr.y], qc = a.q_t[tr.z];
-    const float4 la = a.lamF[tr.x], lb = a.lamF[tr.y], lc = a.lamF[tr.z];
-    const V3 xb0 = rel(qa, qb), xc0 = rel(qa, qc);
-    const float S0t = a.tri_S0[t];
-    float acc[2][3], dS[2][3];
+// One thread per (triangle, column): column v*3+k seeds coordinate k of vertex
+// b or c (v = 0, 1); the column of a is minus their sum.  The column-0 thread
+// also forms the per-cell products and keeps the normal.
+__global__ void __launch_bounds__(128, 6) k_adj_tris(const __grid_constant__ AdjArgs a) {
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = tid / 6, col = tid - 6 * (tid / 6);
+    const bool valid = t < a.n_tris;   // every lane stays for the per-cell warp sums
+    int cell = -1;
     float lc1 = 0.f, lc2 = 0.f;
-    V3 n0;
-#pragma unroll 1
-    for (int col = 0; col < 6; ++col) {
-        V3 xb = xb0, xc = xc0;
+    if (valid) {
+        const int4 tr = a.tris[t];
+        const CellDev& C = a.cells[tr.w];
+        const float2 rel_sv = a.rel_t[tr.w];   // (dS/S0, dV/V0) of this step
+        const float c1 = C.kag * rel_sv.x, c2 = C.kv * rel_sv.y / 6.0f;
+        const Q4 qa = a.q_t[tr.x], qb = a.q_t[tr.y], qc = a.q_t[tr.z];
+        const float4 la = a.lamF[tr.x], lb = a.lamF[tr.y], lc = a.lamF[tr.z];
+        V3 xb = rel(qa, qb), xc = rel(qa, qc);
         const int v = col / 3, k = col % 3;
         if (v == 0) seed(xb, k);
         else seed(xc, k);
         V3 f[3], av[3], n;
         DF St;
-        tri_forces(xb, xc, S0t, C.kal, c1, c2, f, av, n, St);
-        acc[v][k] = tdot(f[0], la) + tdot(f[1], lb) + tdot(f[2], lc);
-        dS[v][k] = St.d;
+        tri_forces(xb, xc, a.tri_S0[t], C.kal, c1, c2, f, av, n, St);
+        const float acc = tdot(f[0], la) + tdot(f[1], lb) + tdot(f[2], lc);
+        atomicAdd(reinterpret_cast<float*>(a.lamX_out + (v == 0 ? tr.y : tr.z)) + k, acc);
+        atomicAdd(reinterpret_cast<float*>(a.lamX_out + tr.x) + k, -acc);
+        reinterpret_cast<float*>(a.tri_dS)[6 * t + col] = St.d;
         if (col == 0) {
+            cell = tr.w;
             lc1 = vdot(av[0], la) + vdot(av[1], lb) + vdot(av[2], lc);
             lc2 = -(vdot(n, la) + vdot(n, lb) + vdot(n, lc));
-            n0 = n;
+            a.tri_n[t] = make_float4(n.x.v, n.y.v, n.z.v, 0.f);
         }
     }
-    atomic_add3(a.lamX_out + tr.y, acc[0][0], acc[0][1], acc[0][2]);
-    atomic_add3(a.lamX_out + tr.z, acc[1][0], acc[1][1], acc[1][2]);
-    atomic_add3(a.lamX_out + tr.x, -(acc[0][0] + acc[1][0]), -(acc[0][1] + acc[1][1]), -(acc[0][2] + acc[1][2]));
-    a.tri_dS[2 * t] = make_float4(dS[0][0], dS[0][1], dS[0][2], 0.f);
-    a.tri_dS[2 * t + 1] = make_float4(dS[1][0], dS[1][1], dS[1][2], 0.f);
-    a.tri_n[t] = make_float4(n0.x.v, n0.y.v, n0.z.v, 0.f);
-    atomicAdd(a.lam_c + 2 * tr.w, (double)lc1);
-    atomicAdd(a.lam_c + 2 * tr.w + 1, (double)lc2);
+    // per-cell sums lam_c1, lam_c2 over the column-0 lanes: one atomic per cell per warp
+    const bool has = cell >= 0;
+    const int lane = threadIdx.x & 31;
+    unsigned rem = __ballot_sync(AFULL, has);
+    while (rem) {
+        const int l0 = __ffs(rem) - 1;
+        const int c = __shfl_sync(AFULL, cell, l0);
+        const bool mine = has && cell == c;
+        double s1 = mine ? (double)lc1 : 0.0, s2 = mine ? (double)lc2 : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            s1 += __shfl_xor_sync(AFULL, s1, o);
+            s2 += __shfl_xor_sync(AFULL, s2, o);
+        }
+        if (lane == l0) {
+            atomicAdd(a.lam_c + 2 * c, s1);
+            atomicAdd(a.lam_c + 2 * c + 1, s2);
+        }
+        rem &= ~__ballot_sync(AFULL, mine);
+    }
 }
 
 // (B6) the cell's global terms: lam_S = lam_c1 kag / S0, lam_V = lam_c2 kv / (6 V0);
@@ -432,7 +332,9 @@ __global__ void k_adj_tris_global(const __grid_constant__ AdjArgs a) {
     const CellDev& C = a.cells[tr.w];
     const float lS = (float)(a.lam_c[2 * tr.w] * (double)C.kag / C.S0);
     const float lV = (float)(a.lam_c[2 * tr.w + 1] * (double)C.kv / (6.0 * C.V0));
-    const float4 db = a.tri_dS[2 * t], dc = a.tri_dS[2 * t + 1], n = a.tri_n[t];
+    const float* ds = reinterpret_cast<const float*>(a.tri_dS) + 6 * t;
+    const float3 db = make_float3(ds[0], ds[1], ds[2]), dc = make_float3(ds[3], ds[4], ds[5]);
+    const float4 n = a.tri_n[t];
     const float vn = lV / 6.0f;
     atomic_add3(a.lamX_out + tr.y, lS * db.x + vn * n.x, lS * db.y + vn * n.y, lS * db.z + vn * n.z);
     atomic_add3(a.lamX_out + tr.z, lS * dc.x + vn * n.x, lS * dc.y + vn * n.y, lS * dc.z + vn * n.z);
@@ -500,10 +402,6 @@ cudaError_t launch_adj_interp(const AdjArgs& a, cudaStream_t s) {
     k_adj_interp<<<(a.M + 127) / 128, 128, 0, s>>>(a);
     return cudaGetLastError();
 }
-cudaError_t launch_adj_collide(const AdjArgs& a, cudaStream_t s) {
-    k_adj_collide<<<(a.ch.n + 127) / 128, 128, 0, s>>>(a);
-    return cudaGetLastError();
-}
 cudaError_t launch_adj_spread(const AdjArgs& a, cudaStream_t s) {
     k_adj_spread<<<(a.M + 127) / 128, 128, 0, s>>>(a);
     return cudaGetLastError();
@@ -511,7 +409,7 @@ cudaError_t launch_adj_spread(const AdjArgs& a, cudaStream_t s) {
 cudaError_t launch_adj_membrane(const AdjArgs& a, cudaStream_t s) {
     if (a.n_edges > 0) k_adj_edges<<<(a.n_edges + 127) / 128, 128, 0, s>>>(a);
     if (a.n_tris > 0) {
-        k_adj_tris<<<(a.n_tris + 127) / 128, 128, 0, s>>>(a);
+        k_adj_tris<<<(6 * a.n_tris + 127) / 128, 128, 0, s>>>(a);
         k_adj_tris_global<<<(a.n_tris + 127) / 128, 128, 0, s>>>(a);
     }
     return cudaGetLastError();

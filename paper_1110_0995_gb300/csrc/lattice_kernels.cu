@@ -967,6 +967,145 @@ cudaError_t launch_stream_collide(const LatticeArgs& a, K3Config cfg, int total_
 }
 
 // ---------------------------------------------------------------------------
+// Adjoint of the stream-collide of the differentiable variant (FP32
+// populations, one node per thread).  The adjoint of this step's output h'_i
+// at x is gathered from the adjoint of the next step's pulled populations:
+// the next step pulled h'_i at x + e_i, or at x itself as direction opp(i)
+// when that link bounces back (bit opp(i) of x's link mask).  Then the
+// vector-Jacobian product of h'_i = (1 - om) f_i + om f^eq_i(rho, u) + S_i(u, g_tot)
+// with u = (j + g/2) / (rho D), g_tot = g - a (j + g/2) / D, D = 1 + a/2,
+// a = alpha phi, with respect to the pulled populations f (lam_out), the force
+// density g (lam_g) and phi (accumulated into Lphi); lam_u carries the
+// interpolation's use of u.
+// ---------------------------------------------------------------------------
+template <int I, bool SLOW>
+__device__ __forceinline__ void adj_pull(const AdjArgs& a, long long NT, int gi, const Nbr& nb, uint32_t lk,
+                                         const ChannelDev& C, int y, float f[Q], float lh[Q]) {
+    const float* hp = a.h_t + (size_t)I * (size_t)NT;       // plane of direction I (warp-uniform)
+    const float* lp = a.lam_in + (size_t)I * (size_t)NT;
+    bool ok, ok2;
+    const int o = src_off<I>(nb, ok);
+    const int o2 = src_off<opp(I)>(nb, ok2);   // offset to x + e_I
+    if constexpr (!SLOW) {
+        // no wall or obstacle link in this warp's group
+        f[I] = __ldg(hp + gi + o);
+        lh[I] = __ldg(lp + gi + o2);
+    } else {
+        if ((lk >> I) & 1u) ok = false;
+        float v = ok ? __ldg(hp + gi + o) : __ldg(a.h_t + (size_t)opp(I) * (size_t)NT + gi);
+        if (!ok && C.has_uw && !C.per[1]) {
+            const int wall = (ey(I) == 1 && y == 0) ? 0 : ((ey(I) == -1 && y == C.ny - 1) ? 1 : -1);
+            if (wall >= 0) v += 6.0f * wgt(I) * (ex(I) * C.uw[wall][0] + ey(I) * C.uw[wall][1] + ez(I) * C.uw[wall][2]);
+        }
+        f[I] = v;
+        if ((lk >> opp(I)) & 1u) ok2 = false;
+        lh[I] = ok2 ? __ldg(lp + gi + o2) : __ldg(a.lam_in + (size_t)opp(I) * (size_t)NT + gi);
+    }
+}
+
+template <bool SLOW>
+__device__ __forceinline__ void adj_node(const AdjArgs& a, const ChannelDev& C, int gi, int x, int y, int z) {
+    const long long gp = gi;
+    Nbr nb;
+    neighbours(C, x, y, z, nb);
+    const long long NT = a.plane;
+    const uint32_t lk = SLOW ? __ldg(a.links + gp) : 0u;
+    float f[Q], lh[Q];
+#define LBIBM_AP(I) adj_pull<I, SLOW>(a, NT, gi, nb, lk, C, y, f, lh);
+    LBIBM_ALL_I(LBIBM_AP)
+#undef LBIBM_AP
+    float drho, jx, jy, jz;
+    moments(f, drho, jx, jy, jz);
+    const float rho = 1.0f + drho;
+    const float irho = 1.0f / rho;
+    // IB force, the interpolation's adjoint and lam_g live on the stencil groups only
+    const bool forced = __ldg(a.fl_t + (gp >> 5)) != 0;
+    float gx = C.G[0], gy = C.G[1], gz = C.G[2];
+    float4 lu = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (forced) {
+        const float4 gs = a.g_t[gp];
+        gx += gs.x; gy += gs.y; gz += gs.z;
+        lu = a.lam_u[gp];
+        a.lam_u[gp] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    const float phi = a.phi ? __ldg(a.phi + gp) : 0.f;
+    const float al = a.alpha * phi;
+    const float iD = 1.0f / (1.0f + 0.5f * al);
+    const float vx = jx + 0.5f * gx, vy = jy + 0.5f * gy, vz = jz + 0.5f * gz;
+    const float s = iD * irho;
+    const float ux = vx * s, uy = vy * s, uz = vz * s;
+    const float tx = gx - al * vx * iD, ty = gy - al * vy * iD, tz = gz - al * vz * iD;   // g_tot
+    const float uu = ux * ux + uy * uy + uz * uz;
+    const float om = C.omega, fp = C.fpre;
+    // sums over the outputs, opposite directions in pairs (e_J = -e_I): with
+    // S = L_I + L_J and D = L_I - L_J every term splits into an even and an odd part
+    float lrho = lh[0] * (om * wgt(0)) * (1.0f - 1.5f * uu);
+    float lux = lh[0] * (-3.0f * wgt(0)) * ((om * rho) * ux + fp * tx);
+    float luy = lh[0] * (-3.0f * wgt(0)) * ((om * rho) * uy + fp * ty);
+    float luz = lh[0] * (-3.0f * wgt(0)) * ((om * rho) * uz + fp * tz);
+    float ltx = lh[0] * (-3.0f * fp * wgt(0)) * ux;
+    float lty = lh[0] * (-3.0f * fp * wgt(0)) * uy;
+    float ltz = lh[0] * (-3.0f * fp * wgt(0)) * uz;
+#pragma unroll
+    for (int i = 1; i < Q; i += 2) {
+        const float Sp = lh[i] + lh[i + 1], Dm = lh[i] - lh[i + 1];
+        const float w = wgt(i);
+        const float eu = ex(i) * ux + ey(i) * uy + ez(i) * uz;
+        const float et = ex(i) * tx + ey(i) * ty + ez(i) * tz;
+        // d feq / d rho: om w (1 + 3 eu + 4.5 eu^2 - 1.5 uu)
+        lrho += (om * w) * (Sp * (1.0f + 4.5f * eu * eu - 1.5f * uu) + 3.0f * eu * Dm);
+        // d h' / d u: e [3 om w rho D + 9 w (om rho eu + fp et) S] - 3 w (om rho u + fp t) S
+        const float ce = 3.0f * (om * w) * rho * Dm + 9.0f * w * ((om * rho) * eu + fp * et) * Sp;
+        const float cu = -3.0f * w * Sp;
+        lux += ce * ex(i) + cu * ((om * rho) * ux + fp * tx);
+        luy += ce * ey(i) + cu * ((om * rho) * uy + fp * ty);
+        luz += ce * ez(i) + cu * ((om * rho) * uz + fp * tz);
+        // d S / d g_tot: fp w (e [3 D + 9 eu S] - 3 u S)
+        const float te = fp * w * (3.0f * Dm + 9.0f * eu * Sp);
+        const float tu = -3.0f * fp * w * Sp;
+        ltx += te * ex(i) + tu * ux;
+        lty += te * ey(i) + tu * uy;
+        ltz += te * ez(i) + tu * uz;
+    }
+    lux += lu.x; luy += lu.y; luz += lu.z;
+    const float lvx = lux * s - ltx * al * iD, lvy = luy * s - lty * al * iD, lvz = luz * s - ltz * al * iD;
+    lrho -= (lux * ux + luy * uy + luz * uz) * irho;
+    const float lgx = 0.5f * lvx + ltx, lgy = 0.5f * lvy + lty, lgz = 0.5f * lvz + ltz;
+    float* lo = a.lam_out;
+#pragma unroll
+    for (int i = 0; i < Q; ++i)
+        lo[(size_t)i * (size_t)NT + gi] = (1.0f - om) * lh[i] + lrho + ex(i) * lvx + ey(i) * lvy + ez(i) * lvz;
+    if (forced) a.lam_g[gp] = make_float4(lgx, lgy, lgz, 0.f);
+    if (al != 0.f) {   // phi is exactly 0 away from the beads (tanh saturates in FP32)
+        const float iD2 = iD * iD;
+        const float lphi = -0.5f * a.alpha * (lux * vx + luy * vy + luz * vz) * iD2 * irho -
+                           a.alpha * (ltx * vx + lty * vy + ltz * vz) * iD2;
+        a.Lphi[gp] += lphi;
+    }
+}
+
+__global__ void __launch_bounds__(128, 8) k_adj_collide(const __grid_constant__ AdjArgs a) {
+    const ChannelDev C = a.ch;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool inr = p < C.n;
+    const long long gp = C.base + p;   // inside the channel's padded range
+    const uint8_t fslow = inr ? __ldg(a.slow + (gp >> 5)) : (uint8_t)0;
+    const bool wslow = __any_sync(0xffffffffu, fslow != 0);
+    if (!inr || solid_at(a.mask, gp)) return;   // bitmask obstacle nodes do not update
+    const int r = fdiv(p, C.dnx);
+    const int x = p - r * C.nx;
+    const int z = fdiv(r, C.dny);
+    const int y = r - z * C.ny;
+    if (wslow) adj_node<true>(a, C, (int)gp, x, y, z);
+    else adj_node<false>(a, C, (int)gp, x, y, z);
+}
+
+cudaError_t launch_adj_collide(const AdjArgs& a, cudaStream_t s) {
+    k_adj_collide<<<(a.ch.n + 127) / 128, 128, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // Fields: rho and the force-corrected velocity of the last collision, from the
 // stored post-collision populations: sum_i e_i f*_i = rho u + g/2.
 // ---------------------------------------------------------------------------

@@ -133,6 +133,10 @@ struct lb_ctx {
         float4 *seg_F = nullptr, *seg_g = nullptr, *seg_u = nullptr, *lam_u = nullptr, *lam_g = nullptr;
         float4 *lamX[2] = {nullptr, nullptr}, *lamF = nullptr, *tri_dS = nullptr, *tri_n = nullptr;
         float4 *fin_u = nullptr, *fin_F = nullptr;
+        uint8_t *seg_fl = nullptr, *fl_zero = nullptr;
+        // captured segment sweeps: forward (key: len, start parity) and
+        // reverse (key: len, population / position adjoint buffer parity)
+        std::map<std::pair<int, int>, cudaGraphExec_t> g_fwd, g_bwd;
         float2* seg_rel = nullptr;
         double *lam_c = nullptr, *grad = nullptr;
     } adj;
@@ -800,6 +804,8 @@ lb_status lb_destroy(lb_ctx* ctx) {
     if (!ctx) return LB_OK;
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     drop_graphs(ctx);
+    for (auto& kv : ctx->adj.g_fwd) cudaGraphExecDestroy(kv.second);
+    for (auto& kv : ctx->adj.g_bwd) cudaGraphExecDestroy(kv.second);
     for (void* p : ctx->allocations) cudaFree(p);
     if (ctx->hq_pinned) cudaFreeHost(ctx->hq_pinned);
     ctx->allocations.clear();
@@ -855,27 +861,71 @@ lb_status lb_set_brinkman(lb_ctx* ctx, const double* beads, int n, double alpha,
 // ---- discrete adjoint of the differentiable variant ----
 namespace {
 
-// Forward step t of the differentiable variant, keeping what the reverse
-// sweep of that step reads: populations and positions at its start, node
-// forces, spread force density, the cells' (dS/S0, dV/V0), the velocity.
-lb_status recompute_step(lb_ctx* ctx, int k) {
+// Forward cycle k of a segment run directly on the segment store: it pulls
+// from populations slot k and writes slot k + 1, advances positions slot k to
+// k + 1, and leaves its node forces, spread force density (zeroed first, no
+// previous-cycle flags to clear), velocity and cells' (dS/S0, dV/V0) in slot
+// k: everything the reverse sweep of that cycle reads.
+lb_status store_step(lb_ctx* ctx, int k) {
     auto& W = ctx->adj;
     const int par = (int)(ctx->step & 1);
-    const size_t hb = sizeof(float) * Q * (size_t)ctx->plane;
+    const size_t hN = (size_t)Q * ctx->plane;
     cudaStream_t s = ctx->stream;
-    LB_CUDA(cudaMemcpyAsync(W.seg_h + (size_t)k * Q * ctx->plane, ctx->h[par], hb, cudaMemcpyDeviceToDevice, s));
-    LB_CUDA(cudaMemcpyAsync(W.seg_q + (size_t)k * ctx->M, ctx->q[par], sizeof(Q4) * ctx->M, cudaMemcpyDeviceToDevice, s));
-    const LatticeArgs la = lattice_args(ctx, par);
-    const IbmArgs ia = ibm_args(ctx, par);
+    float* hs = W.seg_h + (size_t)k * hN;
+    float* hd = W.seg_h + (size_t)(k + 1) * hN;
+    Q4* qs = W.seg_q + (size_t)k * ctx->M;
+    Q4* qd = W.seg_q + (size_t)(k + 1) * ctx->M;
+    float4* gk = W.seg_g + (size_t)k * ctx->Ntot;
+    float4* uk = W.seg_u + (size_t)k * ctx->Ntot;
+    LB_CUDA(cudaMemsetAsync(gk, 0, sizeof(float4) * ctx->Ntot, s));
+    uint8_t* flk = W.seg_fl + (size_t)k * (ctx->Ntot / GROUP);
+    LB_CUDA(cudaMemsetAsync(flk, 0, (size_t)(ctx->Ntot / GROUP), s));
+    LatticeArgs la = lattice_args(ctx, par);
+    IbmArgs ia = ibm_args(ctx, par);
+    la.h0 = par ? (void*)hd : (void*)hs;
+    la.h1 = par ? (void*)hs : (void*)hd;
+    la.u = uk;
+    la.g0 = la.g1 = gk;
+    ia.g0 = ia.g1 = gk;
+    la.fl0 = ia.fl0 = par ? W.fl_zero : flk;
+    la.fl1 = ia.fl1 = par ? flk : W.fl_zero;
+    ia.u = uk;
+    ia.qa = par ? qd : qs;
+    ia.qb = par ? qs : qd;
+    ia.F = W.seg_F + (size_t)k * ctx->M;
+    ia.cell_rel = W.seg_rel + (size_t)k * ctx->C;
     LB_CUDA(launch_elements(ia, s));
     LB_CUDA(launch_forces_spread(ia, s));
-    LB_CUDA(cudaMemcpyAsync(W.seg_g + (size_t)k * ctx->Ntot, ctx->g[par], sizeof(float4) * ctx->Ntot, cudaMemcpyDeviceToDevice, s));
-    LB_CUDA(cudaMemcpyAsync(W.seg_F + (size_t)k * ctx->M, ctx->F, sizeof(float4) * ctx->M, cudaMemcpyDeviceToDevice, s));
-    LB_CUDA(cudaMemcpyAsync(W.seg_rel + (size_t)k * ctx->C, ctx->cell_rel, sizeof(float2) * ctx->C, cudaMemcpyDeviceToDevice, s));
     LB_CUDA(launch_stream_collide(la, ctx->k3, ctx->total_blocks, s));
-    LB_CUDA(cudaMemcpyAsync(W.seg_u + (size_t)k * ctx->Ntot, ctx->u, sizeof(float4) * ctx->Ntot, cudaMemcpyDeviceToDevice, s));
     LB_CUDA(launch_interp_advance(ia, s));
     ctx->step++;
+    return LB_OK;
+}
+
+// The forward cycles 0 .. len-1 of a segment on the segment store, as one
+// CUDA graph per (len, parity of the first cycle), launched on the stream.
+lb_status run_segment_forward(lb_ctx* ctx, int len) {
+    auto& W = ctx->adj;
+    const std::pair<int, int> key(len, (int)(ctx->step & 1));
+    auto it = W.g_fwd.find(key);
+    if (it == W.g_fwd.end()) {
+        const long long step_saved = ctx->step;
+        cudaGraph_t g = nullptr;
+        LB_CUDA(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+        lb_status st = LB_OK;
+        for (int k = 0; k < len && st == LB_OK; ++k) st = store_step(ctx, k);
+        cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+        ctx->step = step_saved;
+        if (st != LB_OK) return st;
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamEndCapture");
+        cudaGraphExec_t ge = nullptr;
+        e = cudaGraphInstantiate(&ge, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphInstantiate");
+        it = W.g_fwd.emplace(key, ge).first;
+    }
+    LB_CUDA(cudaGraphLaunch(it->second, ctx->stream));
+    ctx->step += len;
     return LB_OK;
 }
 
@@ -899,9 +949,9 @@ lb_status copy_state(lb_ctx* ctx, float* h, Q4* q, bool save) {
     return LB_OK;
 }
 
-double mean_x(lb_ctx* ctx, const MeshHost& m) {
+double mean_x(const Q4* qdev, const MeshHost& m) {
     std::vector<Q4> q(m.n);
-    cudaMemcpy(q.data(), ctx->q[ctx->step & 1] + m.node0, sizeof(Q4) * m.n, cudaMemcpyDeviceToHost);
+    cudaMemcpy(q.data(), qdev + m.node0, sizeof(Q4) * m.n, cudaMemcpyDeviceToHost);
     double s = 0.0;
     for (const Q4& v : q) s += (double)v.x / FIX_SCALE;
     return s / m.n;
@@ -931,15 +981,20 @@ lb_status lb_adjoint(lb_ctx* ctx, int n_steps, int ckpt_every, int objective_mes
                         (void*)W.ck_q, (void*)W.seg_q, (void*)W.fin_q, (void*)W.seg_F, (void*)W.seg_g, (void*)W.seg_u,
                         (void*)W.lam_u, (void*)W.lam_g, (void*)W.lamX[0], (void*)W.lamX[1], (void*)W.lamF,
                         (void*)W.tri_dS, (void*)W.tri_n, (void*)W.seg_rel, (void*)W.lam_c, (void*)W.grad,
-                        (void*)W.fin_u, (void*)W.fin_F})
+                        (void*)W.fin_u, (void*)W.fin_F, (void*)W.seg_fl, (void*)W.fl_zero})
             dfree(ctx, p);
+        for (auto& kv : W.g_fwd) cudaGraphExecDestroy(kv.second);
+        for (auto& kv : W.g_bwd) cudaGraphExecDestroy(kv.second);
         W = lb_ctx::AdjWork();
         cudaError_t e = cudaSuccess;
 #define ATRY(x) if (e == cudaSuccess) e = (x)
         ATRY(dalloc(ctx, &W.ck_h, (size_t)n_ck * hN));
         ATRY(dalloc(ctx, &W.ck_q, (size_t)n_ck * ctx->M));
-        ATRY(dalloc(ctx, &W.seg_h, (size_t)K * hN));
-        ATRY(dalloc(ctx, &W.seg_q, (size_t)K * ctx->M));
+        ATRY(dalloc(ctx, &W.seg_h, (size_t)(K + 1) * hN));
+        ATRY(dalloc(ctx, &W.seg_q, (size_t)(K + 1) * ctx->M));
+        ATRY(dalloc(ctx, &W.seg_fl, (size_t)K * (ctx->Ntot / GROUP)));
+        ATRY(dalloc(ctx, &W.fl_zero, (size_t)(ctx->Ntot / GROUP)));
+        if (e == cudaSuccess) e = cudaMemsetAsync(W.fl_zero, 0, (size_t)(ctx->Ntot / GROUP), ctx->stream);
         ATRY(dalloc(ctx, &W.seg_F, (size_t)K * ctx->M));
         ATRY(dalloc(ctx, &W.seg_g, (size_t)K * ctx->Ntot));
         ATRY(dalloc(ctx, &W.seg_u, (size_t)K * ctx->Ntot));
@@ -970,23 +1025,35 @@ lb_status lb_adjoint(lb_ctx* ctx, int n_steps, int ckpt_every, int objective_mes
     }
     cudaStream_t s = ctx->stream;
     const long long step0 = ctx->step;
-    const double x0 = mean_x(ctx, *mo);
-    // forward, keeping a checkpoint at the start of every segment
-    for (int c = 0; c < n_ck; ++c) {
+    const double x0 = mean_x(ctx->q[ctx->step & 1], *mo);
+    const size_t hb = sizeof(float) * hN;
+    // forward: checkpoints at the start of every segment; the last segment
+    // runs on the segment store, so its reverse sweep needs no recompute
+    for (int c = 0; c + 1 < n_ck; ++c) {
         if (copy_state(ctx, W.ck_h + (size_t)c * hN, W.ck_q + (size_t)c * ctx->M, true) != LB_OK) return LB_ERR_CUDA;
-        st = lb_step(ctx, std::min(K, n_steps - c * K));
+        st = lb_step(ctx, K);
         if (st != LB_OK) return st;
     }
+    const int last = n_ck - 1;
+    const int len_last = n_steps - last * K;
+    if (copy_state(ctx, W.seg_h, W.seg_q, true) != LB_OK) return LB_ERR_CUDA;
+    st = run_segment_forward(ctx, len_last);
+    if (st != LB_OK) return st;
+    // the final state, restored into the context at the end
+    LB_CUDA(cudaMemcpyAsync(W.fin_h, W.seg_h + (size_t)len_last * hN, hb, cudaMemcpyDeviceToDevice, s));
+    LB_CUDA(cudaMemcpyAsync(W.fin_q, W.seg_q + (size_t)len_last * ctx->M, sizeof(Q4) * ctx->M, cudaMemcpyDeviceToDevice, s));
+    LB_CUDA(cudaMemcpyAsync(W.fin_u, W.seg_u + (size_t)(len_last - 1) * ctx->Ntot, sizeof(float4) * ctx->Ntot,
+                            cudaMemcpyDeviceToDevice, s));
+    LB_CUDA(cudaMemcpyAsync(W.fin_F, W.seg_F + (size_t)(len_last - 1) * ctx->M, sizeof(float4) * ctx->M,
+                            cudaMemcpyDeviceToDevice, s));
     LB_CUDA(cudaStreamSynchronize(s));
-    const double Jv = mean_x(ctx, *mo) - x0;
-    if (copy_state(ctx, W.fin_h, W.fin_q, true) != LB_OK) return LB_ERR_CUDA;
-    // the last cycle's velocity and node forces (what lb_get_fields / ibm_get_forces report)
-    LB_CUDA(cudaMemcpyAsync(W.fin_u, ctx->u, sizeof(float4) * ctx->Ntot, cudaMemcpyDeviceToDevice, s));
-    LB_CUDA(cudaMemcpyAsync(W.fin_F, ctx->F, sizeof(float4) * ctx->M, cudaMemcpyDeviceToDevice, s));
+    const double Jv = mean_x(W.fin_q, *mo) - x0;
     // reverse sweep
     LB_CUDA(cudaMemsetAsync(W.lam[0], 0, sizeof(float) * hN, s));
     LB_CUDA(cudaMemsetAsync(W.lam[1], 0, sizeof(float) * hN, s));
     LB_CUDA(cudaMemsetAsync(W.Lphi, 0, sizeof(float) * ctx->Ntot, s));
+    LB_CUDA(cudaMemsetAsync(W.lam_u, 0, sizeof(float4) * ctx->Ntot, s));
+    LB_CUDA(cudaMemsetAsync(W.lam_g, 0, sizeof(float4) * ctx->Ntot, s));
     LB_CUDA(cudaMemsetAsync(W.grad, 0, sizeof(double) * (2 + 3 * 64), s));
     {
         std::vector<float4> l0(ctx->M, make_float4(0.f, 0.f, 0.f, 0.f));
@@ -1005,6 +1072,7 @@ lb_status lb_adjoint(lb_ctx* ctx, int n_steps, int ckpt_every, int objective_mes
     A.plane = ctx->plane;
     A.mask = ctx->mask;
     A.links = ctx->links;
+    A.slow = ctx->slow;
     A.phi = ctx->phi;
     A.alpha = ctx->alpha;
     A.delta = ctx->delta;
@@ -1026,29 +1094,56 @@ lb_status lb_adjoint(lb_ctx* ctx, int n_steps, int ckpt_every, int objective_mes
     int lc = 0, xc = 0;
     for (int c = n_ck - 1; c >= 0; --c) {
         const int len = std::min(K, n_steps - c * K);
-        ctx->step = step0 + (long long)c * K;
-        if (copy_state(ctx, W.ck_h + (size_t)c * hN, W.ck_q + (size_t)c * ctx->M, false) != LB_OK) return LB_ERR_CUDA;
-        for (int k = 0; k < len; ++k)
-            if (recompute_step(ctx, k) != LB_OK) return LB_ERR_CUDA;
-        for (int k = len - 1; k >= 0; --k) {
-            A.q_t = W.seg_q + (size_t)k * ctx->M;
-            A.F_t = W.seg_F + (size_t)k * ctx->M;
-            A.g_t = W.seg_g + (size_t)k * ctx->Ntot;
-            A.u_t = W.seg_u + (size_t)k * ctx->Ntot;
-            A.h_t = W.seg_h + (size_t)k * hN;
-            A.rel_t = W.seg_rel + (size_t)k * ctx->C;
-            A.lam_in = W.lam[lc];
-            A.lam_out = W.lam[1 - lc];
-            A.lamX = W.lamX[xc];
-            A.lamX_out = W.lamX[1 - xc];
-            LB_CUDA(cudaMemsetAsync(W.lam_u, 0, sizeof(float4) * ctx->Ntot, s));
-            LB_CUDA(cudaMemsetAsync(W.lam_c, 0, sizeof(double) * 2 * ctx->C, s));
-            LB_CUDA(launch_adj_interp(A, s));
-            LB_CUDA(launch_adj_collide(A, s));
-            LB_CUDA(launch_adj_spread(A, s));
-            LB_CUDA(launch_adj_membrane(A, s));
-            lc = 1 - lc;
-            xc = 1 - xc;
+        if (c < last) {
+            // recompute the segment from its checkpoint on the segment store
+            ctx->step = step0 + (long long)c * K;
+            LB_CUDA(cudaMemcpyAsync(W.seg_h, W.ck_h + (size_t)c * hN, hb, cudaMemcpyDeviceToDevice, s));
+            LB_CUDA(cudaMemcpyAsync(W.seg_q, W.ck_q + (size_t)c * ctx->M, sizeof(Q4) * ctx->M, cudaMemcpyDeviceToDevice, s));
+            st = run_segment_forward(ctx, len);
+            if (st != LB_OK) return st;
+        }
+        {
+            const std::pair<int, int> key(len, lc + 2 * xc);
+            auto it = W.g_bwd.find(key);
+            if (it == W.g_bwd.end()) {
+                cudaGraph_t g = nullptr;
+                LB_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+                int l = lc, x = xc;
+                cudaError_t e = cudaSuccess;
+                for (int k = len - 1; k >= 0 && e == cudaSuccess; --k) {
+                    A.q_t = W.seg_q + (size_t)k * ctx->M;
+                    A.F_t = W.seg_F + (size_t)k * ctx->M;
+                    A.g_t = W.seg_g + (size_t)k * ctx->Ntot;
+                    A.u_t = W.seg_u + (size_t)k * ctx->Ntot;
+                    A.h_t = W.seg_h + (size_t)k * hN;
+                    A.rel_t = W.seg_rel + (size_t)k * ctx->C;
+                    A.fl_t = W.seg_fl + (size_t)k * (ctx->Ntot / GROUP);
+                    A.lam_in = W.lam[l];
+                    A.lam_out = W.lam[1 - l];
+                    A.lamX = W.lamX[x];
+                    A.lamX_out = W.lamX[1 - x];
+                    e = cudaMemsetAsync(W.lam_c, 0, sizeof(double) * 2 * ctx->C, s);
+                    if (e == cudaSuccess) e = launch_adj_interp(A, s);
+                    if (e == cudaSuccess) e = launch_adj_collide(A, s);
+                    if (e == cudaSuccess) e = launch_adj_spread(A, s);
+                    if (e == cudaSuccess) e = launch_adj_membrane(A, s);
+                    l = 1 - l;
+                    x = 1 - x;
+                }
+                cudaError_t e2 = cudaStreamEndCapture(s, &g);
+                if (e != cudaSuccess) return cuda_fail(ctx, e, "adjoint launch");
+                if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "cudaStreamEndCapture");
+                cudaGraphExec_t ge = nullptr;
+                e = cudaGraphInstantiate(&ge, g, 0);
+                cudaGraphDestroy(g);
+                if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphInstantiate");
+                it = W.g_bwd.emplace(key, ge).first;
+            }
+            LB_CUDA(cudaGraphLaunch(it->second, s));
+            if (len & 1) {
+                lc = 1 - lc;
+                xc = 1 - xc;
+            }
         }
     }
     LB_CUDA(launch_adj_bead_grad(A, s));

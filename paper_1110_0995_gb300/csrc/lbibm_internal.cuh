@@ -202,15 +202,18 @@ struct AdjArgs {
     const float4* u_t;        // [plane] velocity of step t's collision
     const float* h_t;         // [19][plane] populations at the start of step t
     const float2* rel_t;      // [C] (dS/S0, dV/V0) of step t
+    const uint8_t* fl_t;      // [plane / 32] groups that received IB force in step t (the stencil groups)
     const uint32_t* mask;
     const uint32_t* links;
+    const uint8_t* slow;      // per 32-node group: any bounce-back link
     const float* phi;
     float alpha, delta;
     const float4* beads;      // [n_beads] (cx, cy, cz, r)
     // adjoint state
     const float* lam_in;      // [19][plane] adjoint of step t+1's pulled populations
     float* lam_out;           // [19][plane] adjoint of step t's pulled populations
-    float4* lam_u;            // [plane] adjoint of step t's velocity (from the interpolation)
+    float4* lam_u;            // [plane] adjoint of step t's velocity (from the interpolation); the
+                              // stream-collide adjoint zeroes what it read
     float4* lam_g;            // [plane] adjoint of step t's force density
     float* Lphi;              // [plane] accumulated adjoint of phi
     const float4* lamX;       // [M] adjoint of X^{t+1}
