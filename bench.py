@@ -32,7 +32,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 BYTES_PER_NODE = {"f32": 152, "f16": 76, "bf16": 76}   # 19 reads + 19 writes per fluid node update
-METRIC = "D3Q19+IBM MLUPS on 1 GB300 (% HBM roofline)"
+METRIC = "D3Q19+IBM MLUPS on 1 GB300 (% HBM roofline); adjoint/forward step ratio"
 
 
 def make_workload(name: str):
@@ -177,6 +177,43 @@ def cpu_baseline_line(target_seconds: float = 15.0):
     return {"value": n * steps / dt / 1e6, "unit": "MLUPS", "cores": cpu_threads(), "kind": "oracle",
             "sample": f"{steps} steps of the full {sc.dims[0]}x{sc.dims[1]}x{sc.dims[2]} filter "
                       f"({len(sc.meshes)} cells), FP64 oracle, {cpu_threads()} OpenMP threads"}
+
+
+def adjoint_ratio(steps: int = 400, ckpt_every: int = 50):
+    """Cost of the discrete adjoint on the 128x64x64 channel with 12 Brinkman
+    beads and 9 cells: forward cycles alone vs lb_adjoint (forward with
+    checkpoints + recompute + reverse sweep), CUDA events on the stream."""
+    import dataclasses
+
+    import torch
+
+    from paper_1110_0995_gb300 import lbibm, scene
+
+    sc = scene.adjoint_channel()
+    bare = dataclasses.replace(sc, spheres=np.zeros((0, 4), np.float32))
+    stream = torch.cuda.Stream()
+    sim = lbibm.Simulation.from_scene(bare, stream=stream.cuda_stream)
+    sim.set_brinkman(np.asarray(sc.spheres, np.float64))
+    sim.step(5)
+    sim.adjoint(steps, ckpt_every)                 # workspace and graphs outside the timed calls
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), out
+
+    t_fwd, _ = timed(lambda: sim.step(steps))
+    t_adj, res = timed(lambda: sim.adjoint(steps, ckpt_every))
+    sim.close()
+    return {"workload": "adjoint_channel_128x64x64 (12 Brinkman beads, 1 tumor + 8 red cells)", "steps": steps,
+            "ckpt_every": ckpt_every, "forward_us_per_step": 1e3 * t_fwd / steps,
+            "adjoint_us_per_step": 1e3 * (t_adj - t_fwd) / steps, "adjoint_over_forward": (t_adj - t_fwd) / t_fwd,
+            "J": res["J"], "note": "adjoint step = recompute share + reverse sweep; gradients checked against the "
+                                   "FP64 oracle's dual numbers in tests/test_gpu_adjoint.py"}
 
 
 def dist_env():
@@ -338,6 +375,7 @@ def run_ours(args):
 
     if rank == 0:
         cpu = None if (args.no_cpu_baseline or world > 1 or len(scenes) > 1) else cpu_baseline_line()
+        adj = None if (args.no_adjoint or world > 1) else adjoint_ratio()
         line = {
             "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -365,6 +403,7 @@ def run_ours(args):
                                         "mass_per_fluid_node": diag[0] / n_fluid, "max_u": diag[5]},
             "clocks": clk.summary(),
             "cpu_baseline": cpu,
+            "adjoint": adj,
             "e2e": e2e,
         }
         print(json.dumps(line), flush=True)
@@ -386,6 +425,7 @@ def main(argv=None):
     ap.add_argument("--variant", default="", help="stream-collide variant 'npt,bs' instead of the autotuner")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint / forward cost measurement")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

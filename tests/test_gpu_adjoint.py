@@ -99,3 +99,23 @@ def test_adjoint_leaves_forward_state_and_time_ratio():
     b.adjoint(T, ckpt_every=20)
     ta = time.perf_counter() - t0
     print(f"forward {1e3 * tf:.2f} ms, adjoint {1e3 * ta:.2f} ms, ratio {ta / tf:.2f}")
+
+
+def test_autograd_function():
+    """torch.autograd through FilterObjective gives lb_adjoint's gradients."""
+    import torch
+
+    from paper_1110_0995_gb300.autograd import filter_objective
+
+    T = 40
+    sc = scene.adjoint_channel_small(steps=T)
+    beads = torch.tensor(np.asarray(sc.spheres, np.float64)[:, :3], requires_grad=True)
+    ks = torch.tensor(float(sc.meshes[0].moduli[0]), dtype=torch.float64, requires_grad=True)
+    kb = torch.tensor(float(sc.meshes[0].moduli[1]), dtype=torch.float64, requires_grad=True)
+    J = filter_objective(beads, ks, kb, sc, T, ckpt_every=20)
+    (2.0 * J).backward()
+    ref = _gpu_sim(sc).adjoint(T, ckpt_every=20)
+    assert float(J.detach()) == pytest.approx(ref["J"], rel=1e-6)
+    assert np.allclose(beads.grad.numpy(), 2.0 * ref["beads"], rtol=1e-4, atol=1e-12)
+    assert float(ks.grad) == pytest.approx(2.0 * ref["ks"], rel=1e-4)
+    assert float(kb.grad) == pytest.approx(2.0 * ref["kb"], rel=1e-4)
