@@ -72,6 +72,7 @@ def lib():
         L.or_sys_destroy.argtypes = [vp]
         L.or_sys_set_solid.argtypes = [vp, P]
         L.or_sys_set_extra_force.argtypes = [vp, P]
+        L.or_sys_set_repulsion.argtypes = [vp, d, d, P, i]
         L.or_sys_init_equilibrium.argtypes = [vp, d, P]
         L.or_sys_get_f.argtypes = [vp, P]
         L.or_sys_set_f.argtypes = [vp, P]
@@ -213,7 +214,16 @@ class System:
             s.set_solid(rasterise(scene.spheres, scene.dims))
         for m in scene.meshes:
             s.add_mesh(m.rest, m.tris, m.moduli)
+        rep = getattr(scene, "repulsion", None)
+        if rep is not None:
+            s.set_repulsion(rep[0], rep[1], scene.spheres)
         return s
+
+    def set_repulsion(self, k: float, dc: float, spheres=None):
+        """Soft-sphere collisions (Sec. 2.4 reading): force k (dc - d) below separation dc."""
+        sph = _f64(np.zeros((0, 4)) if spheres is None else spheres).reshape(-1, 4)
+        self._sph = sph
+        lib().or_sys_set_repulsion(self._h, float(k), float(dc), _p(sph), int(sph.shape[0]))
 
     def __del__(self):
         h = getattr(self, "_h", None)

@@ -563,7 +563,105 @@ struct System {
     Fluid<R> fl;
     std::vector<Cell<R>> cells;
     long steps = 0;
+    double rep_k = 0.0, rep_dc = 0.0;   // soft-sphere repulsion (off when rep_k == 0)
+    std::vector<double> spheres;         // cx, cy, cz, r per bead (for the repulsion)
 };
+
+// Collisions (Sec. 2.4: cells repel each other and the walls through a soft
+// potential cut at an interaction radius; form and constants not printed).
+// Reading: harmonic soft sphere, for a separation d below the cut-off d_c a
+// force k (d_c - d) along the separation on the node, between
+//   * nodes of different cells (equal and opposite; x minimum image when x is
+//     periodic),
+//   * a node and a bead surface (d = |x - c| - r, along x - c),
+//   * a node and a wall of a non-periodic axis (walls half a link outside the
+//     first and last node: d = y + 1/2 or (n - 1/2) - y).
+// The bounded stiffness k keeps the explicit coupling stable.  Added to the
+// membrane forces before spreading.
+template <class R>
+void repulsion(System<R>& s) {
+    const double k = s.rep_k, dc = s.rep_dc;
+    const Fluid<R>& F = s.fl;
+    const int dim[3] = {F.nx, F.ny, F.nz};
+    const int nc = (int)s.cells.size();
+    // node - node of different cells (a cell pair is skipped when its bounding
+    // spheres are farther apart than the cut-off)
+    std::vector<double> cx(3 * nc), rad(nc);
+    for (int a = 0; a < nc; ++a) {
+        const auto& c = s.cells[a];
+        double m[3] = {0, 0, 0};
+        for (int j = 0; j < c.T.n; ++j)
+            for (int d = 0; d < 3; ++d) m[d] += val(c.x[3 * j + d]) / c.T.n;
+        double r2 = 0.0;
+        for (int j = 0; j < c.T.n; ++j) {
+            double q = 0.0;
+            for (int d = 0; d < 3; ++d) q += (val(c.x[3 * j + d]) - m[d]) * (val(c.x[3 * j + d]) - m[d]);
+            r2 = std::max(r2, q);
+        }
+        for (int d = 0; d < 3; ++d) cx[3 * a + d] = m[d];
+        rad[a] = std::sqrt(r2);
+    }
+    auto min_image = [&](R& dx, int d) {
+        if (F.per[d]) {
+            const double L = dim[d];
+            dx = dx - L * std::floor(val(dx) / L + 0.5);
+        }
+    };
+    for (int a = 0; a < nc; ++a)
+        for (int b = a + 1; b < nc; ++b) {
+            double dd[3], q = 0.0;
+            for (int d = 0; d < 3; ++d) {
+                dd[d] = cx[3 * a + d] - cx[3 * b + d];
+                if (F.per[d]) dd[d] -= dim[d] * std::floor(dd[d] / dim[d] + 0.5);
+                q += dd[d] * dd[d];
+            }
+            if (std::sqrt(q) > rad[a] + rad[b] + dc + 1.0) continue;
+            auto& A = s.cells[a];
+            auto& B = s.cells[b];
+            for (int i = 0; i < A.T.n; ++i)
+                for (int j = 0; j < B.T.n; ++j) {
+                    R dv[3];
+                    for (int d = 0; d < 3; ++d) {
+                        dv[d] = A.x[3 * i + d] - B.x[3 * j + d];
+                        min_image(dv[d], d);
+                    }
+                    R d2 = dot3(dv, dv);
+                    if (!(val(d2) < dc * dc) || !(val(d2) > 0.0)) continue;
+                    R dist = sqrt(d2);
+                    R f = k * (dc - dist) / dist;
+                    for (int d = 0; d < 3; ++d) {
+                        A.F[3 * i + d] = A.F[3 * i + d] + f * dv[d];
+                        B.F[3 * j + d] = B.F[3 * j + d] - f * dv[d];
+                    }
+                }
+        }
+    // node - bead and node - wall
+    const int ns = (int)s.spheres.size() / 4;
+    for (auto& c : s.cells)
+        for (int j = 0; j < c.T.n; ++j) {
+            R* x = &c.x[3 * j];
+            for (int b = 0; b < ns; ++b) {
+                R dv[3];
+                for (int d = 0; d < 3; ++d) {
+                    dv[d] = x[d] - s.spheres[4 * b + d];
+                    min_image(dv[d], d);
+                }
+                R d2 = dot3(dv, dv);
+                const double rr = s.spheres[4 * b + 3] + dc;
+                if (!(val(d2) < rr * rr) || !(val(d2) > 0.0)) continue;
+                R dist = sqrt(d2);
+                R gap = dist - s.spheres[4 * b + 3];
+                R f = k * (dc - gap) / dist;
+                for (int d = 0; d < 3; ++d) c.F[3 * j + d] = c.F[3 * j + d] + f * dv[d];
+            }
+            for (int d = 0; d < 3; ++d) {
+                if (F.per[d]) continue;
+                R lo = x[d] + 0.5, hi = (dim[d] - 0.5) - x[d];
+                if (val(lo) < dc) c.F[3 * j + d] = c.F[3 * j + d] + k * (dc - lo);
+                if (val(hi) < dc) c.F[3 * j + d] = c.F[3 * j + d] - k * (dc - hi);
+            }
+        }
+}
 
 // One cycle.  Sec. 2.2 lists: (1) velocity from the grid to the IB points,
 // (2) node forces, (3) spreading with the delta function, (4) fluid and point
@@ -576,10 +674,9 @@ template <class R>
 void system_step(System<R>& s) {
     Fluid<R>& F = s.fl;
     std::fill(F.g.begin(), F.g.end(), R(0.0));
-    for (auto& c : s.cells) {
-        membrane_forces(c.x.data(), c.T, c.rest, c.mod, TERM_ALL, c.F.data());
-        spread(F, c.x.data(), c.F.data(), c.T.n, F.g.data());
-    }
+    for (auto& c : s.cells) membrane_forces(c.x.data(), c.T, c.rest, c.mod, TERM_ALL, c.F.data());
+    if (s.rep_k != 0.0) repulsion(s);
+    for (auto& c : s.cells) spread(F, c.x.data(), c.F.data(), c.T.n, F.g.data());
     lb_step(F);
     for (auto& c : s.cells) {
         interpolate(F, c.x.data(), c.T.n, F.u.data(), c.U.data());
@@ -835,6 +932,13 @@ void or_sys_destroy(void* h) { delete (OrSys*)h; }
 void or_sys_set_solid(void* h, const uint8_t* solid) {
     OrSys* s = (OrSys*)h;
     std::memcpy(s->fl.solid.data(), solid, (size_t)s->fl.n);
+}
+
+void or_sys_set_repulsion(void* h, double k, double dc, const double* spheres, int ns) {
+    OrSys* s = (OrSys*)h;
+    s->rep_k = k;
+    s->rep_dc = dc;
+    s->spheres.assign(spheres, spheres + 4 * ns);
 }
 
 void or_sys_set_extra_force(void* h, const double* g) {
