@@ -96,6 +96,20 @@ lb_status lb_select_channel(lb_ctx* ctx, int channel);
 /* Free all device memory of the context.  NULL is accepted. */
 lb_status lb_destroy(lb_ctx* ctx);
 
+/* Collisions between cells and with walls and beads (Sec. 2.4: a soft
+ * potential between mesh nodes of different cells and between cells and
+ * walls, cut at an interaction radius; form and constants not printed).
+ * Reading: harmonic soft sphere, a force k (dc - d) along the separation for
+ * d < dc, between nodes of different cells of a channel (x minimum image when
+ * x is periodic), between a node and the surface of a bead of
+ * lb_set_obstacles (d = |x - c| - r), and between a node and a wall of a
+ * non-periodic axis (walls half a link outside the first and last node),
+ * added to the membrane forces before spreading.  k = 0 (the default) turns
+ * it off.  Before the first step; not with the differentiable variant
+ * (LB_ERR_STATE).  Candidate lists hold 32 neighbour cells and 64 beads per
+ * cell; an overflow is reported by lb_diagnostics (LB_ERR_STATE). */
+lb_status lb_set_repulsion(lb_ctx* ctx, double k, double dc);
+
 /* Differentiable variant (gradient of a filter objective; single-channel
  * contexts, before the first step).  The beads become a smooth solid
  * fraction phi(x) = 1 - prod_k (1 - phi_k(x)),

@@ -443,6 +443,11 @@ __global__ void __launch_bounds__(FS_BLOCK, IB_MIN_BLOCKS) k_forces_spread(const
         F.y += __shfl_xor_sync(smask, F.y, o);
         F.z += __shfl_xor_sync(smask, F.z, o);
     }
+    if (a.R) {
+        // collisions (Sec. 2.4): every lane holds the reduced total, add to each
+        const float4 r = a.R[i];
+        F.x += r.x; F.y += r.y; F.z += r.z;
+    }
     if (sl == 0) a.F[i] = make_float4(F.x, F.y, F.z, 0.f);
 
     // spreading: g(x) += w(x - X) F at this lane's corner

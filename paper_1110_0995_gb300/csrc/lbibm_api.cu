@@ -27,6 +27,7 @@ struct ChannelHost {
     lb_params p;
     ChannelDev d;
     int n_blocks = 0;
+    std::vector<float> spheres;   // bead spheres of lb_set_obstacles (cx, cy, cz, r)
 };
 
 struct MeshHost {
@@ -120,6 +121,14 @@ struct lb_ctx {
     int* dcount = nullptr;         // [2]
     int* sched_err = nullptr;
     int list_blocks = 0;
+    // collisions (soft sphere): off while rep_k == 0
+    float rep_k = 0.f, rep_dc = 0.f;
+    int rep_cap = 0, rep_nb = 0;
+    float4 *rep_R = nullptr, *rep_bounds = nullptr;
+    int2* rep_pairs = nullptr;
+    int *rep_count = nullptr, *rep_near = nullptr, *rep_near_count = nullptr, *rep_err = nullptr, *rep_bead_ch = nullptr;
+    Q4* rep_bead_q = nullptr;
+    float* rep_bead_r = nullptr;
     // differentiable variant
     float* phi = nullptr;          // bead solid fraction per node (null: off)
     float alpha = 0.f, delta = 0.f;
@@ -266,6 +275,7 @@ IbmArgs ibm_args(const lb_ctx* ctx, int par, bool overlapped = false) {
     a.fl0 = ctx->fl[0];
     a.fl1 = ctx->fl[1];
     a.u = ctx->u;
+    a.R = ctx->rep_k > 0.f ? ctx->rep_R : nullptr;
     a.dmark = ctx->dmap[1 - par];
     a.dcur = overlapped ? ctx->dmap[par] : nullptr;
     a.sched_err = ctx->sched_err;
@@ -305,6 +315,38 @@ lb_status enqueue_step(lb_ctx* ctx, int par) {
     const LatticeArgs la = lattice_args(ctx, par);
     const IbmArgs ia = ibm_args(ctx, par);
     const bool ibm = ctx->M > 0;
+    if (ibm && ctx->rep_k > 0.f) {
+        // collisions (Sec. 2.4), added to the membrane forces in the spreading kernel
+        RepArgs ra;
+        std::memset(&ra, 0, sizeof(ra));
+        ra.k = ctx->rep_k;
+        ra.dc = ctx->rep_dc;
+        ra.n_cells = ctx->C;
+        ra.n_nodes = ctx->M;
+        ra.n_beads = ctx->rep_nb;
+        ra.pair_cap = ctx->rep_cap;
+        ra.q = ctx->q[par];
+        ra.cells = ctx->d_cells;
+        ra.info = ctx->info;
+        ra.ch = ctx->d_ch;
+        ra.bounds = ctx->rep_bounds;
+        ra.pairs = ctx->rep_pairs;
+        ra.pair_count = ctx->rep_count;
+        ra.near = ctx->rep_near;
+        ra.near_count = ctx->rep_near_count;
+        ra.bead_q = ctx->rep_bead_q;
+        ra.bead_r = ctx->rep_bead_r;
+        ra.bead_ch = ctx->rep_bead_ch;
+        ra.R = ctx->rep_R;
+        ra.err = ctx->rep_err;
+        for (size_t k = 0; k < ctx->ch.size() && k < (size_t)MAXCH_P; ++k) ra.chp[k] = ctx->ch[k].d;
+        LB_CUDA(cudaMemsetAsync(ctx->rep_R, 0, sizeof(float4) * ctx->M, ctx->stream));
+        LB_CUDA(cudaMemsetAsync(ctx->rep_count, 0, sizeof(int), ctx->stream));
+        LB_CUDA(cudaMemsetAsync(ctx->rep_near_count, 0, sizeof(int) * ctx->C, ctx->stream));
+        cudaError_t e = launch_repulsion(ra, ctx->sm_count, ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "kernel launch");
+        ctx->launches[1] += 4;
+    }
     for (int k = 0; k < 4; ++k) {
         if (!ibm && k != 2) continue;
         EventPair ep{};
@@ -409,7 +451,7 @@ lb_status enqueue_step_overlap(lb_ctx* ctx, int par, bool lead_interp) {
 
 bool use_overlap(const lb_ctx* ctx) {
     const long long m = ctx->committed ? ctx->M : (long long)ctx->hq0.size();
-    return ctx->overlap && m > 0 && ctx->phi == nullptr && ctx->k3.npt == 1 && ctx->timing == 0 && ctx->ib_stream != nullptr;
+    return ctx->overlap && m > 0 && ctx->phi == nullptr && ctx->rep_k == 0.f && ctx->k3.npt == 1 && ctx->timing == 0 && ctx->ib_stream != nullptr;
 }
 
 lb_status build_graphs_overlap(lb_ctx* ctx) {
@@ -600,6 +642,37 @@ lb_status commit_ibm(lb_ctx* ctx) {
     LB_CUDA(up(&ctx->q[1], ctx->hq));
     LB_CUDA(up(&ctx->info, ctx->hinfo));
     LB_CUDA(up(&ctx->slots, ctx->hslots));
+    if (ctx->rep_k > 0.f) {
+        std::vector<Q4> bq;
+        std::vector<float> br;
+        std::vector<int> bc;
+        for (size_t k = 0; k < ctx->ch.size(); ++k)
+            for (size_t b = 0; b + 3 < ctx->ch[k].spheres.size(); b += 4) {
+                Q4 q;
+                q.x = to_fixed(ctx->ch[k].spheres[b]);
+                q.y = to_fixed(ctx->ch[k].spheres[b + 1]);
+                q.z = to_fixed(ctx->ch[k].spheres[b + 2]);
+                q.w = 0;
+                bq.push_back(q);
+                br.push_back(ctx->ch[k].spheres[b + 3]);
+                bc.push_back((int)k);
+            }
+        ctx->rep_nb = (int)bq.size();
+        ctx->rep_cap = 32 * std::max(ctx->C, 1);
+        LB_CUDA(dalloc(ctx, &ctx->rep_R, ctx->M));
+        LB_CUDA(dalloc(ctx, &ctx->rep_bounds, ctx->C));
+        LB_CUDA(dalloc(ctx, &ctx->rep_pairs, ctx->rep_cap));
+        LB_CUDA(dalloc(ctx, &ctx->rep_count, 1));
+        LB_CUDA(dalloc(ctx, &ctx->rep_near, (size_t)ctx->C * REP_NEARB));
+        LB_CUDA(dalloc(ctx, &ctx->rep_near_count, ctx->C));
+        LB_CUDA(dalloc(ctx, &ctx->rep_err, 1));
+        LB_CUDA(cudaMemsetAsync(ctx->rep_err, 0, sizeof(int), ctx->stream));
+        if (!bq.empty()) {
+            LB_CUDA(up(&ctx->rep_bead_q, bq));
+            LB_CUDA(up(&ctx->rep_bead_r, br));
+            LB_CUDA(up(&ctx->rep_bead_ch, bc));
+        }
+    }
     LB_CUDA(up(&ctx->edges, ctx->hedges));
     LB_CUDA(up(&ctx->edge_rest, ctx->hedge_rest));
     LB_CUDA(dalloc(ctx, &ctx->eS, ctx->E));
@@ -826,10 +899,23 @@ lb_status lb_destroy(lb_ctx* ctx) {
     return LB_OK;
 }
 
+lb_status lb_set_repulsion(lb_ctx* ctx, double k, double dc) {
+    LB_GUARD(ctx);
+    if (ctx->started || ctx->committed) return fail(ctx, LB_ERR_STATE, "collisions must be set before the first step");
+    if (!(k >= 0.0) || !(dc > 0.0) || !std::isfinite(k) || !std::isfinite(dc))
+        return fail(ctx, LB_ERR_ARG, "need k >= 0 and dc > 0");
+    if (k > 0.0 && ctx->phi) return fail(ctx, LB_ERR_STATE, "collisions are not part of the differentiable variant");
+    ctx->rep_k = (float)k;
+    ctx->rep_dc = (float)dc;
+    drop_graphs(ctx);
+    return LB_OK;
+}
+
 lb_status lb_set_brinkman(lb_ctx* ctx, const double* beads, int n, double alpha, double delta) {
     LB_GUARD(ctx);
     if (ctx->started) return fail(ctx, LB_ERR_STATE, "the Brinkman beads must be set before the first step");
     if (ctx->ch.size() != 1) return fail(ctx, LB_ERR_ARG, "the differentiable variant takes a single-channel context");
+    if (ctx->rep_k > 0.f) return fail(ctx, LB_ERR_STATE, "collisions are not part of the differentiable variant");
     if (n < 0 || (n > 0 && !beads) || !(alpha >= 0.0) || !(delta > 0.0))
         return fail(ctx, LB_ERR_ARG, "bad bead list, alpha or delta");
     for (int k = 0; k < 4 * n; ++k)
@@ -1187,6 +1273,7 @@ lb_status lb_set_obstacles(lb_ctx* ctx, const float* spheres, int n, const uint8
         LB_CUDA(cudaMemcpyAsync(dext, extra_mask, (size_t)c.d.n, cudaMemcpyHostToDevice, ctx->stream));
     }
     LB_CUDA(launch_rasterise(dsph, n, dext, c.d, ctx->mask, ctx->stream));
+    ctx->ch[ctx->cur].spheres.assign(spheres, spheres + 4 * (size_t)n);
     LB_CUDA(launch_slow_flags(c.d, ctx->mask, ctx->slow, ctx->links, ctx->stream));
     LB_CUDA(cudaStreamSynchronize(ctx->stream));
     dfree(ctx, dsph);
@@ -1411,6 +1498,7 @@ lb_status lb_step(lb_ctx* ctx, int n_steps) {
             LB_CUDA(cudaGraphLaunch(ctx->gexec[par], ctx->stream));
             for (int c = 0; c < 4; ++c)
                 if (ctx->M > 0 || c == 2) ctx->launches[c] += 1;
+            if (ctx->M > 0 && ctx->rep_k > 0.f) ctx->launches[1] += 4;   // collision kernels
         }
         ctx->step++;
     }
@@ -1733,6 +1821,10 @@ lb_status lb_diagnostics(lb_ctx* ctx, double u_max, double out[6]) {
     LB_CUDA(cudaStreamSynchronize(ctx->stream));
     if (out[4] > 0) return fail(ctx, LB_ERR_NUMERIC, "non-finite populations");
     int serr = 0;
+    if (ctx->rep_err) {
+        LB_CUDA(cudaMemcpy(&serr, ctx->rep_err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (serr > 0) return fail(ctx, LB_ERR_STATE, "collision candidate lists overflowed (more than 32 neighbour cells or 64 beads)");
+    }
     LB_CUDA(cudaMemcpy(&serr, ctx->sched_err, sizeof(int), cudaMemcpyDeviceToHost));
     if (serr > 0)
         return fail(ctx, LB_ERR_NUMERIC, "an IB point moved a lattice unit or more in one step (overlapped schedule)");

@@ -180,6 +180,7 @@ struct IbmArgs {
     uint8_t* fl0;
     uint8_t* fl1;
     const float4* u;
+    const float4* R;      // [M] collision forces added to the membrane forces (null: none)
     // overlapped schedule: map receiving the next step's stencil set, the
     // current step's set (every spread target must lie in it) and the count
     // of spread targets found outside it
@@ -230,6 +231,28 @@ struct AdjArgs {
     float4* tri_n;            // [T]
     double* lam_c;            // [2C]
     double* grad;             // [2 + 3 n_beads] (ks, kb of the objective cell, bead centres)
+};
+
+// Arguments of the collision kernels (repulsion.cu).
+constexpr int REP_NEARB = 64;       // candidate beads per cell
+struct RepArgs {
+    float k, dc;                    // force k (dc - d) for d < dc
+    int n_cells, n_nodes, n_beads, pair_cap;
+    const Q4* q;                    // current positions
+    const CellDev* cells;
+    const int4* info;
+    const ChannelDev* ch;
+    float4* bounds;                 // [C] centre (absolute), radius
+    int2* pairs;                    // [pair_cap] ordered candidate cell pairs
+    int* pair_count;
+    int* near;                      // [C][REP_NEARB] candidate beads per cell
+    int* near_count;                // [C]
+    const Q4* bead_q;               // [nb] bead centres in fixed point
+    const float* bead_r;            // [nb]
+    const int* bead_ch;             // [nb]
+    float4* R;                      // [M] collision force per node (accumulated)
+    int* err;                       // candidate list overflows
+    ChannelDev chp[MAXCH_P];
 };
 
 // D3Q19 velocity set (Sec. 2.1): rest, +-x, +-y, +-z, then the 12 diagonals,
@@ -294,6 +317,7 @@ cudaError_t launch_elements(const IbmArgs& a, cudaStream_t s);
 cudaError_t launch_forces_spread(const IbmArgs& a, cudaStream_t s);
 cudaError_t launch_interp_advance(const IbmArgs& a, cudaStream_t s);
 
+cudaError_t launch_repulsion(const RepArgs& a, int sm_count, cudaStream_t s);
 cudaError_t launch_adj_interp(const AdjArgs& a, cudaStream_t s);
 cudaError_t launch_adj_collide(const AdjArgs& a, cudaStream_t s);
 cudaError_t launch_adj_spread(const AdjArgs& a, cudaStream_t s);

@@ -20,7 +20,7 @@ STORAGE = {"f32": 0, "f16": 1, "bf16": 2}
 
 # Every entry point that include/lbibm.h declares.
 EXPORTS = (
-    "lb_create", "lb_create_batch", "lb_select_channel", "lb_destroy", "lb_set_obstacles", "lb_set_brinkman", "lb_adjoint", "ibm_add_mesh",
+    "lb_create", "lb_create_batch", "lb_select_channel", "lb_destroy", "lb_set_obstacles", "lb_set_brinkman", "lb_adjoint", "lb_set_repulsion", "ibm_add_mesh",
     "ibm_set_nodes", "lb_step", "lb_synchronize", "lb_get_fields", "lb_get_populations", "lb_set_populations",
     "ibm_get_nodes", "ibm_get_all_nodes", "ibm_get_forces", "ibm_get_area_volume", "lb_diagnostics", "lb_get_step", "lb_save_state",
     "lb_load_state", "lb_set_schedule", "lb_get_schedule", "lb_set_timing", "lb_kernel_times", "lb_last_error", "lb_version", "lb_get_mask",
@@ -84,6 +84,7 @@ def lib():
             "lb_load_state": ([P, P, ctypes.c_size_t], I),
             "lb_set_timing": ([P, I], I),
             "lb_set_brinkman": ([P, P, I, D, D], I),
+            "lb_set_repulsion": ([P, D, D], I),
             "lb_adjoint": ([P, I, I, I, P, P, P, P], I),
             "lb_set_schedule": ([P, I], I),
             "lb_get_schedule": ([P, P], I),
@@ -145,6 +146,9 @@ class Simulation:
     def from_scenes(cls, scenes, storage="f32", stream=None) -> "Simulation":
         params = [make_params(s.dims, s.tau, s.body_force, s.periodic, s.wall_velocity, storage) for s in scenes]
         sim = cls(params, stream)
+        rep = getattr(scenes[0], "repulsion", None)
+        if rep is not None:
+            sim.set_repulsion(*rep)
         for k, s in enumerate(scenes):
             sim.select(k)
             if len(s.spheres):
@@ -294,6 +298,10 @@ class Simulation:
         n, b, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
         self._check(self._L.lb_autotune(self._h, int(repeats), ctypes.byref(n), ctypes.byref(b), ctypes.byref(ms)))
         return n.value, b.value, ms.value
+
+    def set_repulsion(self, k: float, dc: float):
+        """Soft-sphere collisions (cells, beads, walls): force k (dc - d) below separation dc."""
+        self._check(self._L.lb_set_repulsion(self._h, float(k), float(dc)))
 
     def set_brinkman(self, beads, alpha: float = 2.0, delta: float = 0.5):
         """Differentiable variant: beads (n x 4: cx, cy, cz, r) as a smooth Brinkman solid fraction."""

@@ -89,6 +89,8 @@ class Scene:
     meshes: List[Mesh] = field(default_factory=list)
     steps: int = 0
     seed: int = 0
+    # soft-sphere collisions (k, d_c), or None for none (Sec. 2.4 reading)
+    repulsion: Optional[Tuple[float, float]] = None
 
     @property
     def n_nodes(self) -> int:
