@@ -397,14 +397,17 @@ template <class S, int NPT, int BS> struct K3MinBlocks {
 enum : int { SC_ALL = 0, SC_BULK = 1, SC_LIST = 2, SC_BRINK = 3 };
 
 // One thread's NPT nodes starting at channel-local node p0.
-template <class S, int NPT, int MODE>
-__device__ __forceinline__ void sc_nodes(const LatticeArgs& a, const ChannelDev& C, int p0, int lane) {
+// ROW: the caller's block lies inside one lattice row, all its nodes in range,
+// and passes the coordinates (y, z are then block-uniform).
+template <class S, int NPT, int MODE, bool ROW = false>
+__device__ __forceinline__ void sc_nodes(const LatticeArgs& a, const ChannelDev& C, int p0, int lane, int xr = 0,
+                                         int yr = 0, int zr = 0) {
     const long long gp0 = C.base + p0;
     const int gi0 = (int)gp0;      // the padded node count of a context is below 2^31
     const int grp = gi0 >> 5;
     const int par = a.par;
     uint8_t* fl_prev = par ? a.fl0 : a.fl1;
-    const bool inr = p0 < C.n;
+    const bool inr = ROW ? true : p0 < C.n;
     // flags first: their latency overlaps the population loads below
     const uint8_t fcur = MODE == SC_BULK ? (uint8_t)0 : __ldg((par ? a.fl1 : a.fl0) + grp);
     const uint8_t fprev = MODE == SC_BULK ? (uint8_t)0 : __ldg(fl_prev + grp);
@@ -412,10 +415,15 @@ __device__ __forceinline__ void sc_nodes(const LatticeArgs& a, const ChannelDev&
     const S* src = (const S*)(par ? a.h1 : a.h0);
     S* dst = (S*)(par ? a.h0 : a.h1);
     const long long NT = a.Ntot;
-    const int r = fdiv(p0, C.dnx);
-    const int x0 = p0 - r * C.nx;
-    const int z = fdiv(r, C.dny);
-    const int y = r - z * C.ny;
+    int x0, y, z;
+    if constexpr (ROW) {
+        x0 = xr; y = yr; z = zr;
+    } else {
+        const int r = fdiv(p0, C.dnx);
+        x0 = p0 - r * C.nx;
+        z = fdiv(r, C.dny);
+        y = r - z * C.ny;
+    }
     Nbr nb;
     neighbours(C, x0, y, z, nb);
     // phase 1: every population load of the vector path in flight at once
@@ -501,6 +509,18 @@ __global__ void __launch_bounds__(BS, K3MinBlocks<S, NPT, BS>::value) k_stream_c
     const ChannelDev C = chan(a, c);   // registers: read once from the parameter bank
     const int lane = threadIdx.x & 31;
     const int p0 = ((b - C.blk0) * BS + (int)threadIdx.x) * NPT;   // first channel-local node of this thread
+    if constexpr (NPT == 1 && sizeof(S) == 2) {
+        // (measured on GB300: faster for 16-bit storage, slower for FP32 -- a
+        // register budget of 48 leaves no room for the extra live values)
+        const int pb = (b - C.blk0) * BS;
+        if (C.nx % BS == 0 && pb + BS <= C.n) {
+            // the block is a piece of one row: y and z are the block's
+            const int r = fdiv(pb, C.dnx);
+            const int z = fdiv(r, C.dny);
+            sc_nodes<S, 1, SC_ALL, true>(a, C, p0, lane, pb - r * C.nx + (int)threadIdx.x, r - z * C.ny, z);
+            return;
+        }
+    }
     sc_nodes<S, NPT, SC_ALL>(a, C, p0, lane);
 }
 
