@@ -176,9 +176,15 @@ lb_status lb_step(lb_ctx* ctx, int n_steps);
  * block_size 128 or 256.  nodes_per_thread 0: staged variant (rows copied to
  * shared memory asynchronously; block_size 256; every channel's row of nx
  * populations a multiple of 16 bytes and nx <= 512).  nodes_per_thread -1:
- * pipelined variant (persistent warps, block_size 128 or 256).  The default
- * is 1 node per thread, 128 threads.  LB_ERR_ARG for an unsupported pair.
- * Results do not depend on the variant. */
+ * pipelined variant (persistent warps, block_size 128 or 256).
+ * nodes_per_thread -2: TMA-staged variant (tensor copies of every direction's
+ * source rows into shared memory, double-buffered, one node per thread;
+ * block_size 256 or 512 = nodes per tile); FP32 storage, one channel, walls
+ * (not periodic) in y and z, nx in {32, 64, 128, 256} dividing block_size and
+ * ny a multiple of block_size / nx.  A block that gives up waiting for its
+ * copies makes lb_diagnostics return LB_ERR_STATE.  The default is 1 node per
+ * thread, 128 threads.  LB_ERR_ARG for an unsupported pair.  Results do not
+ * depend on the variant. */
 lb_status lb_set_kernel_config(lb_ctx* ctx, int nodes_per_thread, int block_size);
 lb_status lb_get_kernel_config(lb_ctx* ctx, int* nodes_per_thread, int* block_size);
 

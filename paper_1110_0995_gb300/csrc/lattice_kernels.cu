@@ -866,6 +866,239 @@ cudaError_t launch_brinkman_phi(const ChannelDev& ch, const float* beads, int nb
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// TMA-staged variant (FP32, one channel, walls in y and z, nx dividing 512).
+// A tile is R = 512 / nx whole rows of one z-plane.  For every direction i the
+// R source rows (y - ey_i, z - ez_i) of plane i are one box of a 4-D tensor
+// map (x, y, z, direction) copied by the tensor-memory accelerator into shared
+// memory; rows outside the channel arrive zero-filled (their links bounce
+// back, read from global memory).  Persistent blocks double-buffer: the
+// copies of the next tile are in flight while the current one is collided.
+// The +-x shift is a wrapped index into the staged row.  Every wait on the
+// tile's mbarrier is bounded; a wait that runs out sets tma_err and the block
+// stops.
+// ---------------------------------------------------------------------------
+constexpr unsigned TMA_WAIT_LIMIT = 1u << 20;
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned phase) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
+        ::"r"(smem_u32(dst)), "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// all 19 boxes of tile t into buffer `buf`, one expect_tx for their bytes
+template <int TILE>
+__device__ __forceinline__ void tma_issue(const CUtensorMap* map, const ChannelDev& C, int R, int t, float* buf,
+                                          uint64_t* bar) {
+    const int tpz = C.ny / R;
+    const int z = t / tpz, y0 = (t - z * tpz) * R;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // earlier generic reads of buf before the async writes
+    mbar_expect_tx(bar, (unsigned)(Q * TILE * sizeof(float)));
+#pragma unroll
+    for (int i = 0; i < Q; ++i) tma_load_4d(buf + i * TILE, map, 0, y0 - ey(i), z - ez(i), i, bar);
+}
+
+template <int TILE, int I>
+__device__ __forceinline__ float tma_pop(const float* buf, int j, int x, int nx) {
+    int xs = x - ex(I);
+    xs += xs < 0 ? nx : 0;
+    xs -= xs >= nx ? nx : 0;
+    return buf[I * TILE + j * nx + xs];
+}
+
+// one thread per node of a TILE-node tile; STAGES tiles in a ring of buffers
+template <int TILE, int STAGES>
+__global__ void __launch_bounds__(TILE, 1024 / TILE) k_stream_collide_tma(const __grid_constant__ LatticeArgs a,
+                                                                    const __grid_constant__ CUtensorMap map0,
+                                                                    const __grid_constant__ CUtensorMap map1) {
+    extern __shared__ __align__(128) unsigned char tma_sm[];
+    float* bufs = reinterpret_cast<float*>(tma_sm);                 // [STAGES][19][TILE]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(tma_sm + STAGES * Q * TILE * sizeof(float));
+    const ChannelDev C = a.chp[0];
+    const int R = TILE / C.nx;
+    const int tiles = (C.ny / R) * C.nz;
+    const int par = a.par;
+    const CUtensorMap* map = par ? &map1 : &map0;
+    const float* src = (const float*)(par ? a.h1 : a.h0);
+    float* dst = (float*)(par ? a.h0 : a.h1);
+    uint8_t* fl_prev = par ? a.fl0 : a.fl1;
+    const uint8_t* fl_cur = par ? a.fl1 : a.fl0;
+    const float4* gcur = par ? a.g1 : a.g0;
+    float4* gprev = par ? a.g0 : a.g1;
+    const long long NT = a.Ntot;
+    const float om = C.omega, fp = C.fpre;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < STAGES; ++k) mbar_init(&bars[k], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    // prologue: the block's first STAGES tiles
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < STAGES; ++k) {
+            const int t = (int)blockIdx.x + k * (int)gridDim.x;
+            if (t < tiles) tma_issue<TILE>(map, C, R, t, bufs + k * Q * TILE, &bars[k]);
+        }
+    }
+    unsigned phase = 0u;   // bit k: parity of buffer k's next completion
+    int sidx = 0;
+    for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
+        // bounded wait for this tile's boxes
+        unsigned it = 0;
+        while (!mbar_try_wait(&bars[sidx], (phase >> sidx) & 1u) && ++it < TMA_WAIT_LIMIT) {
+        }
+        phase ^= 1u << sidx;
+        const float* buf = bufs + sidx * Q * TILE;
+        const int tpz = C.ny / R;
+        const int z = t / tpz, y0 = (t - z * tpz) * R;
+        {
+            const int n = threadIdx.x;
+            const int j = n / C.nx, x = n - j * C.nx;
+            const int y = y0 + j;
+            const int gi = (int)C.base + x + C.nx * (y + C.ny * z);
+            const int grp = gi >> 5;
+            const bool forced = fl_cur[grp] != 0;
+            const bool prevf = fl_prev[grp] != 0;
+            const bool slow = __ldg(a.slow + grp) != 0;
+            float h[Q];
+#define LBIBM_TP(I) h[I] = tma_pop<TILE, I>(buf, j, x, C.nx);
+            LBIBM_ALL_I(LBIBM_TP)
+#undef LBIBM_TP
+            // every thread has its populations in registers: the buffer is free.
+            // A wait that ran out ends the block (all threads together).
+            if (__syncthreads_or(it >= TMA_WAIT_LIMIT)) {
+                if (threadIdx.x == 0) {
+                    atomicAdd(a.tma_err, 1);
+                    // copies still in flight into this block's buffers: wait, bounded, before leaving
+                    for (int k = 0; k < STAGES; ++k) {
+                        const int tk = t + k * (int)gridDim.x;
+                        const int bk = (sidx + k) % STAGES;
+                        const unsigned pk = ((phase >> bk) & 1u) ^ (k == 0 ? 1u : 0u);
+                        unsigned w = 0;
+                        while (tk < tiles && !mbar_try_wait(&bars[bk], pk) && ++w < TMA_WAIT_LIMIT) {
+                        }
+                    }
+                }
+                return;
+            }
+            const int nt = t + STAGES * (int)gridDim.x;
+            if (threadIdx.x == 0 && nt < tiles) tma_issue<TILE>(map, C, R, nt, bufs + sidx * Q * TILE, &bars[sidx]);
+            uint32_t lk = 0u;
+            if (slow) {
+                lk = __ldg(a.links + gi);
+                bounce_back<float>(src, NT, gi, lk, C, y, h);
+            }
+            if (!(lk & 1u)) {
+                float gx = C.G[0], gy = C.G[1], gz = C.G[2];
+                if (forced) {
+                    const float4 g = gcur[gi];
+                    gx += g.x; gy += g.y; gz += g.z;
+                }
+                const Mac m = macro(h, gx, gy, gz);
+                collide_all(h, m, om, fp);
+#define LBIBM_TS(I) dst[(long long)(I) * NT + gi] = h[I];
+                LBIBM_ALL_I(LBIBM_TS)
+#undef LBIBM_TS
+                if (forced) a.u[gi] = make_float4(m.ux, m.uy, m.uz, m.rho);
+                if (prevf) gprev[gi] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            __syncwarp();
+            if (prevf && (gi & 31) == 0) fl_prev[grp] = 0;
+        }
+        sidx = sidx == STAGES - 1 ? 0 : sidx + 1;
+    }
+}
+
+static size_t tma_smem(int tile, int stages) { return stages * ((size_t)Q * tile * sizeof(float) + sizeof(uint64_t)); }
+
+bool tma_variant_ok(const ChannelDev& C, int storage, int n_ch, int tile) {
+    return (tile == 256 || tile == 512) && storage == 0 && n_ch == 1 && !C.per[1] && !C.per[2] && C.nx >= 32 &&
+           C.nx <= 256 && tile % C.nx == 0 && C.ny % (tile / C.nx) == 0;
+}
+
+cudaError_t encode_tma_maps(const ChannelDev& C, int tile, void* h0, void* h1, long long plane, CUtensorMap* maps) {
+    using Enc = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                             const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                             CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || !fn || q != cudaDriverEntryPointSuccess) return cudaErrorNotSupported;
+    const cuuint64_t dims[4] = {(cuuint64_t)C.nx, (cuuint64_t)C.ny, (cuuint64_t)C.nz, (cuuint64_t)Q};
+    const cuuint64_t strides[3] = {(cuuint64_t)C.nx * 4, (cuuint64_t)C.nx * C.ny * 4, (cuuint64_t)plane * 4};
+    const cuuint32_t box[4] = {(cuuint32_t)C.nx, (cuuint32_t)(tile / C.nx), 1, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    void* bases[2] = {h0, h1};
+    for (int k = 0; k < 2; ++k) {
+        float* base = reinterpret_cast<float*>(bases[k]) + C.base;
+        const CUresult r = reinterpret_cast<Enc>(fn)(&maps[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides,
+                                                     box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    }
+    return cudaSuccess;
+}
+
+template <int TILE, int STAGES>
+static cudaError_t launch_tma_typed(const LatticeArgs& a, const CUtensorMap* maps, int blocks, cudaStream_t s) {
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_stream_collide_tma<TILE, STAGES>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma_smem(TILE, STAGES));
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    k_stream_collide_tma<TILE, STAGES><<<blocks, TILE, tma_smem(TILE, STAGES), s>>>(a, maps[0], maps[1]);
+    return cudaGetLastError();
+}
+
+// (measured on GB300, 256x128x64 filter, tile 256: two buffers at 4 blocks per
+// SM and 64 registers, 65.5 us; three buffers 71.5 us, four 91.6 us -- each
+// costs a block of residency, and the kernel is issue-bound, not waiting on
+// its copies; 48 registers spill, 72.2 us)
+constexpr int TMA_STAGES = 2;
+
+template <int TILE>
+static int tma_occ() {
+    int n = 0;
+    cudaError_t e = cudaFuncSetAttribute(k_stream_collide_tma<TILE, TMA_STAGES>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma_smem(TILE, TMA_STAGES));
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_stream_collide_tma<TILE, TMA_STAGES>, TILE,
+                                                          tma_smem(TILE, TMA_STAGES));
+    return e == cudaSuccess && n > 0 ? n : 1;
+}
+
+int tma_blocks_per_sm(int tile) { return tile == 256 ? tma_occ<256>() : tma_occ<512>(); }
+
+cudaError_t launch_stream_collide_tma(const LatticeArgs& a, int tile, const CUtensorMap* maps, int blocks,
+                                      cudaStream_t s) {
+    if (tile == 256) return launch_tma_typed<256, TMA_STAGES>(a, maps, blocks, s);
+    if (tile == 512) return launch_tma_typed<512, TMA_STAGES>(a, maps, blocks, s);
+    return cudaErrorInvalidConfiguration;
+}
+
 template <class S>
 static size_t staged_smem() { return 2 * (size_t)Q * SG_NODES * sizeof(S); }
 
@@ -882,10 +1115,10 @@ cudaError_t prepare_staged(int storage) {
 
 // Supported (nodes per thread, block size) pairs per storage type; npt = 0 is
 // the staged variant, npt = -1 the pipelined one.
-static const K3Config CFG_F32[] = {{-1, 128}, {-1, 256}, {0, 256}, {1, 256}, {2, 256}, {4, 256}, {4, 128}, {2, 128}, {1, 128}};
+static const K3Config CFG_F32[] = {{-2, 256}, {-2, 512}, {-1, 128}, {-1, 256}, {0, 256}, {1, 256}, {2, 256}, {4, 256}, {4, 128}, {2, 128}, {1, 128}};
 static const K3Config CFG_16[] = {{-1, 128}, {-1, 256}, {0, 256}, {2, 256}, {4, 256}, {4, 128}, {2, 128}, {1, 256}, {1, 128}};
 
-int k3_config_count(int storage) { return 9; }
+int k3_config_count(int storage) { return storage == 0 ? 11 : 9; }
 K3Config k3_config_at(int storage, int k) { return storage == 0 ? CFG_F32[k] : CFG_16[k]; }
 bool k3_config_supported(int storage, K3Config c) {
     for (int k = 0; k < k3_config_count(storage); ++k) {

@@ -119,7 +119,9 @@ struct lb_ctx {
     uint8_t* dmap[2] = {nullptr, nullptr};
     int* dlist[2] = {nullptr, nullptr};
     int* dcount = nullptr;         // [2]
-    int* sched_err = nullptr;
+    int* sched_err = nullptr;      // [2]: overlapped-schedule check, TMA-variant waits
+    CUtensorMap tma_maps[2];       // TMA-staged stream-collide: h[0], h[1]
+    bool tma_ready = false;
     int list_blocks = 0;
     // collisions (soft sphere): off while rep_k == 0
     float rep_k = 0.f, rep_dc = 0.f;
@@ -235,7 +237,17 @@ LatticeArgs lattice_args(const lb_ctx* ctx, int par) {
     a.dmap = ctx->dmap[par];
     a.dlist = ctx->dlist[par];
     a.dcount = ctx->dcount ? ctx->dcount + par : nullptr;
+    a.tma_err = ctx->sched_err ? ctx->sched_err + 1 : nullptr;
     return a;
+}
+
+// the stream-collide launch of the context's variant
+cudaError_t k3_launch(const lb_ctx* ctx, const LatticeArgs& la, K3Config c, cudaStream_t s) {
+    if (c.npt == -2) {
+        if (!ctx->tma_ready) return cudaErrorNotSupported;
+        return launch_stream_collide_tma(la, c.bs, ctx->tma_maps, ctx->total_blocks, s);
+    }
+    return launch_stream_collide(la, c, ctx->total_blocks, s);
 }
 
 IbmArgs ibm_args(const lb_ctx* ctx, int par, bool overlapped = false) {
@@ -362,7 +374,7 @@ lb_status enqueue_step(lb_ctx* ctx, int par) {
         switch (k) {
             case 0: e = launch_elements(ia, ctx->stream); break;
             case 1: e = launch_forces_spread(ia, ctx->stream); break;
-            case 2: e = launch_stream_collide(la, ctx->k3, ctx->total_blocks, ctx->stream); break;
+            case 2: e = k3_launch(ctx, la, ctx->k3, ctx->stream); break;
             case 3: e = launch_interp_advance(ia, ctx->stream); break;
         }
         if (e != cudaSuccess) return cuda_fail(ctx, e, "kernel launch");
@@ -565,6 +577,7 @@ long long plane_pad() {
 bool k3_config_valid(const lb_ctx* ctx, K3Config c) {
     if (!k3_config_supported((int)ctx->storage, c)) return false;
     if (ctx->phi && c.npt != 1) return false;   // the differentiable variant runs one node per thread
+    if (c.npt == -2) return ctx->ch.size() == 1 && tma_variant_ok(ctx->ch[0].d, (int)ctx->storage, 1, c.bs);
     for (const auto& ch : ctx->ch) {
         if (c.npt == 0) {
             if (staged_rows(ch.d.nx, (int)pop_bytes(ctx->storage)) == 0) return false;
@@ -584,6 +597,18 @@ K3Config default_k3_config(const lb_ctx* ctx) {
 
 void apply_k3_config(lb_ctx* ctx, K3Config c) {
     ctx->k3 = c;
+    if (c.npt == -2) {
+        // TMA-staged: bs-node tiles, persistent grid at full residency; the
+        // tensor maps address the two population arrays
+        const ChannelDev& d = ctx->ch[0].d;
+        const int tiles = d.ny / (c.bs / d.nx) * d.nz;
+        ctx->ch[0].d.blk0 = 0;
+        ctx->n_groups = tiles;
+        ctx->total_blocks = std::min(tiles, tma_blocks_per_sm(c.bs) * ctx->sm_count);
+        ctx->tma_ready = ctx->h[0] && ctx->h[1] &&
+                         encode_tma_maps(d, c.bs, ctx->h[0], ctx->h[1], ctx->plane, ctx->tma_maps) == cudaSuccess;
+        return;
+    }
     if (c.npt == 0) {
         // staged: row groups per channel, persistent grid of two blocks per SM
         int grp = 0;
@@ -805,7 +830,7 @@ lb_status lb_create_batch(const lb_params* params, int n_channels, void* cuda_st
     TRY(dalloc(ctx, &ctx->dlist[0], NG));
     TRY(dalloc(ctx, &ctx->dlist[1], NG));
     TRY(dalloc(ctx, &ctx->dcount, 2));
-    TRY(dalloc(ctx, &ctx->sched_err, 1));
+    TRY(dalloc(ctx, &ctx->sched_err, 2));
     TRY(dalloc(ctx, &ctx->d_ch, ctx->ch.size()));
     ctx->diag_blocks = 152 * 4;
     TRY(dalloc(ctx, &ctx->diag_partials, (size_t)ctx->diag_blocks * 6));
@@ -823,7 +848,7 @@ lb_status lb_create_batch(const lb_params* params, int n_channels, void* cuda_st
     TRY(cudaMemsetAsync(ctx->dmap[0], 0, NG, ctx->stream));
     TRY(cudaMemsetAsync(ctx->dmap[1], 0, NG, ctx->stream));
     TRY(cudaMemsetAsync(ctx->dcount, 0, 2 * sizeof(int), ctx->stream));
-    TRY(cudaMemsetAsync(ctx->sched_err, 0, sizeof(int), ctx->stream));
+    TRY(cudaMemsetAsync(ctx->sched_err, 0, 2 * sizeof(int), ctx->stream));
     {
         int lo = 0, hi = 0;
         TRY(cudaDeviceGetStreamPriorityRange(&lo, &hi));
@@ -982,7 +1007,7 @@ lb_status store_step(lb_ctx* ctx, int k) {
     ia.cell_rel = W.seg_rel + (size_t)k * ctx->C;
     LB_CUDA(launch_elements(ia, s));
     LB_CUDA(launch_forces_spread(ia, s));
-    LB_CUDA(launch_stream_collide(la, ctx->k3, ctx->total_blocks, s));
+    LB_CUDA(k3_launch(ctx, la, ctx->k3, s));
     LB_CUDA(launch_interp_advance(ia, s));
     ctx->step++;
     return LB_OK;
@@ -1557,9 +1582,9 @@ lb_status lb_autotune(lb_ctx* ctx, int repeats, int* nodes_per_thread, int* bloc
         apply_k3_config(ctx, c);
         if (ctx->ch.size() > (size_t)MAXCH_P && upload_channels(ctx) != LB_OK) return LB_ERR_CUDA;
         const LatticeArgs la = lattice_args(ctx, 0);
-        cudaError_t e = launch_stream_collide(la, c, ctx->total_blocks, ctx->stream);   // warm-up
+        cudaError_t e = k3_launch(ctx, la, c, ctx->stream);   // warm-up
         if (e == cudaSuccess) e = cudaEventRecord(e0, ctx->stream);
-        for (int r = 0; r < repeats && e == cudaSuccess; ++r) e = launch_stream_collide(la, c, ctx->total_blocks, ctx->stream);
+        for (int r = 0; r < repeats && e == cudaSuccess; ++r) e = k3_launch(ctx, la, c, ctx->stream);
         if (e == cudaSuccess) e = cudaEventRecord(e1, ctx->stream);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
         float t = 0.f;
@@ -1825,9 +1850,11 @@ lb_status lb_diagnostics(lb_ctx* ctx, double u_max, double out[6]) {
         LB_CUDA(cudaMemcpy(&serr, ctx->rep_err, sizeof(int), cudaMemcpyDeviceToHost));
         if (serr > 0) return fail(ctx, LB_ERR_STATE, "collision candidate lists overflowed (more than 32 neighbour cells or 64 beads)");
     }
-    LB_CUDA(cudaMemcpy(&serr, ctx->sched_err, sizeof(int), cudaMemcpyDeviceToHost));
-    if (serr > 0)
+    int serr2[2] = {0, 0};
+    LB_CUDA(cudaMemcpy(serr2, ctx->sched_err, 2 * sizeof(int), cudaMemcpyDeviceToHost));
+    if (serr2[0] > 0)
         return fail(ctx, LB_ERR_NUMERIC, "an IB point moved a lattice unit or more in one step (overlapped schedule)");
+    if (serr2[1] > 0) return fail(ctx, LB_ERR_STATE, "a TMA-staged stream-collide block gave up waiting for its copies");
     if (u_max > 0 && !(out[5] <= u_max)) return fail(ctx, LB_ERR_NUMERIC, "velocity above the stability bound");
     return LB_OK;
 }

@@ -37,6 +37,7 @@
 //                float4 tN[T]     unnormalised outward normal of the triangle
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
@@ -141,6 +142,7 @@ struct LatticeArgs {
     // the Brinkman coefficient alpha
     const float* phi;
     float alpha;
+    int* tma_err;         // TMA variant: mbarrier waits that ran out
     ChannelDev chp[MAXCH_P];   // copy of the first channels (constant bank)
 };
 
@@ -272,7 +274,9 @@ __host__ __device__ constexpr double wgt_d(int i) { return i == 0 ? (1.0 / 3.0) 
 
 // Stream-collide kernel variants: nodes per thread along x and block size.
 // npt = 0 selects the staged variant (rows copied to shared memory with
-// asynchronous copies, persistent grid of bs-thread blocks).
+// asynchronous copies, persistent grid of bs-thread blocks), npt = -1 the
+// pipelined one, npt = -2 the TMA-staged one (tensor copies of every
+// direction's source rows into shared memory, FP32, one channel; bs = tile).
 struct K3Config {
     int npt;
     int bs;
@@ -300,6 +304,13 @@ cudaError_t launch_rasterise(const float* spheres, int n_spheres, const uint8_t*
 cudaError_t launch_slow_flags(const ChannelDev& ch, const uint32_t* mask, uint8_t* slow, uint32_t* links,
                               cudaStream_t s);
 cudaError_t launch_stream_collide(const LatticeArgs& a, K3Config cfg, int total_blocks, cudaStream_t s);
+// TMA-staged variant: tile geometry, descriptor encoding and launch
+// (tile = nodes per tile = threads per block, 256 or 512: R = tile / nx whole rows)
+bool tma_variant_ok(const ChannelDev& C, int storage, int n_ch, int tile);
+cudaError_t encode_tma_maps(const ChannelDev& C, int tile, void* h0, void* h1, long long plane, CUtensorMap* maps);
+int tma_blocks_per_sm(int tile);
+cudaError_t launch_stream_collide_tma(const LatticeArgs& a, int tile, const CUtensorMap* maps, int blocks,
+                                      cudaStream_t s);
 // mode 1: bulk (groups outside a.dmap; `smem` bytes of unused dynamic shared
 // memory per block cap its residency), mode 2: the first (blocks * bs / 32)
 // groups of a.dlist, mode 3: the groups of a.dlist from entry `smem` on

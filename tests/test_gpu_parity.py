@@ -107,6 +107,47 @@ def test_lattice_parity_every_kernel_variant(npt, bs):
     np.testing.assert_allclose(sim.populations()[:, fluid], ref.get_f()[:, fluid], rtol=0, atol=2e-7)
 
 
+@pytest.mark.parametrize("dims,periodic,wall", [((64, 24, 19), (1, 0, 0), ((0, 0, 0), (0.02, 0, 0.01))),
+                                                ((32, 32, 7), (0, 0, 0), ((0.01, 0, 0), (0, 0, 0))),
+                                                ((256, 6, 5), (1, 0, 0), ((0, 0, 0), (0, 0, 0)))])
+@pytest.mark.parametrize("tile", [256, 512])
+def test_tma_staged_variant(dims, periodic, wall, tile):
+    """The TMA-staged stream-collide (FP32, one channel, walls in y and z, nx
+    dividing the tile): tiles of whole rows, zero-filled boxes beyond the
+    walls replaced by bounce-back; random state, obstacles, moving walls."""
+    sc = _ragged_scene(periodic, wall, dims=dims)
+    sc.spheres = scene.quantize(sc.spheres * np.array([dims[0] / 37, dims[1] / 23, dims[2] / 19, 1.0]),
+                                scene.SPHERE_QUANTUM).astype(np.float32)
+    sim = _sim(sc)
+    sim.set_kernel_config(-2, tile)
+    ref = oracle.System.from_scene(sc)
+    f0 = ref.get_f() * (1 + 0.01 * scene.random_field(9, (19, ref.N)))
+    f0[:, ref.solid == 1] = ref.get_f()[:, ref.solid == 1]
+    ref.set_f(f0)
+    sim.set_populations(f0)
+    sim.step(25)
+    ref.step(25)
+    fluid = ref.solid == 0
+    _, u = sim.fields()
+    _, uo = ref.fields()
+    assert rel_l2(u[:, fluid], uo[:, fluid]) < 1e-5
+    np.testing.assert_allclose(sim.populations()[:, fluid], ref.get_f()[:, fluid], rtol=0, atol=2e-7)
+    assert sim.diagnostics() is not None
+
+
+def test_tma_staged_variant_refused_where_it_does_not_apply():
+    from paper_1110_0995_gb300 import lbibm
+
+    for dims, periodic in (((36, 24, 8), (1, 0, 0)), ((64, 24, 8), (1, 1, 0)), ((64, 22, 8), (1, 0, 0))):
+        sim = _sim(_ragged_scene(periodic, dims=dims))
+        for tile in (256, 512):
+            with pytest.raises(lbibm.LbError):
+                sim.set_kernel_config(-2, tile)
+    sim = _sim(_ragged_scene((1, 0, 0), dims=(64, 24, 8)), storage="f16")
+    with pytest.raises(lbibm.LbError):
+        sim.set_kernel_config(-2, 256)
+
+
 @pytest.mark.parametrize("npt,bs", [(-1, 128), (0, 256), (1, 256), (2, 256), (4, 128)])
 def test_plain_channel_every_kernel_variant(npt, bs):
     sc = scene.channel_plain(seed=1, steps=150)
