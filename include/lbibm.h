@@ -188,19 +188,23 @@ lb_status lb_step(lb_ctx* ctx, int n_steps);
 lb_status lb_set_kernel_config(lb_ctx* ctx, int nodes_per_thread, int block_size);
 lb_status lb_get_kernel_config(lb_ctx* ctx, int* nodes_per_thread, int* block_size);
 
-/* Step schedule.  overlapped = 1: when the context has IB meshes
- * and the stream-collide variant has one node per thread, each cycle runs the
- * immersed-boundary kernels on a second, higher-priority stream concurrently
- * with the stream-collide of every 32-node group that no IB point can reach
- * in that step, then updates the reachable groups; the results equal the
- * sequential cycle as long as no IB point moves one lattice unit or more in
- * one step (a spreading target outside the reachable set is counted and
- * reported by lb_diagnostics as LB_ERR_NUMERIC).  overlapped = 0 (default):
- * the four kernels run one after another.  On GB300 the overlapped schedule
- * is currently slower: the latency-bound IB kernels hold SM slots that the
- * concurrent stream-collide needs.  Per-kernel timing (lb_set_timing) always
- * uses the sequential schedule.  lb_get_schedule reports the schedule the
- * next lb_step will use. */
+/* Step schedule.  overlapped = 0 (default): the four kernels of the cycle
+ * run one after another, each launched as a programmatic dependent of its
+ * predecessor (its blocks are scheduled during the predecessor's last wave
+ * and wait for the predecessor to complete before touching memory).
+ * overlapped = 2: the same cycle with ordinary launches.  overlapped = 1: when
+ * the context has IB meshes and the stream-collide variant has one node per
+ * thread, each cycle runs the immersed-boundary kernels on a second,
+ * higher-priority stream concurrently with the stream-collide of every
+ * 32-node group that no IB point can reach in that step, then updates the
+ * reachable groups; the results equal the sequential cycle as long as no IB
+ * point moves one lattice unit or more in one step (a spreading target
+ * outside the reachable set is counted and reported by lb_diagnostics as
+ * LB_ERR_NUMERIC).  On GB300 the overlapped schedule is currently slower: the
+ * latency-bound IB kernels hold SM slots that the concurrent stream-collide
+ * needs.  Per-kernel timing (lb_set_timing) always uses the sequential
+ * schedule with ordinary launches.  All schedules give the same results.
+ * lb_get_schedule reports the schedule the next lb_step will use. */
 lb_status lb_set_schedule(lb_ctx* ctx, int overlapped);
 lb_status lb_get_schedule(lb_ctx* ctx, int* overlapped);
 

@@ -263,6 +263,7 @@ cudaError_t launch_cell_sums(const IbmArgs& a, cudaStream_t s) {
 // (neo-Hookean bond) and bending of edge (a, b), each evaluated once.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(CS_BLOCK, 6) k_elements(const __grid_constant__ IbmArgs a) {
+    pdl_entry();
     if ((int)blockIdx.x < a.n_chunks) {
         tri_chunk<true>(a, blockIdx.x);
         return;
@@ -284,8 +285,7 @@ __global__ void __launch_bounds__(CS_BLOCK, 6) k_elements(const __grid_constant_
 cudaError_t launch_elements(const IbmArgs& a, cudaStream_t s) {
     const int blocks = a.n_chunks + (a.n_edges + CS_BLOCK - 1) / CS_BLOCK;
     if (blocks <= 0) return cudaSuccess;
-    k_elements<<<blocks, CS_BLOCK, 0, s>>>(a);
-    return cudaGetLastError();
+    return launch_ex(k_elements, blocks, CS_BLOCK, 0, s, a.pdl, a);
 }
 
 // ---------------------------------------------------------------------------
@@ -396,23 +396,31 @@ cudaError_t launch_compact_groups(const uint8_t* map, int n_groups, int* list, i
 constexpr int FS_BLOCK = 128;
 
 __global__ void __launch_bounds__(FS_BLOCK, IB_MIN_BLOCKS) k_forces_spread(const __grid_constant__ IbmArgs a) {
+    pdl_trigger();
     const int i = (blockIdx.x * FS_BLOCK + threadIdx.x) / SUB;
     const int sl = threadIdx.x & (SUB - 1);
-    if (i >= a.n_nodes) return;   // whole groups of eight lanes leave together
+    const bool live = i < a.n_nodes;
+    // before the element pass has finished: the node's static data, its
+    // position (advanced in the previous cycle) and this lane's stencil corner
+    // (Sec. 2.2 step 3) with its obstacle bit
+    int4 inf = make_int4(0, 0, 0, 0);
+    Q4 qi = {};
+    long long g = 0;
+    float w = 0.f;
+    bool hit = false;
+    if (live) {
+        inf = a.info[i];
+        qi = (a.par ? a.qb : a.qa)[i];
+        hit = corner(chan(a, inf.w >> 8), qi, sl, g, w);
+        if (hit) hit = !((__ldg(a.mask + (g >> 5)) >> (g & 31)) & 1u);
+    }
+    pdl_wait();
+    if (!live) return;   // whole groups of eight lanes leave together
     const unsigned smask = 0xffu << (threadIdx.x & 24);
-    const int4 inf = a.info[i];
-    const Q4 qi = (a.par ? a.qb : a.qa)[i];
     const int cid = inf.x, k0 = inf.z, k = inf.w & 0xff, chn = inf.w >> 8;
     const CellDev& C = a.cells[cid];
     const float2 rel = a.cell_rel[cid];
-
-    // this lane's stencil corner (Sec. 2.2 step 3), resolved before the
-    // gather so that the mask load is in flight with it
     const ChannelDev Ch = chan(a, chn);
-    long long g;
-    float w;
-    bool hit = corner(Ch, qi, sl, g, w);
-    if (hit) hit = !((__ldg(a.mask + (g >> 5)) >> (g & 31)) & 1u);
     if (a.dcur) {
         // overlapped schedule: the target must be in this step's stencil set
         // (it is whenever no point moved a lattice unit in one step), and the
@@ -462,8 +470,7 @@ __global__ void __launch_bounds__(FS_BLOCK, IB_MIN_BLOCKS) k_forces_spread(const
 cudaError_t launch_forces_spread(const IbmArgs& a, cudaStream_t s) {
     if (a.n_nodes <= 0) return cudaSuccess;
     const long long threads = (long long)a.n_nodes * SUB;
-    k_forces_spread<<<(unsigned)((threads + FS_BLOCK - 1) / FS_BLOCK), FS_BLOCK, 0, s>>>(a);
-    return cudaGetLastError();
+    return launch_ex(k_forces_spread, (unsigned)((threads + FS_BLOCK - 1) / FS_BLOCK), FS_BLOCK, 0, s, a.pdl, a);
 }
 
 // ---------------------------------------------------------------------------
@@ -475,18 +482,25 @@ cudaError_t launch_forces_spread(const IbmArgs& a, cudaStream_t s) {
 constexpr int IA_BLOCK = 128;
 
 __global__ void __launch_bounds__(IA_BLOCK, IB_MIN_BLOCKS) k_interp_advance(const __grid_constant__ IbmArgs a) {
+    pdl_trigger();
     const int i = blockIdx.x * IA_BLOCK + threadIdx.x;
-    if (i >= a.n_nodes) return;
-    const int chn = a.info[i].w >> 8;
-    const ChannelDev Ch = chan(a, chn);
-    const Q4 q = cur_q(a)[i];
-    float4 u[8];
+    const bool live = i < a.n_nodes;
+    // before the stream-collide has finished: position and stencil weights
+    Q4 q = {};
+    long long g[8];
     float w[8];
+    bool ok[8];
+    if (live) {
+        const ChannelDev Ch = chan(a, a.info[i].w >> 8);
+        q = cur_q(a)[i];
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        long long g;
-        u[c] = corner(Ch, q, c, g, w[c]) ? a.u[g] : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int c = 0; c < 8; ++c) ok[c] = corner(Ch, q, c, g[c], w[c]);
     }
+    pdl_wait();
+    if (!live) return;
+    float4 u[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) u[c] = ok[c] ? a.u[g[c]] : make_float4(0.f, 0.f, 0.f, 0.f);
     float ux = 0.f, uy = 0.f, uz = 0.f;
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
@@ -503,8 +517,7 @@ __global__ void __launch_bounds__(IA_BLOCK, IB_MIN_BLOCKS) k_interp_advance(cons
 
 cudaError_t launch_interp_advance(const IbmArgs& a, cudaStream_t s) {
     if (a.n_nodes <= 0) return cudaSuccess;
-    k_interp_advance<<<(unsigned)((a.n_nodes + IA_BLOCK - 1) / IA_BLOCK), IA_BLOCK, 0, s>>>(a);
-    return cudaGetLastError();
+    return launch_ex(k_interp_advance, (unsigned)((a.n_nodes + IA_BLOCK - 1) / IA_BLOCK), IA_BLOCK, 0, s, a.pdl, a);
 }
 
 }  // namespace lbibm

@@ -111,6 +111,7 @@ struct lb_ctx {
     // overlapped schedule: the immersed-boundary chain on a second stream of
     // higher priority, concurrent with the bulk of the stream-collide
     bool overlap = false;          // chosen by the caller (lb_set_schedule)
+    bool pdl = true;               // sequential cycle: programmatic dependent launches
     bool dvalid = false;           // the stencil set of the next step is current
     cudaStream_t ib_stream = nullptr;
     cudaEvent_t ev_fork[2] = {nullptr, nullptr}, ev_join[2] = {nullptr, nullptr};
@@ -324,8 +325,12 @@ cudaEvent_t take_event(lb_ctx* ctx) {
 
 // ---- one cycle (Sec. 2.2) ----
 lb_status enqueue_step(lb_ctx* ctx, int par) {
-    const LatticeArgs la = lattice_args(ctx, par);
-    const IbmArgs ia = ibm_args(ctx, par);
+    LatticeArgs la = lattice_args(ctx, par);
+    IbmArgs ia = ibm_args(ctx, par);
+    // each kernel of the cycle is scheduled during its predecessor's last wave
+    // and waits for it to complete before touching memory (not under per-kernel
+    // timing, whose events separate the launches)
+    la.pdl = ia.pdl = ctx->pdl && ctx->timing == 0;
     const bool ibm = ctx->M > 0;
     if (ibm && ctx->rep_k > 0.f) {
         // collisions (Sec. 2.4), added to the membrane forces in the spreading kernel
@@ -1544,16 +1549,19 @@ lb_status lb_set_kernel_config(lb_ctx* ctx, int nodes_per_thread, int block_size
 
 lb_status lb_set_schedule(lb_ctx* ctx, int overlapped) {
     LB_GUARD(ctx);
-    if (overlapped != 0 && overlapped != 1) return fail(ctx, LB_ERR_ARG, "schedule must be 0 or 1");
+    if (overlapped < 0 || overlapped > 2) return fail(ctx, LB_ERR_ARG, "schedule must be 0, 1 or 2");
     LB_CUDA(cudaStreamSynchronize(ctx->stream));
-    ctx->overlap = overlapped != 0;
+    ctx->overlap = overlapped == 1;
+    const bool pdl = overlapped != 2;
+    if (pdl != ctx->pdl) drop_graphs(ctx);
+    ctx->pdl = pdl;
     ctx->dvalid = false;
     return LB_OK;
 }
 
 lb_status lb_get_schedule(lb_ctx* ctx, int* overlapped) {
     LB_GUARD(ctx);
-    if (overlapped) *overlapped = use_overlap(ctx) ? 1 : 0;
+    if (overlapped) *overlapped = use_overlap(ctx) ? 1 : ctx->pdl ? 0 : 2;
     return LB_OK;
 }
 

@@ -39,11 +39,44 @@
 
 #include <cuda.h>
 #include <cuda_runtime.h>
+#include <utility>
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
 
 namespace lbibm {
+
+// ---- programmatic dependent launch ----
+// A kernel of the cycle may be launched before its predecessor in the stream
+// has finished (its blocks are scheduled during the predecessor's last wave).
+// Before pdl_wait it may only read data that no kernel of the current cycle
+// writes (static tables, the positions of the previous cycle); pdl_wait
+// returns once the predecessor has completed and its writes are visible.
+// pdl_trigger lets the next kernel of the cycle be scheduled.  Both are no-ops
+// for a kernel launched the ordinary way.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_entry() {
+    pdl_wait();
+    pdl_trigger();
+}
+
+template <typename... K, typename... A>
+inline cudaError_t launch_ex(void (*kern)(K...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, bool pdl,
+                             A&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, std::forward<A>(args)...);
+}
+
 
 constexpr int Q = 19;
 constexpr int GROUP = 32;           // nodes per mask word / flag
@@ -118,6 +151,7 @@ struct CellDev {
 struct LatticeArgs {
     const ChannelDev* ch; // all channels (global memory)
     int n_ch;
+    int pdl;              // launched as a programmatic dependent of the previous kernel
     int storage;          // lb_storage
     int par;              // step parity: read h[par], write h[1-par]; forces in g[par]
     int has_last;         // a step has completed (fields / diagnostics)
@@ -147,6 +181,7 @@ struct LatticeArgs {
 };
 
 struct IbmArgs {
+    int pdl;              // launched as a programmatic dependent of the previous kernel
     int n_nodes;          // M
     int n_cells;
     int par;              // step parity: positions q[par] are current, q[1-par] receive the advance

@@ -320,9 +320,13 @@ class Simulation:
                                        _ptr(gb), ctypes.byref(gks), ctypes.byref(gkb)))
         return {"J": J.value, "beads": gb[:nb].copy(), "ks": gks.value, "kb": gkb.value}
 
-    def set_schedule(self, overlapped: bool):
-        """Overlapped (IB chain concurrent with the bulk stream-collide) or sequential cycle."""
-        self._check(self._L.lb_set_schedule(self._h, int(bool(overlapped))))
+    SEQUENTIAL, OVERLAPPED, SEQUENTIAL_PLAIN = 0, 1, 2
+
+    def set_schedule(self, schedule):
+        """0 (or False): sequential cycle with programmatic dependent launches;
+        1 (or True): IB chain concurrent with the bulk stream-collide;
+        2: sequential cycle with ordinary launches."""
+        self._check(self._L.lb_set_schedule(self._h, int(schedule)))
 
     def schedule(self) -> int:
         v = ctypes.c_int(0)

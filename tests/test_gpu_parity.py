@@ -253,11 +253,12 @@ def test_small_filter_parity():
 
 def test_overlapped_schedule_matches_sequential():
     """The overlapped cycle (IB chain concurrent with the bulk stream-collide)
-    gives the sequential cycle's result, across several lb_step calls, and
-    against the oracle; the default schedule is the sequential one."""
+    and the sequential cycle with ordinary launches give the result of the
+    default cycle (sequential, programmatic dependent launches), across several
+    lb_step calls, and against the oracle."""
     sc = scene.small_filter(seed=5, steps=0)
     runs = {}
-    for ov in (1, 0):
+    for ov in (1, 2, 0):
         sim = _sim(sc)
         sim.set_schedule(ov)
         assert sim.schedule() == ov
@@ -268,11 +269,13 @@ def test_overlapped_schedule_matches_sequential():
         runs[ov] = (sim.fields()[1], [sim.nodes(m) for m in range(len(sc.meshes))])
     ref = oracle.System.from_scene(sc)
     ref.step(100)
-    assert rel_l2(runs[1][0], runs[0][0]) < 1e-6
-    assert rel_l2(runs[1][0], ref.fields()[1]) < 1e-5
+    for ov in (1, 2):
+        assert rel_l2(runs[ov][0], runs[0][0]) < 1e-6
+        for m in range(len(sc.meshes)):
+            assert np.abs(runs[ov][1][m] - runs[0][1][m]).max() < 1e-6
+    assert rel_l2(runs[0][0], ref.fields()[1]) < 1e-5
     for m in range(len(sc.meshes)):
-        assert np.abs(runs[1][1][m] - runs[0][1][m]).max() < 1e-6
-        assert np.abs(runs[1][1][m] - ref.nodes(m)).max() < 1e-5
+        assert np.abs(runs[0][1][m] - ref.nodes(m)).max() < 1e-5
     assert _sim(sc).schedule() == 0
 
 
