@@ -263,15 +263,22 @@ cudaError_t launch_cell_sums(const IbmArgs& a, cudaStream_t s) {
 // (neo-Hookean bond) and bending of edge (a, b), each evaluated once.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(CS_BLOCK, 6) k_elements(const __grid_constant__ IbmArgs a) {
-    pdl_entry();
     if ((int)blockIdx.x < a.n_chunks) {
+        pdl_entry();
         tri_chunk<true>(a, blockIdx.x);
         return;
     }
+    // the edge's static data before the previous advance has finished
     const int e = ((int)blockIdx.x - a.n_chunks) * CS_BLOCK + (int)threadIdx.x;
-    if (e >= a.n_edges) return;
-    const int4 ev = a.edges[e];
-    const float4 r = a.edge_rest[e];   // (L0, theta0, ks, kb)
+    const bool live = e < a.n_edges;
+    int4 ev = make_int4(0, 0, 0, 0);
+    float4 r = make_float4(0.f, 0.f, 0.f, 0.f);   // (L0, theta0, ks, kb)
+    if (live) {
+        ev = a.edges[e];
+        r = a.edge_rest[e];
+    }
+    pdl_entry();
+    if (!live) return;
     const Q4* qc = cur_q(a);
     const Pt A = load_pt(a, qc, ev.x), B = load_pt(a, qc, ev.y), Cc = load_pt(a, qc, ev.z), D = load_pt(a, qc, ev.w);
     const float3 fs = stretch_on_a(A, B, r.x, r.z);
@@ -396,7 +403,6 @@ cudaError_t launch_compact_groups(const uint8_t* map, int n_groups, int* list, i
 constexpr int FS_BLOCK = 128;
 
 __global__ void __launch_bounds__(FS_BLOCK, IB_MIN_BLOCKS) k_forces_spread(const __grid_constant__ IbmArgs a) {
-    pdl_trigger();
     const int i = (blockIdx.x * FS_BLOCK + threadIdx.x) / SUB;
     const int sl = threadIdx.x & (SUB - 1);
     const bool live = i < a.n_nodes;
@@ -414,7 +420,7 @@ __global__ void __launch_bounds__(FS_BLOCK, IB_MIN_BLOCKS) k_forces_spread(const
         hit = corner(chan(a, inf.w >> 8), qi, sl, g, w);
         if (hit) hit = !((__ldg(a.mask + (g >> 5)) >> (g & 31)) & 1u);
     }
-    pdl_wait();
+    pdl_entry();
     if (!live) return;   // whole groups of eight lanes leave together
     const unsigned smask = 0xffu << (threadIdx.x & 24);
     const int cid = inf.x, k0 = inf.z, k = inf.w & 0xff, chn = inf.w >> 8;
@@ -482,7 +488,6 @@ cudaError_t launch_forces_spread(const IbmArgs& a, cudaStream_t s) {
 constexpr int IA_BLOCK = 128;
 
 __global__ void __launch_bounds__(IA_BLOCK, IB_MIN_BLOCKS) k_interp_advance(const __grid_constant__ IbmArgs a) {
-    pdl_trigger();
     const int i = blockIdx.x * IA_BLOCK + threadIdx.x;
     const bool live = i < a.n_nodes;
     // before the stream-collide has finished: position and stencil weights
@@ -496,7 +501,7 @@ __global__ void __launch_bounds__(IA_BLOCK, IB_MIN_BLOCKS) k_interp_advance(cons
 #pragma unroll
         for (int c = 0; c < 8; ++c) ok[c] = corner(Ch, q, c, g[c], w[c]);
     }
-    pdl_wait();
+    pdl_entry();
     if (!live) return;
     float4 u[8];
 #pragma unroll

@@ -430,9 +430,6 @@ __device__ __forceinline__ void sc_nodes(const LatticeArgs& a, const ChannelDev&
     const int par = a.par;
     uint8_t* fl_prev = par ? a.fl0 : a.fl1;
     const bool inr = ROW ? true : p0 < C.n;
-    // flags first: their latency overlaps the population loads below
-    const uint8_t fcur = MODE == SC_BULK ? (uint8_t)0 : __ldg((par ? a.fl1 : a.fl0) + grp);
-    const uint8_t fprev = MODE == SC_BULK ? (uint8_t)0 : __ldg(fl_prev + grp);
     const uint8_t fslow = inr ? __ldg(a.slow + grp) : (uint8_t)0;
     const S* src = (const S*)(par ? a.h1 : a.h0);
     S* dst = (S*)(par ? a.h0 : a.h1);
@@ -453,6 +450,12 @@ __device__ __forceinline__ void sc_nodes(const LatticeArgs& a, const ChannelDev&
 #define LBIBM_IV(I) issue_vec<S, NPT, I>(src, NT, gi0, nb, C, x0, lane, inr, v[I], extra[I]);
     LBIBM_ALL_I(LBIBM_IV)
 #undef LBIBM_IV
+    // the populations are the previous cycle's (launched as a programmatic
+    // dependent only behind the spreading kernel); the force flags and
+    // densities come from that kernel
+    pdl_entry();
+    const uint8_t fcur = MODE == SC_BULK ? (uint8_t)0 : __ldg((par ? a.fl1 : a.fl0) + grp);
+    const uint8_t fprev = MODE == SC_BULK ? (uint8_t)0 : __ldg(fl_prev + grp);
     const bool forced = fcur != 0;
     const bool prevf = fprev != 0;
     const bool wslow = __any_sync(FULL, fslow != 0);
@@ -524,7 +527,7 @@ __device__ __forceinline__ void sc_nodes(const LatticeArgs& a, const ChannelDev&
 
 template <class S, int NPT, int BS>
 __global__ void __launch_bounds__(BS, K3MinBlocks<S, NPT, BS>::value) k_stream_collide(const __grid_constant__ LatticeArgs a) {
-    pdl_entry();
+    // (sc_nodes waits for the predecessor after its population loads)
     const int b = blockIdx.x;
     int c = 0;
     for (int k = 1; k < a.n_ch; ++k)

@@ -108,6 +108,7 @@ struct lb_ctx {
     long long step = 0;
     bool started = false;
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    cudaGraphExec_t gexec_blk[2] = {nullptr, nullptr};   // GRAPH_BLOCK consecutive cycles from parity p
     // overlapped schedule: the immersed-boundary chain on a second stream of
     // higher priority, concurrent with the bulk of the stream-collide
     bool overlap = false;          // chosen by the caller (lb_set_schedule)
@@ -328,9 +329,12 @@ lb_status enqueue_step(lb_ctx* ctx, int par) {
     LatticeArgs la = lattice_args(ctx, par);
     IbmArgs ia = ibm_args(ctx, par);
     // each kernel of the cycle is scheduled during its predecessor's last wave
-    // and waits for it to complete before touching memory (not under per-kernel
-    // timing, whose events separate the launches)
-    la.pdl = ia.pdl = ctx->pdl && ctx->timing == 0;
+    // and waits for it before touching what it wrote (not under per-kernel
+    // timing, whose events separate the launches).  The stream-collide reads
+    // the previous cycle's populations before its wait, so it is a
+    // programmatic dependent only when the spreading kernel precedes it.
+    ia.pdl = ctx->pdl && ctx->timing == 0;
+    la.pdl = ia.pdl && ctx->M > 0;
     const bool ibm = ctx->M > 0;
     if (ibm && ctx->rep_k > 0.f) {
         // collisions (Sec. 2.4), added to the membrane forces in the spreading kernel
@@ -391,22 +395,29 @@ lb_status enqueue_step(lb_ctx* ctx, int par) {
     return LB_OK;
 }
 
+// Cycles per block graph: within a block every kernel, the first of each
+// cycle included, is a programmatic dependent of the one before it.
+constexpr int GRAPH_BLOCK = 8;
+
 lb_status build_graphs(lb_ctx* ctx) {
-    for (int par = 0; par < 2; ++par) {
-        if (ctx->gexec[par]) continue;
-        cudaGraph_t g = nullptr;
-        long long saved[4];
-        std::copy(ctx->launches, ctx->launches + 4, saved);   // capture launches nothing
-        LB_CUDA(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
-        lb_status s = enqueue_step(ctx, par);
-        cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
-        std::copy(saved, saved + 4, ctx->launches);
-        if (s != LB_OK) return s;
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamEndCapture");
-        e = cudaGraphInstantiate(&ctx->gexec[par], g, 0);
-        cudaGraphDestroy(g);
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphInstantiate");
-    }
+    for (int blk = 0; blk < 2; ++blk)
+        for (int par = 0; par < 2; ++par) {
+            cudaGraphExec_t& ge = blk ? ctx->gexec_blk[par] : ctx->gexec[par];
+            if (ge) continue;
+            cudaGraph_t g = nullptr;
+            long long saved[4];
+            std::copy(ctx->launches, ctx->launches + 4, saved);   // capture launches nothing
+            LB_CUDA(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+            lb_status s = LB_OK;
+            for (int k = 0; k < (blk ? GRAPH_BLOCK : 1) && s == LB_OK; ++k) s = enqueue_step(ctx, (par + k) & 1);
+            cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+            std::copy(saved, saved + 4, ctx->launches);
+            if (s != LB_OK) return s;
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamEndCapture");
+            e = cudaGraphInstantiate(&ge, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphInstantiate");
+        }
     return LB_OK;
 }
 
@@ -528,6 +539,10 @@ void drop_graphs(lb_ctx* ctx) {
         if (ctx->gexec[par]) {
             cudaGraphExecDestroy(ctx->gexec[par]);
             ctx->gexec[par] = nullptr;
+        }
+        if (ctx->gexec_blk[par]) {
+            cudaGraphExecDestroy(ctx->gexec_blk[par]);
+            ctx->gexec_blk[par] = nullptr;
         }
         for (int lead = 0; lead < 2; ++lead)
             if (ctx->gexec_ov[par][lead]) {
@@ -1519,18 +1534,22 @@ lb_status lb_step(lb_ctx* ctx, int n_steps) {
         s = build_graphs(ctx);
         if (s != LB_OK) return s;
     }
-    for (int k = 0; k < n_steps; ++k) {
+    for (int k = 0; k < n_steps;) {
         const int par = (int)(ctx->step & 1);
         if (ctx->timing) {
             s = enqueue_step(ctx, par);
             if (s != LB_OK) return s;
-        } else {
-            LB_CUDA(cudaGraphLaunch(ctx->gexec[par], ctx->stream));
-            for (int c = 0; c < 4; ++c)
-                if (ctx->M > 0 || c == 2) ctx->launches[c] += 1;
-            if (ctx->M > 0 && ctx->rep_k > 0.f) ctx->launches[1] += 4;   // collision kernels
+            ctx->step++;
+            ++k;
+            continue;
         }
-        ctx->step++;
+        const int n = n_steps - k >= GRAPH_BLOCK ? GRAPH_BLOCK : 1;
+        LB_CUDA(cudaGraphLaunch(n > 1 ? ctx->gexec_blk[par] : ctx->gexec[par], ctx->stream));
+        for (int c = 0; c < 4; ++c)
+            if (ctx->M > 0 || c == 2) ctx->launches[c] += n;
+        if (ctx->M > 0 && ctx->rep_k > 0.f) ctx->launches[1] += 4 * n;   // collision kernels
+        ctx->step += n;
+        k += n;
     }
     LB_CUDA(cudaGetLastError());
     return LB_OK;

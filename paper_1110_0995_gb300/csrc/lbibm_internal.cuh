@@ -48,12 +48,12 @@ namespace lbibm {
 
 // ---- programmatic dependent launch ----
 // A kernel of the cycle may be launched before its predecessor in the stream
-// has finished (its blocks are scheduled during the predecessor's last wave).
-// Before pdl_wait it may only read data that no kernel of the current cycle
-// writes (static tables, the positions of the previous cycle); pdl_wait
-// returns once the predecessor has completed and its writes are visible.
-// pdl_trigger lets the next kernel of the cycle be scheduled.  Both are no-ops
-// for a kernel launched the ordinary way.
+// has finished.  pdl_wait returns once the predecessor has completed and its
+// writes are visible; pdl_trigger, issued by every block only after its
+// pdl_wait, lets the next kernel be scheduled.  So when a kernel starts, every
+// kernel before its predecessor has completed: before pdl_wait it may read
+// anything but what its immediate predecessor writes.  Both are no-ops for a
+// kernel launched the ordinary way.
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 __device__ __forceinline__ void pdl_entry() {
