@@ -120,7 +120,11 @@ __device__ __forceinline__ bool acorner(const ChannelDev& C, const Q4& q, int c,
 // (B1) interpolation + advance, reversed: lam_u(x_c) += w_c lamX, and
 // lamX_out = lamX + sum_c grad w_c (u(x_c) . lamX).
 __global__ void k_adj_interp(const __grid_constant__ AdjArgs a) {
+    pdl_entry();
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    // the cycle's per-cell sums (B5) start from zero; the previous cycle's
+    // reader (B6) has completed
+    for (int t = j; t < 2 * a.n_cells; t += gridDim.x * blockDim.x) a.lam_c[t] = 0.0;
     if (j >= a.M) return;
     const Q4 q = a.q_t[j];
     const float4 l = a.lamX[j];
@@ -142,6 +146,7 @@ __global__ void k_adj_interp(const __grid_constant__ AdjArgs a) {
 // (B3) spreading, reversed: lamF_j = sum_c w_c lam_g(x_c);
 // lamX_out += sum_c grad w_c (F_j . lam_g(x_c)).
 __global__ void k_adj_spread(const __grid_constant__ AdjArgs a) {
+    pdl_entry();
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= a.M) return;
     const Q4 q = a.q_t[j];
@@ -209,6 +214,7 @@ __device__ __forceinline__ void edge_forces(const V3& xb, const V3& xc, const V3
 // seeded with the adjoint itself (relative to vertex a, the seeds are
 // lamF_v - lamF_a).
 __global__ void __launch_bounds__(128) k_adj_edges(const __grid_constant__ AdjArgs a) {
+    pdl_entry();
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     double gks = 0.0, gkb = 0.0;
     if (e < a.n_edges) {
@@ -271,6 +277,7 @@ __device__ __forceinline__ void tri_forces(const V3& xb, const V3& xc, float S0t
 // b or c (v = 0, 1); the column of a is minus their sum.  The column-0 thread
 // also forms the per-cell products and keeps the normal.
 __global__ void __launch_bounds__(128, 6) k_adj_tris(const __grid_constant__ AdjArgs a) {
+    pdl_entry();
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int t = tid / 6, col = tid - 6 * (tid / 6);
     const bool valid = t < a.n_tris;   // every lane stays for the per-cell warp sums
@@ -326,6 +333,7 @@ __global__ void __launch_bounds__(128, 6) k_adj_tris(const __grid_constant__ Adj
 // (B6) the cell's global terms: lam_S = lam_c1 kag / S0, lam_V = lam_c2 kv / (6 V0);
 // dS/dx from the triangles' areas, dV/dx_k = sum over triangles at k of n_t / 6.
 __global__ void k_adj_tris_global(const __grid_constant__ AdjArgs a) {
+    pdl_entry();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= a.n_tris) return;
     const int4 tr = a.tris[t];
@@ -399,20 +407,19 @@ __global__ void k_adj_bead_grad(const __grid_constant__ AdjArgs a) {
 
 // ---- launchers ----
 cudaError_t launch_adj_interp(const AdjArgs& a, cudaStream_t s) {
-    k_adj_interp<<<(a.M + 127) / 128, 128, 0, s>>>(a);
-    return cudaGetLastError();
+    return launch_ex(k_adj_interp, (a.M + 127) / 128, 128, 0, s, a.pdl, a);
 }
 cudaError_t launch_adj_spread(const AdjArgs& a, cudaStream_t s) {
-    k_adj_spread<<<(a.M + 127) / 128, 128, 0, s>>>(a);
-    return cudaGetLastError();
+    return launch_ex(k_adj_spread, (a.M + 127) / 128, 128, 0, s, a.pdl, a);
 }
 cudaError_t launch_adj_membrane(const AdjArgs& a, cudaStream_t s) {
-    if (a.n_edges > 0) k_adj_edges<<<(a.n_edges + 127) / 128, 128, 0, s>>>(a);
-    if (a.n_tris > 0) {
-        k_adj_tris<<<(6 * a.n_tris + 127) / 128, 128, 0, s>>>(a);
-        k_adj_tris_global<<<(a.n_tris + 127) / 128, 128, 0, s>>>(a);
+    cudaError_t e = cudaSuccess;
+    if (a.n_edges > 0) e = launch_ex(k_adj_edges, (a.n_edges + 127) / 128, 128, 0, s, a.pdl, a);
+    if (a.n_tris > 0 && e == cudaSuccess) {
+        e = launch_ex(k_adj_tris, (6 * a.n_tris + 127) / 128, 128, 0, s, a.pdl, a);
+        if (e == cudaSuccess) e = launch_ex(k_adj_tris_global, (a.n_tris + 127) / 128, 128, 0, s, a.pdl, a);
     }
-    return cudaGetLastError();
+    return e;
 }
 cudaError_t launch_adj_bead_grad(const AdjArgs& a, cudaStream_t s) {
     if (a.n_beads <= 0) return cudaSuccess;

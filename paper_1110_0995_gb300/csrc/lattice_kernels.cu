@@ -1364,6 +1364,7 @@ __device__ __forceinline__ void adj_node(const AdjArgs& a, const ChannelDev& C, 
 }
 
 __global__ void __launch_bounds__(128, 8) k_adj_collide(const __grid_constant__ AdjArgs a) {
+    pdl_entry();
     const ChannelDev C = a.ch;
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     const bool inr = p < C.n;
@@ -1380,8 +1381,7 @@ __global__ void __launch_bounds__(128, 8) k_adj_collide(const __grid_constant__ 
 }
 
 cudaError_t launch_adj_collide(const AdjArgs& a, cudaStream_t s) {
-    k_adj_collide<<<(a.ch.n + 127) / 128, 128, 0, s>>>(a);
-    return cudaGetLastError();
+    return launch_ex(k_adj_collide, (a.ch.n + 127) / 128, 128, 0, s, a.pdl, a);
 }
 
 // ---------------------------------------------------------------------------

@@ -1008,9 +1008,7 @@ lb_status store_step(lb_ctx* ctx, int k) {
     Q4* qd = W.seg_q + (size_t)(k + 1) * ctx->M;
     float4* gk = W.seg_g + (size_t)k * ctx->Ntot;
     float4* uk = W.seg_u + (size_t)k * ctx->Ntot;
-    LB_CUDA(cudaMemsetAsync(gk, 0, sizeof(float4) * ctx->Ntot, s));
     uint8_t* flk = W.seg_fl + (size_t)k * (ctx->Ntot / GROUP);
-    LB_CUDA(cudaMemsetAsync(flk, 0, (size_t)(ctx->Ntot / GROUP), s));
     LatticeArgs la = lattice_args(ctx, par);
     IbmArgs ia = ibm_args(ctx, par);
     la.h0 = par ? (void*)hd : (void*)hs;
@@ -1025,7 +1023,11 @@ lb_status store_step(lb_ctx* ctx, int k) {
     ia.qb = par ? qs : qd;
     ia.F = W.seg_F + (size_t)k * ctx->M;
     ia.cell_rel = W.seg_rel + (size_t)k * ctx->C;
+    // programmatic dependents as in the plain cycle, except the segment's
+    // first kernel (it follows the zeroing of the segment's force slots)
+    ia.pdl = ctx->pdl && k > 0;
     LB_CUDA(launch_elements(ia, s));
+    ia.pdl = la.pdl = ctx->pdl;
     LB_CUDA(launch_forces_spread(ia, s));
     LB_CUDA(k3_launch(ctx, la, ctx->k3, s));
     LB_CUDA(launch_interp_advance(ia, s));
@@ -1035,6 +1037,7 @@ lb_status store_step(lb_ctx* ctx, int k) {
 
 // The forward cycles 0 .. len-1 of a segment on the segment store, as one
 // CUDA graph per (len, parity of the first cycle), launched on the stream.
+// Every cycle's force density and flags start from zero.
 lb_status run_segment_forward(lb_ctx* ctx, int len) {
     auto& W = ctx->adj;
     const std::pair<int, int> key(len, (int)(ctx->step & 1));
@@ -1043,10 +1046,13 @@ lb_status run_segment_forward(lb_ctx* ctx, int len) {
         const long long step_saved = ctx->step;
         cudaGraph_t g = nullptr;
         LB_CUDA(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
-        lb_status st = LB_OK;
+        cudaError_t e0 = cudaMemsetAsync(W.seg_g, 0, sizeof(float4) * ctx->Ntot * (size_t)len, ctx->stream);
+        if (e0 == cudaSuccess) e0 = cudaMemsetAsync(W.seg_fl, 0, (size_t)(ctx->Ntot / GROUP) * len, ctx->stream);
+        lb_status st = e0 == cudaSuccess ? LB_OK : LB_ERR_CUDA;
         for (int k = 0; k < len && st == LB_OK; ++k) st = store_step(ctx, k);
         cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
         ctx->step = step_saved;
+        if (e0 != cudaSuccess) return cuda_fail(ctx, e0, "cudaMemsetAsync");
         if (st != LB_OK) return st;
         if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamEndCapture");
         cudaGraphExec_t ge = nullptr;
@@ -1200,6 +1206,7 @@ lb_status lb_adjoint(lb_ctx* ctx, int n_steps, int ckpt_every, int objective_mes
     A.n_tris = ctx->T;
     A.n_beads = nb;
     A.obj_cell = mo->cell;
+    A.n_cells = ctx->C;
     A.plane = ctx->plane;
     A.mask = ctx->mask;
     A.links = ctx->links;
@@ -1253,8 +1260,11 @@ lb_status lb_adjoint(lb_ctx* ctx, int n_steps, int ckpt_every, int objective_mes
                     A.lam_out = W.lam[1 - l];
                     A.lamX = W.lamX[x];
                     A.lamX_out = W.lamX[1 - x];
-                    e = cudaMemsetAsync(W.lam_c, 0, sizeof(double) * 2 * ctx->C, s);
-                    if (e == cudaSuccess) e = launch_adj_interp(A, s);
+                    // each kernel a programmatic dependent of the one before it,
+                    // except the graph's first
+                    A.pdl = ctx->pdl && k < len - 1;
+                    e = launch_adj_interp(A, s);
+                    A.pdl = ctx->pdl;
                     if (e == cudaSuccess) e = launch_adj_collide(A, s);
                     if (e == cudaSuccess) e = launch_adj_spread(A, s);
                     if (e == cudaSuccess) e = launch_adj_membrane(A, s);
@@ -1277,6 +1287,7 @@ lb_status lb_adjoint(lb_ctx* ctx, int n_steps, int ckpt_every, int objective_mes
             }
         }
     }
+    A.pdl = 0;
     LB_CUDA(launch_adj_bead_grad(A, s));
     std::vector<double> g(2 + 3 * 64);
     LB_CUDA(cudaMemcpyAsync(g.data(), W.grad, sizeof(double) * g.size(), cudaMemcpyDeviceToHost, s));

@@ -232,6 +232,8 @@ struct IbmArgs {
 struct AdjArgs {
     ChannelDev ch;
     int M, n_edges, n_tris, n_beads, obj_cell;
+    int n_cells;
+    int pdl;                  // launched as a programmatic dependent of the previous kernel
     long long plane;          // population plane stride
     // the forward step t (recomputed and stored)
     const Q4* q_t;            // [M] positions at the start of step t
