@@ -82,6 +82,10 @@ def lib():
         L.or_sys_set_nodes.argtypes = [vp, i, P]
         L.or_sys_get_nodes.argtypes = [vp, i, P]
         L.or_sys_get_forces.argtypes = [vp, i, P]
+        L.or_sys_set_dynamics.restype = i
+        L.or_sys_set_dynamics.argtypes = [vp, d, d]
+        L.or_sys_get_velocities.argtypes = [vp, i, P]
+        L.or_drag_coefficients.argtypes = [d, d, P]
         L.or_sys_step.argtypes = [vp, i]
         L.or_constants.argtypes = [P, P, P]
         L.or_equilibrium.argtypes = [d, P, P]
@@ -141,6 +145,14 @@ def guo_source(tau: float, u, g) -> np.ndarray:
     out = np.zeros(19)
     lib().or_guo_source(float(tau), _p(_f64(u)), _p(_f64(g)), _p(out))
     return out
+
+
+def drag_coefficients(m: float, gamma: float):
+    """(a, p1, E) of the exact drag drift of IB points with mass (a = gamma / m,
+    p1 = (1 - e^-a) / a, E = e^-a)."""
+    out = np.zeros(3)
+    lib().or_drag_coefficients(float(m), float(gamma), _p(out))
+    return tuple(out)
 
 
 def rasterise(spheres: np.ndarray, dims) -> np.ndarray:
@@ -217,6 +229,9 @@ class System:
         rep = getattr(scene, "repulsion", None)
         if rep is not None:
             s.set_repulsion(rep[0], rep[1], scene.spheres)
+        dyn = getattr(scene, "ib_dynamics", None)
+        if dyn is not None:
+            s.set_dynamics(dyn[0], dyn[1])
         return s
 
     def set_repulsion(self, k: float, dc: float, spheres=None):
@@ -282,6 +297,17 @@ class System:
         F = np.zeros((self.n_nodes[m], 3))
         lib().or_sys_get_forces(self._h, m, _p(F))
         return F
+
+    def set_dynamics(self, m: float, gamma: float):
+        """IB points with mass m and drag gamma (Sec. 2.2 reading B); m = 0: massless."""
+        if lib().or_sys_set_dynamics(self._h, float(m), float(gamma)) != 0:
+            raise ValueError("mass and drag must be finite and >= 0")
+
+    def velocities(self, m: int) -> np.ndarray:
+        """Point velocities after the last step's drift (W)."""
+        v = np.zeros((self.n_nodes[m], 3))
+        lib().or_sys_get_velocities(self._h, m, _p(v))
+        return v
 
     def step(self, n: int = 1):
         lib().or_sys_step(self._h, int(n))

@@ -22,7 +22,8 @@
 // equilibrium, Guo forcing, halfway bounce-back, trilinear delta, Dupin-style
 // neo-Hookean stretching, dihedral-angle bending energy, homocentric area
 // forces, facet-normal volume forces, massless IB points advected with the
-// interpolated velocity) are each stated at the function that implements them.
+// interpolated velocity, or points with mass and a frictional coupling) are
+// each stated at the function that implements them.
 //
 // Layouts: lattice node p = x + nx*(y + ny*z); populations f[i*N + p];
 // vector fields SoA v[d*N + p]; IB node positions / forces AoS x[3*j + d].
@@ -556,6 +557,7 @@ struct Cell {
     double mod[5];
     std::vector<double> x0;
     std::vector<R> x, F, U;
+    std::vector<R> V;   // point velocities (IB points with mass only)
 };
 
 template <class R>
@@ -565,6 +567,7 @@ struct System {
     long steps = 0;
     double rep_k = 0.0, rep_dc = 0.0;   // soft-sphere repulsion (off when rep_k == 0)
     std::vector<double> spheres;         // cx, cy, cz, r per bead (for the repulsion)
+    double ib_m = 0.0, ib_gamma = 0.0;   // IB points with mass m and drag gamma (massless when ib_m == 0)
 };
 
 // Collisions (Sec. 2.4: cells repel each other and the walls through a soft
@@ -681,6 +684,71 @@ void system_step(System<R>& s) {
     for (auto& c : s.cells) {
         interpolate(F, c.x.data(), c.T.n, F.u.data(), c.U.data());
         for (int j = 0; j < 3 * c.T.n; ++j) c.x[j] = c.x[j] + c.U[j];
+    }
+    s.steps++;
+}
+
+// IB points with mass (Sec. 2.2: m d^2X/dt^2 = F; the coupling force comes
+// from the motion of the point relative to the fluid).  Reading: a frictional
+// coupling -gamma (V - U), with U the fluid velocity of the last collision
+// interpolated at X, the fluid receiving the opposite impulse; the membrane
+// and collision forces F act on the points only.  One step splits into a kick
+// by F and a drift under the drag with U held, solved exactly:
+//   V      = W + F / m                                (kick)
+//   X(1)   = X + U + (V - U) p1,   p1 = (1 - e^{-a}) / a,  a = gamma / m
+//   W(1)   = U + (V - U) e^{-a}                       (drift, exact)
+//   J      = integral of gamma (V(t) - U) dt = gamma (V - U) p1 = m (V - W(1))
+// W is the point velocity after the drift (the state carried between steps,
+// zero at the start).  For gamma = 0 this is the symplectic kick-drift
+// (leapfrog) step and nothing reaches the fluid; for m -> 0, J -> F and
+// X(1) -> X + U + F / gamma (the massless cycle with the velocity of the
+// previous collision).  The fluid gains sum J, the points m sum (W(1) - W) =
+// sum (F - J) = -sum J: momentum is conserved.
+struct DragCoef {
+    double a, p1, E;
+};
+
+DragCoef drag_coefficients(double m, double gamma) {
+    DragCoef c;
+    c.a = gamma / m;
+    const double a = c.a;
+    c.E = std::exp(-a);
+    if (a < 1e-3) c.p1 = 1.0 - a / 2.0 + a * a / 6.0 - a * a * a / 24.0 + a * a * a * a / 120.0;
+    else c.p1 = -std::expm1(-a) / a;
+    return c;
+}
+
+// One cycle with massive IB points:
+//   F^t = F(X^t); U^t = interp(u of the last collision, X^t);
+//   kick, exact drag drift, impulse J^t as above; g^t = spread(J^t, X^t);
+//   fluid update; X^{t+1}, W^{t+1}.
+template <class R>
+void system_step_massive(System<R>& s) {
+    Fluid<R>& F = s.fl;
+    std::fill(F.g.begin(), F.g.end(), R(0.0));
+    for (auto& c : s.cells) membrane_forces(c.x.data(), c.T, c.rest, c.mod, TERM_ALL, c.F.data());
+    if (s.rep_k != 0.0) repulsion(s);
+    const double m = s.ib_m, gam = s.ib_gamma;
+    const DragCoef k = drag_coefficients(m, gam);
+    std::vector<std::vector<R>> dX(s.cells.size());
+    for (size_t ci = 0; ci < s.cells.size(); ++ci) {
+        auto& c = s.cells[ci];
+        interpolate(F, c.x.data(), c.T.n, F.u.data(), c.U.data());
+        std::vector<R> J(3 * c.T.n);
+        dX[ci].resize(3 * c.T.n);
+        for (int j = 0; j < 3 * c.T.n; ++j) {
+            const R U = c.U[j];
+            const R V = c.V[j] + c.F[j] / m;
+            J[j] = gam * (V - U) * k.p1;
+            dX[ci][j] = U + (V - U) * k.p1;
+            c.V[j] = U + (V - U) * k.E;
+        }
+        spread(F, c.x.data(), J.data(), c.T.n, F.g.data());
+    }
+    lb_step(F);
+    for (size_t ci = 0; ci < s.cells.size(); ++ci) {
+        auto& c = s.cells[ci];
+        for (int j = 0; j < 3 * c.T.n; ++j) c.x[j] = c.x[j] + dX[ci][j];
     }
     s.steps++;
 }
@@ -987,6 +1055,7 @@ int or_sys_add_mesh(void* h, const double* x0, int n, const int* tri, int nt, co
     c.x.assign(x0, x0 + 3 * n);
     c.F.assign(3 * n, 0.0);
     c.U.assign(3 * n, 0.0);
+    c.V.assign(3 * n, 0.0);
     s->cells.push_back(std::move(c));
     return (int)s->cells.size() - 1;
 }
@@ -1012,7 +1081,38 @@ void or_sys_get_forces(void* h, int m, double* F) {
 
 void or_sys_step(void* h, int n_steps) {
     OrSys* s = (OrSys*)h;
-    for (int k = 0; k < n_steps; ++k) system_step(*s);
+    for (int k = 0; k < n_steps; ++k) {
+        if (s->ib_m > 0.0) system_step_massive(*s);
+        else system_step(*s);
+    }
+}
+
+// IB points with mass m > 0 and drag gamma >= 0 (m = 0: massless points);
+// the carried velocities W start at zero.
+int or_sys_set_dynamics(void* h, double m, double gamma) {
+    OrSys* s = (OrSys*)h;
+    if (!(m >= 0.0) || !(gamma >= 0.0) || !std::isfinite(m) || !std::isfinite(gamma)) return -1;
+    s->ib_m = m;
+    s->ib_gamma = gamma;
+    for (auto& c : s->cells) c.V.assign(3 * c.T.n, 0.0);
+    return 0;
+}
+
+void or_sys_get_velocities(void* h, int m, double* v) {
+    OrSys* s = (OrSys*)h;
+    auto& c = s->cells[m];
+    if (c.V.empty()) {
+        std::memset(v, 0, sizeof(double) * 3 * c.T.n);
+        return;
+    }
+    std::memcpy(v, c.V.data(), sizeof(double) * 3 * c.T.n);
+}
+
+void or_drag_coefficients(double m, double gamma, double* a_p1_E) {
+    const DragCoef c = drag_coefficients(m, gamma);
+    a_p1_E[0] = c.a;
+    a_p1_E[1] = c.p1;
+    a_p1_E[2] = c.E;
 }
 
 // Differentiable variant (see diff_run).

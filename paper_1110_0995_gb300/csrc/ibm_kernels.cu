@@ -409,13 +409,16 @@ __global__ void __launch_bounds__(FS_BLOCK, IB_MIN_BLOCKS) k_forces_spread(const
     // before the element pass has finished: the node's static data, its
     // position (advanced in the previous cycle) and this lane's stencil corner
     // (Sec. 2.2 step 3) with its obstacle bit
+    // and the lane's first ring slot
     int4 inf = make_int4(0, 0, 0, 0);
+    int4 sr0 = make_int4(0, 0, 0, 0);
     Q4 qi = {};
     long long g = 0;
     float w = 0.f;
     bool hit = false;
     if (live) {
         inf = a.info[i];
+        if (sl < (inf.w & 0xff)) sr0 = a.slots[inf.z + sl];
         qi = (a.par ? a.qb : a.qa)[i];
         hit = corner(chan(a, inf.w >> 8), qi, sl, g, w);
         if (hit) hit = !((__ldg(a.mask + (g >> 5)) >> (g & 31)) & 1u);
@@ -439,7 +442,7 @@ __global__ void __launch_bounds__(FS_BLOCK, IB_MIN_BLOCKS) k_forces_spread(const
     const float kv_dV6 = C.kv * rel.y * (1.0f / 6.0f);
     float3 F = make_float3(0.f, 0.f, 0.f);
     for (int s = sl; s < k; s += SUB) {
-        const int4 sr = a.slots[k0 + s];
+        const int4 sr = s == sl ? sr0 : a.slots[k0 + s];
         const float4 ta = a.tA[sr.x];
         const float4 tn = a.tN[sr.w];
         const float4 es = a.eS[sr.y >> 2];

@@ -91,6 +91,8 @@ class Scene:
     seed: int = 0
     # soft-sphere collisions (k, d_c), or None for none (Sec. 2.4 reading)
     repulsion: Optional[Tuple[float, float]] = None
+    # IB points with mass and drag (m, gamma), or None for massless points (Sec. 2.2)
+    ib_dynamics: Optional[Tuple[float, float]] = None
 
     @property
     def n_nodes(self) -> int:
