@@ -110,6 +110,24 @@ lb_status lb_destroy(lb_ctx* ctx);
  * cell; an overflow is reported by lb_diagnostics (LB_ERR_STATE). */
 lb_status lb_set_repulsion(lb_ctx* ctx, double k, double dc);
 
+/* IB points with mass (Sec. 2.2: m d^2X/dt^2 = F; the coupling force comes
+ * from the motion of a point relative to the fluid).  Reading: a frictional
+ * coupling -gamma (V - U), U the fluid velocity of the last collision
+ * interpolated at X; the membrane and collision forces F act on the points
+ * only.  Each cycle: kick V = W + F / mass, then the drift under the drag with
+ * U held, solved exactly (a = gamma / mass, p1 = (1 - e^-a) / a):
+ * X += U + p1 (V - U), W = U + e^-a (V - U); the fluid receives the drag's
+ * impulse gamma p1 (V - U), spread at the old position.  W (the point
+ * velocity after the drift) starts at zero.  mass = 0 (the default): massless
+ * points advected with the interpolated velocity.  mass > 0, gamma >= 0,
+ * finite; before the first step (LB_ERR_STATE); not with the differentiable
+ * variant or lb_adjoint.  Uses the sequential schedule. */
+lb_status lb_set_ib_dynamics(lb_ctx* ctx, double mass, double gamma);
+
+/* Velocities W of one mesh's points (n x 3, host) after the last step
+ * (zeros for massless points). */
+lb_status ibm_get_velocities(lb_ctx* ctx, int mesh_id, double* v);
+
 /* Differentiable variant (gradient of a filter objective; single-channel
  * contexts, before the first step).  The beads become a smooth solid
  * fraction phi(x) = 1 - prod_k (1 - phi_k(x)),

@@ -467,13 +467,50 @@ __global__ void __launch_bounds__(FS_BLOCK, IB_MIN_BLOCKS) k_forces_spread(const
     }
     if (sl == 0) a.F[i] = make_float4(F.x, F.y, F.z, 0.f);
 
-    // spreading: g(x) += w(x - X) F at this lane's corner
-    if (hit) atomicAdd((a.par ? a.g1 : a.g0) + g, make_float4(w * F.x, w * F.y, w * F.z, 0.f));
+    uint8_t* fl = a.par ? a.fl1 : a.fl0;
+    const unsigned active = __activemask();
+    float3 S = F;   // what reaches the fluid
+    if (a.W) {
+        // points with mass (Sec. 2.2 Newton equation): the fluid velocity of
+        // the last collision at X (this lane's corner, summed over the eight
+        // lanes), kick by F, exact drag drift; the fluid receives the drag's
+        // impulse and the point moves now (no interpolation kernel follows)
+        float4 uc = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (hit) uc = a.u[g];
+        float3 U = make_float3(w * uc.x, w * uc.y, w * uc.z);
+#pragma unroll
+        for (int o = SUB / 2; o > 0; o >>= 1) {
+            U.x += __shfl_xor_sync(smask, U.x, o);
+            U.y += __shfl_xor_sync(smask, U.y, o);
+            U.z += __shfl_xor_sync(smask, U.z, o);
+        }
+        const float4 W = a.W[i];
+        const float3 D = make_float3(W.x + F.x * a.ib_inv_m - U.x, W.y + F.y * a.ib_inv_m - U.y,
+                                     W.z + F.z * a.ib_inv_m - U.z);   // V - U
+        S = make_float3(a.ib_gp1 * D.x, a.ib_gp1 * D.y, a.ib_gp1 * D.z);
+        Q4 qn = qi;
+        qn.x += float_to_fixed(U.x + a.ib_p1 * D.x);
+        qn.y += float_to_fixed(U.y + a.ib_p1 * D.y);
+        qn.z += float_to_fixed(U.z + a.ib_p1 * D.z);
+        if (sl == 0) {
+            a.W[i] = make_float4(U.x + a.ib_E * D.x, U.y + a.ib_E * D.y, U.z + a.ib_E * D.z, 0.f);
+            (a.par ? a.qa : a.qb)[i] = qn;
+        }
+        // the stencil at the new position needs this step's velocity there:
+        // flag its groups so that the stream-collide writes it
+        long long g2;
+        float w2;
+        const long long grp2 = corner(Ch, qn, sl, g2, w2) ? (g2 >> 5) : -1;
+        const unsigned same2 = __match_any_sync(active, grp2);
+        if (grp2 >= 0 && (__ffs(same2) - 1) == (int)(threadIdx.x & 31)) fl[grp2] = 1;
+    }
+
+    // spreading: g(x) += w(x - X) S at this lane's corner
+    if (hit) atomicAdd((a.par ? a.g1 : a.g0) + g, make_float4(w * S.x, w * S.y, w * S.z, 0.f));
     // flag the 32-node groups that received force: one store per distinct group of this warp
     const long long grp = hit ? (g >> 5) : -1;
-    const unsigned active = __activemask();
     const unsigned same = __match_any_sync(active, grp);
-    if (hit && (__ffs(same) - 1) == (int)(threadIdx.x & 31)) (a.par ? a.fl1 : a.fl0)[grp] = 1;
+    if (hit && (__ffs(same) - 1) == (int)(threadIdx.x & 31)) fl[grp] = 1;
 }
 
 cudaError_t launch_forces_spread(const IbmArgs& a, cudaStream_t s) {

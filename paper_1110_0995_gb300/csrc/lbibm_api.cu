@@ -127,6 +127,8 @@ struct lb_ctx {
     int list_blocks = 0;
     // collisions (soft sphere): off while rep_k == 0
     float rep_k = 0.f, rep_dc = 0.f;
+    double ib_m = 0.0, ib_gamma = 0.0;   // IB points with mass (ib_m > 0) and drag
+    float4* W = nullptr;                 // [M] their velocities
     int rep_cap = 0, rep_nb = 0;
     float4 *rep_R = nullptr, *rep_bounds = nullptr;
     int2* rep_pairs = nullptr;
@@ -290,6 +292,16 @@ IbmArgs ibm_args(const lb_ctx* ctx, int par, bool overlapped = false) {
     a.fl1 = ctx->fl[1];
     a.u = ctx->u;
     a.R = ctx->rep_k > 0.f ? ctx->rep_R : nullptr;
+    if (ctx->ib_m > 0.0 && ctx->W) {
+        // kick / exact drag drift constants: a = gamma / m, p1 = (1 - e^-a) / a, E = e^-a
+        const double m = ctx->ib_m, gam = ctx->ib_gamma, aa = gam / m;
+        const double p1 = aa < 1e-4 ? 1.0 - aa * (0.5 - aa * (1.0 / 6.0 - aa / 24.0)) : -std::expm1(-aa) / aa;
+        a.W = ctx->W;
+        a.ib_inv_m = (float)(1.0 / m);
+        a.ib_gp1 = (float)(gam * p1);
+        a.ib_p1 = (float)p1;
+        a.ib_E = (float)std::exp(-aa);
+    }
     a.dmark = ctx->dmap[1 - par];
     a.dcur = overlapped ? ctx->dmap[par] : nullptr;
     a.sched_err = ctx->sched_err;
@@ -370,6 +382,7 @@ lb_status enqueue_step(lb_ctx* ctx, int par) {
     }
     for (int k = 0; k < 4; ++k) {
         if (!ibm && k != 2) continue;
+        if (k == 3 && ctx->W) continue;   // points with mass move in the spreading kernel
         EventPair ep{};
         const bool timed = (ctx->timing >> k) & 1;
         ctx->launches[k] += 1;
@@ -479,7 +492,8 @@ lb_status enqueue_step_overlap(lb_ctx* ctx, int par, bool lead_interp) {
 
 bool use_overlap(const lb_ctx* ctx) {
     const long long m = ctx->committed ? ctx->M : (long long)ctx->hq0.size();
-    return ctx->overlap && m > 0 && ctx->phi == nullptr && ctx->rep_k == 0.f && ctx->k3.npt == 1 && ctx->timing == 0 && ctx->ib_stream != nullptr;
+    return ctx->overlap && m > 0 && ctx->phi == nullptr && ctx->rep_k == 0.f && ctx->ib_m == 0.0 && ctx->k3.npt == 1 &&
+           ctx->timing == 0 && ctx->ib_stream != nullptr;
 }
 
 lb_status build_graphs_overlap(lb_ctx* ctx) {
@@ -729,6 +743,10 @@ lb_status commit_ibm(lb_ctx* ctx) {
     LB_CUDA(up(&ctx->chunks, ctx->hchunks));
     LB_CUDA(up(&ctx->d_cells, ctx->hcells));
     LB_CUDA(dalloc(ctx, &ctx->F, ctx->M));
+    if (ctx->ib_m > 0.0) {
+        LB_CUDA(dalloc(ctx, &ctx->W, ctx->M));
+        LB_CUDA(cudaMemsetAsync(ctx->W, 0, sizeof(float4) * ctx->M, ctx->stream));
+    }
     LB_CUDA(cudaMallocHost((void**)&ctx->hq_pinned, sizeof(Q4) * (size_t)ctx->M));
     LB_CUDA(cudaMemsetAsync(ctx->F, 0, sizeof(float4) * ctx->M, ctx->stream));
     LB_CUDA(dalloc(ctx, &ctx->partials, ctx->NCH));
@@ -956,11 +974,47 @@ lb_status lb_set_repulsion(lb_ctx* ctx, double k, double dc) {
     return LB_OK;
 }
 
+lb_status lb_set_ib_dynamics(lb_ctx* ctx, double mass, double gamma) {
+    LB_GUARD(ctx);
+    if (ctx->started || ctx->committed)
+        return fail(ctx, LB_ERR_STATE, "the IB point dynamics must be set before the first step");
+    if (!(mass >= 0.0) || !(gamma >= 0.0) || !std::isfinite(mass) || !std::isfinite(gamma))
+        return fail(ctx, LB_ERR_ARG, "need finite mass >= 0 and gamma >= 0");
+    if (mass > 0.0 && ctx->phi) return fail(ctx, LB_ERR_STATE, "the differentiable variant has massless points");
+    ctx->ib_m = mass;
+    ctx->ib_gamma = gamma;
+    drop_graphs(ctx);
+    return LB_OK;
+}
+
+lb_status ibm_get_velocities(lb_ctx* ctx, int mesh_id, double* v) {
+    LB_GUARD(ctx);
+    const MeshHost* mh;
+    if (check_channel_mesh(ctx, mesh_id, &mh) != LB_OK) return LB_ERR_ARG;
+    if (!v) return fail(ctx, LB_ERR_ARG, "null output");
+    lb_status st = commit_ibm(ctx);
+    if (st != LB_OK) return st;
+    if (!ctx->W) {
+        for (int j = 0; j < 3 * mh->n; ++j) v[j] = 0.0;
+        return LB_OK;
+    }
+    std::vector<float4> w(mh->n);
+    LB_CUDA(cudaMemcpyAsync(w.data(), ctx->W + mh->node0, sizeof(float4) * mh->n, cudaMemcpyDeviceToHost, ctx->stream));
+    LB_CUDA(cudaStreamSynchronize(ctx->stream));
+    for (int j = 0; j < mh->n; ++j) {
+        v[3 * j] = w[j].x;
+        v[3 * j + 1] = w[j].y;
+        v[3 * j + 2] = w[j].z;
+    }
+    return LB_OK;
+}
+
 lb_status lb_set_brinkman(lb_ctx* ctx, const double* beads, int n, double alpha, double delta) {
     LB_GUARD(ctx);
     if (ctx->started) return fail(ctx, LB_ERR_STATE, "the Brinkman beads must be set before the first step");
     if (ctx->ch.size() != 1) return fail(ctx, LB_ERR_ARG, "the differentiable variant takes a single-channel context");
     if (ctx->rep_k > 0.f) return fail(ctx, LB_ERR_STATE, "collisions are not part of the differentiable variant");
+    if (ctx->ib_m > 0.0) return fail(ctx, LB_ERR_STATE, "the differentiable variant has massless points");
     if (n < 0 || (n > 0 && !beads) || !(alpha >= 0.0) || !(delta > 0.0))
         return fail(ctx, LB_ERR_ARG, "bad bead list, alpha or delta");
     for (int k = 0; k < 4 * n; ++k)
@@ -1100,6 +1154,7 @@ lb_status lb_adjoint(lb_ctx* ctx, int n_steps, int ckpt_every, int objective_mes
                      double* grad_ks, double* grad_kb) {
     LB_GUARD(ctx);
     if (!ctx->phi) return fail(ctx, LB_ERR_STATE, "lb_adjoint needs the differentiable variant (lb_set_brinkman)");
+    if (ctx->ib_m > 0.0) return fail(ctx, LB_ERR_STATE, "lb_adjoint needs massless IB points");
     if (ctx->storage != LB_F32) return fail(ctx, LB_ERR_ARG, "lb_adjoint needs FP32 populations");
     if (n_steps < 1 || ckpt_every < 1) return fail(ctx, LB_ERR_ARG, "n_steps and ckpt_every must be >= 1");
     if (ctx->timing) return fail(ctx, LB_ERR_STATE, "per-kernel timing is on");
@@ -1557,7 +1612,7 @@ lb_status lb_step(lb_ctx* ctx, int n_steps) {
         const int n = n_steps - k >= GRAPH_BLOCK ? GRAPH_BLOCK : 1;
         LB_CUDA(cudaGraphLaunch(n > 1 ? ctx->gexec_blk[par] : ctx->gexec[par], ctx->stream));
         for (int c = 0; c < 4; ++c)
-            if (ctx->M > 0 || c == 2) ctx->launches[c] += n;
+            if ((ctx->M > 0 || c == 2) && !(c == 3 && ctx->W)) ctx->launches[c] += n;
         if (ctx->M > 0 && ctx->rep_k > 0.f) ctx->launches[1] += 4 * n;   // collision kernels
         ctx->step += n;
         k += n;

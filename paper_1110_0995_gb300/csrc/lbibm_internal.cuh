@@ -218,6 +218,11 @@ struct IbmArgs {
     uint8_t* fl1;
     const float4* u;
     const float4* R;      // [M] collision forces added to the membrane forces (null: none)
+    // IB points with mass (null W: massless points advected by k_interp_advance):
+    // kick V = W + F / m, drift X += U + p1 (V - U), W <- U + E (V - U), the
+    // fluid receiving J = gamma p1 (V - U); U interpolated at X from u
+    float4* W;            // [M] point velocities carried between steps
+    float ib_inv_m, ib_gp1, ib_p1, ib_E;
     // overlapped schedule: map receiving the next step's stencil set, the
     // current step's set (every spread target must lie in it) and the count
     // of spread targets found outside it

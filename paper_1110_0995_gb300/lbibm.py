@@ -20,7 +20,8 @@ STORAGE = {"f32": 0, "f16": 1, "bf16": 2}
 
 # Every entry point that include/lbibm.h declares.
 EXPORTS = (
-    "lb_create", "lb_create_batch", "lb_select_channel", "lb_destroy", "lb_set_obstacles", "lb_set_brinkman", "lb_adjoint", "lb_set_repulsion", "ibm_add_mesh",
+    "lb_create", "lb_create_batch", "lb_select_channel", "lb_destroy", "lb_set_obstacles", "lb_set_brinkman", "lb_adjoint", "lb_set_repulsion", "lb_set_ib_dynamics",
+    "ibm_get_velocities", "ibm_add_mesh",
     "ibm_set_nodes", "lb_step", "lb_synchronize", "lb_get_fields", "lb_get_populations", "lb_set_populations",
     "ibm_get_nodes", "ibm_get_all_nodes", "ibm_get_forces", "ibm_get_area_volume", "lb_diagnostics", "lb_get_step", "lb_save_state",
     "lb_load_state", "lb_set_schedule", "lb_get_schedule", "lb_set_timing", "lb_kernel_times", "lb_last_error", "lb_version", "lb_get_mask",
@@ -85,6 +86,8 @@ def lib():
             "lb_set_timing": ([P, I], I),
             "lb_set_brinkman": ([P, P, I, D, D], I),
             "lb_set_repulsion": ([P, D, D], I),
+            "lb_set_ib_dynamics": ([P, D, D], I),
+            "ibm_get_velocities": ([P, I, P], I),
             "lb_adjoint": ([P, I, I, I, P, P, P, P], I),
             "lb_set_schedule": ([P, I], I),
             "lb_get_schedule": ([P, P], I),
@@ -149,6 +152,9 @@ class Simulation:
         rep = getattr(scenes[0], "repulsion", None)
         if rep is not None:
             sim.set_repulsion(*rep)
+        dyn = getattr(scenes[0], "ib_dynamics", None)
+        if dyn is not None:
+            sim.set_ib_dynamics(*dyn)
         for k, s in enumerate(scenes):
             sim.select(k)
             if len(s.spheres):
@@ -302,6 +308,16 @@ class Simulation:
     def set_repulsion(self, k: float, dc: float):
         """Soft-sphere collisions (cells, beads, walls): force k (dc - d) below separation dc."""
         self._check(self._L.lb_set_repulsion(self._h, float(k), float(dc)))
+
+    def set_ib_dynamics(self, mass: float, gamma: float):
+        """IB points with mass and drag (kick + exact drag drift); mass 0: massless points."""
+        self._check(self._L.lb_set_ib_dynamics(self._h, float(mass), float(gamma)))
+
+    def velocities(self, mesh: int) -> np.ndarray:
+        """Point velocities after the last step (zeros for massless points)."""
+        v = np.zeros((self.n_mesh_nodes[self.channel][mesh], 3))
+        self._check(self._L.ibm_get_velocities(self._h, int(mesh), _ptr(v)))
+        return v
 
     def set_brinkman(self, beads, alpha: float = 2.0, delta: float = 0.5):
         """Differentiable variant: beads (n x 4: cx, cy, cz, r) as a smooth Brinkman solid fraction."""
