@@ -86,6 +86,11 @@ def lib():
         L.or_sys_set_dynamics.argtypes = [vp, d, d]
         L.or_sys_get_velocities.argtypes = [vp, i, P]
         L.or_drag_coefficients.argtypes = [d, d, P]
+        L.or_dipole_force.argtypes = [P, P, P, d, P]
+        L.or_dipole_energy.restype = d
+        L.or_dipole_energy.argtypes = [P, P, P, d]
+        L.or_bead_forces.argtypes = [P, P, i, P, P, P]
+        L.or_bead_relax.argtypes = [P, P, i, P, P, i]
         L.or_sys_step.argtypes = [vp, i]
         L.or_constants.argtypes = [P, P, P]
         L.or_equilibrium.argtypes = [d, P, P]
@@ -153,6 +158,41 @@ def drag_coefficients(m: float, gamma: float):
     out = np.zeros(3)
     lib().or_drag_coefficients(float(m), float(gamma), _p(out))
     return tuple(out)
+
+
+def dipole_force(m1, m2, r, c: float) -> np.ndarray:
+    """Force on bead 2 from bead 1 (Sec. 2.5), r = x2 - x1, c = mu0 / (4 pi)."""
+    F = np.zeros(3)
+    lib().or_dipole_force(_p(_f64(m1)), _p(_f64(m2)), _p(_f64(r)), float(c), _p(F))
+    return F
+
+
+def dipole_energy(m1, m2, r, c: float) -> float:
+    return float(lib().or_dipole_energy(_p(_f64(m1)), _p(_f64(m2)), _p(_f64(r)), float(c)))
+
+
+def _bead_params(c, radius, k, mobility, dt, box, periodic):
+    pr = _f64([c, radius, k, mobility, dt, *box])
+    per = np.ascontiguousarray(periodic, dtype=np.int32)
+    return pr, per
+
+
+def bead_forces(x, m, c, radius, k, box=(1, 1, 1), periodic=(0, 0, 0)) -> np.ndarray:
+    """Dipole + contact forces on every bead (n x 3)."""
+    xx, mm = _f64(x), _f64(m)
+    pr, per = _bead_params(c, radius, k, 0.0, 0.0, box, periodic)
+    F = np.zeros_like(xx)
+    lib().or_bead_forces(_p(xx), _p(mm), int(xx.shape[0]), _p(pr), _p(per), _p(F))
+    return F
+
+
+def bead_relax(x, m, c, radius, k, mobility, dt, steps, box=(1, 1, 1), periodic=(0, 0, 0)) -> np.ndarray:
+    """Overdamped bead assembly: positions after `steps` steps."""
+    xx = _f64(x).copy()
+    mm = _f64(m)
+    pr, per = _bead_params(c, radius, k, mobility, dt, box, periodic)
+    lib().or_bead_relax(_p(xx), _p(mm), int(xx.shape[0]), _p(pr), _p(per), int(steps))
+    return xx
 
 
 def rasterise(spheres: np.ndarray, dims) -> np.ndarray:

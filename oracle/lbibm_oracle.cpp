@@ -753,6 +753,81 @@ void system_step_massive(System<R>& s) {
     s.steps++;
 }
 
+// Magnetic bead interaction (Sec. 2.5): the force on bead 2 from bead 1 with
+// moments m1, m2, r = x2 - x1 and c = mu0 / (4 pi), as printed (its bracket is
+// left open; closed after the last term):
+//   F = 3c / |r|^5 [ (m1.r) m2 + (m2.r) m1 + (m1.m2) r - 5 (m1.r)(m2.r) r / |r|^2 ]
+void dipole_force(const double* m1, const double* m2, const double* r, double c, double* F) {
+    const double r2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+    const double rr = std::sqrt(r2);
+    const double m1r = m1[0] * r[0] + m1[1] * r[1] + m1[2] * r[2];
+    const double m2r = m2[0] * r[0] + m2[1] * r[1] + m2[2] * r[2];
+    const double m12 = m1[0] * m2[0] + m1[1] * m2[1] + m1[2] * m2[2];
+    const double pre = 3.0 * c / (r2 * r2 * rr);
+    for (int d = 0; d < 3; ++d)
+        F[d] = pre * (m1r * m2[d] + m2r * m1[d] + m12 * r[d] - 5.0 * m1r * m2r * r[d] / r2);
+}
+
+// Energy of the pair (for the pins only): U = c / |r|^3 [m1.m2 - 3 (m1.r)(m2.r) / |r|^2].
+double dipole_energy(const double* m1, const double* m2, const double* r, double c) {
+    const double r2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+    const double m1r = m1[0] * r[0] + m1[1] * r[1] + m1[2] * r[2];
+    const double m2r = m2[0] * r[0] + m2[1] * r[1] + m2[2] * r[2];
+    const double m12 = m1[0] * m2[0] + m1[1] * m2[1] + m1[2] * m2[2];
+    return c / (r2 * std::sqrt(r2)) * (m12 - 3.0 * m1r * m2r / r2);
+}
+
+struct BeadParams {
+    double c;          // mu0 / (4 pi)
+    double radius;     // bead radius R
+    double k;          // contact stiffness
+    double mobility;   // velocity per unit force (overdamped friction)
+    double dt;
+    double box[3];
+    int per[3];
+};
+
+// Forces on every bead: the dipole interaction of every other bead plus, for
+// two beads closer than 2R, a contact force k (2R - d) along their separation
+// (the paper adds collision forces without a form; reading: harmonic).  On a
+// periodic axis the separation is the minimum image.
+void bead_forces(const double* x, const double* m, int n, const BeadParams& p, double* F) {
+    for (int i = 0; i < 3 * n; ++i) F[i] = 0.0;
+    for (int b = 0; b < n; ++b)
+        for (int a = 0; a < n; ++a) {
+            if (a == b) continue;
+            double r[3];
+            for (int d = 0; d < 3; ++d) {
+                r[d] = x[3 * b + d] - x[3 * a + d];
+                if (p.per[d]) r[d] -= p.box[d] * std::floor(r[d] / p.box[d] + 0.5);
+            }
+            double f[3];
+            dipole_force(&m[3 * a], &m[3 * b], r, p.c, f);
+            const double dist = std::sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+            const double overlap = 2.0 * p.radius - dist;
+            for (int d = 0; d < 3; ++d) {
+                F[3 * b + d] += f[d];
+                if (overlap > 0.0) F[3 * b + d] += p.k * overlap * r[d] / dist;
+            }
+        }
+}
+
+// Overdamped bead motion (the paper's friction): x += mobility F dt, every
+// bead from the forces at the same positions; wrapped into the box on
+// periodic axes.
+void bead_relax(double* x, const double* m, int n, const BeadParams& p, int steps) {
+    std::vector<double> F(3 * (size_t)n);
+    for (int s = 0; s < steps; ++s) {
+        bead_forces(x, m, n, p, F.data());
+        for (int i = 0; i < n; ++i)
+            for (int d = 0; d < 3; ++d) {
+                double v = x[3 * i + d] + p.mobility * F[3 * i + d] * p.dt;
+                if (p.per[d]) v -= p.box[d] * std::floor(v / p.box[d]);
+                x[3 * i + d] = v;
+            }
+    }
+}
+
 // Obstacles (Sec. 2.4 and 2.5: bead chains fixed in space are boundary
 // nodes).  A lattice node is solid iff it lies inside or on any sphere,
 // |x - c|^2 <= r^2, evaluated in double from the float inputs.
@@ -1106,6 +1181,37 @@ void or_sys_get_velocities(void* h, int m, double* v) {
         return;
     }
     std::memcpy(v, c.V.data(), sizeof(double) * 3 * c.T.n);
+}
+
+void or_dipole_force(const double* m1, const double* m2, const double* r, double c, double* F) {
+    dipole_force(m1, m2, r, c, F);
+}
+
+double or_dipole_energy(const double* m1, const double* m2, const double* r, double c) {
+    return dipole_energy(m1, m2, r, c);
+}
+
+static BeadParams bead_params(const double* pr, const int* per) {
+    BeadParams p;
+    p.c = pr[0];
+    p.radius = pr[1];
+    p.k = pr[2];
+    p.mobility = pr[3];
+    p.dt = pr[4];
+    for (int d = 0; d < 3; ++d) {
+        p.box[d] = pr[5 + d];
+        p.per[d] = per[d];
+    }
+    return p;
+}
+
+// params: c, radius, k, mobility, dt, box[3]
+void or_bead_forces(const double* x, const double* m, int n, const double* params, const int* per, double* F) {
+    bead_forces(x, m, n, bead_params(params, per), F);
+}
+
+void or_bead_relax(double* x, const double* m, int n, const double* params, const int* per, int steps) {
+    bead_relax(x, m, n, bead_params(params, per), steps);
 }
 
 void or_drag_coefficients(double m, double gamma, double* a_p1_E) {
