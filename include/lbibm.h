@@ -294,6 +294,39 @@ lb_status ibm_area_volume_noalloc(const double* xyz, const int32_t* tris, const 
                                   const int32_t* cell_tri_start_host, int n_cells, double* area, double* volume,
                                   void* cuda_stream);
 
+/* ---- magnetic bead assembly (Sec. 2.5), context-free ----
+ * The force of bead a on bead b with moments m_a, m_b at r = x_b - x_a is the
+ * printed dipole interaction (its bracket closed after the last term),
+ *   F = 3c / |r|^5 [(m_a.r) m_b + (m_b.r) m_a + (m_a.m_b) r - 5 (m_a.r)(m_b.r) r / |r|^2],
+ * c = mu0 / (4 pi) in the caller's units, plus for |r| < 2R a contact force
+ * k (2R - |r|) along r (the paper adds collision forces without a form;
+ * reading: harmonic).  Separations use the minimum image on periodic axes.
+ * The external field's gradient force needs the charge-sheet field, which
+ * the paper does not give: moments are inputs (e.g. all along a uniform
+ * field).  FP32 on the device, all pairs. */
+typedef struct {
+    double mu0_4pi;      /* c */
+    double radius;       /* R >= 0 */
+    double k_contact;    /* k >= 0 */
+    double mobility;     /* overdamped friction: velocity per unit force */
+    double dt;           /* time step of bead_relax */
+    double box[3];       /* box edges; > 0 on periodic axes */
+    int periodic[3];
+    int reserved[5];     /* must be zero */
+} bead_params;
+
+/* Forces on n beads (xyz, moments: n x 3 host arrays; F: n x 3 host output).
+ * Coincident beads are undefined.  LB_ERR_ARG for n < 1, null pointers or bad
+ * parameters; LB_ERR_OOM / LB_ERR_CUDA on device failure.  Synchronous on
+ * `cuda_stream` (NULL = default stream); allocates its device buffers. */
+lb_status bead_forces(const double* xyz, const double* moments, int n, const bead_params* p, double* F,
+                      void* cuda_stream);
+
+/* Overdamped bead motion: `steps` steps of x += mobility * F(x) * dt, every
+ * bead from the positions of the same step, wrapped into the box on periodic
+ * axes; xyz (n x 3, host) is updated in place.  Errors as bead_forces. */
+lb_status bead_relax(double* xyz, const double* moments, int n, const bead_params* p, int steps, void* cuda_stream);
+
 /* Conservation diagnostics of the selected channel, FP64 on the device:
  * out[0] = sum of rho over fluid nodes, out[1..3] = sum of sum_i e_i f_i
  * after the last collision, out[4] = number of non-finite populations,

@@ -10,7 +10,7 @@ ROOT = os.path.dirname(HERE)
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "liblbibm.so")
-UNITS = ["lattice_kernels.cu", "ibm_kernels.cu", "lbibm_api.cu", "noalloc.cu", "adjoint.cu", "repulsion.cu"]
+UNITS = ["lattice_kernels.cu", "ibm_kernels.cu", "lbibm_api.cu", "noalloc.cu", "adjoint.cu", "repulsion.cu", "beads.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"), "-I", SRC]
 

@@ -26,6 +26,7 @@ EXPORTS = (
     "ibm_get_nodes", "ibm_get_all_nodes", "ibm_get_forces", "ibm_get_area_volume", "lb_diagnostics", "lb_get_step", "lb_save_state",
     "lb_load_state", "lb_set_schedule", "lb_get_schedule", "lb_set_timing", "lb_kernel_times", "lb_last_error", "lb_version", "lb_get_mask",
     "lb_set_kernel_config", "lb_get_kernel_config", "lb_autotune", "ibm_area_volume_noalloc",
+    "bead_forces", "bead_relax",
 )
 
 
@@ -39,6 +40,12 @@ class LbParams(ctypes.Structure):
 class IbmModuli(ctypes.Structure):
     _fields_ = [("ks", ctypes.c_double), ("kb", ctypes.c_double), ("kal", ctypes.c_double),
                 ("kag", ctypes.c_double), ("kv", ctypes.c_double)]
+
+
+class BeadParams(ctypes.Structure):
+    _fields_ = [("mu0_4pi", ctypes.c_double), ("radius", ctypes.c_double), ("k_contact", ctypes.c_double),
+                ("mobility", ctypes.c_double), ("dt", ctypes.c_double), ("box", ctypes.c_double * 3),
+                ("periodic", ctypes.c_int * 3), ("reserved", ctypes.c_int * 5)]
 
 
 class LbError(RuntimeError):
@@ -99,6 +106,8 @@ def lib():
             "lb_get_kernel_config": ([P, ctypes.POINTER(I), ctypes.POINTER(I)], I),
             "lb_autotune": ([P, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(D)], I),
             "ibm_area_volume_noalloc": ([P, P, P, P, I, P, P, P], I),
+            "bead_forces": ([P, P, I, P, P, P], I),
+            "bead_relax": ([P, P, I, P, I, P], I),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -359,3 +368,37 @@ class Simulation:
         n = np.zeros(4, np.int64)
         self._check(self._L.lb_kernel_times(self._h, _ptr(ms), _ptr(n)))
         return ms, n
+
+
+# ---- magnetic bead assembly (context-free) ----------------------------------
+def _bead_params(c, radius, k, mobility=0.0, dt=0.0, box=(1.0, 1.0, 1.0), periodic=(0, 0, 0)) -> BeadParams:
+    p = BeadParams()
+    p.mu0_4pi, p.radius, p.k_contact, p.mobility, p.dt = float(c), float(radius), float(k), float(mobility), float(dt)
+    for d in range(3):
+        p.box[d] = float(box[d])
+        p.periodic[d] = int(periodic[d])
+    return p
+
+
+def bead_forces(xyz, moments, c, radius, k, box=(1.0, 1.0, 1.0), periodic=(0, 0, 0), stream=None) -> np.ndarray:
+    """Dipole + contact forces on every bead (n x 3), computed on the GPU."""
+    x = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1, 3)
+    m = np.ascontiguousarray(moments, dtype=np.float64).reshape(-1, 3)
+    F = np.zeros_like(x)
+    p = _bead_params(c, radius, k, box=box, periodic=periodic)
+    st = lib().bead_forces(_ptr(x), _ptr(m), int(x.shape[0]), ctypes.byref(p), _ptr(F), stream)
+    if st != 0:
+        raise LbError(st, "bead_forces")
+    return F
+
+
+def bead_relax(xyz, moments, c, radius, k, mobility, dt, steps, box=(1.0, 1.0, 1.0), periodic=(0, 0, 0),
+               stream=None) -> np.ndarray:
+    """Overdamped bead assembly on the GPU: positions after `steps` steps."""
+    x = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1, 3).copy()
+    m = np.ascontiguousarray(moments, dtype=np.float64).reshape(-1, 3)
+    p = _bead_params(c, radius, k, mobility, dt, box, periodic)
+    st = lib().bead_relax(_ptr(x), _ptr(m), int(x.shape[0]), ctypes.byref(p), int(steps), stream)
+    if st != 0:
+        raise LbError(st, "bead_relax")
+    return x
