@@ -261,6 +261,17 @@ lb_status ibm_get_nodes(lb_ctx* ctx, int mesh_id, double* xyz);
  * record cell trajectories (Sec. 3); this is that readback. */
 lb_status ibm_get_all_nodes(lb_ctx* ctx, double* xyz);
 
+/* Asynchronous form of ibm_get_all_nodes for trajectory recording alongside
+ * the stepping: enqueues on the context's stream the conversion of the
+ * selected channel's positions to double (on the device) and their copy into
+ * xyz (host, caller-owned, page-locked for the copy to overlap later steps),
+ * then returns.  slot (0 or 1) names the readback; xyz is complete once
+ * lb_readback_wait(ctx, slot) has returned LB_OK, and must not be reused
+ * before.  Alternating slots lets the host consume one readback while the
+ * next runs behind further steps. */
+lb_status ibm_get_all_nodes_async(lb_ctx* ctx, double* xyz, int slot);
+lb_status lb_readback_wait(lb_ctx* ctx, int slot);
+
 /* Node forces spread in the last step (n x 3, host). */
 lb_status ibm_get_forces(lb_ctx* ctx, int mesh_id, double* f);
 

@@ -565,4 +565,21 @@ cudaError_t launch_interp_advance(const IbmArgs& a, cudaStream_t s) {
     return launch_ex(k_interp_advance, (unsigned)((a.n_nodes + IA_BLOCK - 1) / IA_BLOCK), IA_BLOCK, 0, s, a.pdl, a);
 }
 
+// Positions as doubles (x, y, z per node) for an asynchronous readback; the
+// 2^-40 fixed point converts exactly for |x| < 2^13 lu.
+__global__ void k_positions_to_double(const Q4* __restrict__ q, int n, double* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const Q4 v = q[i];
+    out[3 * i] = (double)v.x * (1.0 / FIX_SCALE);
+    out[3 * i + 1] = (double)v.y * (1.0 / FIX_SCALE);
+    out[3 * i + 2] = (double)v.z * (1.0 / FIX_SCALE);
+}
+
+cudaError_t launch_positions_to_double(const Q4* q, int n, double* out, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_positions_to_double<<<(n + 255) / 256, 256, 0, s>>>(q, n, out);
+    return cudaGetLastError();
+}
+
 }  // namespace lbibm

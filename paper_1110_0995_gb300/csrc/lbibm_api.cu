@@ -89,6 +89,8 @@ struct lb_ctx {
     Q4* q0 = nullptr;
     float4* F = nullptr;
     Q4* hq_pinned = nullptr;       // page-locked staging of positions for readback [M]
+    double* d_xyz = nullptr;       // [3M] device staging of asynchronous readbacks
+    cudaEvent_t rb_ev[2] = {nullptr, nullptr};
     int4* info = nullptr;
     int4* slots = nullptr;
     int4* edges = nullptr;
@@ -953,6 +955,7 @@ lb_status lb_destroy(lb_ctx* ctx) {
         cudaStreamDestroy(ctx->ib_stream);
     }
     for (int k = 0; k < 2; ++k) {
+        if (ctx->rb_ev[k]) cudaEventDestroy(ctx->rb_ev[k]);
         if (ctx->ev_fork[k]) cudaEventDestroy(ctx->ev_fork[k]);
         if (ctx->ev_join[k]) cudaEventDestroy(ctx->ev_join[k]);
         if (ctx->ev_fork2[k]) cudaEventDestroy(ctx->ev_fork2[k]);
@@ -1891,6 +1894,41 @@ lb_status ibm_get_all_nodes(lb_ctx* ctx, double* xyz) {
     for (int id : ctx->ch_meshes[ctx->cur]) ms.push_back(&ctx->meshes[id]);
     if (ms.empty()) return LB_OK;
     return read_positions(ctx, ms, xyz);
+}
+
+lb_status ibm_get_all_nodes_async(lb_ctx* ctx, double* xyz, int slot) {
+    LB_GUARD(ctx);
+    if (!xyz || (slot != 0 && slot != 1)) return fail(ctx, LB_ERR_ARG, "null output or slot not 0 or 1");
+    lb_status st = commit_ibm(ctx);
+    if (st != LB_OK) return st;
+    std::vector<const MeshHost*> ms;
+    for (int id : ctx->ch_meshes[ctx->cur]) ms.push_back(&ctx->meshes[id]);
+    if (!ctx->rb_ev[slot]) LB_CUDA(cudaEventCreateWithFlags(&ctx->rb_ev[slot], cudaEventDisableTiming));
+    if (!ms.empty()) {
+        if (!ctx->d_xyz) LB_CUDA(dalloc(ctx, &ctx->d_xyz, 3 * (size_t)ctx->M));
+        const Q4* src = ctx->q[ctx->step & 1];
+        size_t k = 0, o = 0;
+        while (k < ms.size()) {
+            size_t e = k + 1;
+            while (e < ms.size() && ms[e]->node0 == ms[e - 1]->node0 + ms[e - 1]->n) ++e;
+            const int n0 = ms[k]->node0, n1 = ms[e - 1]->node0 + ms[e - 1]->n;
+            LB_CUDA(launch_positions_to_double(src + n0, n1 - n0, ctx->d_xyz + 3 * (size_t)n0, ctx->stream));
+            LB_CUDA(cudaMemcpyAsync(xyz + 3 * o, ctx->d_xyz + 3 * (size_t)n0, sizeof(double) * 3 * (size_t)(n1 - n0),
+                                    cudaMemcpyDeviceToHost, ctx->stream));
+            o += (size_t)(n1 - n0);
+            k = e;
+        }
+    }
+    LB_CUDA(cudaEventRecord(ctx->rb_ev[slot], ctx->stream));
+    return LB_OK;
+}
+
+lb_status lb_readback_wait(lb_ctx* ctx, int slot) {
+    LB_GUARD(ctx);
+    if (slot != 0 && slot != 1) return fail(ctx, LB_ERR_ARG, "slot not 0 or 1");
+    if (!ctx->rb_ev[slot]) return LB_OK;
+    LB_CUDA(cudaEventSynchronize(ctx->rb_ev[slot]));
+    return LB_OK;
 }
 
 lb_status ibm_get_forces(lb_ctx* ctx, int mesh_id, double* f) {

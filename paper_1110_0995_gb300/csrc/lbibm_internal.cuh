@@ -369,6 +369,7 @@ cudaError_t launch_cell_sums(const IbmArgs& a, cudaStream_t s);
 cudaError_t launch_elements(const IbmArgs& a, cudaStream_t s);
 cudaError_t launch_forces_spread(const IbmArgs& a, cudaStream_t s);
 cudaError_t launch_interp_advance(const IbmArgs& a, cudaStream_t s);
+cudaError_t launch_positions_to_double(const Q4* q, int n, double* out, cudaStream_t s);
 
 cudaError_t launch_repulsion(const RepArgs& a, int sm_count, cudaStream_t s);
 cudaError_t launch_adj_interp(const AdjArgs& a, cudaStream_t s);

@@ -26,7 +26,7 @@ EXPORTS = (
     "ibm_get_nodes", "ibm_get_all_nodes", "ibm_get_forces", "ibm_get_area_volume", "lb_diagnostics", "lb_get_step", "lb_save_state",
     "lb_load_state", "lb_set_schedule", "lb_get_schedule", "lb_set_timing", "lb_kernel_times", "lb_last_error", "lb_version", "lb_get_mask",
     "lb_set_kernel_config", "lb_get_kernel_config", "lb_autotune", "ibm_area_volume_noalloc",
-    "bead_forces", "bead_relax",
+    "bead_forces", "bead_relax", "ibm_get_all_nodes_async", "lb_readback_wait",
 )
 
 
@@ -107,6 +107,8 @@ def lib():
             "lb_autotune": ([P, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(D)], I),
             "ibm_area_volume_noalloc": ([P, P, P, P, I, P, P, P], I),
             "bead_forces": ([P, P, I, P, P, P], I),
+            "ibm_get_all_nodes_async": ([P, P, I], I),
+            "lb_readback_wait": ([P, I], I),
             "bead_relax": ([P, P, I, P, I, P], I),
         }
         for name, (args, res) in sig.items():
@@ -269,6 +271,14 @@ class Simulation:
     def all_nodes_into(self, out: np.ndarray):
         """Positions of every mesh of the selected channel, concatenated (one transfer)."""
         self._check(self._L.ibm_get_all_nodes(self._h, _ptr(out)))
+
+    def all_nodes_into_async(self, out: np.ndarray, slot: int):
+        """Enqueue the readback of every mesh's positions of the selected channel into
+        `out` (page-locked for overlap); complete after wait_readback(slot)."""
+        self._check(self._L.ibm_get_all_nodes_async(self._h, _ptr(out), int(slot)))
+
+    def wait_readback(self, slot: int):
+        self._check(self._L.lb_readback_wait(self._h, int(slot)))
 
     def forces(self, mesh: int) -> np.ndarray:
         f = np.zeros((self.n_mesh_nodes[self.channel][mesh], 3))

@@ -279,6 +279,33 @@ def test_overlapped_schedule_matches_sequential():
     assert _sim(sc).schedule() == 0
 
 
+def test_async_readback_matches_sync():
+    """Asynchronous trajectory readback (device conversion, two slots) gives the
+    synchronous readback's positions exactly, with steps between the calls."""
+    import torch
+
+    sc = scene.small_filter(seed=5, steps=0)
+    sim = _sim(sc)
+    n = sum(m.n_nodes for m in sc.meshes)
+    bufs = [torch.empty((n, 3), dtype=torch.float64, pin_memory=True).numpy() for _ in range(2)]
+    ref = np.zeros((n, 3))
+    for k in range(4):
+        sim.step(7)
+        sim.all_nodes_into_async(bufs[k & 1], k & 1)
+        sim.all_nodes_into(ref)
+        sim.wait_readback(k & 1)
+        assert np.array_equal(bufs[k & 1], ref)
+    sim.step(3)
+    sim.all_nodes_into_async(bufs[0], 0)
+    sim.step(5)   # enqueued behind the copy
+    sim.wait_readback(0)
+    expect = np.concatenate([sim.nodes(m) for m in range(len(sc.meshes))])
+    assert not np.array_equal(bufs[0], expect)   # the readback is of the earlier step
+    sim.all_nodes_into_async(bufs[1], 1)
+    sim.wait_readback(1)
+    assert np.array_equal(bufs[1], expect)
+
+
 def test_micropost_filter_full_size_parity():
     """Full 256x128x64 filter (62 cells, 120 beads): 200 steps against the oracle."""
     sc = scene.micropost_filter(seed=11)
