@@ -1979,7 +1979,7 @@ lb_status lb_diagnostics(lb_ctx* ctx, double u_max, double out[6]) {
     int serr = 0;
     if (ctx->rep_err) {
         LB_CUDA(cudaMemcpy(&serr, ctx->rep_err, sizeof(int), cudaMemcpyDeviceToHost));
-        if (serr > 0) return fail(ctx, LB_ERR_STATE, "collision candidate lists overflowed (more than 32 neighbour cells or 64 beads)");
+        if (serr > 0) return fail(ctx, LB_ERR_STATE, "collision candidate lists overflowed (more than 32 neighbour cells or 256 beads)");
     }
     int serr2[2] = {0, 0};
     LB_CUDA(cudaMemcpy(serr2, ctx->sched_err, 2 * sizeof(int), cudaMemcpyDeviceToHost));

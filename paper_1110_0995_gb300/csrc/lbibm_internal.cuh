@@ -278,7 +278,7 @@ struct AdjArgs {
 };
 
 // Arguments of the collision kernels (repulsion.cu).
-constexpr int REP_NEARB = 64;       // candidate beads per cell
+constexpr int REP_NEARB = 256;      // candidate beads per cell
 struct RepArgs {
     float k, dc;                    // force k (dc - d) for d < dc
     int n_cells, n_nodes, n_beads, pair_cap;

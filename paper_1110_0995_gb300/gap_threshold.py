@@ -1,0 +1,120 @@
+"""Gap-threshold experiment (Sec. 3): a red cell and a tumor cell are pushed
+by the flow toward a slit in a bead plate; the slit's width is varied and the
+smallest width each cell passes is recorded.  The paper reports a red cell
+passing down to 2 um and a tumor cell stopped below 12 um; it gives no
+mapping from its units to lattice units, so the comparison is qualitative:
+here a red cell has diameter 8 lu and a tumor cell 16 lu.
+
+Every (kind, gap) is one channel of a single batched context, so all cases
+advance in the same launches.  A case is
+
+* ``passed`` once the cell's centroid is more than the cell radius + 2 lu
+  downstream of the plate (its x tracked unwrapped across the periodic axis),
+* ``unstable`` if its channel's populations turn non-finite,
+* ``captured`` otherwise after the run.
+
+    python -m paper_1110_0995_gb300.gap_threshold [--steps N] [--gaps 2,4,...]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+
+from . import scene
+
+CELL_RADIUS = {"rbc": scene.RBC_RADIUS, "ctc": scene.CTC_RADIUS}
+# The tumor cell's 2562-node mesh (edges ~0.6 lu) has an unstable mode under
+# the explicit massless coupling that grows faster the stiffer the membrane
+# (in the FP64 oracle as well); with these moduli it outlasts the 40000-step
+# runs in the gap experiment.
+SOFT_CTC_MODULI = (0.003, 0.003, 0.003, 0.5, 0.9)
+
+
+def cases(gaps, kinds=("rbc", "ctc"), dims=(96, 40, 32), steps=10000, body_force=2e-5, moduli=None):
+    moduli = moduli or {}
+    return [(k, float(g), scene.gap_cell(k, float(g), dims, steps, body_force, moduli.get(k))) for k in kinds
+            for g in gaps]
+
+
+def run(case_list, steps: int, every: int = 100, storage: str = "f32", stream=None):
+    """Advance every case together; returns one record per case."""
+    from . import lbibm
+
+    scenes = [c[2] for c in case_list]
+    sim = lbibm.Simulation.from_scenes(scenes, storage=storage, stream=stream)
+    nx = scenes[0].dims[0]
+    x_plate = nx / 2.0
+    n = [s.meshes[0].n_nodes for s in scenes]
+    bufs = [np.zeros((k, 3)) for k in n]
+    prev = [s.meshes[0].rest[:, 0].mean() for s in scenes]
+    xun = list(prev)                       # unwrapped centroid x
+    out = [{"kind": k, "gap": g, "outcome": "captured", "step": None, "x_max": xun[i] - x_plate}
+           for i, (k, g, _) in enumerate(case_list)]
+    t0 = time.perf_counter()
+    done = 0
+    while done < steps:
+        k = min(every, steps - done)
+        sim.step(k)
+        done += k
+        for c in range(len(scenes)):
+            rec = out[c]
+            if rec["outcome"] != "captured":
+                continue
+            sim.select(c)
+            if sim.diagnostics()[4] > 0:
+                rec["outcome"], rec["step"] = "unstable", done
+                continue
+            sim.all_nodes_into(bufs[c])
+            x = float(bufs[c][:, 0].mean())
+            d = x - prev[c]
+            d -= nx * np.round(d / nx)
+            xun[c] += d
+            prev[c] = x
+            rec["x_max"] = max(rec["x_max"], xun[c] - x_plate)
+            if xun[c] - x_plate > CELL_RADIUS[rec["kind"]] + 2.0:
+                rec["outcome"], rec["step"] = "passed", done
+        sim.select(0)
+    sim.synchronize()
+    wall = time.perf_counter() - t0
+    sim.close()
+    nodes = sum(s.dims[0] * s.dims[1] * s.dims[2] for s in scenes)
+    return out, {"steps": steps, "channels": len(scenes), "lattice_nodes": nodes, "seconds": wall,
+                 "mlups": nodes * steps / wall / 1e6}
+
+
+def thresholds(records):
+    """Smallest gap each kind passed, and the largest it did not."""
+    res = {}
+    for kind in sorted({r["kind"] for r in records}):
+        rs = [r for r in records if r["kind"] == kind]
+        passed = [r["gap"] for r in rs if r["outcome"] == "passed"]
+        blocked = [r["gap"] for r in rs if r["outcome"] == "captured"]
+        res[kind] = {"smallest_passed": min(passed) if passed else None,
+                     "largest_captured": max(blocked) if blocked else None}
+    return res
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("--steps", type=int, default=40000)
+    ap.add_argument("--gaps", default="2,4,6,8,10,12,14,16")
+    ap.add_argument("--every", type=int, default=250)
+    ap.add_argument("--force", type=float, default=1e-5, help="body force along x (lu)")
+    ap.add_argument("--ctc-moduli", default="", help="ks,kb,kal,kag,kv of the tumor cell (default: SOFT_CTC_MODULI)")
+    ap.add_argument("--rbc-moduli", default="", help="ks,kb,kal,kag,kv of the red cell (default: the stable set)")
+    args = ap.parse_args(argv)
+    gaps = [float(g) for g in args.gaps.split(",")]
+    mod = {"ctc": SOFT_CTC_MODULI}
+    for k, v in (("ctc", args.ctc_moduli), ("rbc", args.rbc_moduli)):
+        if v:
+            mod[k] = tuple(float(x) for x in v.split(","))
+    recs, perf = run(cases(gaps, steps=args.steps, body_force=args.force, moduli=mod), args.steps, args.every)
+    print(json.dumps({"force": args.force, "moduli": {k: list(v) for k, v in mod.items()}, "cases": recs,
+                      "thresholds": thresholds(recs), "run": perf}))
+
+
+if __name__ == "__main__":
+    main()

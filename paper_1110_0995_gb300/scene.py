@@ -376,6 +376,50 @@ def gap_sweep(seed: int = 21, n_channels: int = 24, steps: int = 5000) -> List[S
     return out
 
 
+def slit_barrier(dims, gap: float, x0: float, radius: float = 2.2, spacing: float = 3.0) -> np.ndarray:
+    """A plate of overlapping beads across the channel at x = x0 with a slit of
+    surface-to-surface width ``gap`` along z, centred in y.  Beads of radius
+    2.2 at a 3.0 pitch leave no fluid node between four neighbours (the
+    square's centre lies 2.12 from each), so the fluid and the cells cross
+    the plate only through the slit."""
+    nx, ny, nz = dims
+    yc = (ny - 1) / 2.0
+    out = []
+    for y in np.arange(-0.5, ny - 0.5 + spacing, spacing):
+        if abs(y - yc) < gap / 2.0 + radius:
+            continue
+        for z in np.arange(-0.5, nz - 0.5 + spacing, spacing):
+            out.append((x0, float(y), float(z), radius))
+    # the beads closest to the slit, on its two edges, at every z
+    for sgn in (-1.0, 1.0):
+        y = yc + sgn * (gap / 2.0 + radius)
+        for z in np.arange(-0.5, nz - 0.5 + spacing, spacing):
+            out.append((x0, float(y), float(z), radius))
+    a = quantize(np.array(out, dtype=np.float64).reshape(-1, 4), SPHERE_QUANTUM)
+    return a.astype(np.float32)
+
+
+def gap_cell(kind: str, gap: float, dims=(96, 40, 32), steps: int = 10000, body_force: float = 2e-5,
+             moduli=None) -> Scene:
+    """One cell upstream of a slit of width ``gap`` (Sec. 3 gap experiment):
+    a red cell edge-on to the slit (its disc in the x-z plane) or a tumor cell,
+    the stable moduli, collisions on so that the cell cannot enter the beads."""
+    nx, ny, nz = dims
+    x0 = nx / 2.0
+    spheres = slit_barrier(dims, gap, x0)
+    v, t = cell_template(kind)
+    if kind == "rbc":
+        v = v[:, [0, 2, 1]]          # disc axis along y: edge-on to a slit narrow in y
+        t = t[:, [0, 2, 1]]          # keep the outward orientation after the swap
+    r_cell = RBC_RADIUS if kind == "rbc" else CTC_RADIUS
+    centre = np.array([x0 - 2.2 - r_cell - 6.0, (ny - 1) / 2.0, (nz - 1) / 2.0])
+    rest = quantize(v + centre, POS_QUANTUM)
+    mesh = Mesh(kind, rest, np.ascontiguousarray(t, dtype=np.int32), STABLE[kind] if moduli is None else moduli)
+    return Scene(name=f"gap_{kind}_{gap:g}", dims=dims, tau=1.0, body_force=(body_force, 0.0, 0.0),
+                 periodic=(1, 0, 0), spheres=spheres, meshes=[mesh], steps=steps, seed=0,
+                 repulsion=(0.01, 1.0))
+
+
 def adjoint_channel(seed: int = 41, steps: int = 400) -> Scene:
     """128x64x64 channel with two 6-bead posts, 8 red cells and 1 tumor cell."""
     rng = np.random.default_rng(seed)

@@ -1,0 +1,65 @@
+"""Gap-threshold experiment (Sec. 3): geometry of the slit plate, the cells'
+placement, parity of a two-case batch against the oracle, and the two
+clear-cut outcomes (a red cell through a slit wider than itself, a tumor cell
+stopped by a slit a quarter of its diameter)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1110_0995_gb300 import gap_threshold, scene
+
+
+@pytest.mark.parametrize("gap", [2.0, 6.0, 12.0])
+def test_plate_is_closed_except_for_the_slit(gap):
+    sc = scene.gap_cell("rbc", gap)
+    nx, ny, nz = sc.dims
+    solid = oracle.rasterise(sc.spheres, sc.dims).reshape(nz, ny, nx)
+    blocked = solid[:, :, int(nx / 2) - 3:int(nx / 2) + 4].max(axis=2)   # any solid node across the plate
+    yc = (ny - 1) / 2.0
+    y = np.arange(ny)
+    outside = np.abs(y - yc) > gap / 2.0 + 1.0
+    assert blocked[:, outside].all()                       # no path around the slit
+    inside = np.abs(y - yc) < gap / 2.0
+    assert inside.any() and not blocked[:, inside].any()   # the slit itself is open
+
+
+@pytest.mark.parametrize("kind", ["rbc", "ctc"])
+def test_cell_starts_upstream_with_positive_volume(kind):
+    sc = scene.gap_cell(kind, 8.0)
+    m = sc.meshes[0]
+    S, V = oracle.mesh_area_volume(m.rest, m.tris)
+    assert V > 0 and S > 0
+    x_plate = sc.dims[0] / 2.0
+    assert m.rest[:, 0].max() < x_plate - 2.2 - 4.0        # clear of the plate
+    solid = oracle.rasterise(sc.spheres, sc.dims)
+    assert not solid.reshape(sc.dims[2], sc.dims[1], sc.dims[0])[
+        np.round(m.rest[:, 2]).astype(int), np.round(m.rest[:, 1]).astype(int),
+        np.round(m.rest[:, 0]).astype(int)].any()
+
+
+@pytest.mark.gpu
+def test_two_case_batch_matches_oracle():
+    from paper_1110_0995_gb300 import lbibm
+
+    cs = gap_threshold.cases([6.0], kinds=("rbc", "ctc"), steps=150, body_force=1e-5,
+                             moduli={"ctc": gap_threshold.SOFT_CTC_MODULI})
+    scenes = [c[2] for c in cs]
+    sim = lbibm.Simulation.from_scenes(scenes)
+    sim.step(150)
+    for k, sc in enumerate(scenes):
+        ref = oracle.System.from_scene(sc)
+        ref.step(150)
+        sim.select(k)
+        _, u = sim.fields()
+        _, uo = ref.fields()
+        assert np.linalg.norm(u - uo) / np.linalg.norm(uo) < 1e-5
+        assert np.abs(sim.nodes(0) - ref.nodes(0)).max() < 1e-5
+
+
+@pytest.mark.gpu
+def test_clear_outcomes():
+    recs, _ = gap_threshold.run(gap_threshold.cases([16.0, 4.0], kinds=("rbc", "ctc"), steps=6000, body_force=1e-5,
+                                                    moduli={"ctc": gap_threshold.SOFT_CTC_MODULI}), 6000, every=250)
+    out = {(r["kind"], r["gap"]): r["outcome"] for r in recs}
+    assert out[("rbc", 16.0)] == "passed"
+    assert out[("ctc", 4.0)] == "captured"
