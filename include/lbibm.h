@@ -107,7 +107,7 @@ lb_status lb_destroy(lb_ctx* ctx);
  * added to the membrane forces before spreading.  k = 0 (the default) turns
  * it off.  Before the first step; not with the differentiable variant
  * (LB_ERR_STATE).  Candidate lists hold 32 neighbour cells and 256 beads per
-X
+ * cell; an overflow is reported by lb_diagnostics (LB_ERR_STATE). */
 lb_status lb_set_repulsion(lb_ctx* ctx, double k, double dc);
 
 /* IB points with mass (Sec. 2.2: m d^2X/dt^2 = F; the coupling force comes
