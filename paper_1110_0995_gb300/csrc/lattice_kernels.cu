@@ -396,7 +396,7 @@ __device__ __forceinline__ void bounce_back(const S* src, long long NT, int gi, 
 // for 16-bit ones, the fastest of the budgets measured on GB300; two nodes per
 // thread: 512 (128 registers); four: 256 (255 registers).
 #ifndef LBIBM_K3_THREADS1
-#define LBIBM_K3_THREADS1 1280
+#define LBIBM_K3_THREADS1 1152
 #endif
 #ifndef LBIBM_K3_THREADS1_16
 #define LBIBM_K3_THREADS1_16 1024
@@ -535,9 +535,9 @@ __global__ void __launch_bounds__(BS, K3MinBlocks<S, NPT, BS>::value) k_stream_c
     const ChannelDev C = chan(a, c);   // registers: read once from the parameter bank
     const int lane = threadIdx.x & 31;
     const int p0 = ((b - C.blk0) * BS + (int)threadIdx.x) * NPT;   // first channel-local node of this thread
-    if constexpr (NPT == 1 && sizeof(S) == 2) {
-        // (measured on GB300: faster for 16-bit storage, slower for FP32 -- a
-        // register budget of 48 leaves no room for the extra live values)
+    if constexpr (NPT == 1) {
+        // (measured on GB300, 256x128x64 filter: FP32 62.4 -> 60.6 us with the
+        // 56-register budget, 16-bit 59.6 -> 57.5 us)
         const int pb = (b - C.blk0) * BS;
         if (C.nx % BS == 0 && pb + BS <= C.n) {
             // the block is a piece of one row: y and z are the block's

@@ -148,6 +148,34 @@ def test_tma_staged_variant_refused_where_it_does_not_apply():
         sim.set_kernel_config(-2, 256)
 
 
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+@pytest.mark.parametrize("bs", [128, 256])
+def test_row_aligned_blocks(storage, bs):
+    """One node per thread with nx a multiple of the block: every block is a
+    piece of one row (the y, z of the block path), walls, a moving wall,
+    obstacles, random state."""
+    sc = _ragged_scene((1, 0, 1), ((0, 0, 0), (0.02, 0, 0.01)), dims=(256, 13, 11))
+    sc.spheres = scene.quantize(sc.spheres * np.array([256 / 37, 13 / 23, 11 / 19, 1.0]),
+                                scene.SPHERE_QUANTUM).astype(np.float32)
+    sim = _sim(sc, storage=storage)
+    sim.set_kernel_config(1, bs)
+    ref = oracle.System.from_scene(sc)
+    f0 = ref.get_f() * (1 + 0.01 * scene.random_field(10, (19, ref.N)))
+    f0[:, ref.solid == 1] = ref.get_f()[:, ref.solid == 1]
+    ref.set_f(f0)
+    sim.set_populations(f0)
+    sim.step(25)
+    ref.step(25)
+    fluid = ref.solid == 0
+    _, u = sim.fields()
+    _, uo = ref.fields()
+    if storage == "f32":
+        assert rel_l2(u[:, fluid], uo[:, fluid]) < 1e-5
+        np.testing.assert_allclose(sim.populations()[:, fluid], ref.get_f()[:, fluid], rtol=0, atol=2e-7)
+    else:   # 16-bit storage of the shifted populations: one rounding per step
+        assert rel_l2(u[:, fluid], uo[:, fluid]) < 2e-2
+
+
 @pytest.mark.parametrize("npt,bs", [(-1, 128), (0, 256), (1, 256), (2, 256), (4, 128)])
 def test_plain_channel_every_kernel_variant(npt, bs):
     sc = scene.channel_plain(seed=1, steps=150)
