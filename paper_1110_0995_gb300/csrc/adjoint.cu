@@ -75,10 +75,7 @@ __device__ __forceinline__ V3 rel(const Q4& a, const Q4& b) {   // x_b - x_a
 }
 
 __device__ __forceinline__ void atomic_add3(float4* p, float x, float y, float z) {
-    float* f = reinterpret_cast<float*>(p);
-    atomicAdd(f, x);
-    atomicAdd(f + 1, y);
-    atomicAdd(f + 2, z);
+    atomicAdd(p, make_float4(x, y, z, 0.f));   // one 16-byte vector reduction
 }
 
 __device__ __forceinline__ const ChannelDev& achan(const AdjArgs& a) { return a.ch; }
@@ -117,57 +114,77 @@ __device__ __forceinline__ bool acorner(const ChannelDev& C, const Q4& q, int c,
     return ok;
 }
 
+// Eight lanes per IB node, lane c taking stencil corner c; partial sums are
+// added over the eight lanes by shuffles.
+constexpr int ADJ_SUB = 8;
+
+__device__ __forceinline__ float sub_sum(float v, unsigned smask) {
+#pragma unroll
+    for (int o = ADJ_SUB / 2; o > 0; o >>= 1) v += __shfl_xor_sync(smask, v, o);
+    return v;
+}
+
 // (B1) interpolation + advance, reversed: lam_u(x_c) += w_c lamX, and
 // lamX_out = lamX + sum_c grad w_c (u(x_c) . lamX).
 __global__ void k_adj_interp(const __grid_constant__ AdjArgs a) {
     pdl_entry();
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
     // the cycle's per-cell sums (B5) start from zero; the previous cycle's
     // reader (B6) has completed
-    for (int t = j; t < 2 * a.n_cells; t += gridDim.x * blockDim.x) a.lam_c[t] = 0.0;
-    if (j >= a.M) return;
+    for (int k = t; k < 2 * a.n_cells; k += gridDim.x * blockDim.x) a.lam_c[k] = 0.0;
+    const int j = t / ADJ_SUB, c = t & (ADJ_SUB - 1);
+    if (j >= a.M) return;   // whole groups of eight lanes leave together
+    const unsigned smask = 0xffu << (threadIdx.x & 24);
     const Q4 q = a.q_t[j];
     const float4 l = a.lamX[j];
-    float gx = l.x, gy = l.y, gz = l.z;
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        long long g;
-        float w;
-        float3 dw;
-        if (!acorner(a.ch, q, c, g, w, dw)) continue;
+    float gx = 0.f, gy = 0.f, gz = 0.f;
+    long long g;
+    float w;
+    float3 dw;
+    if (acorner(a.ch, q, c, g, w, dw)) {
         const float4 u = a.u_t[g];
         const float s = u.x * l.x + u.y * l.y + u.z * l.z;
-        gx += dw.x * s; gy += dw.y * s; gz += dw.z * s;
-        atomic_add3(a.lam_u + g, w * l.x, w * l.y, w * l.z);
+        gx = dw.x * s; gy = dw.y * s; gz = dw.z * s;
+        atomicAdd(a.lam_u + g, make_float4(w * l.x, w * l.y, w * l.z, 0.f));
     }
-    a.lamX_out[j] = make_float4(gx, gy, gz, 0.f);
+    gx = sub_sum(gx, smask);
+    gy = sub_sum(gy, smask);
+    gz = sub_sum(gz, smask);
+    if (c == 0) a.lamX_out[j] = make_float4(l.x + gx, l.y + gy, l.z + gz, 0.f);
 }
 
 // (B3) spreading, reversed: lamF_j = sum_c w_c lam_g(x_c);
 // lamX_out += sum_c grad w_c (F_j . lam_g(x_c)).
 __global__ void k_adj_spread(const __grid_constant__ AdjArgs a) {
     pdl_entry();
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = t / ADJ_SUB, c = t & (ADJ_SUB - 1);
     if (j >= a.M) return;
+    const unsigned smask = 0xffu << (threadIdx.x & 24);
     const Q4 q = a.q_t[j];
     const float4 F = a.F_t[j];
     float lx = 0.f, ly = 0.f, lz = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        long long g;
-        float w;
-        float3 dw;
-        if (!acorner(a.ch, q, c, g, w, dw)) continue;
-        if ((__ldg(a.mask + (g >> 5)) >> (g & 31)) & 1u) continue;
+    long long g;
+    float w;
+    float3 dw;
+    if (acorner(a.ch, q, c, g, w, dw) && !((__ldg(a.mask + (g >> 5)) >> (g & 31)) & 1u)) {
         const float4 lg = a.lam_g[g];
-        lx += w * lg.x; ly += w * lg.y; lz += w * lg.z;
+        lx = w * lg.x; ly = w * lg.y; lz = w * lg.z;
         const float s = F.x * lg.x + F.y * lg.y + F.z * lg.z;
-        gx += dw.x * s; gy += dw.y * s; gz += dw.z * s;
+        gx = dw.x * s; gy = dw.y * s; gz = dw.z * s;
     }
-    a.lamF[j] = make_float4(lx, ly, lz, 0.f);
-    float4 o = a.lamX_out[j];
-    o.x += gx; o.y += gy; o.z += gz;
-    a.lamX_out[j] = o;
+    lx = sub_sum(lx, smask);
+    ly = sub_sum(ly, smask);
+    lz = sub_sum(lz, smask);
+    gx = sub_sum(gx, smask);
+    gy = sub_sum(gy, smask);
+    gz = sub_sum(gz, smask);
+    if (c == 0) {
+        a.lamF[j] = make_float4(lx, ly, lz, 0.f);
+        float4 o = a.lamX_out[j];
+        o.x += gx; o.y += gy; o.z += gz;
+        a.lamX_out[j] = o;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -407,10 +424,10 @@ __global__ void k_adj_bead_grad(const __grid_constant__ AdjArgs a) {
 
 // ---- launchers ----
 cudaError_t launch_adj_interp(const AdjArgs& a, cudaStream_t s) {
-    return launch_ex(k_adj_interp, (a.M + 127) / 128, 128, 0, s, a.pdl, a);
+    return launch_ex(k_adj_interp, (ADJ_SUB * a.M + 127) / 128, 128, 0, s, a.pdl, a);
 }
 cudaError_t launch_adj_spread(const AdjArgs& a, cudaStream_t s) {
-    return launch_ex(k_adj_spread, (a.M + 127) / 128, 128, 0, s, a.pdl, a);
+    return launch_ex(k_adj_spread, (ADJ_SUB * a.M + 127) / 128, 128, 0, s, a.pdl, a);
 }
 cudaError_t launch_adj_membrane(const AdjArgs& a, cudaStream_t s) {
     cudaError_t e = cudaSuccess;
