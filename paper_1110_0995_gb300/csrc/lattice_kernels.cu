@@ -392,14 +392,15 @@ __device__ __forceinline__ void bounce_back(const S* src, long long NT, int gi, 
 }
 
 // Resident threads per SM the register budget is sized for.  One node per
-// thread: 1280 threads (48 registers) for FP32 populations, 1024 (64 registers)
-// for 16-bit ones, the fastest of the budgets measured on GB300; two nodes per
-// thread: 512 (128 registers); four: 256 (255 registers).
+// thread: 1152 threads (56 registers) for FP32 and for 16-bit populations, the
+// fastest of the budgets measured on GB300 with row-aligned blocks (FP32: 1280
+// 61.0 us, 1152 60.6, 1024 64.1; 16-bit: 1280 56.2, 1152 55.9, 1024 58.3); two
+// nodes per thread: 512 (128 registers); four: 256 (255 registers).
 #ifndef LBIBM_K3_THREADS1
 #define LBIBM_K3_THREADS1 1152
 #endif
 #ifndef LBIBM_K3_THREADS1_16
-#define LBIBM_K3_THREADS1_16 1024
+#define LBIBM_K3_THREADS1_16 1152
 #endif
 #ifndef LBIBM_K3_THREADS2
 #define LBIBM_K3_THREADS2 512
