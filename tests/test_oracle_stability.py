@@ -40,3 +40,32 @@ def test_stated_stretching_modulus_amplifies_perturbations():
 def test_stable_stretching_modulus_damps_perturbations():
     s = _sensitivity(scene.STABLE, [500, 500])
     assert s[1] < s[0] < 1e-7
+
+
+def _tumor_cell_at_rest(moduli, blocks=6, every=500):
+    """max |u| every `every` steps of a tumor cell (2562-node mesh, radius 8)
+    at rest in a still fluid, its nodes moved by 1e-6 lu."""
+    v, t = scene.cell_template("ctc")
+    rest = scene.quantize(v + np.array([19.5, 15.5, 15.5]), scene.POS_QUANTUM)
+    sc = scene.Scene(name="ctc_rest", dims=(40, 32, 32), tau=1.0, body_force=(0, 0, 0), periodic=(1, 0, 0),
+                     meshes=[scene.Mesh("ctc", rest, t, moduli)], steps=0)
+    s = oracle.System.from_scene(sc)
+    s.set_nodes(0, rest + 1e-6 * np.random.default_rng(0).standard_normal(rest.shape))
+    out = []
+    for _ in range(blocks):
+        s.step(every)
+        _, u = s.fields()
+        out.append(np.abs(u).max())
+    return out
+
+
+@pytest.mark.slow
+def test_tumor_cell_mesh_grows_at_the_stable_red_cell_moduli():
+    """The 2562-node tumor-cell mesh (edges ~0.6 lu) has a mode that the
+    explicit cycle amplifies at ks = 0.03, kb = kal = 0.01 (x5 per 500 steps
+    once it dominates), and damps at ks = kb = kal = 0.003: the long filter
+    runs end on it, and the gap experiment uses the softer set."""
+    grow = _tumor_cell_at_rest((0.03, 0.01, 0.01, 0.5, 0.9))
+    assert grow[5] > 20 * grow[3] and grow[5] > 1e-6
+    soft = _tumor_cell_at_rest((0.003, 0.003, 0.003, 0.5, 0.9))
+    assert soft[5] < soft[1] < 2e-8
