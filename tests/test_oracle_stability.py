@@ -60,11 +60,11 @@ def _tumor_cell_at_rest(moduli, blocks=6, every=500):
 
 
 @pytest.mark.slow
-def test_tumor_cell_mesh_grows_at_the_stable_red_cell_moduli():
+def test_tumor_cell_mesh_grows_at_ks_0_03_and_damps_at_0_003():
     """The 2562-node tumor-cell mesh (edges ~0.6 lu) has a mode that the
     explicit cycle amplifies at ks = 0.03, kb = kal = 0.01 (x5 per 500 steps
-    once it dominates), and damps at ks = kb = kal = 0.003: the long filter
-    runs end on it, and the gap experiment uses the softer set."""
+    once it dominates), and damps at ks = kb = kal = 0.003, the workloads'
+    tumor-cell set."""
     grow = _tumor_cell_at_rest((0.03, 0.01, 0.01, 0.5, 0.9))
     assert grow[5] > 20 * grow[3] and grow[5] > 1e-6
     soft = _tumor_cell_at_rest((0.003, 0.003, 0.003, 0.5, 0.9))
