@@ -402,7 +402,12 @@ cudaError_t launch_compact_groups(const uint8_t* map, int n_groups, int* list, i
 // ---------------------------------------------------------------------------
 constexpr int FS_BLOCK = 128;
 
-__global__ void __launch_bounds__(FS_BLOCK, IB_MIN_BLOCKS) k_forces_spread(const __grid_constant__ IbmArgs a) {
+#ifndef LBIBM_FS_MINB
+#define LBIBM_FS_MINB 10
+#endif
+// (massless points: 48 registers, 10 blocks of 128 per SM; with mass: 64, 8)
+template <bool MASSIVE>
+__global__ void __launch_bounds__(FS_BLOCK, MASSIVE ? IB_MIN_BLOCKS : LBIBM_FS_MINB) k_forces_spread(const __grid_constant__ IbmArgs a) {
     const int i = (blockIdx.x * FS_BLOCK + threadIdx.x) / SUB;
     const int sl = threadIdx.x & (SUB - 1);
     const bool live = i < a.n_nodes;
@@ -470,7 +475,7 @@ __global__ void __launch_bounds__(FS_BLOCK, IB_MIN_BLOCKS) k_forces_spread(const
     uint8_t* fl = a.par ? a.fl1 : a.fl0;
     const unsigned active = __activemask();
     float3 S = F;   // what reaches the fluid
-    if (a.W) {
+    if (MASSIVE) {
         // points with mass (Sec. 2.2 Newton equation): the fluid velocity of
         // the last collision at X (this lane's corner, summed over the eight
         // lanes), kick by F, exact drag drift; the fluid receives the drag's
@@ -516,7 +521,8 @@ __global__ void __launch_bounds__(FS_BLOCK, IB_MIN_BLOCKS) k_forces_spread(const
 cudaError_t launch_forces_spread(const IbmArgs& a, cudaStream_t s) {
     if (a.n_nodes <= 0) return cudaSuccess;
     const long long threads = (long long)a.n_nodes * SUB;
-    return launch_ex(k_forces_spread, (unsigned)((threads + FS_BLOCK - 1) / FS_BLOCK), FS_BLOCK, 0, s, a.pdl, a);
+    if (a.W) return launch_ex(k_forces_spread<true>, (unsigned)((threads + FS_BLOCK - 1) / FS_BLOCK), FS_BLOCK, 0, s, a.pdl, a);
+    return launch_ex(k_forces_spread<false>, (unsigned)((threads + FS_BLOCK - 1) / FS_BLOCK), FS_BLOCK, 0, s, a.pdl, a);
 }
 
 // ---------------------------------------------------------------------------
