@@ -216,6 +216,23 @@ def adjoint_ratio(steps: int = 400, ckpt_every: int = 50):
                                    "FP64 oracle's dual numbers in tests/test_gpu_adjoint.py"}
 
 
+def max_over_ranks(values, device="cuda"):
+    """The element-wise maximum of a list of floats over all ranks (the job's
+    time is its slowest replica's)."""
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def job_mlups(world: int, nodes_per_replica: int, steps: int, ms: float) -> float:
+    """Whole-job MLUPS of `world` replicas that each advance `nodes_per_replica`
+    nodes `steps` times, timed at `ms` milliseconds (the slowest replica)."""
+    return world * nodes_per_replica * steps / (ms * 1e-3) / 1e6
+
+
 def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
 
@@ -327,12 +344,8 @@ def run_ours(args):
     # the per-kernel durations (events add a few microseconds per launch)
     ms_ev, kms, _, diag_ev, clk_ev = timed_pass(15)
     if world > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([ms, ms_ev], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, ms_ev = (float(v) for v in t.tolist())
-    value = world * n_nodes * args.steps / (ms * 1e-3) / 1e6
+        ms, ms_ev = max_over_ranks([ms, ms_ev])
+    value = job_mlups(world, n_nodes, args.steps, ms)
 
     # roofline of the dominant kernel (fused stream-collide)
     k3_ms = kms[2] / max(1, kn[2])             # kn: launches per class (same in both passes)
