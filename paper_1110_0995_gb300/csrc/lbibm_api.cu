@@ -1407,6 +1407,28 @@ lb_status lb_get_mask(lb_ctx* ctx, uint8_t* solid) {
     return LB_OK;
 }
 
+namespace {
+// Directed edges a -> b of one mesh with an int each, kept per tail node
+// (valence <= 64, so a lookup scans a handful of entries).
+struct DirEdges {
+    std::vector<std::vector<std::pair<int, int>>> out;
+    explicit DirEdges(int n) : out(n) {}
+    int* find(int a, int b) {
+        for (auto& e : out[a])
+            if (e.first == b) return &e.second;
+        return nullptr;
+    }
+    void put(int a, int b, int v) {
+        if (int* p = find(a, b)) *p = v;
+        else out[a].emplace_back(b, v);
+    }
+    int at(int a, int b) {
+        int* p = find(a, b);
+        return p ? *p : -1;
+    }
+};
+}  // namespace
+
 lb_status ibm_add_mesh(lb_ctx* ctx, const double* rest_xyz, int n, const int32_t* tris, int nt,
                        const ibm_moduli* mod, int* mesh_id) {
     LB_GUARD(ctx);
@@ -1419,35 +1441,40 @@ lb_status ibm_add_mesh(lb_ctx* ctx, const double* rest_xyz, int n, const int32_t
         if (!std::isfinite(rest_xyz[k]) || std::fabs(rest_xyz[k]) > 4.0e6)
             return fail(ctx, LB_ERR_ARG, "node positions must be finite and |x| < 4e6");
     // directed edge -> third vertex
-    std::map<std::pair<int, int>, int> third;
+    DirEdges third(n);
     std::vector<int> out_deg(n, 0);
     for (int t = 0; t < nt; ++t) {
         const int v[3] = {tris[3 * t], tris[3 * t + 1], tris[3 * t + 2]};
-        for (int k = 0; k < 3; ++k) {
+        for (int k = 0; k < 3; ++k)
             if (v[k] < 0 || v[k] >= n) return fail(ctx, LB_ERR_ARG, "triangle index out of range");
-            const std::pair<int, int> key(v[k], v[(k + 1) % 3]);
-            if (key.first == key.second) return fail(ctx, LB_ERR_ARG, "degenerate triangle");
-            if (third.count(key)) return fail(ctx, LB_ERR_ARG, "mesh is not an oriented 2-manifold (edge used twice)");
-            third[key] = v[(k + 2) % 3];
-            out_deg[v[k]]++;
+        for (int k = 0; k < 3; ++k) {
+            const int a = v[k], b = v[(k + 1) % 3];
+            if (a == b) return fail(ctx, LB_ERR_ARG, "degenerate triangle");
+            if (third.find(a, b)) return fail(ctx, LB_ERR_ARG, "mesh is not an oriented 2-manifold (edge used twice)");
+            if ((int)third.out[a].size() >= MAX_VALENCE)
+                return fail(ctx, LB_ERR_ARG, "mesh vertex is not a single fan (non-manifold) or valence > 64");
+            third.put(a, b, v[(k + 2) % 3]);
+            out_deg[a]++;
         }
     }
-    for (auto& kv : third)
-        if (!third.count(std::make_pair(kv.first.second, kv.first.first)))
-            return fail(ctx, LB_ERR_ARG, "mesh is not closed");
-    // node rings, counter-clockwise seen from outside: ring[j+1] = third(i -> ring[j])
+    for (int a = 0; a < n; ++a) {
+        std::sort(third.out[a].begin(), third.out[a].end());
+        for (const auto& e : third.out[a])
+            if (!third.find(e.first, a)) return fail(ctx, LB_ERR_ARG, "mesh is not closed");
+    }
+    // node rings, counter-clockwise seen from outside: ring[j+1] = third(i -> ring[j]),
+    // each starting at the node's smallest neighbour
     std::vector<std::vector<int>> ringv(n);
-    for (auto& kv : third) {
-        const int i = kv.first.first;
-        if (!ringv[i].empty()) continue;
-        int a = kv.first.second;
+    for (int i = 0; i < n; ++i) {
+        if (third.out[i].empty()) continue;
+        int a = third.out[i][0].first;
         std::vector<int>& r = ringv[i];
         for (int guard = 0; guard <= MAX_VALENCE; ++guard) {
             r.push_back(a);
-            a = third[std::make_pair(i, a)];
-            if (a == r[0]) break;
+            a = third.at(i, a);
+            if (a < 0 || a == r[0]) break;
         }
-        if ((int)r.size() != out_deg[i] || (int)r.size() > MAX_VALENCE)
+        if ((int)r.size() != out_deg[i] || (int)r.size() > MAX_VALENCE || a != r[0])
             return fail(ctx, LB_ERR_ARG, "mesh vertex is not a single fan (non-manifold) or valence > 64");
     }
     for (int i = 0; i < n; ++i)
@@ -1467,8 +1494,8 @@ lb_status ibm_add_mesh(lb_ctx* ctx, const double* rest_xyz, int n, const int32_t
 
     auto theta0 = [&](int a, int b) {
         if (a > b) std::swap(a, b);
-        const int c = third[std::make_pair(a, b)];
-        const int d = third[std::make_pair(b, a)];
+        const int c = third.at(a, b);
+        const int d = third.at(b, a);
         return dihedral_host(x + 3 * a, x + 3 * b, x + 3 * c, x + 3 * d);
     };
     const int node0 = (int)ctx->hq0.size();
@@ -1484,28 +1511,28 @@ lb_status ibm_add_mesh(lb_ctx* ctx, const double* rest_xyz, int n, const int32_t
     // triangles, and for each directed edge u -> v the triangle and position
     // of u in it; edges (a, b) with a < b in triangle order
     const int tri0 = (int)ctx->htris.size();
-    std::map<std::pair<int, int>, int> tri_of;    // directed edge -> 3 t + position
-    std::map<std::pair<int, int>, int> edge_of;   // (a, b), a < b -> edge index
+    DirEdges tri_of(n);    // directed edge -> 3 t + position
+    DirEdges edge_of(n);   // (a, b), a < b -> edge index
     for (int t = 0; t < nt; ++t) {
         const int v[3] = {tris[3 * t], tris[3 * t + 1], tris[3 * t + 2]};
         ctx->htris.push_back(make_int4(node0 + v[0], node0 + v[1], node0 + v[2], cell));
         ctx->htriS0.push_back((float)tri_area_host(x + 3 * v[0], x + 3 * v[1], x + 3 * v[2]));
         for (int k = 0; k < 3; ++k) {
             const int a = v[k], b = v[(k + 1) % 3];
-            tri_of[std::make_pair(a, b)] = 3 * (tri0 + t) + k;
+            tri_of.put(a, b, 3 * (tri0 + t) + k);
             if (a < b) {
-                const int c = third[std::make_pair(a, b)], d = third[std::make_pair(b, a)];
+                const int c = third.at(a, b), d = third.at(b, a);
                 const double* xa = x + 3 * a;
                 const double* xb = x + 3 * b;
                 const double L0 = std::sqrt((xb[0] - xa[0]) * (xb[0] - xa[0]) + (xb[1] - xa[1]) * (xb[1] - xa[1]) +
                                             (xb[2] - xa[2]) * (xb[2] - xa[2]));
-                edge_of[std::make_pair(a, b)] = (int)ctx->hedges.size();
+                edge_of.put(a, b, (int)ctx->hedges.size());
                 ctx->hedges.push_back(make_int4(node0 + a, node0 + b, node0 + c, node0 + d));
                 ctx->hedge_rest.push_back(make_float4((float)L0, (float)theta0(a, b), (float)mod->ks, (float)mod->kb));
             }
         }
     }
-    auto edge_id = [&](int u, int v) { return edge_of[std::make_pair(std::min(u, v), std::max(u, v))]; };
+    auto edge_id = [&](int u, int v) { return edge_of.at(std::min(u, v), std::max(u, v)); };
     for (int i = 0; i < n; ++i) {
         ctx->hq0.push_back(q0[i]);
         ctx->hq.push_back(q0[i]);
@@ -1515,7 +1542,7 @@ lb_status ibm_add_mesh(lb_ctx* ctx, const double* rest_xyz, int n, const int32_t
         for (int j = 0; j < k; ++j) {
             // slot j: triangle (i, nb, nx), edge (i, nb), opposite edge (nb, nx)
             const int nb = r[j], nx = r[(j + 1) % k];
-            const int tk = tri_of[std::make_pair(i, nb)];
+            const int tk = tri_of.at(i, nb);
             const int role1 = i < nb ? 0 : 1;    // i is a or b of edge (i, nb)
             const int role2 = nb < nx ? 2 : 3;   // i is c or d of edge (nb, nx)
             ctx->hslots.push_back(make_int4(tk, 4 * edge_id(i, nb) + role1, 4 * edge_id(nb, nx) + role2, tk / 3));

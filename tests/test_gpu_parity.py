@@ -334,6 +334,36 @@ def test_async_readback_matches_sync():
     assert np.array_equal(bufs[1], expect)
 
 
+def test_mesh_validation():
+    """ibm_add_mesh accepts a closed, outward, manifold mesh and refuses the
+    rest with LB_ERR_ARG: a missing face, inward orientation, an edge used
+    twice, an index out of range, a degenerate face, an isolated node."""
+    from paper_1110_0995_gb300 import lbibm
+
+    x, t = scene.icosphere(1)
+    x = 2.0 * x + 8.0
+    sc = scene.Scene(name="box", dims=(16, 16, 16), periodic=(1, 1, 1), steps=0)
+
+    def add(xx, tt):
+        sim = _sim(sc)
+        try:
+            sim.add_mesh(xx, tt, (0.01, 0.01, 0.01, 0.5, 0.9))
+            return True
+        except lbibm.LbError as e:
+            assert e.status == lbibm.LB_ERR_ARG
+            return False
+
+    assert add(x, t)
+    assert not add(x, t[1:])                                    # open
+    assert not add(x, t[:, ::-1])                               # inward
+    assert not add(x, np.concatenate([t, t[:1]]))               # edge used twice
+    bad = t.copy(); bad[0, 0] = len(x)
+    assert not add(x, bad)                                      # index out of range
+    bad = t.copy(); bad[0, 1] = bad[0, 0]
+    assert not add(x, bad)                                      # degenerate
+    assert not add(np.concatenate([x, [[8.0, 8.0, 8.0]]]), t)  # isolated node
+
+
 def test_micropost_filter_runs_its_20000_steps():
     """The 256x128x64 filter (62 cells, 120 beads) over its stated horizon:
     finite, mass conserved, velocities well below the lattice sound speed."""
