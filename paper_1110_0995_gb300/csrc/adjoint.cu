@@ -230,9 +230,8 @@ __device__ __forceinline__ void edge_forces(const V3& xb, const V3& xc, const V3
 // Jacobian-vector product along lamF: one forward-mode evaluation per edge,
 // seeded with the adjoint itself (relative to vertex a, the seeds are
 // lamF_v - lamF_a).
-__global__ void __launch_bounds__(128) k_adj_edges(const __grid_constant__ AdjArgs a) {
-    pdl_entry();
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void adj_edges_block(const AdjArgs& a, int blk) {
+    const int e = blk * blockDim.x + threadIdx.x;
     double gks = 0.0, gkb = 0.0;
     if (e < a.n_edges) {
         const int4 ev = a.edges[e];
@@ -293,9 +292,8 @@ __device__ __forceinline__ void tri_forces(const V3& xb, const V3& xc, float S0t
 // One thread per (triangle, column): column v*3+k seeds coordinate k of vertex
 // b or c (v = 0, 1); the column of a is minus their sum.  The column-0 thread
 // also forms the per-cell products and keeps the normal.
-__global__ void __launch_bounds__(128, 6) k_adj_tris(const __grid_constant__ AdjArgs a) {
-    pdl_entry();
-    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void adj_tris_block(const AdjArgs& a, int blk) {
+    const int tid = blk * blockDim.x + threadIdx.x;
     const int t = tid / 6, col = tid - 6 * (tid / 6);
     const bool valid = t < a.n_tris;   // every lane stays for the per-cell warp sums
     int cell = -1;
@@ -345,6 +343,14 @@ __global__ void __launch_bounds__(128, 6) k_adj_tris(const __grid_constant__ Adj
         }
         rem &= ~__ballot_sync(AFULL, mine);
     }
+}
+
+// (B4) + (B5) in one launch: blocks [0, edge_blocks) take the edges, the rest
+// the triangle columns (the two are independent; B6 follows).
+__global__ void __launch_bounds__(128, 6) k_adj_membrane(const __grid_constant__ AdjArgs a, int edge_blocks) {
+    pdl_entry();
+    if ((int)blockIdx.x < edge_blocks) adj_edges_block(a, blockIdx.x);
+    else adj_tris_block(a, (int)blockIdx.x - edge_blocks);
 }
 
 // (B6) the cell's global terms: lam_S = lam_c1 kag / S0, lam_V = lam_c2 kv / (6 V0);
@@ -430,12 +436,10 @@ cudaError_t launch_adj_spread(const AdjArgs& a, cudaStream_t s) {
     return launch_ex(k_adj_spread, (ADJ_SUB * a.M + 127) / 128, 128, 0, s, a.pdl, a);
 }
 cudaError_t launch_adj_membrane(const AdjArgs& a, cudaStream_t s) {
-    cudaError_t e = cudaSuccess;
-    if (a.n_edges > 0) e = launch_ex(k_adj_edges, (a.n_edges + 127) / 128, 128, 0, s, a.pdl, a);
-    if (a.n_tris > 0 && e == cudaSuccess) {
-        e = launch_ex(k_adj_tris, (6 * a.n_tris + 127) / 128, 128, 0, s, a.pdl, a);
-        if (e == cudaSuccess) e = launch_ex(k_adj_tris_global, (a.n_tris + 127) / 128, 128, 0, s, a.pdl, a);
-    }
+    const int eb = (a.n_edges + 127) / 128, tb = (6 * a.n_tris + 127) / 128;
+    if (eb + tb == 0) return cudaSuccess;
+    cudaError_t e = launch_ex(k_adj_membrane, eb + tb, 128, 0, s, a.pdl, a, eb);
+    if (a.n_tris > 0 && e == cudaSuccess) e = launch_ex(k_adj_tris_global, (a.n_tris + 127) / 128, 128, 0, s, a.pdl, a);
     return e;
 }
 cudaError_t launch_adj_bead_grad(const AdjArgs& a, cudaStream_t s) {
