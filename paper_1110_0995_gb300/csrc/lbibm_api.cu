@@ -1408,24 +1408,42 @@ lb_status lb_get_mask(lb_ctx* ctx, uint8_t* solid) {
 }
 
 namespace {
-// Directed edges a -> b of one mesh with an int each, kept per tail node
-// (valence <= 64, so a lookup scans a handful of entries).
+// Directed edges a -> b of one mesh with an int each, stored per tail node in
+// one flat array (a node's slots are as many as the triangles around it, at
+// most the valence limit, so a lookup scans a handful of entries).
 struct DirEdges {
-    std::vector<std::vector<std::pair<int, int>>> out;
-    explicit DirEdges(int n) : out(n) {}
+    std::vector<int> off, cnt, key, val;
+    DirEdges(int n, const int32_t* tris, int nt) : off(n + 1, 0), cnt(n, 0), key(3 * (size_t)nt), val(3 * (size_t)nt) {
+        for (int k = 0; k < 3 * nt; ++k) off[tris[k] + 1]++;
+        for (int i = 0; i < n; ++i) off[i + 1] += off[i];
+    }
+    int size(int a) const { return cnt[a]; }
     int* find(int a, int b) {
-        for (auto& e : out[a])
-            if (e.first == b) return &e.second;
+        for (int i = off[a]; i < off[a] + cnt[a]; ++i)
+            if (key[i] == b) return &val[i];
         return nullptr;
     }
     void put(int a, int b, int v) {
-        if (int* p = find(a, b)) *p = v;
-        else out[a].emplace_back(b, v);
+        if (int* p = find(a, b)) {
+            *p = v;
+            return;
+        }
+        key[off[a] + cnt[a]] = b;
+        val[off[a] + cnt[a]] = v;
+        cnt[a]++;
     }
     int at(int a, int b) {
         int* p = find(a, b);
         return p ? *p : -1;
     }
+    void sort_node(int a) {   // by head vertex (insertion sort: a handful of entries)
+        for (int i = off[a] + 1; i < off[a] + cnt[a]; ++i)
+            for (int j = i; j > off[a] && key[j - 1] > key[j]; --j) {
+                std::swap(key[j - 1], key[j]);
+                std::swap(val[j - 1], val[j]);
+            }
+    }
+    int first(int a) const { return key[off[a]]; }
 };
 }  // namespace
 
@@ -1441,33 +1459,33 @@ lb_status ibm_add_mesh(lb_ctx* ctx, const double* rest_xyz, int n, const int32_t
         if (!std::isfinite(rest_xyz[k]) || std::fabs(rest_xyz[k]) > 4.0e6)
             return fail(ctx, LB_ERR_ARG, "node positions must be finite and |x| < 4e6");
     // directed edge -> third vertex
-    DirEdges third(n);
+    for (int k = 0; k < 3 * nt; ++k)
+        if (tris[k] < 0 || tris[k] >= n) return fail(ctx, LB_ERR_ARG, "triangle index out of range");
+    DirEdges third(n, tris, nt);
     std::vector<int> out_deg(n, 0);
     for (int t = 0; t < nt; ++t) {
         const int v[3] = {tris[3 * t], tris[3 * t + 1], tris[3 * t + 2]};
-        for (int k = 0; k < 3; ++k)
-            if (v[k] < 0 || v[k] >= n) return fail(ctx, LB_ERR_ARG, "triangle index out of range");
         for (int k = 0; k < 3; ++k) {
             const int a = v[k], b = v[(k + 1) % 3];
             if (a == b) return fail(ctx, LB_ERR_ARG, "degenerate triangle");
             if (third.find(a, b)) return fail(ctx, LB_ERR_ARG, "mesh is not an oriented 2-manifold (edge used twice)");
-            if ((int)third.out[a].size() >= MAX_VALENCE)
-                return fail(ctx, LB_ERR_ARG, "mesh vertex is not a single fan (non-manifold) or valence > 64");
             third.put(a, b, v[(k + 2) % 3]);
             out_deg[a]++;
         }
     }
     for (int a = 0; a < n; ++a) {
-        std::sort(third.out[a].begin(), third.out[a].end());
-        for (const auto& e : third.out[a])
-            if (!third.find(e.first, a)) return fail(ctx, LB_ERR_ARG, "mesh is not closed");
+        if (out_deg[a] > MAX_VALENCE)
+            return fail(ctx, LB_ERR_ARG, "mesh vertex is not a single fan (non-manifold) or valence > 64");
+        third.sort_node(a);
+        for (int i = third.off[a]; i < third.off[a] + third.cnt[a]; ++i)
+            if (!third.find(third.key[i], a)) return fail(ctx, LB_ERR_ARG, "mesh is not closed");
     }
     // node rings, counter-clockwise seen from outside: ring[j+1] = third(i -> ring[j]),
     // each starting at the node's smallest neighbour
     std::vector<std::vector<int>> ringv(n);
     for (int i = 0; i < n; ++i) {
-        if (third.out[i].empty()) continue;
-        int a = third.out[i][0].first;
+        if (third.size(i) == 0) continue;
+        int a = third.first(i);
         std::vector<int>& r = ringv[i];
         for (int guard = 0; guard <= MAX_VALENCE; ++guard) {
             r.push_back(a);
@@ -1511,8 +1529,8 @@ lb_status ibm_add_mesh(lb_ctx* ctx, const double* rest_xyz, int n, const int32_t
     // triangles, and for each directed edge u -> v the triangle and position
     // of u in it; edges (a, b) with a < b in triangle order
     const int tri0 = (int)ctx->htris.size();
-    DirEdges tri_of(n);    // directed edge -> 3 t + position
-    DirEdges edge_of(n);   // (a, b), a < b -> edge index
+    DirEdges tri_of(n, tris, nt);    // directed edge -> 3 t + position
+    DirEdges edge_of(n, tris, nt);   // (a, b), a < b -> edge index
     for (int t = 0; t < nt; ++t) {
         const int v[3] = {tris[3 * t], tris[3 * t + 1], tris[3 * t + 2]};
         ctx->htris.push_back(make_int4(node0 + v[0], node0 + v[1], node0 + v[2], cell));
