@@ -601,13 +601,10 @@ long long to_fixed(double x) { return std::llround(x * FIX_SCALE); }
 
 // Extra nodes between population planes.  Planes of exactly 2^k nodes put all
 // 38 read / write streams of the stream-collide kernel at identical large
-// power-of-two offsets; a pad staggers them across DRAM channels.
-long long plane_pad() {
-    const char* e = std::getenv("LBIBM_PLANE_PAD");
-    long long v = e ? std::atoll(e) : 1088;
-    if (v < 0) v = 0;
-    return (v + 63) / 64 * 64;
-}
+// power-of-two offsets; a pad (a multiple of 64 nodes) staggers them across
+// DRAM channels.
+constexpr long long PLANE_PAD = 1088;
+long long plane_pad() { return PLANE_PAD; }
 
 // Grid of the stream-collide kernel for a (nodes per thread, block size)
 // variant: channel k's blocks start at blk0 and cover its padded node range.
