@@ -334,6 +334,31 @@ def test_async_readback_matches_sync():
     assert np.array_equal(bufs[1], expect)
 
 
+def test_api_edge_cases():
+    """Zero steps do nothing, negative steps and out-of-range channels, slots
+    and variants are refused with LB_ERR_ARG, and a context with no meshes
+    steps the lattice alone; the fields before any step are the rest state."""
+    from paper_1110_0995_gb300 import lbibm
+
+    sc = _ragged_scene(G=(0, 0, 0))
+    sim = _sim(sc)
+    rho, u = sim.fields()
+    assert np.all(rho == 1.0) and np.all(u == 0.0)
+    sim.step(0)
+    assert sim.steps_done == 0
+    for call in (lambda: sim.step(-1), lambda: sim.select(1), lambda: sim.select(-1),
+                 lambda: sim.set_kernel_config(3, 128), lambda: sim.set_kernel_config(1, 96),
+                 lambda: sim.all_nodes_into_async(np.zeros((1, 3)), 2), lambda: sim.wait_readback(5),
+                 lambda: sim.set_schedule(3)):
+        with pytest.raises(lbibm.LbError) as e:
+            call()
+        assert e.value.status == lbibm.LB_ERR_ARG
+    sim.step(5)
+    assert sim.steps_done == 5
+    rho, u = sim.fields()
+    assert np.abs(rho - 1.0).max() < 1e-6 and np.abs(u).max() < 1e-7   # no force, no meshes: at rest
+
+
 def test_mesh_validation():
     """ibm_add_mesh accepts a closed, outward, manifold mesh and refuses the
     rest with LB_ERR_ARG: a missing face, inward orientation, an edge used
