@@ -124,6 +124,16 @@ lb_status lb_set_repulsion(lb_ctx* ctx, double k, double dc);
  * variant or lb_adjoint.  Uses the sequential schedule. */
 lb_status lb_set_ib_dynamics(lb_ctx* ctx, double mass, double gamma);
 
+/* Deterministic cycle (on = 1): the spreading kernel accumulates the force
+ * density in 64-bit fixed point (2^-40; integer sums do not depend on the
+ * order of the atomic additions) and a conversion kernel writes it to the
+ * FP32 force field, so that repeated runs give bit-identical populations and
+ * positions (one more kernel per cycle, 24 bytes per lattice node).  on = 0
+ * (the default): FP32 atomic additions, whose order varies from run to run at
+ * the rounding level.  Not with collisions (LB_ERR_STATE); the adjoint keeps
+ * FP32 atomics.  Uses the sequential schedule. */
+lb_status lb_set_deterministic(lb_ctx* ctx, int on);
+
 /* Velocities W of one mesh's points (n x 3, host) after the last step
  * (zeros for massless points). */
 lb_status ibm_get_velocities(lb_ctx* ctx, int mesh_id, double* v);

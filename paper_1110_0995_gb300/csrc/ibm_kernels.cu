@@ -510,8 +510,18 @@ __global__ void __launch_bounds__(FS_BLOCK, MASSIVE ? IB_MIN_BLOCKS : LBIBM_FS_M
         if (grp2 >= 0 && (__ffs(same2) - 1) == (int)(threadIdx.x & 31)) fl[grp2] = 1;
     }
 
-    // spreading: g(x) += w(x - X) S at this lane's corner
-    if (hit) atomicAdd((a.par ? a.g1 : a.g0) + g, make_float4(w * S.x, w * S.y, w * S.z, 0.f));
+    // spreading: g(x) += w(x - X) S at this lane's corner; in 2^-40 fixed
+    // point when deterministic (integer sums do not depend on their order)
+    if (hit) {
+        if (a.gfix) {
+            const float c[3] = {w * S.x, w * S.y, w * S.z};
+#pragma unroll
+            for (int d = 0; d < 3; ++d)
+                atomicAdd(a.gfix + d * a.gfix_stride + g, (unsigned long long)__float2ll_rn(c[d] * FIX_SCALE_F));
+        } else {
+            atomicAdd((a.par ? a.g1 : a.g0) + g, make_float4(w * S.x, w * S.y, w * S.z, 0.f));
+        }
+    }
     // flag the 32-node groups that received force: one store per distinct group of this warp
     const long long grp = hit ? (g >> 5) : -1;
     const unsigned same = __match_any_sync(active, grp);
@@ -523,6 +533,28 @@ cudaError_t launch_forces_spread(const IbmArgs& a, cudaStream_t s) {
     const long long threads = (long long)a.n_nodes * SUB;
     if (a.W) return launch_ex(k_forces_spread<true>, (unsigned)((threads + FS_BLOCK - 1) / FS_BLOCK), FS_BLOCK, 0, s, a.pdl, a);
     return launch_ex(k_forces_spread<false>, (unsigned)((threads + FS_BLOCK - 1) / FS_BLOCK), FS_BLOCK, 0, s, a.pdl, a);
+}
+
+// Deterministic spreading: the fixed-point force density of the flagged
+// 32-node groups into g (one warp per group; a group's flag is the same for
+// all its lanes), clearing the fixed-point sums for the next step.
+__global__ void __launch_bounds__(256) k_gfix_to_g(const __grid_constant__ IbmArgs a) {
+    pdl_entry();
+    const long long gi = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gi >= a.gfix_stride) return;
+    if (!(a.par ? a.fl1 : a.fl0)[gi >> 5]) return;
+    unsigned long long* p = a.gfix + gi;
+    const long long x = (long long)p[0], y = (long long)p[a.gfix_stride], z = (long long)p[2 * a.gfix_stride];
+    const float inv = 1.0f / FIX_SCALE_F;
+    (a.par ? a.g1 : a.g0)[gi] = make_float4((float)x * inv, (float)y * inv, (float)z * inv, 0.f);
+    p[0] = 0ull;
+    p[a.gfix_stride] = 0ull;
+    p[2 * a.gfix_stride] = 0ull;
+}
+
+cudaError_t launch_gfix_to_g(const IbmArgs& a, cudaStream_t s) {
+    if (!a.gfix || a.gfix_stride <= 0) return cudaSuccess;
+    return launch_ex(k_gfix_to_g, (unsigned)((a.gfix_stride + 255) / 256), 256, 0, s, a.pdl, a);
 }
 
 // ---------------------------------------------------------------------------

@@ -131,6 +131,8 @@ struct lb_ctx {
     // collisions (soft sphere): off while rep_k == 0
     float rep_k = 0.f, rep_dc = 0.f;
     double ib_m = 0.0, ib_gamma = 0.0;   // IB points with mass (ib_m > 0) and drag
+    bool deterministic = false;          // fixed-point spreading, run-to-run identical results
+    unsigned long long* gfix = nullptr;  // [3][Ntot] its sums
     float4* W = nullptr;                 // [M] their velocities
     int rep_cap = 0, rep_nb = 0;
     float4 *rep_R = nullptr, *rep_bounds = nullptr;
@@ -295,6 +297,10 @@ IbmArgs ibm_args(const lb_ctx* ctx, int par, bool overlapped = false) {
     a.fl1 = ctx->fl[1];
     a.u = ctx->u;
     a.R = ctx->rep_k > 0.f ? ctx->rep_R : nullptr;
+    if (ctx->deterministic && ctx->gfix) {
+        a.gfix = ctx->gfix;
+        a.gfix_stride = ctx->Ntot;
+    }
     if (ctx->ib_m > 0.0 && ctx->W) {
         // kick / exact drag drift constants: a = gamma / m, p1 = (1 - e^-a) / a, E = e^-a
         const double m = ctx->ib_m, gam = ctx->ib_gamma, aa = gam / m;
@@ -388,7 +394,7 @@ lb_status enqueue_step(lb_ctx* ctx, int par) {
         if (k == 3 && ctx->W) continue;   // points with mass move in the spreading kernel
         EventPair ep{};
         const bool timed = (ctx->timing >> k) & 1;
-        ctx->launches[k] += 1;
+        ctx->launches[k] += (k == 1 && ctx->deterministic) ? 2 : 1;   // + the fixed-point conversion
         if (timed) {
             ep.a = take_event(ctx);
             ep.b = take_event(ctx);
@@ -398,7 +404,10 @@ lb_status enqueue_step(lb_ctx* ctx, int par) {
         cudaError_t e = cudaSuccess;
         switch (k) {
             case 0: e = launch_elements(ia, ctx->stream); break;
-            case 1: e = launch_forces_spread(ia, ctx->stream); break;
+            case 1:
+                e = launch_forces_spread(ia, ctx->stream);
+                if (e == cudaSuccess && ia.gfix) e = launch_gfix_to_g(ia, ctx->stream);
+                break;
             case 2: e = k3_launch(ctx, la, ctx->k3, ctx->stream); break;
             case 3: e = launch_interp_advance(ia, ctx->stream); break;
         }
@@ -495,7 +504,8 @@ lb_status enqueue_step_overlap(lb_ctx* ctx, int par, bool lead_interp) {
 
 bool use_overlap(const lb_ctx* ctx) {
     const long long m = ctx->committed ? ctx->M : (long long)ctx->hq0.size();
-    return ctx->overlap && m > 0 && ctx->phi == nullptr && ctx->rep_k == 0.f && ctx->ib_m == 0.0 && ctx->k3.npt == 1 &&
+    return ctx->overlap && m > 0 && ctx->phi == nullptr && ctx->rep_k == 0.f && ctx->ib_m == 0.0 && !ctx->deterministic &&
+           ctx->k3.npt == 1 &&
            ctx->timing == 0 && ctx->ib_stream != nullptr;
 }
 
@@ -969,6 +979,7 @@ lb_status lb_set_repulsion(lb_ctx* ctx, double k, double dc) {
     if (!(k >= 0.0) || !(dc > 0.0) || !std::isfinite(k) || !std::isfinite(dc))
         return fail(ctx, LB_ERR_ARG, "need k >= 0 and dc > 0");
     if (k > 0.0 && ctx->phi) return fail(ctx, LB_ERR_STATE, "collisions are not part of the differentiable variant");
+    if (k > 0.0 && ctx->deterministic) return fail(ctx, LB_ERR_STATE, "collisions accumulate with float atomics");
     ctx->rep_k = (float)k;
     ctx->rep_dc = (float)dc;
     drop_graphs(ctx);
@@ -985,6 +996,21 @@ lb_status lb_set_ib_dynamics(lb_ctx* ctx, double mass, double gamma) {
     ctx->ib_m = mass;
     ctx->ib_gamma = gamma;
     drop_graphs(ctx);
+    return LB_OK;
+}
+
+lb_status lb_set_deterministic(lb_ctx* ctx, int on) {
+    LB_GUARD(ctx);
+    if (on != 0 && on != 1) return fail(ctx, LB_ERR_ARG, "on must be 0 or 1");
+    if (on && ctx->rep_k > 0.f) return fail(ctx, LB_ERR_STATE, "collisions accumulate with float atomics");
+    LB_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (on && !ctx->gfix) {
+        LB_CUDA(dalloc(ctx, &ctx->gfix, 3 * (size_t)ctx->Ntot));
+        LB_CUDA(cudaMemsetAsync(ctx->gfix, 0, sizeof(unsigned long long) * 3 * (size_t)ctx->Ntot, ctx->stream));
+    }
+    if ((on != 0) != ctx->deterministic) drop_graphs(ctx);
+    ctx->deterministic = on != 0;
+    ctx->dvalid = false;
     return LB_OK;
 }
 
@@ -1078,6 +1104,7 @@ lb_status store_step(lb_ctx* ctx, int k) {
     ia.qb = par ? qs : qd;
     ia.F = W.seg_F + (size_t)k * ctx->M;
     ia.cell_rel = W.seg_rel + (size_t)k * ctx->C;
+    ia.gfix = nullptr;   // the adjoint's forward spreads with float atomics
     // programmatic dependents as in the plain cycle, except the segment's
     // first kernel (it follows the zeroing of the segment's force slots)
     ia.pdl = ctx->pdl && k > 0;
@@ -1658,7 +1685,8 @@ lb_status lb_step(lb_ctx* ctx, int n_steps) {
         const int n = n_steps - k >= GRAPH_BLOCK ? GRAPH_BLOCK : 1;
         LB_CUDA(cudaGraphLaunch(n > 1 ? ctx->gexec_blk[par] : ctx->gexec[par], ctx->stream));
         for (int c = 0; c < 4; ++c)
-            if ((ctx->M > 0 || c == 2) && !(c == 3 && ctx->W)) ctx->launches[c] += n;
+            if ((ctx->M > 0 || c == 2) && !(c == 3 && ctx->W))
+                ctx->launches[c] += (c == 1 && ctx->deterministic) ? 2 * n : n;   // + the fixed-point conversion
         if (ctx->M > 0 && ctx->rep_k > 0.f) ctx->launches[1] += 4 * n;   // collision kernels
         ctx->step += n;
         k += n;

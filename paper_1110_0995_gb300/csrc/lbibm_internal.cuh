@@ -223,6 +223,10 @@ struct IbmArgs {
     // fluid receiving J = gamma p1 (V - U); U interpolated at X from u
     float4* W;            // [M] point velocities carried between steps
     float ib_inv_m, ib_gp1, ib_p1, ib_E;
+    // deterministic spreading (null: float atomics): force density in 2^-40
+    // fixed point, [3][gfix_stride], converted to g by k_gfix_to_g
+    unsigned long long* gfix;
+    long long gfix_stride;
     // overlapped schedule: map receiving the next step's stencil set, the
     // current step's set (every spread target must lie in it) and the count
     // of spread targets found outside it
@@ -368,6 +372,7 @@ cudaError_t launch_diagnostics(const LatticeArgs& a, int ch_index, double* parti
 cudaError_t launch_cell_sums(const IbmArgs& a, cudaStream_t s);
 cudaError_t launch_elements(const IbmArgs& a, cudaStream_t s);
 cudaError_t launch_forces_spread(const IbmArgs& a, cudaStream_t s);
+cudaError_t launch_gfix_to_g(const IbmArgs& a, cudaStream_t s);
 cudaError_t launch_interp_advance(const IbmArgs& a, cudaStream_t s);
 cudaError_t launch_positions_to_double(const Q4* q, int n, double* out, cudaStream_t s);
 

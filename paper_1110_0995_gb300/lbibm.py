@@ -20,7 +20,7 @@ STORAGE = {"f32": 0, "f16": 1, "bf16": 2}
 
 # Every entry point that include/lbibm.h declares.
 EXPORTS = (
-    "lb_create", "lb_create_batch", "lb_select_channel", "lb_destroy", "lb_set_obstacles", "lb_set_brinkman", "lb_adjoint", "lb_set_repulsion", "lb_set_ib_dynamics",
+    "lb_create", "lb_create_batch", "lb_select_channel", "lb_destroy", "lb_set_obstacles", "lb_set_brinkman", "lb_adjoint", "lb_set_repulsion", "lb_set_ib_dynamics", "lb_set_deterministic",
     "ibm_get_velocities", "ibm_add_mesh",
     "ibm_set_nodes", "lb_step", "lb_synchronize", "lb_get_fields", "lb_get_populations", "lb_set_populations",
     "ibm_get_nodes", "ibm_get_all_nodes", "ibm_get_forces", "ibm_get_area_volume", "lb_diagnostics", "lb_get_step", "lb_save_state",
@@ -94,6 +94,7 @@ def lib():
             "lb_set_brinkman": ([P, P, I, D, D], I),
             "lb_set_repulsion": ([P, D, D], I),
             "lb_set_ib_dynamics": ([P, D, D], I),
+            "lb_set_deterministic": ([P, I], I),
             "ibm_get_velocities": ([P, I, P], I),
             "lb_adjoint": ([P, I, I, I, P, P, P, P], I),
             "lb_set_schedule": ([P, I], I),
@@ -331,6 +332,10 @@ class Simulation:
     def set_ib_dynamics(self, mass: float, gamma: float):
         """IB points with mass and drag (kick + exact drag drift); mass 0: massless points."""
         self._check(self._L.lb_set_ib_dynamics(self._h, float(mass), float(gamma)))
+
+    def set_deterministic(self, on: bool = True):
+        """Fixed-point spreading: bit-identical results from run to run."""
+        self._check(self._L.lb_set_deterministic(self._h, int(bool(on))))
 
     def velocities(self, mesh: int) -> np.ndarray:
         """Point velocities after the last step (zeros for massless points)."""

@@ -334,6 +334,34 @@ def test_async_readback_matches_sync():
     assert np.array_equal(bufs[1], expect)
 
 
+def test_deterministic_cycle_is_bit_reproducible():
+    """Fixed-point spreading: two runs give bit-identical populations and
+    positions (FP32 atomics do not), and the result matches the oracle and
+    the default cycle within the usual tolerances."""
+    from paper_1110_0995_gb300 import lbibm
+
+    sc = scene.small_filter(seed=5, steps=0)
+    runs = []
+    for det in (True, True, False):
+        sim = _sim(sc)
+        sim.set_deterministic(det)
+        for n in (37, 8, 55):
+            sim.step(n)
+        runs.append((sim.populations(), np.concatenate([sim.nodes(m) for m in range(len(sc.meshes))]),
+                     sim.fields()[1]))
+    assert np.array_equal(runs[0][0], runs[1][0]) and np.array_equal(runs[0][1], runs[1][1])
+    assert rel_l2(runs[0][2], runs[2][2]) < 1e-6
+    assert np.abs(runs[0][1] - runs[2][1]).max() < 1e-6
+    ref = oracle.System.from_scene(sc)
+    ref.step(100)
+    assert rel_l2(runs[0][2], ref.fields()[1]) < 1e-5
+    assert np.abs(runs[0][1] - np.concatenate([ref.nodes(m) for m in range(len(sc.meshes))])).max() < 1e-5
+    with pytest.raises(lbibm.LbError):
+        sim2 = _sim(sc)
+        sim2.set_deterministic(True)
+        sim2.set_repulsion(0.01, 1.0)
+
+
 def test_api_edge_cases():
     """Zero steps do nothing, negative steps and out-of-range channels, slots
     and variants are refused with LB_ERR_ARG, and a context with no meshes
