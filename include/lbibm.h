@@ -210,7 +210,7 @@ lb_status lb_step(lb_ctx* ctx, int n_steps);
  * block_size 256 or 512 = nodes per tile); FP32 storage, one channel, walls
  * (not periodic) in y and z, nx in {32, 64, 128, 256} dividing block_size and
  * ny a multiple of block_size / nx.  A block that gives up waiting for its
- * copies makes lb_diagnostics return LB_ERR_STATE.  The default is 1 node per
+ * copies makes lb_diagnostics return LB_ERR_TIMEOUT.  The default is 1 node per
  * thread, 128 threads.  LB_ERR_ARG for an unsupported pair.  Results do not
  * depend on the variant. */
 lb_status lb_set_kernel_config(lb_ctx* ctx, int nodes_per_thread, int block_size);
@@ -352,7 +352,11 @@ lb_status bead_relax(double* xyz, const double* moments, int n, const bead_param
  * out[0] = sum of rho over fluid nodes, out[1..3] = sum of sum_i e_i f_i
  * after the last collision, out[4] = number of non-finite populations,
  * out[5] = max |u| over fluid nodes.  Returns LB_ERR_NUMERIC when out[4] > 0
- * or out[5] > `u_max` (pass u_max <= 0 to skip the bound). */
+ * or out[5] > `u_max` (pass u_max <= 0 to skip the bound), or when an IB
+ * point moved a lattice unit in one step under the overlapped schedule;
+ * LB_ERR_STATE when the collision candidate lists overflowed; LB_ERR_TIMEOUT
+ * when a block of the TMA-staged variant gave up waiting for its copies.  The
+ * sums are filled in every case. */
 lb_status lb_diagnostics(lb_ctx* ctx, double u_max, double out[6]);
 
 /* Number of completed steps. */

@@ -2056,7 +2056,7 @@ lb_status lb_diagnostics(lb_ctx* ctx, double u_max, double out[6]) {
     LB_CUDA(cudaMemcpy(serr2, ctx->sched_err, 2 * sizeof(int), cudaMemcpyDeviceToHost));
     if (serr2[0] > 0)
         return fail(ctx, LB_ERR_NUMERIC, "an IB point moved a lattice unit or more in one step (overlapped schedule)");
-    if (serr2[1] > 0) return fail(ctx, LB_ERR_STATE, "a TMA-staged stream-collide block gave up waiting for its copies");
+    if (serr2[1] > 0) return fail(ctx, LB_ERR_TIMEOUT, "a TMA-staged stream-collide block gave up waiting for its copies");
     if (u_max > 0 && !(out[5] <= u_max)) return fail(ctx, LB_ERR_NUMERIC, "velocity above the stability bound");
     return LB_OK;
 }
