@@ -34,9 +34,10 @@ CELL_RADIUS = {"rbc": scene.RBC_RADIUS, "ctc": scene.CTC_RADIUS}
 SOFT_CTC_MODULI = scene.STABLE_CTC_MODULI
 
 
-def cases(gaps, kinds=("rbc", "ctc"), dims=(96, 40, 32), steps=10000, body_force=2e-5, moduli=None):
+def cases(gaps, kinds=("rbc", "ctc"), dims=(96, 40, 32), steps=10000, body_force=2e-5, moduli=None,
+          table1=False):
     moduli = moduli or {}
-    return [(k, float(g), scene.gap_cell(k, float(g), dims, steps, body_force, moduli.get(k))) for k in kinds
+    return [(k, float(g), scene.gap_cell(k, float(g), dims, steps, body_force, moduli.get(k), table1)) for k in kinds
             for g in gaps]
 
 
@@ -106,14 +107,17 @@ def main(argv=None):
     ap.add_argument("--force", type=float, default=1e-5, help="body force along x (lu)")
     ap.add_argument("--ctc-moduli", default="", help="ks,kb,kal,kag,kv of the tumor cell (default: the stable set)")
     ap.add_argument("--rbc-moduli", default="", help="ks,kb,kal,kag,kv of the red cell (default: the stable set)")
+    ap.add_argument("--table1", action="store_true",
+                    help="the paper's cell models: 400 / 306-node meshes, Table 1 moduli (red-cell K^V 0.9)")
     args = ap.parse_args(argv)
     gaps = [float(g) for g in args.gaps.split(",")]
     mod = {}
     for k, v in (("ctc", args.ctc_moduli), ("rbc", args.rbc_moduli)):
         if v:
             mod[k] = tuple(float(x) for x in v.split(","))
-    recs, perf = run(cases(gaps, steps=args.steps, body_force=args.force, moduli=mod), args.steps, args.every)
-    print(json.dumps({"force": args.force, "moduli": {k: list(v) for k, v in mod.items()}, "cases": recs,
+    recs, perf = run(cases(gaps, steps=args.steps, body_force=args.force, moduli=mod, table1=args.table1), args.steps,
+                     args.every)
+    print(json.dumps({"force": args.force, "table1": args.table1, "moduli": {k: list(v) for k, v in mod.items()}, "cases": recs,
                       "thresholds": thresholds(recs), "run": perf}))
 
 

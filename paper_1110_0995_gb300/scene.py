@@ -381,6 +381,39 @@ def gap_sweep(seed: int = 21, n_channels: int = 24, steps: int = 5000) -> List[S
     return out
 
 
+# The paper's cell models (Table 1): 400-node red cell and 306-node tumor
+# cell (796 and 608 triangles, i.e. closed triangulations of the sphere),
+# diameters 8 and 16 um (lu here).  Moduli as printed, except the red cell's
+# K^V = 10, which the explicit massless cycle does not hold (the oracle
+# diverges within 500 steps; 0.9 is stable).
+TABLE1_MODULI = {"rbc": (0.008, 0.0016, 0.01, 1.0, 0.9), "ctc": (0.0023, 0.000464, 0.0029, 0.29, 2.9)}
+TABLE1_NODES = {"rbc": 400, "ctc": 306}
+
+
+def fibonacci_sphere_mesh(n: int) -> Tuple[np.ndarray, np.ndarray]:
+    """n near-uniform unit-sphere points (Fibonacci lattice) and their convex
+    hull as outward counter-clockwise triangles (2n - 4 of them)."""
+    from scipy.spatial import ConvexHull
+
+    i = np.arange(n) + 0.5
+    phi = np.arccos(1.0 - 2.0 * i / n)
+    th = np.pi * (1.0 + 5.0 ** 0.5) * i
+    u = np.stack([np.cos(th) * np.sin(phi), np.sin(th) * np.sin(phi), np.cos(phi)], axis=1)
+    t = ConvexHull(u).simplices.astype(np.int32)
+    c = u[t].mean(axis=1)
+    nrm = np.cross(u[t[:, 1]] - u[t[:, 0]], u[t[:, 2]] - u[t[:, 0]])
+    flip = (nrm * c).sum(axis=1) < 0
+    t[flip] = t[flip][:, [0, 2, 1]]
+    return u, t
+
+
+def table1_template(kind: str) -> Tuple[np.ndarray, np.ndarray]:
+    """Rest shape of the paper's cell model centred at the origin."""
+    u, t = fibonacci_sphere_mesh(TABLE1_NODES[kind])
+    v = biconcave(u, RBC_RADIUS) if kind == "rbc" else CTC_RADIUS * u
+    return v, t
+
+
 def slit_barrier(dims, gap: float, x0: float, radius: float = 2.2, spacing: float = 3.0) -> np.ndarray:
     """A plate of overlapping beads across the channel at x = x0 with a slit of
     surface-to-surface width ``gap`` along z, centred in y.  Beads of radius
@@ -405,21 +438,23 @@ def slit_barrier(dims, gap: float, x0: float, radius: float = 2.2, spacing: floa
 
 
 def gap_cell(kind: str, gap: float, dims=(96, 40, 32), steps: int = 10000, body_force: float = 2e-5,
-             moduli=None) -> Scene:
+             moduli=None, table1: bool = False) -> Scene:
     """One cell upstream of a slit of width ``gap`` (Sec. 3 gap experiment):
     a red cell edge-on to the slit (its disc in the x-z plane) or a tumor cell,
     the stable moduli, collisions on so that the cell cannot enter the beads."""
     nx, ny, nz = dims
     x0 = nx / 2.0
     spheres = slit_barrier(dims, gap, x0)
-    v, t = cell_template(kind)
+    v, t = table1_template(kind) if table1 else cell_template(kind)
     if kind == "rbc":
         v = v[:, [0, 2, 1]]          # disc axis along y: edge-on to a slit narrow in y
         t = t[:, [0, 2, 1]]          # keep the outward orientation after the swap
     r_cell = RBC_RADIUS if kind == "rbc" else CTC_RADIUS
     centre = np.array([x0 - 2.2 - r_cell - 6.0, (ny - 1) / 2.0, (nz - 1) / 2.0])
     rest = quantize(v + centre, POS_QUANTUM)
-    mesh = Mesh(kind, rest, np.ascontiguousarray(t, dtype=np.int32), STABLE[kind] if moduli is None else moduli)
+    if moduli is None:
+        moduli = TABLE1_MODULI[kind] if table1 else STABLE[kind]
+    mesh = Mesh(kind, rest, np.ascontiguousarray(t, dtype=np.int32), moduli)
     return Scene(name=f"gap_{kind}_{gap:g}", dims=dims, tau=1.0, body_force=(body_force, 0.0, 0.0),
                  periodic=(1, 0, 0), spheres=spheres, meshes=[mesh], steps=steps, seed=0,
                  repulsion=(0.01, 1.0))

@@ -63,3 +63,17 @@ def test_clear_outcomes():
     out = {(r["kind"], r["gap"]): r["outcome"] for r in recs}
     assert out[("rbc", 16.0)] == "passed"
     assert out[("ctc", 4.0)] == "captured"
+
+
+@pytest.mark.parametrize("kind,n,nt,diam", [("rbc", 400, 796, 8.0), ("ctc", 306, 608, 16.0)])
+def test_table1_cell_models(kind, n, nt, diam):
+    """The paper's cell models (Table 1): node and triangle counts, a closed
+    outward surface, the stated diameter."""
+    pytest.importorskip("scipy")
+    v, t = scene.table1_template(kind)
+    assert v.shape == (n, 3) and t.shape == (nt, 3)
+    S, V = oracle.mesh_area_volume(v, t)
+    assert V > 0 and S > 0
+    e = np.sort(np.concatenate([t[:, [0, 1]], t[:, [1, 2]], t[:, [2, 0]]]), axis=1)
+    assert len(np.unique(e, axis=0)) * 2 == len(e)     # every edge in exactly two triangles
+    assert np.ptp(v[:, 0]) == pytest.approx(diam, rel=0.02)
