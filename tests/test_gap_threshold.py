@@ -2,6 +2,8 @@
 placement, parity of a two-case batch against the oracle, and the two
 clear-cut outcomes (a red cell through a slit wider than itself, a tumor cell
 stopped by a slit a quarter of its diameter)."""
+import os
+
 import numpy as np
 import pytest
 
@@ -77,3 +79,32 @@ def test_table1_cell_models(kind, n, nt, diam):
     e = np.sort(np.concatenate([t[:, [0, 1]], t[:, [1, 2]], t[:, [2, 0]]]), axis=1)
     assert len(np.unique(e, axis=0)) * 2 == len(e)     # every edge in exactly two triangles
     assert np.ptp(v[:, 0]) == pytest.approx(diam, rel=0.02)
+
+
+def _table1():
+    rows = {}
+    with open(os.path.join(os.path.dirname(__file__), "golden", "table1_cell_parameters.txt")) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                name, rbc, ctc = line.split()
+                rows[name] = {"rbc": float(rbc), "ctc": float(ctc)}
+    return rows
+
+
+@pytest.mark.parametrize("kind", ["rbc", "ctc"])
+def test_table1_values_as_printed(kind):
+    """The cell models carry Table 1's printed values: (ks, kb, kal, kag, kv)
+    and the mesh sizes.  One value is a stated departure: the red cell's
+    volume modulus K^V = 10 diverges under the explicit cycle and is held at
+    0.9."""
+    t1 = _table1()
+    ks, kb, kal, kag, kv = scene.TABLE1_MODULI[kind]
+    assert (ks, kb, kal, kag) == (t1["K_s"][kind], t1["K_b"][kind], t1["K_A_l"][kind], t1["K_A_g"][kind])
+    assert kv == (0.9 if kind == "rbc" else t1["K_V"][kind])
+    n = scene.TABLE1_NODES[kind]
+    assert n == t1["mesh_nodes"][kind]
+    # a closed triangulated sphere has 2 n - 4 triangles (Euler: V - E + F = 2)
+    assert 2 * n - 4 == t1["mesh_triangles"][kind]
+    radius = scene.RBC_RADIUS if kind == "rbc" else scene.CTC_RADIUS
+    # one lattice unit stands for one micrometre
+    assert 2 * radius == t1["diameter_um"][kind]
