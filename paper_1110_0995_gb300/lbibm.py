@@ -124,6 +124,25 @@ def _ptr(a: np.ndarray):
     return a.ctypes.data_as(ctypes.c_void_p)
 
 
+def _f64_out(out: np.ndarray, n_points: int) -> np.ndarray:
+    """Check a caller's output buffer for n_points x 3 doubles before the
+    library writes into it: float64, C-contiguous, writable and large enough."""
+    if not isinstance(out, np.ndarray) or out.dtype != np.float64 or not out.flags.c_contiguous \
+            or not out.flags.writeable:
+        raise ValueError("output buffer must be a writable C-contiguous float64 array")
+    if out.size < 3 * n_points:
+        raise ValueError(f"output buffer holds {out.size} doubles, {3 * n_points} needed")
+    return out
+
+
+def _f64_in(xyz, n_points: int) -> np.ndarray:
+    """n_points x 3 doubles, C-contiguous; raises on any other size."""
+    x = np.ascontiguousarray(xyz, dtype=np.float64)
+    if x.size != 3 * n_points:
+        raise ValueError(f"expected {n_points} x 3 coordinates, got {x.shape}")
+    return x
+
+
 def make_params(dims, tau=1.0, body_force=(0.0, 0.0, 0.0), periodic=(1, 0, 0),
                 wall_velocity=((0, 0, 0), (0, 0, 0)), storage="f32") -> LbParams:
     p = LbParams()
@@ -151,6 +170,7 @@ class Simulation:
         self.dims = [(p.nx, p.ny, p.nz) for p in params]
         self.n_mesh_nodes = [[] for _ in params]
         self.channel = 0
+        self._n_beads = 0
 
     # -- construction ------------------------------------------------------
     @classmethod
@@ -225,8 +245,14 @@ class Simulation:
         self.n_mesh_nodes[self.channel].append(int(x.shape[0]))
         return mid.value
 
+    def _mesh_nodes(self, mesh: int) -> int:
+        meshes = self.n_mesh_nodes[self.channel]
+        if not 0 <= int(mesh) < len(meshes):
+            raise IndexError(f"mesh {mesh} out of range (channel {self.channel} has {len(meshes)})")
+        return meshes[int(mesh)]
+
     def set_nodes(self, mesh: int, xyz: np.ndarray):
-        x = np.ascontiguousarray(xyz, dtype=np.float64)
+        x = _f64_in(xyz, self._mesh_nodes(mesh))
         self._check(self._L.ibm_set_nodes(self._h, int(mesh), _ptr(x)))
 
     # -- stepping ----------------------------------------------------------
@@ -262,27 +288,31 @@ class Simulation:
         self._check(self._L.lb_set_populations(self._h, _ptr(ff)))
 
     def nodes(self, mesh: int) -> np.ndarray:
-        x = np.zeros((self.n_mesh_nodes[self.channel][mesh], 3))
+        x = np.zeros((self._mesh_nodes(mesh), 3))
         self._check(self._L.ibm_get_nodes(self._h, int(mesh), _ptr(x)))
         return x
 
     def nodes_into(self, mesh: int, out: np.ndarray):
+        out = _f64_out(out, self._mesh_nodes(mesh))
         self._check(self._L.ibm_get_nodes(self._h, int(mesh), _ptr(out)))
 
     def all_nodes_into(self, out: np.ndarray):
         """Positions of every mesh of the selected channel, concatenated (one transfer)."""
+        out = _f64_out(out, sum(self.n_mesh_nodes[self.channel]))
         self._check(self._L.ibm_get_all_nodes(self._h, _ptr(out)))
 
     def all_nodes_into_async(self, out: np.ndarray, slot: int):
         """Enqueue the readback of every mesh's positions of the selected channel into
-        `out` (page-locked for overlap); complete after wait_readback(slot)."""
+        `out` (page-locked for overlap); complete after wait_readback(slot).  `out`
+        must stay alive until then."""
+        out = _f64_out(out, sum(self.n_mesh_nodes[self.channel]))
         self._check(self._L.ibm_get_all_nodes_async(self._h, _ptr(out), int(slot)))
 
     def wait_readback(self, slot: int):
         self._check(self._L.lb_readback_wait(self._h, int(slot)))
 
     def forces(self, mesh: int) -> np.ndarray:
-        f = np.zeros((self.n_mesh_nodes[self.channel][mesh], 3))
+        f = np.zeros((self._mesh_nodes(mesh), 3))
         self._check(self._L.ibm_get_forces(self._h, int(mesh), _ptr(f)))
         return f
 
@@ -339,7 +369,7 @@ class Simulation:
 
     def velocities(self, mesh: int) -> np.ndarray:
         """Point velocities after the last step (zeros for massless points)."""
-        v = np.zeros((self.n_mesh_nodes[self.channel][mesh], 3))
+        v = np.zeros((self._mesh_nodes(mesh), 3))
         self._check(self._L.ibm_get_velocities(self._h, int(mesh), _ptr(v)))
         return v
 
@@ -350,7 +380,8 @@ class Simulation:
         self._n_beads = int(b.shape[0])
 
     def adjoint(self, n_steps: int, ckpt_every: int = 50, objective_mesh: int = 0) -> dict:
-        """J and its gradient (bead centres, ks, kb of the objective cell) by the discrete adjoint."""
+        """J and its gradient (bead centres, ks, kb of the objective cell) by the discrete adjoint
+        (after set_brinkman)."""
         nb = self._n_beads
         J = ctypes.c_double()
         gks = ctypes.c_double()

@@ -45,3 +45,25 @@ def test_null_context_is_rejected_without_gpu():
     p = lbibm.make_params((4, 4, 4), tau=0.5)
     assert L.lb_create(ctypes.byref(p), None, ctypes.byref(out)) == lbibm.LB_ERR_ARG
     assert not out.value
+
+
+def test_binding_checks_caller_buffers():
+    """The binding refuses a buffer the library would write past or read past
+    (wrong dtype, layout, size) before any call crosses the C ABI."""
+    import numpy as np
+
+    from paper_1110_0995_gb300 import lbibm
+
+    ok = np.zeros((10, 3))
+    assert lbibm._f64_out(ok, 10) is ok
+    assert lbibm._f64_out(np.zeros(40), 10) is not None          # larger is fine
+    for bad in (np.zeros((9, 3)), np.zeros((10, 3), np.float32), np.zeros((3, 10)).T):
+        with pytest.raises(ValueError):
+            lbibm._f64_out(bad, 10)
+    ro = np.zeros((10, 3))
+    ro.flags.writeable = False
+    with pytest.raises(ValueError):
+        lbibm._f64_out(ro, 10)
+    assert lbibm._f64_in(np.ones((10, 3), np.float32), 10).dtype == np.float64
+    with pytest.raises(ValueError):
+        lbibm._f64_in(np.ones((11, 3)), 10)
