@@ -2069,8 +2069,10 @@ struct StateHeader {
     int64_t Ntot;
     int32_t storage;
     int32_t M;
+    int32_t massive;   // 1: the IB points carry velocities W, saved after F
+    int32_t reserved;
 };
-constexpr uint64_t STATE_MAGIC = 0x4c4249424d535431ULL;
+constexpr uint64_t STATE_MAGIC = 0x4c4249424d535432ULL;
 }  // namespace
 
 lb_status lb_save_state(lb_ctx* ctx, void* buf, size_t* bytes) {
@@ -2083,10 +2085,11 @@ lb_status lb_save_state(lb_ctx* ctx, void* buf, size_t* bytes) {
     const size_t fb = (size_t)ctx->Ntot / GROUP;
     const size_t qb = (size_t)ctx->M * sizeof(Q4);
     const size_t Fb = (size_t)ctx->M * sizeof(float4);
-    const size_t total = sizeof(StateHeader) + hb + gb + fb + qb + Fb;
+    const size_t Wb = ctx->W ? Fb : 0;
+    const size_t total = sizeof(StateHeader) + hb + gb + fb + qb + Fb + Wb;
     if (!buf) { *bytes = total; return LB_OK; }
     if (*bytes < total) return fail(ctx, LB_ERR_ARG, "checkpoint buffer too small");
-    StateHeader hd{STATE_MAGIC, ctx->step, ctx->Ntot, (int32_t)ctx->storage, ctx->M};
+    StateHeader hd{STATE_MAGIC, ctx->step, ctx->Ntot, (int32_t)ctx->storage, ctx->M, ctx->W ? 1 : 0, 0};
     char* p = (char*)buf;
     std::memcpy(p, &hd, sizeof(hd));
     p += sizeof(hd);
@@ -2098,6 +2101,7 @@ lb_status lb_save_state(lb_ctx* ctx, void* buf, size_t* bytes) {
     if (ctx->M) {
         LB_CUDA(cudaMemcpy(p, ctx->q[par], qb, cudaMemcpyDeviceToHost)); p += qb;
         LB_CUDA(cudaMemcpy(p, ctx->F, Fb, cudaMemcpyDeviceToHost)); p += Fb;
+        if (ctx->W) { LB_CUDA(cudaMemcpy(p, ctx->W, Wb, cudaMemcpyDeviceToHost)); p += Wb; }
     }
     *bytes = total;
     return LB_OK;
@@ -2110,14 +2114,16 @@ lb_status lb_load_state(lb_ctx* ctx, const void* buf, size_t bytes) {
     if (s != LB_OK) return s;
     StateHeader hd;
     std::memcpy(&hd, buf, sizeof(hd));
-    if (hd.magic != STATE_MAGIC || hd.Ntot != ctx->Ntot || hd.storage != (int32_t)ctx->storage || hd.M != ctx->M)
+    if (hd.magic != STATE_MAGIC || hd.Ntot != ctx->Ntot || hd.storage != (int32_t)ctx->storage || hd.M != ctx->M ||
+        hd.massive != (ctx->W ? 1 : 0))
         return fail(ctx, LB_ERR_ARG, "checkpoint does not match this context");
     const size_t hb = (size_t)Q * ctx->plane * pop_bytes(ctx->storage);
     const size_t gb = (size_t)ctx->Ntot * sizeof(float4);
     const size_t fb = (size_t)ctx->Ntot / GROUP;
     const size_t qb = (size_t)ctx->M * sizeof(Q4);
     const size_t Fb = (size_t)ctx->M * sizeof(float4);
-    if (bytes < sizeof(StateHeader) + hb + gb + fb + qb + Fb) return fail(ctx, LB_ERR_ARG, "checkpoint truncated");
+    const size_t Wb = ctx->W ? Fb : 0;
+    if (bytes < sizeof(StateHeader) + hb + gb + fb + qb + Fb + Wb) return fail(ctx, LB_ERR_ARG, "checkpoint truncated");
     const char* p = (const char*)buf + sizeof(hd);
     ctx->step = hd.step;
     const int par = (int)(ctx->step & 1);
@@ -2130,6 +2136,7 @@ lb_status lb_load_state(lb_ctx* ctx, const void* buf, size_t bytes) {
     if (ctx->M) {
         LB_CUDA(cudaMemcpy(ctx->q[par], p, qb, cudaMemcpyHostToDevice)); p += qb;
         LB_CUDA(cudaMemcpy(ctx->F, p, Fb, cudaMemcpyHostToDevice)); p += Fb;
+        if (ctx->W) { LB_CUDA(cudaMemcpy(ctx->W, p, Wb, cudaMemcpyHostToDevice)); p += Wb; }
         ctx->dvalid = false;
     }
     LB_CUDA(cudaStreamSynchronize(ctx->stream));

@@ -107,3 +107,31 @@ def test_dynamics_arguments_and_state():
     sim.step(3)
     with pytest.raises(lbibm.LbError):
         sim.set_ib_dynamics(0.5, 1.0)   # only before the first step
+
+
+def test_checkpoint_resume_with_massive_points():
+    """A checkpoint of a context whose points carry mass holds their
+    velocities: resuming from it repeats the same 60 cycles, and a massless
+    context refuses it."""
+    sc = scene.small_filter(seed=5, steps=0)
+    sc.ib_dynamics = (2.0, 0.05)
+    sim = _sim(sc)
+    sim.step(80)
+    state = sim.save_state()
+    sim.step(60)
+    xa, va, (_, ua) = sim.nodes(0), sim.velocities(0), sim.fields()
+    assert np.abs(va).max() > 1e-6
+    sim.step(40)                       # move the velocities away from the saved ones
+    sim.load_state(state)
+    assert sim.steps_done == 80
+    sim.step(60)
+    xb, vb, (_, ub) = sim.nodes(0), sim.velocities(0), sim.fields()
+    assert np.abs(xa - xb).max() < 1e-7
+    assert np.abs(va - vb).max() <= 1e-5 * np.abs(va).max()
+    assert rel_l2(ub, ua) < 1e-6
+    from paper_1110_0995_gb300 import lbibm
+
+    sc.ib_dynamics = None
+    plain = _sim(sc)
+    with pytest.raises(lbibm.LbError):
+        plain.load_state(state)
