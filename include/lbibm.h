@@ -363,9 +363,9 @@ lb_status lb_diagnostics(lb_ctx* ctx, double u_max, double out[6]);
 lb_status lb_get_step(lb_ctx* ctx, int64_t* step);
 
 /* Checkpoint: with buf == NULL, *bytes receives the size; otherwise the
- * whole device state (populations, force fields, positions, the velocities
- * of IB points with mass, step) is copied into buf (host, *bytes large
- * enough). */
+ * whole device state (populations, force fields, positions, step; for IB
+ * points with mass also their velocities and the fluid velocity of the last
+ * collision) is copied into buf (host, *bytes large enough). */
 lb_status lb_save_state(lb_ctx* ctx, void* buf, size_t* bytes);
 lb_status lb_load_state(lb_ctx* ctx, const void* buf, size_t bytes);
 

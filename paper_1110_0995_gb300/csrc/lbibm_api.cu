@@ -2069,7 +2069,9 @@ struct StateHeader {
     int64_t Ntot;
     int32_t storage;
     int32_t M;
-    int32_t massive;   // 1: the IB points carry velocities W, saved after F
+    int32_t massive;   // 1: points with mass; their velocities W and the fluid
+                       // velocity u of the last collision (read by the next
+                       // spreading) follow F
     int32_t reserved;
 };
 constexpr uint64_t STATE_MAGIC = 0x4c4249424d535432ULL;
@@ -2086,7 +2088,8 @@ lb_status lb_save_state(lb_ctx* ctx, void* buf, size_t* bytes) {
     const size_t qb = (size_t)ctx->M * sizeof(Q4);
     const size_t Fb = (size_t)ctx->M * sizeof(float4);
     const size_t Wb = ctx->W ? Fb : 0;
-    const size_t total = sizeof(StateHeader) + hb + gb + fb + qb + Fb + Wb;
+    const size_t ub = ctx->W ? (size_t)ctx->Ntot * sizeof(float4) : 0;
+    const size_t total = sizeof(StateHeader) + hb + gb + fb + qb + Fb + Wb + ub;
     if (!buf) { *bytes = total; return LB_OK; }
     if (*bytes < total) return fail(ctx, LB_ERR_ARG, "checkpoint buffer too small");
     StateHeader hd{STATE_MAGIC, ctx->step, ctx->Ntot, (int32_t)ctx->storage, ctx->M, ctx->W ? 1 : 0, 0};
@@ -2101,7 +2104,10 @@ lb_status lb_save_state(lb_ctx* ctx, void* buf, size_t* bytes) {
     if (ctx->M) {
         LB_CUDA(cudaMemcpy(p, ctx->q[par], qb, cudaMemcpyDeviceToHost)); p += qb;
         LB_CUDA(cudaMemcpy(p, ctx->F, Fb, cudaMemcpyDeviceToHost)); p += Fb;
-        if (ctx->W) { LB_CUDA(cudaMemcpy(p, ctx->W, Wb, cudaMemcpyDeviceToHost)); p += Wb; }
+        if (ctx->W) {
+            LB_CUDA(cudaMemcpy(p, ctx->W, Wb, cudaMemcpyDeviceToHost)); p += Wb;
+            LB_CUDA(cudaMemcpy(p, ctx->u, ub, cudaMemcpyDeviceToHost)); p += ub;
+        }
     }
     *bytes = total;
     return LB_OK;
@@ -2123,7 +2129,9 @@ lb_status lb_load_state(lb_ctx* ctx, const void* buf, size_t bytes) {
     const size_t qb = (size_t)ctx->M * sizeof(Q4);
     const size_t Fb = (size_t)ctx->M * sizeof(float4);
     const size_t Wb = ctx->W ? Fb : 0;
-    if (bytes < sizeof(StateHeader) + hb + gb + fb + qb + Fb + Wb) return fail(ctx, LB_ERR_ARG, "checkpoint truncated");
+    const size_t ub = ctx->W ? (size_t)ctx->Ntot * sizeof(float4) : 0;
+    if (bytes < sizeof(StateHeader) + hb + gb + fb + qb + Fb + Wb + ub)
+        return fail(ctx, LB_ERR_ARG, "checkpoint truncated");
     const char* p = (const char*)buf + sizeof(hd);
     ctx->step = hd.step;
     const int par = (int)(ctx->step & 1);
@@ -2136,7 +2144,10 @@ lb_status lb_load_state(lb_ctx* ctx, const void* buf, size_t bytes) {
     if (ctx->M) {
         LB_CUDA(cudaMemcpy(ctx->q[par], p, qb, cudaMemcpyHostToDevice)); p += qb;
         LB_CUDA(cudaMemcpy(ctx->F, p, Fb, cudaMemcpyHostToDevice)); p += Fb;
-        if (ctx->W) { LB_CUDA(cudaMemcpy(ctx->W, p, Wb, cudaMemcpyHostToDevice)); p += Wb; }
+        if (ctx->W) {
+            LB_CUDA(cudaMemcpy(ctx->W, p, Wb, cudaMemcpyHostToDevice)); p += Wb;
+            LB_CUDA(cudaMemcpy(ctx->u, p, ub, cudaMemcpyHostToDevice)); p += ub;
+        }
         ctx->dvalid = false;
     }
     LB_CUDA(cudaStreamSynchronize(ctx->stream));
