@@ -190,6 +190,17 @@ lb_status lb_get_mask(lb_ctx* ctx, uint8_t* solid);
 lb_status ibm_add_mesh(lb_ctx* ctx, const double* rest_xyz, int n_nodes, const int32_t* tris, int n_tris,
                        const ibm_moduli* moduli, int* mesh_id);
 
+/* The check ibm_add_mesh applies to a cell mesh, without a context and
+ * without the GPU (host code only): n_nodes >= 4 and n_tris >= 4, finite
+ * positions with |x| < 4e6, indices in range, no degenerate triangle, every
+ * directed edge in exactly one triangle and its reverse in another (closed,
+ * consistently oriented), every node a single fan of at most 64 triangles,
+ * no isolated node, positive volume (outward orientation).  Returns LB_OK or
+ * LB_ERR_ARG; when `why` is not NULL the reason (empty when LB_OK) is
+ * written into it, at most why_len - 1 characters and a terminating NUL. */
+lb_status ibm_check_mesh(const double* rest_xyz, int n_nodes, const int32_t* tris, int n_tris, char* why,
+                         int why_len);
+
 /* Overwrite the current node positions of one mesh (n_nodes x 3, host). */
 lb_status ibm_set_nodes(lb_ctx* ctx, int mesh_id, const double* xyz);
 

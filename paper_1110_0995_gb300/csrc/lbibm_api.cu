@@ -13,6 +13,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -1471,57 +1472,62 @@ struct DirEdges {
 };
 }  // namespace
 
-lb_status ibm_add_mesh(lb_ctx* ctx, const double* rest_xyz, int n, const int32_t* tris, int nt,
-                       const ibm_moduli* mod, int* mesh_id) {
-    LB_GUARD(ctx);
-    if (ctx->started || ctx->committed) return fail(ctx, LB_ERR_STATE, "meshes must be added before the first step");
-    if (!rest_xyz || !tris || !mod || n < 4 || nt < 4) return fail(ctx, LB_ERR_ARG, "mesh needs >= 4 nodes and triangles");
-    const double mv[5] = {mod->ks, mod->kb, mod->kal, mod->kag, mod->kv};
-    for (double v : mv)
-        if (!std::isfinite(v)) return fail(ctx, LB_ERR_ARG, "moduli must be finite");
+namespace {
+// A cell mesh checked for use: directed edge a -> b with the third vertex of
+// its triangle, every node's ring of neighbours, the rest area and volume.
+struct MeshTopology {
+    DirEdges third;
+    std::vector<int> out_deg;
+    std::vector<std::vector<int>> ringv;
+    double S0 = 0.0, V0 = 0.0;
+    MeshTopology(int n, const int32_t* tris, int nt) : third(n, tris, nt), out_deg(n, 0), ringv(n) {}
+};
+
+// Checks that (x, tris) is a closed, outward, oriented 2-manifold whose every
+// node is a single fan of at most MAX_VALENCE triangles, and builds its
+// topology into *topo.  Returns nullptr, or why the mesh is refused.  Host
+// code only.
+const char* mesh_topology(const double* x, int n, const int32_t* tris, int nt, std::unique_ptr<MeshTopology>& topo) {
+    if (!x || !tris || n < 4 || nt < 4) return "mesh needs >= 4 nodes and triangles";
     for (int k = 0; k < 3 * n; ++k)
-        if (!std::isfinite(rest_xyz[k]) || std::fabs(rest_xyz[k]) > 4.0e6)
-            return fail(ctx, LB_ERR_ARG, "node positions must be finite and |x| < 4e6");
-    // directed edge -> third vertex
+        if (!std::isfinite(x[k]) || std::fabs(x[k]) > 4.0e6) return "node positions must be finite and |x| < 4e6";
     for (int k = 0; k < 3 * nt; ++k)
-        if (tris[k] < 0 || tris[k] >= n) return fail(ctx, LB_ERR_ARG, "triangle index out of range");
-    DirEdges third(n, tris, nt);
-    std::vector<int> out_deg(n, 0);
+        if (tris[k] < 0 || tris[k] >= n) return "triangle index out of range";
+    topo.reset(new MeshTopology(n, tris, nt));
+    DirEdges& third = topo->third;
+    std::vector<int>& out_deg = topo->out_deg;
     for (int t = 0; t < nt; ++t) {
         const int v[3] = {tris[3 * t], tris[3 * t + 1], tris[3 * t + 2]};
         for (int k = 0; k < 3; ++k) {
             const int a = v[k], b = v[(k + 1) % 3];
-            if (a == b) return fail(ctx, LB_ERR_ARG, "degenerate triangle");
-            if (third.find(a, b)) return fail(ctx, LB_ERR_ARG, "mesh is not an oriented 2-manifold (edge used twice)");
+            if (a == b) return "degenerate triangle";
+            if (third.find(a, b)) return "mesh is not an oriented 2-manifold (edge used twice)";
             third.put(a, b, v[(k + 2) % 3]);
             out_deg[a]++;
         }
     }
     for (int a = 0; a < n; ++a) {
-        if (out_deg[a] > MAX_VALENCE)
-            return fail(ctx, LB_ERR_ARG, "mesh vertex is not a single fan (non-manifold) or valence > 64");
+        if (out_deg[a] > MAX_VALENCE) return "mesh vertex is not a single fan (non-manifold) or valence > 64";
         third.sort_node(a);
         for (int i = third.off[a]; i < third.off[a] + third.cnt[a]; ++i)
-            if (!third.find(third.key[i], a)) return fail(ctx, LB_ERR_ARG, "mesh is not closed");
+            if (!third.find(third.key[i], a)) return "mesh is not closed";
     }
     // node rings, counter-clockwise seen from outside: ring[j+1] = third(i -> ring[j]),
     // each starting at the node's smallest neighbour
-    std::vector<std::vector<int>> ringv(n);
     for (int i = 0; i < n; ++i) {
         if (third.size(i) == 0) continue;
         int a = third.first(i);
-        std::vector<int>& r = ringv[i];
+        std::vector<int>& r = topo->ringv[i];
         for (int guard = 0; guard <= MAX_VALENCE; ++guard) {
             r.push_back(a);
             a = third.at(i, a);
             if (a < 0 || a == r[0]) break;
         }
         if ((int)r.size() != out_deg[i] || (int)r.size() > MAX_VALENCE || a != r[0])
-            return fail(ctx, LB_ERR_ARG, "mesh vertex is not a single fan (non-manifold) or valence > 64");
+            return "mesh vertex is not a single fan (non-manifold) or valence > 64";
     }
     for (int i = 0; i < n; ++i)
-        if (ringv[i].empty()) return fail(ctx, LB_ERR_ARG, "mesh has an isolated node");
-    const double* x = rest_xyz;
+        if (topo->ringv[i].empty()) return "mesh has an isolated node";
     // rest area / volume (FP64)
     double S0 = 0.0, V0 = 0.0;
     for (int t = 0; t < nt; ++t) {
@@ -1532,7 +1538,37 @@ lb_status ibm_add_mesh(lb_ctx* ctx, const double* rest_xyz, int n, const int32_t
         V0 += (a[0] * (b[1] * c[2] - b[2] * c[1]) + a[1] * (b[2] * c[0] - b[0] * c[2]) +
                a[2] * (b[0] * c[1] - b[1] * c[0])) / 6.0;
     }
-    if (!(V0 > 0.0)) return fail(ctx, LB_ERR_ARG, "mesh volume must be positive (outward orientation)");
+    if (!(V0 > 0.0)) return "mesh volume must be positive (outward orientation)";
+    topo->S0 = S0;
+    topo->V0 = V0;
+    return nullptr;
+}
+}  // namespace
+
+lb_status ibm_check_mesh(const double* rest_xyz, int n, const int32_t* tris, int nt, char* why, int why_len) {
+    std::unique_ptr<MeshTopology> topo;
+    const char* err = mesh_topology(rest_xyz, n, tris, nt, topo);
+    if (why && why_len > 0) {
+        std::strncpy(why, err ? err : "", (size_t)why_len - 1);
+        why[why_len - 1] = '\0';
+    }
+    return err ? LB_ERR_ARG : LB_OK;
+}
+
+lb_status ibm_add_mesh(lb_ctx* ctx, const double* rest_xyz, int n, const int32_t* tris, int nt,
+                       const ibm_moduli* mod, int* mesh_id) {
+    LB_GUARD(ctx);
+    if (ctx->started || ctx->committed) return fail(ctx, LB_ERR_STATE, "meshes must be added before the first step");
+    if (!mod) return fail(ctx, LB_ERR_ARG, "null moduli");
+    const double mv[5] = {mod->ks, mod->kb, mod->kal, mod->kag, mod->kv};
+    for (double v : mv)
+        if (!std::isfinite(v)) return fail(ctx, LB_ERR_ARG, "moduli must be finite");
+    std::unique_ptr<MeshTopology> topo;
+    if (const char* err = mesh_topology(rest_xyz, n, tris, nt, topo)) return fail(ctx, LB_ERR_ARG, err);
+    DirEdges& third = topo->third;
+    const std::vector<std::vector<int>>& ringv = topo->ringv;
+    const double S0 = topo->S0, V0 = topo->V0;
+    const double* x = rest_xyz;
 
     auto theta0 = [&](int a, int b) {
         if (a > b) std::swap(a, b);

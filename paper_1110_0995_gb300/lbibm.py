@@ -26,7 +26,7 @@ EXPORTS = (
     "ibm_get_nodes", "ibm_get_all_nodes", "ibm_get_forces", "ibm_get_area_volume", "lb_diagnostics", "lb_get_step", "lb_save_state",
     "lb_load_state", "lb_set_schedule", "lb_get_schedule", "lb_set_timing", "lb_kernel_times", "lb_last_error", "lb_version", "lb_get_mask",
     "lb_set_kernel_config", "lb_get_kernel_config", "lb_autotune", "ibm_area_volume_noalloc",
-    "bead_forces", "bead_relax", "ibm_get_all_nodes_async", "lb_readback_wait",
+    "bead_forces", "bead_relax", "ibm_get_all_nodes_async", "lb_readback_wait", "ibm_check_mesh",
 )
 
 
@@ -111,6 +111,7 @@ def lib():
             "ibm_get_all_nodes_async": ([P, P, I], I),
             "lb_readback_wait": ([P, I], I),
             "bead_relax": ([P, P, I, P, I, P], I),
+            "ibm_check_mesh": ([P, I, P, I, ctypes.c_char_p, I], I),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -414,6 +415,19 @@ class Simulation:
         n = np.zeros(4, np.int64)
         self._check(self._L.lb_kernel_times(self._h, _ptr(ms), _ptr(n)))
         return ms, n
+
+
+def check_mesh(rest: np.ndarray, tris: np.ndarray) -> str:
+    """'' when ibm_add_mesh would accept the mesh, else the reason it refuses
+    it (host code of the library; needs no GPU)."""
+    x = np.ascontiguousarray(rest, dtype=np.float64).reshape(-1, 3)
+    t = np.ascontiguousarray(tris, dtype=np.int32).reshape(-1, 3)
+    why = ctypes.create_string_buffer(256)
+    st = lib().ibm_check_mesh(_ptr(x), int(x.shape[0]), _ptr(t), int(t.shape[0]), why, len(why))
+    msg = why.value.decode()
+    if (st == LB_OK) != (msg == ""):
+        raise LbError(st, f"ibm_check_mesh: status and reason disagree ({msg!r})")
+    return msg
 
 
 # ---- magnetic bead assembly (context-free) ----------------------------------
