@@ -61,9 +61,9 @@ typedef enum { LB_F32 = 0, LB_F16_SHIFTED = 1, LB_BF16_SHIFTED = 2 } lb_storage;
 typedef struct {
     int nx, ny, nz;              /* lattice dimensions, each >= 1; nx*ny*nz <= 2^31 - 1 */
     double tau;                  /* BGK relaxation time (Sec. 2.1), > 1/2 */
-    double body_force[3];        /* uniform force density at every fluid node */
+    double body_force[3];        /* uniform force density at every fluid node (finite) */
     int periodic[3];             /* 1 = periodic axis, 0 = bounce-back walls */
-    double wall_velocity[2][3];  /* velocity of the y = -1/2 and y = ny - 1/2 walls */
+    double wall_velocity[2][3];  /* velocity of the y = -1/2 and y = ny - 1/2 walls (finite) */
     lb_storage storage;
     int reserved[4];             /* must be zero */
 } lb_params;
@@ -79,8 +79,9 @@ typedef struct {
 
 /* Create a context: allocates the lattice (two population buffers, force and
  * velocity fields) and fills it with the rest equilibrium rho = 1, u = 0.
- * `cuda_stream` is a cudaStream_t (or NULL).  LB_ERR_ARG for invalid params,
- * LB_ERR_OOM if the lattice does not fit. */
+ * `cuda_stream` is a cudaStream_t (or NULL).  LB_ERR_ARG for invalid params
+ * (checked on the host before any CUDA call), LB_ERR_OOM if the lattice does
+ * not fit. */
 lb_status lb_create(const lb_params* params, void* cuda_stream, lb_ctx** out);
 
 /* Batched variant: `n_channels` independent lattices (one params entry each,

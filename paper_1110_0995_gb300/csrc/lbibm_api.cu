@@ -325,6 +325,9 @@ lb_status validate_params(const lb_params& p, std::string& why) {
     if (!(p.tau > 0.5) || !std::isfinite(p.tau)) { why = "tau must be > 1/2"; return LB_ERR_ARG; }
     for (int d = 0; d < 3; ++d)
         if (!std::isfinite(p.body_force[d])) { why = "body force must be finite"; return LB_ERR_ARG; }
+    for (int w = 0; w < 2; ++w)
+        for (int d = 0; d < 3; ++d)
+            if (!std::isfinite(p.wall_velocity[w][d])) { why = "wall velocities must be finite"; return LB_ERR_ARG; }
     if (p.storage != LB_F32 && p.storage != LB_F16_SHIFTED && p.storage != LB_BF16_SHIFTED) {
         why = "unknown storage";
         return LB_ERR_ARG;

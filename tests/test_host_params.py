@@ -1,0 +1,54 @@
+"""lb_create / lb_create_batch refuse invalid lattice parameters on the host,
+before any CUDA call (so this runs without a GPU)."""
+import ctypes
+import math
+
+import pytest
+
+
+@pytest.fixture(scope="module")
+def lbibm():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1110_0995_gb300 import lbibm
+
+    return lbibm
+
+
+def _bad_params(lbibm):
+    mk = lbibm.make_params
+    yield "dims", mk((0, 8, 8))
+    yield "too many nodes", mk((2048, 2048, 1024))
+    yield "tau = 1/2", mk((8, 8, 8), tau=0.5)
+    yield "tau nan", mk((8, 8, 8), tau=math.nan)
+    yield "force inf", mk((8, 8, 8), body_force=(math.inf, 0.0, 0.0))
+    yield "wall nan", mk((8, 8, 8), wall_velocity=((0, 0, 0), (math.nan, 0, 0)))
+    yield "storage", mk((8, 8, 8), storage=7)
+    p = mk((8, 8, 8))
+    p.reserved[2] = 1
+    yield "reserved", p
+
+
+def test_invalid_params_are_refused_on_the_host(lbibm):
+    L = lbibm.lib()
+    for name, p in _bad_params(lbibm):
+        h = ctypes.c_void_p(123)
+        st = L.lb_create(ctypes.byref(p), None, ctypes.byref(h))
+        assert st == lbibm.LB_ERR_ARG, name
+        assert h.value is None, name          # *out is cleared
+        arr = (lbibm.LbParams * 2)(lbibm.make_params((8, 8, 8)), p)
+        assert L.lb_create_batch(arr, 2, None, ctypes.byref(h)) == lbibm.LB_ERR_ARG, name
+
+
+def test_batch_arguments_are_refused_on_the_host(lbibm):
+    L = lbibm.lib()
+    h = ctypes.c_void_p()
+    a, b = lbibm.make_params((8, 8, 8)), lbibm.make_params((8, 8, 8), storage="f16")
+    mixed = (lbibm.LbParams * 2)(a, b)
+    assert L.lb_create_batch(mixed, 2, None, ctypes.byref(h)) == lbibm.LB_ERR_ARG   # one storage per batch
+    one = (lbibm.LbParams * 1)(a)
+    assert L.lb_create_batch(one, 0, None, ctypes.byref(h)) == lbibm.LB_ERR_ARG
+    assert L.lb_create_batch(one, 4097, None, ctypes.byref(h)) == lbibm.LB_ERR_ARG
+    assert L.lb_create_batch(None, 1, None, ctypes.byref(h)) == lbibm.LB_ERR_ARG
+    assert L.lb_create_batch(one, 1, None, None) == lbibm.LB_ERR_ARG
