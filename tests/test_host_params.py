@@ -52,3 +52,31 @@ def test_batch_arguments_are_refused_on_the_host(lbibm):
     assert L.lb_create_batch(one, 4097, None, ctypes.byref(h)) == lbibm.LB_ERR_ARG
     assert L.lb_create_batch(None, 1, None, ctypes.byref(h)) == lbibm.LB_ERR_ARG
     assert L.lb_create_batch(one, 1, None, None) == lbibm.LB_ERR_ARG
+
+
+def test_bead_arguments_are_refused_on_the_host(lbibm):
+    """bead_forces / bead_relax check their arguments before any CUDA call."""
+    import numpy as np
+
+    x = np.zeros((4, 3))
+    x[:, 0] = np.arange(4) * 3.0
+    m = np.tile([0.0, 0.0, 1.0], (4, 1))
+    bad = [
+        dict(xyz=x[:0], moments=m[:0], c=1.0, radius=1.0, k=1.0),                  # no beads
+        dict(xyz=x, moments=m, c=1.0, radius=-1.0, k=1.0),                         # negative radius
+        dict(xyz=x, moments=m, c=1.0, radius=1.0, k=-2.0),                         # negative stiffness
+        dict(xyz=x, moments=m, c=math.nan, radius=1.0, k=1.0),                     # non-finite constant
+        dict(xyz=x, moments=m, c=1.0, radius=1.0, k=1.0, box=(0.0, 1.0, 1.0), periodic=(1, 0, 0)),
+    ]
+    for kw in bad:
+        with pytest.raises(lbibm.LbError) as e:
+            lbibm.bead_forces(**kw)
+        assert e.value.status == lbibm.LB_ERR_ARG
+    with pytest.raises(lbibm.LbError) as e:
+        lbibm.bead_relax(x, m, 1.0, 1.0, 1.0, 1.0, 0.1, steps=-1)
+    assert e.value.status == lbibm.LB_ERR_ARG
+    p = lbibm._bead_params(1.0, 1.0, 1.0)
+    p.reserved[0] = 3
+    L = lbibm.lib()
+    F = np.zeros_like(x)
+    assert L.bead_forces(lbibm._ptr(x), lbibm._ptr(m), 4, ctypes.byref(p), lbibm._ptr(F), None) == lbibm.LB_ERR_ARG
