@@ -29,6 +29,19 @@ Parity status per function (what pins it, in ``tests/test_oracle_*.py``):
 * DiffProblem (differentiable   : dual-number derivatives vs central finite
   variant, Brinkman beads)        differences; phi = 0 reproduces the plain cycle;
                                   phi = 1 with alpha = 2 holds u at g / 2
+* repulsion (Sec. 2.4)          : forces are minus the gradient of the pair
+                                  potential (finite differences), cell-cell sums
+                                  conserve momentum, cut-off and periodic image
+* drag_coefficients,            : p1 and e^-a against 40-digit values; one step in
+  system_step_massive             uniform flow against the closed form; total
+  (IB points with mass)           momentum conserved; gamma = 0 leaves the fluid at
+                                  rest; the massless limit's first cycle
+* dipole_force, bead_forces,    : axial attraction / transverse repulsion of two
+  bead_relax (Sec. 2.5)           dipoles, minus the gradient of the dipole energy,
+                                  third law, minimum image, a pair relaxing to its
+                                  force balance
+* coupled-cycle stability       : the explicit coupling amplifies perturbations
+                                  of a stiff membrane and damps a soft one
 """
 from __future__ import annotations
 
