@@ -26,7 +26,8 @@
  *   - Work is queued on the CUDA stream given to lb_create (NULL = the legacy
  *     default stream).  Calls that return data synchronise that stream.
  *   - No exception or abort crosses the ABI.  Every call returns an
- *     lb_status; lb_last_error() gives a message.  A CUDA error poisons the
+ *     lb_status; lb_last_error(ctx) gives a message (lb_last_error(NULL) for
+ *     the calls that have no context).  A CUDA error poisons the
  *     context: every later call returns LB_ERR_CUDA.
  *   - One context per stream; calls on one context are not thread-safe.
  */
@@ -394,7 +395,11 @@ lb_status lb_load_state(lb_ctx* ctx, const void* buf, size_t bytes);
 lb_status lb_set_timing(lb_ctx* ctx, int kernel_mask);
 lb_status lb_kernel_times(lb_ctx* ctx, double ms[4], int64_t launches[4]);
 
-/* Static message for the last error on this context (never NULL). */
+/* Message of the last error on this context (never NULL; valid until the
+ * context's next failing call).  With ctx == NULL: the message of the last
+ * failed call of the calling thread that has no context (lb_create,
+ * lb_create_batch, ibm_check_mesh, bead_forces, bead_relax), "no error"
+ * before any; valid until that thread's next such failure. */
 const char* lb_last_error(const lb_ctx* ctx);
 
 /* Library version: major * 10000 + minor * 100 + patch. */

@@ -16,6 +16,8 @@
 #include <vector>
 
 namespace lbibm {
+lb_status context_free_error(lb_status s, const char* msg);   // lbibm_api.cu
+
 namespace {
 
 constexpr int BEAD_TILE = 256;
@@ -173,12 +175,12 @@ lb_status upload(const double* xyz, const double* moments, int n, BeadBuffers& B
     if (cudaMalloc(&B.x[0], bytes) != cudaSuccess || cudaMalloc(&B.x[1], bytes) != cudaSuccess ||
         cudaMalloc(&B.m, bytes) != cudaSuccess || cudaMalloc(&B.F, bytes) != cudaSuccess) {
         cudaGetLastError();
-        return LB_ERR_OOM;
+        return context_free_error(LB_ERR_OOM, "bead buffers: device allocation failed");
     }
     if (cudaMemcpyAsync(B.x[0], hx.data(), bytes, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(B.m, hm.data(), bytes, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
-        return LB_ERR_CUDA;
+        return context_free_error(LB_ERR_CUDA, "bead upload: CUDA error");
     return LB_OK;
 }
 
@@ -186,7 +188,7 @@ lb_status download(const float4* d, int n, double* out, cudaStream_t s) {
     std::vector<float4> h(n);
     if (cudaMemcpyAsync(h.data(), d, sizeof(float4) * (size_t)n, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
-        return LB_ERR_CUDA;
+        return context_free_error(LB_ERR_CUDA, "bead readback: CUDA error");
     for (int i = 0; i < n; ++i) {
         out[3 * i] = h[i].x;
         out[3 * i + 1] = h[i].y;
@@ -204,7 +206,8 @@ extern "C" {
 
 lb_status bead_forces(const double* xyz, const double* moments, int n, const bead_params* p, double* F,
                       void* cuda_stream) {
-    if (!xyz || !moments || !F || !params_ok(p, n)) return LB_ERR_ARG;
+    if (!xyz || !moments || !F || !params_ok(p, n))
+        return context_free_error(LB_ERR_ARG, "null array, n < 1 or invalid bead parameters");
     cudaStream_t s = (cudaStream_t)cuda_stream;
     BeadBuffers B;
     lb_status st = upload(xyz, moments, n, B, s);
@@ -212,14 +215,16 @@ lb_status bead_forces(const double* xyz, const double* moments, int n, const bea
     const BeadDev d = dev_params(p, n);
     int jt = 1;
     const dim3 grid = force_grid(n, jt);
-    if (cudaMemsetAsync(B.F, 0, sizeof(float4) * (size_t)n, s) != cudaSuccess) return LB_ERR_CUDA;
+    if (cudaMemsetAsync(B.F, 0, sizeof(float4) * (size_t)n, s) != cudaSuccess)
+        return context_free_error(LB_ERR_CUDA, "bead forces: CUDA error");
     k_bead_forces<<<grid, BEAD_TILE, 0, s>>>(B.x[0], B.m, d, jt, B.F);
-    if (cudaGetLastError() != cudaSuccess) return LB_ERR_CUDA;
+    if (cudaGetLastError() != cudaSuccess) return context_free_error(LB_ERR_CUDA, "bead forces: launch failed");
     return download(B.F, n, F, s);
 }
 
 lb_status bead_relax(double* xyz, const double* moments, int n, const bead_params* p, int steps, void* cuda_stream) {
-    if (!xyz || !moments || steps < 0 || !params_ok(p, n)) return LB_ERR_ARG;
+    if (!xyz || !moments || steps < 0 || !params_ok(p, n))
+        return context_free_error(LB_ERR_ARG, "null array, n < 1, steps < 0 or invalid bead parameters");
     cudaStream_t s = (cudaStream_t)cuda_stream;
     BeadBuffers B;
     lb_status st = upload(xyz, moments, n, B, s);
@@ -227,11 +232,12 @@ lb_status bead_relax(double* xyz, const double* moments, int n, const bead_param
     const BeadDev d = dev_params(p, n);
     int jt = 1;
     const dim3 grid = force_grid(n, jt);
-    if (cudaMemsetAsync(B.F, 0, sizeof(float4) * (size_t)n, s) != cudaSuccess) return LB_ERR_CUDA;
+    if (cudaMemsetAsync(B.F, 0, sizeof(float4) * (size_t)n, s) != cudaSuccess)
+        return context_free_error(LB_ERR_CUDA, "bead relax: CUDA error");
     for (int k = 0; k < steps; ++k) {
         k_bead_forces<<<grid, BEAD_TILE, 0, s>>>(B.x[k & 1], B.m, d, jt, B.F);
         k_bead_move<<<(n + 255) / 256, 256, 0, s>>>(B.x[k & 1], B.F, d, B.x[(k + 1) & 1]);
-        if (cudaGetLastError() != cudaSuccess) return LB_ERR_CUDA;
+        if (cudaGetLastError() != cudaSuccess) return context_free_error(LB_ERR_CUDA, "bead relax: launch failed");
     }
     return download(B.x[steps & 1], n, xyz, s);
 }

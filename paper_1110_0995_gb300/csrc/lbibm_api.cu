@@ -172,6 +172,16 @@ struct lb_ctx {
     std::vector<void*> allocations;
 };
 
+namespace lbibm {
+// Message of the last failed call of this thread that has no context to hold
+// it (lb_create, lb_create_batch, ibm_check_mesh, bead_forces, bead_relax).
+thread_local std::string context_free_err = "no error";
+lb_status context_free_error(lb_status s, const char* msg) {
+    context_free_err = msg;
+    return s;
+}
+}  // namespace lbibm
+
 namespace {
 
 lb_status fail(lb_ctx* c, lb_status s, const std::string& msg) {
@@ -794,16 +804,19 @@ extern "C" {
 
 int lb_version(void) { return 10000; }
 
-const char* lb_last_error(const lb_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+const char* lb_last_error(const lb_ctx* ctx) { return ctx ? ctx->err.c_str() : context_free_err.c_str(); }
 
 lb_status lb_create_batch(const lb_params* params, int n_channels, void* cuda_stream, lb_ctx** out) {
-    if (!out) return LB_ERR_ARG;
+    if (!out) return context_free_error(LB_ERR_ARG, "null output handle");
     *out = nullptr;
-    if (!params || n_channels < 1 || n_channels > 4096) return LB_ERR_ARG;
+    if (!params || n_channels < 1 || n_channels > 4096)
+        return context_free_error(LB_ERR_ARG, "need 1 to 4096 channel parameter sets");
     for (int k = 0; k < n_channels; ++k) {
         std::string why;
-        if (validate_params(params[k], why) != LB_OK) return LB_ERR_ARG;
-        if (params[k].storage != params[0].storage) return LB_ERR_ARG;
+        if (validate_params(params[k], why) != LB_OK)
+            return context_free_error(LB_ERR_ARG, ("channel " + std::to_string(k) + ": " + why).c_str());
+        if (params[k].storage != params[0].storage)
+            return context_free_error(LB_ERR_ARG, "every channel of a batch needs the same storage");
     }
     lb_ctx* ctx = new lb_ctx();
     ctx->storage = params[0].storage;
@@ -843,12 +856,12 @@ lb_status lb_create_batch(const lb_params* params, int n_channels, void* cuda_st
         if (prepare_staged((int)ctx->storage) != cudaSuccess) {
             cudaGetLastError();
             delete ctx;
-            return LB_ERR_CUDA;
+            return context_free_error(LB_ERR_CUDA, "kernel setup failed (no usable CUDA device?)");
         }
     }
     if (ctx->plane >= (1LL << 31)) {   // node indices are 32-bit inside the kernels
         delete ctx;
-        return LB_ERR_ARG;
+        return context_free_error(LB_ERR_ARG, "lattice too large: the padded node count must be < 2^31");
     }
     apply_k3_config(ctx, default_k3_config(ctx));
     ctx->ch_meshes.resize(n_channels);
@@ -857,7 +870,7 @@ lb_status lb_create_batch(const lb_params* params, int n_channels, void* cuda_st
         cudaError_t e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
         if (e != cudaSuccess) {
             delete ctx;
-            return e == cudaErrorMemoryAllocation ? LB_ERR_OOM : LB_ERR_CUDA;
+            return context_free_error(e == cudaErrorMemoryAllocation ? LB_ERR_OOM : LB_ERR_CUDA, cudaGetErrorString(e));
         }
         ctx->own_stream = true;
     } else {
@@ -926,15 +939,19 @@ lb_status lb_create_batch(const lb_params* params, int n_channels, void* cuda_st
         lb_status s = e == cudaErrorMemoryAllocation ? LB_ERR_OOM : LB_ERR_CUDA;
         cudaGetLastError();
         lb_destroy(ctx);
-        return s;
+        return context_free_error(s, cudaGetErrorString(e));
     }
-    if (upload_channels(ctx) != LB_OK) { lb_destroy(ctx); return LB_ERR_CUDA; }
+    const char* setup_err = "lattice setup failed (CUDA error)";
+    if (upload_channels(ctx) != LB_OK) { lb_destroy(ctx); return context_free_error(LB_ERR_CUDA, setup_err); }
     for (size_t k = 0; k < ctx->ch.size(); ++k)
         if (launch_slow_flags(ctx->ch[k].d, ctx->mask, ctx->slow, ctx->links, ctx->stream) != cudaSuccess) {
             lb_destroy(ctx);
-            return LB_ERR_CUDA;
+            return context_free_error(LB_ERR_CUDA, setup_err);
         }
-    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) { lb_destroy(ctx); return LB_ERR_CUDA; }
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+        lb_destroy(ctx);
+        return context_free_error(LB_ERR_CUDA, setup_err);
+    }
     *out = ctx;
     return LB_OK;
 }
@@ -1551,6 +1568,7 @@ const char* mesh_topology(const double* x, int n, const int32_t* tris, int nt, s
 lb_status ibm_check_mesh(const double* rest_xyz, int n, const int32_t* tris, int nt, char* why, int why_len) {
     std::unique_ptr<MeshTopology> topo;
     const char* err = mesh_topology(rest_xyz, n, tris, nt, topo);
+    if (err) context_free_error(LB_ERR_ARG, err);
     if (why && why_len > 0) {
         std::strncpy(why, err ? err : "", (size_t)why_len - 1);
         why[why_len - 1] = '\0';

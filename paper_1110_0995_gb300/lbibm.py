@@ -121,6 +121,11 @@ def lib():
     return _lib
 
 
+def last_error() -> str:
+    """Message of this thread's last failed call that has no context."""
+    return lib().lb_last_error(None).decode()
+
+
 def _ptr(a: np.ndarray):
     return a.ctypes.data_as(ctypes.c_void_p)
 
@@ -167,7 +172,7 @@ class Simulation:
         arr = (LbParams * len(params))(*params)
         st = self._L.lb_create_batch(arr, len(params), ctypes.c_void_p(stream or 0), ctypes.byref(self._h))
         if st != LB_OK:
-            raise LbError(st, "lb_create_batch failed")
+            raise LbError(st, "lb_create_batch: " + last_error())
         self.dims = [(p.nx, p.ny, p.nz) for p in params]
         self.n_mesh_nodes = [[] for _ in params]
         self.channel = 0
@@ -448,7 +453,7 @@ def bead_forces(xyz, moments, c, radius, k, box=(1.0, 1.0, 1.0), periodic=(0, 0,
     p = _bead_params(c, radius, k, box=box, periodic=periodic)
     st = lib().bead_forces(_ptr(x), _ptr(m), int(x.shape[0]), ctypes.byref(p), _ptr(F), stream)
     if st != 0:
-        raise LbError(st, "bead_forces")
+        raise LbError(st, "bead_forces: " + last_error())
     return F
 
 
@@ -460,5 +465,5 @@ def bead_relax(xyz, moments, c, radius, k, mobility, dt, steps, box=(1.0, 1.0, 1
     p = _bead_params(c, radius, k, mobility, dt, box, periodic)
     st = lib().bead_relax(_ptr(x), _ptr(m), int(x.shape[0]), ctypes.byref(p), int(steps), stream)
     if st != 0:
-        raise LbError(st, "bead_relax")
+        raise LbError(st, "bead_relax: " + last_error())
     return x

@@ -80,3 +80,35 @@ def test_bead_arguments_are_refused_on_the_host(lbibm):
     L = lbibm.lib()
     F = np.zeros_like(x)
     assert L.bead_forces(lbibm._ptr(x), lbibm._ptr(m), 4, ctypes.byref(p), lbibm._ptr(F), None) == lbibm.LB_ERR_ARG
+
+
+def test_context_free_calls_say_why(lbibm):
+    """A failed call without a context leaves its reason for lb_last_error(NULL),
+    per thread; the binding puts it into the exception."""
+    import threading
+
+    import numpy as np
+
+    L = lbibm.lib()
+    h = ctypes.c_void_p()
+    p = lbibm.make_params((8, 8, 8), tau=0.4)
+    assert L.lb_create(ctypes.byref(p), None, ctypes.byref(h)) == lbibm.LB_ERR_ARG
+    assert "tau must be > 1/2" in lbibm.last_error()
+    arr = (lbibm.LbParams * 2)(lbibm.make_params((8, 8, 8)), lbibm.make_params((8, 8, 8), storage="bf16"))
+    assert L.lb_create_batch(arr, 2, None, ctypes.byref(h)) == lbibm.LB_ERR_ARG
+    assert "same storage" in lbibm.last_error()
+    with pytest.raises(lbibm.LbError, match="channel 1: wall velocities must be finite"):
+        lbibm.Simulation([lbibm.make_params((8, 8, 8)),
+                          lbibm.make_params((8, 8, 8), wall_velocity=((0, 0, 0), (0, math.inf, 0)))])
+    with pytest.raises(lbibm.LbError, match="invalid bead parameters"):
+        lbibm.bead_forces(np.zeros((2, 3)), np.zeros((2, 3)), 1.0, -1.0, 1.0)
+    assert "invalid bead parameters" in lbibm.last_error()
+    # another thread has its own message
+    seen = []
+    t = threading.Thread(target=lambda: seen.append(lbibm.last_error()))
+    t.start()
+    t.join()
+    assert seen == ["no error"]
+    x, tr = np.eye(3), np.array([[0, 1, 2]] * 4, np.int32)
+    assert lbibm.check_mesh(x, tr) != ""
+    assert ">= 4 nodes" in lbibm.last_error()
