@@ -234,8 +234,10 @@ lb_status lb_get_kernel_config(lb_ctx* ctx, int* nodes_per_thread, int* block_si
  * predecessor (its blocks are scheduled during the predecessor's last wave
  * and wait for the predecessor to complete before touching memory).
  * overlapped = 2: the same cycle with ordinary launches.  overlapped = 1: when
- * the context has IB meshes and the stream-collide variant has one node per
- * thread, each cycle runs the immersed-boundary kernels on a second,
+ * the context has IB meshes, the stream-collide variant has one node per
+ * thread and none of collisions, points with mass, the deterministic cycle
+ * or the differentiable variant is on (otherwise the sequential cycle with
+ * programmatic dependent launches runs), each cycle runs the immersed-boundary kernels on a second,
  * higher-priority stream concurrently with the stream-collide of every
  * 32-node group that no IB point can reach in that step, then updates the
  * reachable groups; the results equal the sequential cycle as long as no IB
