@@ -192,8 +192,9 @@ lb_status lb_get_mask(lb_ctx* ctx, uint8_t* solid);
 lb_status ibm_add_mesh(lb_ctx* ctx, const double* rest_xyz, int n_nodes, const int32_t* tris, int n_tris,
                        const ibm_moduli* moduli, int* mesh_id);
 
-/* The check ibm_add_mesh applies to a cell mesh, without a context and
- * without the GPU (host code only): n_nodes >= 4 and n_tris >= 4, finite
+/* The check ibm_add_mesh applies to a cell membrane mesh (Sec. 2.3.1: a
+ * closed triangulated surface of IB points), without a context and without
+ * the GPU (host code only): n_nodes >= 4 and n_tris >= 4, finite
  * positions with |x| < 4e6, indices in range, no degenerate triangle, every
  * directed edge in exactly one triangle and its reverse in another (closed,
  * consistently oriented), every node a single fan of at most 64 triangles,
