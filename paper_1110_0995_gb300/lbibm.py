@@ -185,6 +185,12 @@ class Simulation:
 
     @classmethod
     def from_scenes(cls, scenes, storage="f32", stream=None) -> "Simulation":
+        """One context with a channel per scene.  Collisions and the point
+        dynamics are settings of the whole context: every scene must agree."""
+        for attr in ("repulsion", "ib_dynamics"):
+            vals = {None if getattr(s, attr, None) is None else tuple(getattr(s, attr)) for s in scenes}
+            if len(vals) > 1:
+                raise ValueError(f"scenes of one batch differ in {attr}: {sorted(map(str, vals))}")
         params = [make_params(s.dims, s.tau, s.body_force, s.periodic, s.wall_velocity, storage) for s in scenes]
         sim = cls(params, stream)
         rep = getattr(scenes[0], "repulsion", None)

@@ -112,3 +112,16 @@ def test_context_free_calls_say_why(lbibm):
     x, tr = np.eye(3), np.array([[0, 1, 2]] * 4, np.int32)
     assert lbibm.check_mesh(x, tr) != ""
     assert ">= 4 nodes" in lbibm.last_error()
+
+
+def test_batch_scenes_must_agree_on_context_settings(lbibm):
+    """Collisions and point dynamics belong to the whole context: a batch of
+    scenes that differ in them is refused before anything is created."""
+    from paper_1110_0995_gb300 import scene
+
+    a = scene.Scene(name="a", dims=(8, 8, 8))
+    b = scene.Scene(name="b", dims=(8, 8, 8), ib_dynamics=(1.0, 0.5))
+    c = scene.Scene(name="c", dims=(8, 8, 8), repulsion=(0.01, 1.0))
+    for pair in ((a, b), (a, c)):
+        with pytest.raises(ValueError, match="differ in"):
+            lbibm.Simulation.from_scenes(list(pair))
