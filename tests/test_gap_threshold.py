@@ -108,3 +108,71 @@ def test_table1_values_as_printed(kind):
     radius = scene.RBC_RADIUS if kind == "rbc" else scene.CTC_RADIUS
     # one lattice unit stands for one micrometre
     assert 2 * radius == t1["diameter_um"][kind]
+
+
+class _DriftSim:
+    """Stand-in for a batched context (host logic only): channel c's cell
+    drifts rigidly along x at velocity[c] lu per step; a channel listed in
+    blow_up turns non-finite at that step.  The library returns positions
+    unwrapped; a cell whose centroid leaves [0, nx) is shifted here by the
+    box length as a whole, which the experiment's unwrapping must undo."""
+
+    velocity = {}
+    blow_up = {}
+
+    def __init__(self, scenes):
+        self.scenes, self.t, self.c = scenes, 0, 0
+
+    @classmethod
+    def from_scenes(cls, scenes, storage="f32", stream=None):
+        return cls(scenes)
+
+    def step(self, k):
+        self.t += k
+
+    def select(self, c):
+        self.c = c
+
+    def diagnostics(self):
+        out = np.zeros(6)
+        b = self.blow_up.get(self.c)
+        out[4] = 1.0 if b is not None and self.t >= b else 0.0
+        return out
+
+    def all_nodes_into(self, buf):
+        sc = self.scenes[self.c]
+        x = sc.meshes[0].rest.copy()
+        x[:, 0] += self.velocity.get(self.c, 0.0) * self.t
+        x[:, 0] -= sc.dims[0] * np.floor(x[:, 0].mean() / sc.dims[0])
+        buf[:] = x
+
+    def synchronize(self):
+        pass
+
+    def close(self):
+        pass
+
+
+def test_outcomes_and_unwrapping_across_the_periodic_axis(monkeypatch):
+    """The classification of the gap experiment on known trajectories: a cell
+    moving downstream passes at the step its centroid clears the plate by its
+    radius + 2 lu; a cell at rest is captured; a channel that turns
+    non-finite is unstable; and a cell drifting upstream across the periodic
+    boundary (its shifted x jumps past the plate) is captured, not passed."""
+    from paper_1110_0995_gb300 import lbibm
+
+    cs = gap_threshold.cases([8.0], kinds=("rbc",), steps=4000) * 4
+    x0 = cs[0][2].meshes[0].rest[:, 0].mean()
+    nx = cs[0][2].dims[0]
+    monkeypatch.setattr(lbibm, "Simulation", _DriftSim)
+    monkeypatch.setattr(_DriftSim, "velocity", {0: 0.01, 2: 0.01, 3: -0.02})
+    monkeypatch.setattr(_DriftSim, "blow_up", {2: 300})
+    recs, perf = gap_threshold.run(cs, 4000, every=100)
+    assert [r["outcome"] for r in recs] == ["passed", "captured", "unstable", "captured"]
+    need = nx / 2.0 + gap_threshold.CELL_RADIUS["rbc"] + 2.0 - x0      # distance to clear the plate
+    assert recs[0]["step"] == int(np.ceil(need / 0.01 / 100)) * 100
+    assert recs[2]["step"] == 300
+    assert x0 - 0.02 * 4000 < 0 and recs[3]["x_max"] < 0    # it crossed x = 0 going upstream
+    assert perf["channels"] == 4
+    th = gap_threshold.thresholds(recs)
+    assert th == {"rbc": {"smallest_passed": 8.0, "largest_captured": 8.0}}
