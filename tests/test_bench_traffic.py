@@ -1,0 +1,48 @@
+"""Host logic of the bench line's `roofline.traffic` (no GPU): the DRAM bytes
+of the committed ncu summary are reported only for the captured kernel
+variant and only while the kernel sources still match the digests recorded
+with the capture."""
+import hashlib
+import os
+import shutil
+
+import bench
+
+NAME = "k_stream_collide_micropost_filter_256x128x64_f32.md"
+SRCS = ("lattice_kernels.cu", "lbibm_internal.cuh")
+
+
+def _tree(tmp_path):
+    root = tmp_path / "repo"
+    (root / "profiles").mkdir(parents=True)
+    (root / "paper_1110_0995_gb300" / "csrc").mkdir(parents=True)
+    shutil.copy(os.path.join(bench.ROOT, "profiles", NAME), root / "profiles" / NAME)
+    for f in SRCS:
+        shutil.copy(os.path.join(bench.ROOT, "paper_1110_0995_gb300", "csrc", f),
+                    root / "paper_1110_0995_gb300" / "csrc" / f)
+    # digests of the copied sources, so that this tests the logic whether or
+    # not the committed summary is current
+    prof = root / "profiles" / NAME
+    digests = " ".join(f"{f} {hashlib.sha256((root / 'paper_1110_0995_gb300' / 'csrc' / f).read_bytes()).hexdigest()}"
+                       for f in SRCS)
+    prof.write_text("\n".join(f"kernel_source_sha256: {digests}" if l.startswith("kernel_source_sha256: ") else l
+                              for l in prof.read_text().splitlines()) + "\n")
+    return root
+
+
+def _recorded():
+    text = open(os.path.join(bench.ROOT, "profiles", NAME)).read()
+    line = [l for l in text.splitlines() if l.startswith("dram_bytes_per_launch: ")][0]
+    return int(line.split(": ")[1])
+
+
+def test_traffic_only_for_the_captured_kernel(tmp_path, monkeypatch):
+    root = _tree(tmp_path)
+    monkeypatch.setattr(bench, "ROOT", str(root))
+    wl, st, var = "micropost_filter_256x128x64", "f32", {"npt": 1, "bs": 128}
+    assert bench.profiled_traffic(wl, st, var) == _recorded()
+    assert bench.profiled_traffic(wl, st, {"npt": 2, "bs": 256}) is None       # another variant
+    assert bench.profiled_traffic(wl, "f16", var) is None                      # no summary for it
+    src = root / "paper_1110_0995_gb300" / "csrc" / SRCS[1]
+    src.write_text(src.read_text() + "\n")                                      # the kernel changed
+    assert bench.profiled_traffic(wl, st, var) is None
