@@ -1,4 +1,4 @@
-"""Host logic of the bench line's `roofline.traffic` (no GPU): the DRAM bytes
+"""Host logic of the bench line (no GPU).  `roofline.traffic`: the DRAM bytes
 of the committed ncu summary are reported only for the captured kernel
 variant and only while the kernel sources still match the digests recorded
 with the capture."""
@@ -46,3 +46,22 @@ def test_traffic_only_for_the_captured_kernel(tmp_path, monkeypatch):
     src = root / "paper_1110_0995_gb300" / "csrc" / SRCS[1]
     src.write_text(src.read_text() + "\n")                                      # the kernel changed
     assert bench.profiled_traffic(wl, st, var) is None
+
+
+def test_clock_summary_from_nvidia_smi_lines():
+    """The clocks object of the bench line from sampled nvidia-smi CSV rows:
+    median SM clock of the busy samples, the maximum, every active throttle
+    reason; no samples -> 'unavailable'."""
+    s = bench.ClockSampler(0)
+    s.lines = ["1965, 2070, Not Active, Not Active, Not Active, Not Active",
+               "2070, 2070, Not Active, Not Active, Not Active, Active",
+               "2070, 2070, Not Active, Not Active, Not Active, Not Active",
+               "2055, 2070, Not Active, Not Active, Not Active, Not Active",
+               "[N/A], 2070, Not Active, Not Active, Not Active, Not Active",
+               "garbage"]
+    out = s.summary()
+    assert out == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 4}
+    s.lines = ["600, 2070, Active, Not Active, Active, Not Active"] * 3
+    assert s.summary()["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
+    s.lines = []
+    assert s.summary()["reasons"] == ["unavailable"]
