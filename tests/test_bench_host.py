@@ -65,3 +65,28 @@ def test_clock_summary_from_nvidia_smi_lines():
     assert s.summary()["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
     s.lines = []
     assert s.summary()["reasons"] == ["unavailable"]
+
+
+def test_workloads_and_oracle_samples():
+    """The bench's named workloads have the sizes they are named for, an
+    unknown name is refused, and the oracle's bounded sample is the largest
+    filter instance within the node budget."""
+    import pytest
+
+    (f,) = bench.make_workload("micropost_filter_256x128x64")
+    assert f.dims == (256, 128, 64) and len(f.meshes) == 62
+    (c,) = bench.make_workload("channel_32x16x64_1rbc")
+    assert c.dims == (32, 16, 64) and len(c.meshes) == 1
+    with pytest.raises(ValueError):
+        bench.make_workload("no_such_workload")
+    for budget, dims in ((256 * 128 * 64, (256, 128, 64)), (256 * 128 * 64 - 1, (128, 64, 64)),
+                         (64 * 64 * 64, (64, 64, 64)), (10, (32, 32, 16))):
+        sc, n = bench.oracle_sample_scene(budget)
+        assert sc.dims == dims and n == dims[0] * dims[1] * dims[2]
+
+
+def test_peak_from_the_measured_file(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.measured_peak() == (6800.0, "fallback")
+    (tmp_path / "MEASURED_PEAKS.json").write_text('{"hbm_gbs": 6791.0, "bf16_tflops": 1873.4}')
+    assert bench.measured_peak() == (6791.0, "measured")
