@@ -316,17 +316,22 @@ lb_status ibm_get_area_volume(lb_ctx* ctx, double* area, double* volume);
  *   tris            device, n_tris x 3 int32 node indices, outward counter-clockwise
  *   cell_tri_start  device, n_cells + 1 int32: cell c owns triangles
  *                   [cell_tri_start[c], cell_tri_start[c+1])
- *   cell_tri_start_host  the same offsets in host memory (sizes the grid)
+ *   cell_tri_start_host  the same offsets in host memory (sizes the grid;
+ *                   offsets on the device that disagree with these give
+ *                   wrong sums but no access outside the scratch array)
  *   area, volume    device, n_cells doubles each (outputs)
  * FP64 throughout; queued on cuda_stream (NULL = legacy default stream),
  * asynchronous.  Scratch is a fixed 1 MiB device array (65,536 partial sums
  * of 256 triangles each) that every GPU loading the library holds until the
  * process exits: LB_ERR_ARG when n_cells times the largest number of
  * 256-triangle chunks of one cell exceeds 65,536, or n_cells > 65,535.  The
- * first call on a device looks the array's address up (cudaGetSymbolAddress);
- * make that first call before any stream capture.  Every call shares the
- * array, so calls that overlap on the GPU race.  Calls no cudaMalloc or
- * cudaFree. */
+ * first call on a device looks the array's address up (cudaGetSymbolAddress)
+ * and so does the first call after the device's current context changed (a
+ * cudaDeviceReset, or another driver context made current); make such a call
+ * before any stream capture.  Every call shares the array, so calls that
+ * overlap on the GPU race.  LB_ERR_CUDA when a launch is refused; an error
+ * left over from an earlier, unrelated call is not consumed.  Calls no
+ * cudaMalloc or cudaFree.  n_cells = 0 does nothing and returns LB_OK. */
 lb_status ibm_area_volume_noalloc(const double* xyz, const int32_t* tris, const int32_t* cell_tri_start,
                                   const int32_t* cell_tri_start_host, int n_cells, double* area, double* volume,
                                   void* cuda_stream);

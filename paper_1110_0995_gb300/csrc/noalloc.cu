@@ -14,8 +14,14 @@
 // call's contents; each call writes every partial it later reads, so nothing
 // has to start at zero.  Two calls whose kernels overlap on the GPU (different
 // streams, or different host threads) race on the array.
+//
+// The array's device address belongs to the CUDA context that loaded the
+// module.  It is looked up on a device's first call and again whenever the
+// context current on that device changes (a cudaDeviceReset, or a driver
+// context the caller made current), keyed by the context's unique id.
 #include "lbibm.h"
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -35,20 +41,52 @@ static __device__ __align__(256) double2 g_noalloc_partials[NA_MAX_PARTIALS];
 
 std::mutex g_setup_mutex;
 void* g_scratch_ptr[NA_MAX_DEVICES] = {};
+unsigned long long g_scratch_ctx[NA_MAX_DEVICES] = {};
 
-// Device address of the scratch array on the current device, looked up once
-// per device (under a lock) with that device current.
+// Unique id of the context current on the calling thread (driver entry points
+// through the runtime, so the library needs no link against libcuda).
+typedef CUresult (*ctx_get_current_fn)(CUcontext*);
+typedef CUresult (*ctx_get_id_fn)(CUcontext, unsigned long long*);
+
+cudaError_t current_context_id(unsigned long long* id) {
+    static ctx_get_current_fn get_current = nullptr;
+    static ctx_get_id_fn get_id = nullptr;
+    if (!get_current || !get_id) {
+        void* a = nullptr;
+        void* b = nullptr;
+        cudaDriverEntryPointQueryResult qa, qb;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 12000, cudaEnableDefault, &qa);
+        if (e != cudaSuccess || qa != cudaDriverEntryPointSuccess) return e != cudaSuccess ? e : cudaErrorNotSupported;
+        e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &qb);
+        if (e != cudaSuccess || qb != cudaDriverEntryPointSuccess) return e != cudaSuccess ? e : cudaErrorNotSupported;
+        get_current = (ctx_get_current_fn)a;
+        get_id = (ctx_get_id_fn)b;
+    }
+    CUcontext c = nullptr;
+    if (get_current(&c) != CUDA_SUCCESS || !c) return cudaErrorDeviceUninitialized;
+    if (get_id(c, id) != CUDA_SUCCESS) return cudaErrorDeviceUninitialized;
+    return cudaSuccess;
+}
+
+// Device address of the scratch array in the current context, looked up
+// (under a lock) on the first call on a device and whenever that device's
+// current context has changed since the last lookup.
 cudaError_t scratch_address(double2** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= NA_MAX_DEVICES) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_ptr[dev]) {
+    unsigned long long id = 0;
+    const bool have_id = current_context_id(&id) == cudaSuccess;   // false: no context current yet
+    if (!have_id || !g_scratch_ptr[dev] || g_scratch_ctx[dev] != id) {
         void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+        e = cudaGetSymbolAddress(&p, g_noalloc_partials);   // makes the primary context current if none is
+        if (e != cudaSuccess) return e;
+        e = current_context_id(&id);
         if (e != cudaSuccess) return e;
         g_scratch_ptr[dev] = p;
+        g_scratch_ctx[dev] = id;
     }
     *out = (double2*)g_scratch_ptr[dev];
     return cudaSuccess;
@@ -101,14 +139,18 @@ __global__ void __launch_bounds__(NA_BLOCK) k_area_volume_partials(const double*
     }
 }
 
-// Pass 2: one warp per cell adds the cell's partials in a fixed order.
+// Pass 2: one warp per cell adds the cell's partials in a fixed order.  The
+// chunk count comes from the device offsets and is clamped to the row stride
+// the host derived from its copy, so offsets that disagree with the host copy
+// give a wrong sum but never a read outside the cell's row of partials.
 __global__ void k_area_volume_final(const int* __restrict__ cell_start, int n_cells, int max_chunks,
                                     const double2* partials, double* area, double* volume) {
     const int c = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (c >= n_cells) return;
     const int nt = cell_start[c + 1] - cell_start[c];
-    const int nk = (nt + NA_BLOCK - 1) / NA_BLOCK;
+    int nk = (nt + NA_BLOCK - 1) / NA_BLOCK;
+    nk = nk < 0 ? 0 : (nk > max_chunks ? max_chunks : nk);
     double S = 0.0, V = 0.0;
     for (int k = lane; k < nk; k += 32) {
         const double2 p = partials[(long long)c * max_chunks + k];
@@ -145,8 +187,20 @@ extern "C" lb_status ibm_area_volume_noalloc(const double* xyz, const int32_t* t
     double2* scratch = nullptr;
     if (scratch_address(&scratch) != cudaSuccess) return LB_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)cuda_stream;
-    k_area_volume_partials<<<dim3(max_chunks, n_cells), NA_BLOCK, 0, s>>>(xyz, tris, cell_tri_start, max_chunks,
-                                                                          scratch);
-    k_area_volume_final<<<(n_cells + 7) / 8, 256, 0, s>>>(cell_tri_start, n_cells, max_chunks, scratch, area, volume);
-    return cudaGetLastError() == cudaSuccess ? LB_OK : LB_ERR_CUDA;
+    // each launch's own status (cudaLaunchKernel returns it; an error left over
+    // from an unrelated earlier call is neither consumed nor reported here)
+    const double* a_xyz = xyz;
+    const int* a_tris = tris;
+    const int* a_start = cell_tri_start;
+    void* args1[] = {(void*)&a_xyz, (void*)&a_tris, (void*)&a_start, (void*)&max_chunks, (void*)&scratch};
+    if (cudaLaunchKernel((const void*)k_area_volume_partials, dim3(max_chunks, n_cells), dim3(NA_BLOCK), args1, 0,
+                         s) != cudaSuccess)
+        return LB_ERR_CUDA;
+    const double2* a_scr = scratch;
+    void* args2[] = {(void*)&a_start, (void*)&n_cells, (void*)&max_chunks, (void*)&a_scr, (void*)&area,
+                     (void*)&volume};
+    if (cudaLaunchKernel((const void*)k_area_volume_final, dim3((n_cells + 7) / 8), dim3(256), args2, 0, s) !=
+        cudaSuccess)
+        return LB_ERR_CUDA;
+    return LB_OK;
 }
