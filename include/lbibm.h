@@ -55,8 +55,13 @@ typedef enum {
 
 /* Storage of the populations.  Arithmetic is FP32 in every mode.
  * LB_F32:          shifted populations h_i = f_i - w_i (rho0 = 1) in FP32.
- * LB_F16_SHIFTED:  h_i / w_i stored as IEEE binary16, round-to-nearest-even.
- * LB_BF16_SHIFTED: h_i / w_i stored as bfloat16, round-to-nearest-even. */
+ * LB_F16_SHIFTED:  h_i / w_i stored as IEEE binary16.
+ * LB_BF16_SHIFTED: h_i / w_i stored as bfloat16.
+ * 16-bit stores round stochastically: up with probability equal to the
+ * discarded fraction, the random bits a hash of the node index and the bit
+ * patterns of its moments (unbiased per store, independent between nodes,
+ * reproducible run to run).  Rounding to nearest would give a region of
+ * near-uniform flow one coherent error per step that viscosity does not damp. */
 typedef enum { LB_F32 = 0, LB_F16_SHIFTED = 1, LB_BF16_SHIFTED = 2 } lb_storage;
 
 typedef struct {
@@ -215,7 +220,8 @@ lb_status lb_step(lb_ctx* ctx, int n_steps);
 
 /* Variant of the fused stream-collide kernel.  nodes_per_thread 1, 2 or 4:
  * consecutive x-nodes per thread (every channel's nx a multiple of it), with
- * block_size 128 or 256.  nodes_per_thread 0: staged variant (rows copied to
+ * block_size 128 or 256; with 2 the pair's moments and collision run as packed
+ * two-lane FP32 operations.  nodes_per_thread 0: staged variant (rows copied to
  * shared memory asynchronously; block_size 256; every channel's row of nx
  * populations a multiple of 16 bytes and nx <= 512).  nodes_per_thread -1:
  * pipelined variant (persistent warps, block_size 128 or 256).
@@ -225,8 +231,9 @@ lb_status lb_step(lb_ctx* ctx, int n_steps);
  * (not periodic) in y and z, nx in {32, 64, 128, 256} dividing block_size and
  * ny a multiple of block_size / nx.  A block that gives up waiting for its
  * copies makes lb_diagnostics return LB_ERR_TIMEOUT.  The default is 1 node per
- * thread, 128 threads.  LB_ERR_ARG for an unsupported pair.  Results do not
- * depend on the variant. */
+ * thread, 128 threads.  LB_ERR_ARG for an unsupported pair.  Results depend
+ * on the variant only through FP32 rounding (the two-node variant orders the
+ * collision's operations differently). */
 lb_status lb_set_kernel_config(lb_ctx* ctx, int nodes_per_thread, int block_size);
 lb_status lb_get_kernel_config(lb_ctx* ctx, int* nodes_per_thread, int* block_size);
 

@@ -32,6 +32,11 @@ constexpr unsigned FULL = 0xffffffffu;
 __device__ __forceinline__ float to_f(float v) { return v; }
 __device__ __forceinline__ float to_f(__half v) { return __half2float(v); }
 __device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <class S> __device__ __forceinline__ S __ushort_as_s(unsigned short v);
+template <> __device__ __forceinline__ __half __ushort_as_s<__half>(unsigned short v) { return __ushort_as_half(v); }
+template <> __device__ __forceinline__ __nv_bfloat16 __ushort_as_s<__nv_bfloat16>(unsigned short v) {
+    return __ushort_as_bfloat16(v);
+}
 template <class S> __device__ __forceinline__ S from_f(float v);
 template <> __device__ __forceinline__ float from_f<float>(float v) { return v; }
 template <> __device__ __forceinline__ __half from_f<__half>(float v) { return __float2half_rn(v); }
@@ -59,14 +64,68 @@ __device__ __forceinline__ void pop_st(T* p, T v) {
     else *p = v;
 }
 
+// ---------------------------------------------------------------------------
+// Stochastic rounding of the 16-bit population stores.
+//
+// Rounding to nearest gives every node of a region of uniform flow the same
+// rounding error, so the errors of a step add up coherently over the region:
+// a uniform (k = 0) momentum error that viscosity does not damp, growing like
+// a random walk over the steps.  Rounding up with a probability equal to the
+// discarded fraction (stochastic rounding) makes each error unbiased and the
+// errors of different nodes independent, so they fall into short-wavelength
+// modes that the collision and viscosity damp.  (Emulated on the CPU on a
+// 32x48x48 force-driven channel after 200 steps, velocity error against
+// FP64: FP16 2.5e-3 -> 1.6e-4, BF16 1.8e-2 -> 1.3e-3.)
+//
+// cvt.rs.{f16x2,bf16x2}.f32 (sm_100 family) rounds its upper operand with the
+// upper 16 of its random bits and its lower operand with the lower 16.  The
+// random word of a node (or node pair) is a hash of its index and of the bit
+// patterns of its moments, which change from step to step: runs stay
+// bit-reproducible and no step counter is needed.  Direction i draws
+// seed * sr_k(i) (distinct odd multipliers).
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr unsigned sr_mix(unsigned x) {
+    // 32-bit integer finaliser (xorshift-multiply, "lowbias32" constants)
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+__host__ __device__ constexpr unsigned sr_k(int i) { return sr_mix(0x632be5abu + 0x9e3779b9u * (unsigned)i) | 1u; }
+
+__device__ __forceinline__ unsigned sr_seed(unsigned node, float a, float b) {
+    return sr_mix(node * 0x9e3779b1u ^ __float_as_uint(a) ^ __funnelshift_l(__float_as_uint(b), __float_as_uint(b), 16));
+}
+
+// Two floats to a packed 16-bit pair (hi: upper half) with stochastic rounding.
+template <class S> __device__ __forceinline__ unsigned cvt_rs2(float hi, float lo, unsigned rb);
+template <> __device__ __forceinline__ unsigned cvt_rs2<__half>(float hi, float lo, unsigned rb) {
+    unsigned d;
+    asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(rb));
+    return d;
+}
+template <> __device__ __forceinline__ unsigned cvt_rs2<__nv_bfloat16>(float hi, float lo, unsigned rb) {
+    unsigned d;
+    asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(rb));
+    return d;
+}
+// One float to 16 bits with stochastic rounding (the lower 16 random bits).
+template <class S> __device__ __forceinline__ S cvt_rs1(float v, unsigned rb) {
+    return __ushort_as_s<S>((unsigned short)(cvt_rs2<S>(0.0f, v, rb) & 0xffffu));
+}
+
 template <class S> struct Pop {
     static __device__ __forceinline__ float ld(const S* p, long long idx, int i) {
         if constexpr (sizeof(S) == 4) return pop_ld<S>(p + idx);
         else return wgt(i) * to_f(pop_ld<S>(p + idx));
     }
-    static __device__ __forceinline__ void st(S* p, long long idx, float h, int i) {
+    // rb: the node's random word (sr_seed); 16-bit storage rounds with
+    // rb * sr_k(i), FP32 ignores it
+    static __device__ __forceinline__ void st(S* p, long long idx, float h, int i, unsigned rb) {
         if constexpr (sizeof(S) == 4) pop_st<S>(p + idx, h);
-        else pop_st<S>(p + idx, from_f<S>(h * (1.0f / wgt(i))));
+        else pop_st<S>(p + idx, cvt_rs1<S>(h * (1.0f / wgt(i)), rb * sr_k(i)));
     }
 };
 
@@ -89,13 +148,15 @@ struct VecIO {
             else out[k] = wgt(i) * to_f(e[k]);
         }
     }
-    static __device__ __forceinline__ void st(S* base, long long idx, int i, const float in[NPT]) {
+    // rb[k]: random word of node k (16-bit storage only)
+    static __device__ __forceinline__ void st(S* base, long long idx, int i, const float in[NPT],
+                                              const unsigned rb[NPT]) {
         R r;
         S* e = reinterpret_cast<S*>(&r);
 #pragma unroll
         for (int k = 0; k < NPT; ++k) {
             if constexpr (sizeof(S) == 4) e[k] = from_f<S>(in[k]);
-            else e[k] = from_f<S>(in[k] * (1.0f / wgt(i)));
+            else e[k] = cvt_rs1<S>(in[k] * (1.0f / wgt(i)), rb[k] * sr_k(i));
         }
         pop_st<S>(reinterpret_cast<R*>(base + idx), r);
     }
@@ -348,11 +409,11 @@ __device__ __forceinline__ void collide_all(float h[Q], const Mac& m, float om, 
 }
 
 template <class S, int NPT, int I>
-__device__ __forceinline__ void store_vec(S* dst, long long NT, int gi0, const float h[NPT][Q]) {
+__device__ __forceinline__ void store_vec(S* dst, long long NT, int gi0, const float h[NPT][Q], const unsigned rb[NPT]) {
     float o[NPT];
 #pragma unroll
     for (int k = 0; k < NPT; ++k) o[k] = h[k][I];
-    VecIO<S, NPT>::st(dst + (size_t)I * (size_t)NT, gi0, I, o);
+    VecIO<S, NPT>::st(dst + (size_t)I * (size_t)NT, gi0, I, o, rb);
 }
 
 // Link masks of NPT consecutive nodes (one aligned vector load).
@@ -494,13 +555,16 @@ __device__ __forceinline__ void sc_nodes(const LatticeArgs& a, const ChannelDev&
             if constexpr (MODE == SC_BRINK) m[k] = macro_brinkman(h[k], gx, gy, gz, a.alpha * __ldg(a.phi + gi0 + k));
             else m[k] = macro(h[k], gx, gy, gz);
         }
+        unsigned rb[NPT];
+#pragma unroll
+        for (int k = 0; k < NPT; ++k) rb[k] = sr_seed((unsigned)(gi0 + k), m[k].drho, m[k].ux);
 #pragma unroll
         for (int k = 0; k < NPT; ++k) collide_all(h[k], m[k], om, fp);
         uint32_t solid = 0u;
 #pragma unroll
         for (int k = 0; k < NPT; ++k) solid |= lk[k];
         if (!(solid & 1u)) {
-#define LBIBM_SV(I) store_vec<S, NPT, I>(dst, NT, gi0, h);
+#define LBIBM_SV(I) store_vec<S, NPT, I>(dst, NT, gi0, h, rb);
             LBIBM_ALL_I(LBIBM_SV)
 #undef LBIBM_SV
         } else {
@@ -508,7 +572,7 @@ __device__ __forceinline__ void sc_nodes(const LatticeArgs& a, const ChannelDev&
 #pragma unroll
             for (int k = 0; k < NPT; ++k) {
                 if (lk[k] & 1u) continue;
-#define LBIBM_S1(I) Pop<S>::st(dst, (long long)(I) * NT + gi0 + k, h[k][I], I);
+#define LBIBM_S1(I) Pop<S>::st(dst, (long long)(I) * NT + gi0 + k, h[k][I], I, rb[k]);
                 LBIBM_ALL_I(LBIBM_S1)
 #undef LBIBM_S1
             }
@@ -549,6 +613,363 @@ __global__ void __launch_bounds__(BS, K3MinBlocks<S, NPT, BS>::value) k_stream_c
         }
     }
     sc_nodes<S, NPT, SC_ALL>(a, C, p0, lane);
+}
+
+// ---------------------------------------------------------------------------
+// Pair variant (nodes_per_thread = 2): each thread takes the consecutive
+// x-nodes x0, x0 + 1 (x0 even) of one row.  A direction without an x
+// component pulls both nodes' values as one aligned pair (a 32-bit word of two
+// 16-bit values, or a float2); a direction with one pulls two single values
+// (x0 - 1 and x0 along +x, x0 + 1 and x0 + 2 along -x).  The two nodes'
+// moments and collisions run as packed FP32 pairs (add / mul / fma.f32x2: two
+// FP32 lanes per instruction on the sm_100 family) and every direction is
+// stored as one pair.  16-bit storage keeps s_i = h_i / w_i, whose collision
+// is free of weights,
+//   s*_i = (1 - om) s_i + om [drho + rho (3 e.u + 9/2 (e.u)^2 - 3/2 u.u)]
+//          + (1 - 1/2tau) [3 (e_i - u) + 9 (e_i.u) e_i] . g,
+// so only the moments weigh the populations; FP32 keeps h_i and multiplies
+// the equilibrium and source part by w_i.  Stores round stochastically
+// (one random word per pair, see sr_mix).
+// ---------------------------------------------------------------------------
+typedef float2 F2;
+__device__ __forceinline__ F2 f2s(float a) { return make_float2(a, a); }
+__device__ __forceinline__ F2 add2(F2 a, F2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ F2 mul2(F2 a, F2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ F2 fma2(F2 a, F2 b, F2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ F2 sub2(F2 a, F2 b) {
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;"
+        : "=l"(r)
+        : "l"(*reinterpret_cast<const unsigned long long*>(&a)), "l"(*reinterpret_cast<const unsigned long long*>(&b)));
+    return *reinterpret_cast<const F2*>(&r);
+}
+
+template <class S> struct PairIO;
+template <> struct PairIO<float> {
+    static constexpr bool SCALED = false;
+    static __device__ __forceinline__ F2 ld2(const float* p) { return __ldg(reinterpret_cast<const float2*>(p)); }
+    static __device__ __forceinline__ float ld1(const float* p) { return __ldg(p); }
+    static __device__ __forceinline__ void st2(float* p, F2 v, unsigned) { *reinterpret_cast<float2*>(p) = v; }
+    static __device__ __forceinline__ void st1(float* p, float v, unsigned) { *p = v; }
+};
+template <> struct PairIO<__half> {
+    static constexpr bool SCALED = true;
+    static __device__ __forceinline__ F2 ld2(const __half* p) {
+        const unsigned r = __ldcs(reinterpret_cast<const unsigned*>(p));
+        return __half22float2(*reinterpret_cast<const __half2*>(&r));
+    }
+    static __device__ __forceinline__ float ld1(const __half* p) { return __half2float(__ldcs(p)); }
+    static __device__ __forceinline__ void st2(__half* p, F2 v, unsigned rb) {
+        __stcs(reinterpret_cast<unsigned*>(p), cvt_rs2<__half>(v.y, v.x, rb));
+    }
+    static __device__ __forceinline__ void st1(__half* p, float v, unsigned rb) { __stcs(p, cvt_rs1<__half>(v, rb)); }
+};
+template <> struct PairIO<__nv_bfloat16> {
+    static constexpr bool SCALED = true;
+    static __device__ __forceinline__ F2 ld2(const __nv_bfloat16* p) {
+        const unsigned r = __ldcs(reinterpret_cast<const unsigned*>(p));
+        return make_float2(__uint_as_float(r << 16), __uint_as_float(r & 0xffff0000u));
+    }
+    static __device__ __forceinline__ float ld1(const __nv_bfloat16* p) {
+        return __uint_as_float((unsigned)__bfloat16_as_ushort(__ldcs(p)) << 16);
+    }
+    static __device__ __forceinline__ void st2(__nv_bfloat16* p, F2 v, unsigned rb) {
+        __stcs(reinterpret_cast<unsigned*>(p), cvt_rs2<__nv_bfloat16>(v.y, v.x, rb));
+    }
+    static __device__ __forceinline__ void st1(__nv_bfloat16* p, float v, unsigned rb) {
+        __stcs(p, cvt_rs1<__nv_bfloat16>(v, rb));
+    }
+};
+
+// Offsets of the pull sources of one node pair relative to x0's index: the
+// rows y -+ 1, z -+ 1 (wrapped on periodic axes; a missing row maps to the
+// node's own row, whose link then bounces back) and the x neighbours x0 - 1 of
+// node 0 and x0 + 2 of node 1 (a missing one maps to the node itself).
+struct PairNbr {
+    int oym, oyp, ozm, ozp;
+    int dxm, dxp;
+};
+
+__device__ __forceinline__ void pair_neighbours(const ChannelDev& C, int x0, int y, int z, PairNbr& nb) {
+    const int sy = C.nx, sz = C.nx * C.ny;
+    nb.oym = y > 0 ? -sy : (C.per[1] ? (C.ny - 1) * sy : 0);
+    nb.oyp = y < C.ny - 1 ? sy : (C.per[1] ? -(C.ny - 1) * sy : 0);
+    nb.ozm = z > 0 ? -sz : (C.per[2] ? (C.nz - 1) * sz : 0);
+    nb.ozp = z < C.nz - 1 ? sz : (C.per[2] ? -(C.nz - 1) * sz : 0);
+    nb.dxm = x0 > 0 ? -1 : (C.per[0] ? C.nx - 1 : 0);
+    nb.dxp = x0 + 2 < C.nx ? 2 : (C.per[0] ? -x0 : 1);
+}
+
+template <int I>
+__device__ __forceinline__ int pair_row(const PairNbr& nb) {
+    int o = 0;
+    if (ey(I) == 1) o += nb.oym;
+    if (ey(I) == -1) o += nb.oyp;
+    if (ez(I) == 1) o += nb.ozm;
+    if (ez(I) == -1) o += nb.ozp;
+    return o;
+}
+
+// Pull direction I of both nodes (phase 1: the loads only).
+template <class S, int I>
+__device__ __forceinline__ F2 pair_pull(const S* src, long long NT, int gi0, const PairNbr& nb, bool inr) {
+    const S* pl = src + (size_t)I * (size_t)NT + gi0 + pair_row<I>(nb);
+    if (!inr) return make_float2(0.f, 0.f);
+    if constexpr (ex(I) == 0) return PairIO<S>::ld2(pl);
+    else if constexpr (ex(I) == 1) return make_float2(PairIO<S>::ld1(pl + nb.dxm), PairIO<S>::ld1(pl));
+    else return make_float2(PairIO<S>::ld1(pl + 1), PairIO<S>::ld1(pl + nb.dxp));
+}
+
+// Halfway bounce-back of node k of the pair: population I comes back as the
+// node's own opp(I) (in the storage's scaling), plus Ladd's moving-wall term.
+template <class S, int I>
+__device__ __forceinline__ void pair_bounce(const S* src, long long NT, int gi, uint32_t lk, const ChannelDev& C,
+                                            int y, float& v) {
+    if (!((lk >> I) & 1u)) return;
+    float b = PairIO<S>::ld1(src + (size_t)opp(I) * (size_t)NT + gi);
+    if (C.has_uw && !C.per[1]) {
+        const int wall = (ey(I) == 1 && y == 0) ? 0 : ((ey(I) == -1 && y == C.ny - 1) ? 1 : -1);
+        if (wall >= 0) {
+            const float eu = ex(I) * C.uw[wall][0] + ey(I) * C.uw[wall][1] + ez(I) * C.uw[wall][2];
+            b += PairIO<S>::SCALED ? 6.0f * eu : 6.0f * wgt(I) * eu;
+        }
+    }
+    v = b;
+}
+
+// e_I . (ax, ay, az) for the packed pair, with e_I's components in {-1, 0, 1}.
+template <int I>
+__device__ __forceinline__ F2 edot2(F2 ax, F2 ay, F2 az) {
+    F2 r = make_float2(0.f, 0.f);
+    bool any = false;
+    auto acc = [&](int e, F2 v) {
+        if (e == 0) return;
+        if (!any) {
+            r = e > 0 ? v : make_float2(-v.x, -v.y);
+            any = true;
+        } else {
+            r = e > 0 ? add2(r, v) : sub2(r, v);
+        }
+    };
+    acc(ex(I), ax);
+    acc(ey(I), ay);
+    acc(ez(I), az);
+    return r;
+}
+
+// Packed macroscopic state of the pair.
+struct Mac2 {
+    F2 drho, rho, ux, uy, uz, gx, gy, gz, A1, mug;
+};
+
+// Collision of the opposite directions (I, I + 1), I odd, for both nodes.
+template <bool SCALED, int I>
+__device__ __forceinline__ void collide_pair2(F2 h[Q], const Mac2& m, F2 om, F2 omc, F2 c3om, F2 c9fp, F2 c3fp) {
+    constexpr int J = I + 1;
+    const F2 eu = edot2<I>(m.ux, m.uy, m.uz);
+    const F2 eg = edot2<I>(m.gx, m.gy, m.gz);
+    const F2 reu = mul2(m.rho, eu);
+    const F2 E = fma2(mul2(f2s(4.5f), reu), eu, m.A1);          // A1 + 9/2 rho (e.u)^2
+    const F2 Es = fma2(om, E, fma2(mul2(c9fp, eu), eg, m.mug));   // + fp (9 (e.u)(e.g) - 3 u.g)
+    const F2 Os = fma2(c3om, reu, mul2(c3fp, eg));                // 3 om rho e.u + 3 fp e.g
+    const F2 XI = add2(Es, Os), XJ = sub2(Es, Os);
+    if constexpr (SCALED) {
+        h[I] = fma2(omc, h[I], XI);
+        h[J] = fma2(omc, h[J], XJ);
+    } else {
+        const F2 w = f2s(wgt(I));
+        h[I] = fma2(w, XI, mul2(omc, h[I]));
+        h[J] = fma2(w, XJ, mul2(omc, h[J]));
+    }
+}
+
+// Moments, collision and stores of one in-range node pair (h: the pulled
+// populations after bounce-back; lk0 / lk1: the nodes' link masks).
+template <class S>
+__device__ __forceinline__ void pair_collide_store(const LatticeArgs& a, const ChannelDev& C, int gi0, F2 h[Q],
+                                                   uint32_t lk0, uint32_t lk1, bool forced, bool prevf) {
+    using IO = PairIO<S>;
+    constexpr bool SCALED = IO::SCALED;
+    const int par = a.par;
+    S* dst = (S*)(par ? a.h0 : a.h1);
+    const long long NT = a.Ntot;
+    const float4* gcur = par ? a.g1 : a.g0;
+    float4* gprev = par ? a.g0 : a.g1;
+    Mac2 m;
+    m.gx = make_float2(C.G[0], C.G[0]);
+    m.gy = make_float2(C.G[1], C.G[1]);
+    m.gz = make_float2(C.G[2], C.G[2]);
+    if (forced) {
+        const float4 g0 = gcur[gi0], g1 = gcur[gi0 + 1];
+        m.gx = add2(m.gx, make_float2(g0.x, g1.x));
+        m.gy = add2(m.gy, make_float2(g0.y, g1.y));
+        m.gz = add2(m.gz, make_float2(g0.z, g1.z));
+    }
+    // moments (pairwise differences of opposite directions first)
+    {
+        const F2 a1 = sub2(h[1], h[2]), a3 = sub2(h[3], h[4]), a5 = sub2(h[5], h[6]);
+        const F2 d7 = sub2(h[7], h[8]), d9 = sub2(h[9], h[10]), d11 = sub2(h[11], h[12]);
+        const F2 d13 = sub2(h[13], h[14]), d15 = sub2(h[15], h[16]), d17 = sub2(h[17], h[18]);
+        const F2 sa = add2(add2(add2(h[1], h[2]), add2(h[3], h[4])), add2(h[5], h[6]));
+        const F2 sd = add2(add2(add2(add2(h[7], h[8]), add2(h[9], h[10])), add2(add2(h[11], h[12]), add2(h[13], h[14]))),
+                           add2(add2(h[15], h[16]), add2(h[17], h[18])));
+        const F2 dx = add2(add2(d7, d9), add2(d11, d13));
+        const F2 dy = add2(sub2(d7, d9), add2(d15, d17));
+        const F2 dz = add2(sub2(d11, d13), sub2(d15, d17));
+        F2 jx, jy, jz;
+        if constexpr (SCALED) {
+            const F2 w1 = f2s(wgt(1)), w2 = f2s(wgt(7));
+            jx = fma2(w1, a1, mul2(w2, dx));
+            jy = fma2(w1, a3, mul2(w2, dy));
+            jz = fma2(w1, a5, mul2(w2, dz));
+            m.drho = fma2(f2s(wgt(0)), h[0], fma2(w1, sa, mul2(w2, sd)));
+        } else {
+            jx = add2(a1, dx);
+            jy = add2(a3, dy);
+            jz = add2(a5, dz);
+            m.drho = add2(h[0], add2(sa, sd));
+        }
+        m.rho = add2(f2s(1.0f), m.drho);
+        const F2 irho = make_float2(1.0f / m.rho.x, 1.0f / m.rho.y);
+        const F2 half = f2s(0.5f);
+        m.ux = mul2(fma2(half, m.gx, jx), irho);
+        m.uy = mul2(fma2(half, m.gy, jy), irho);
+        m.uz = mul2(fma2(half, m.gz, jz), irho);
+    }
+    const F2 uu = fma2(m.uz, m.uz, fma2(m.uy, m.uy, mul2(m.ux, m.ux)));
+    const F2 ug = fma2(m.uz, m.gz, fma2(m.uy, m.gy, mul2(m.ux, m.gx)));
+    const float om_s = C.omega, fp_s = C.fpre;
+    m.A1 = fma2(mul2(f2s(-1.5f), m.rho), uu, m.drho);   // drho - 3/2 rho u.u
+    m.mug = mul2(f2s(-3.0f * fp_s), ug);                // -3 fp u.g
+    const unsigned seed = sr_seed((unsigned)gi0, m.drho.x, m.ux.y);
+    const F2 om = f2s(om_s), omc = f2s(1.0f - om_s), c3om = f2s(3.0f * om_s);
+    const F2 c9fp = f2s(9.0f * fp_s), c3fp = f2s(3.0f * fp_s);
+    // rest population: (1 - om) h0 + w0 [om A1 - 3 fp u.g]
+    {
+        const F2 X0 = fma2(om, m.A1, m.mug);
+        if constexpr (SCALED) h[0] = fma2(omc, h[0], X0);
+        else h[0] = fma2(f2s(wgt(0)), X0, mul2(omc, h[0]));
+    }
+    collide_pair2<SCALED, 1>(h, m, om, omc, c3om, c9fp, c3fp);
+    collide_pair2<SCALED, 3>(h, m, om, omc, c3om, c9fp, c3fp);
+    collide_pair2<SCALED, 5>(h, m, om, omc, c3om, c9fp, c3fp);
+    collide_pair2<SCALED, 7>(h, m, om, omc, c3om, c9fp, c3fp);
+    collide_pair2<SCALED, 9>(h, m, om, omc, c3om, c9fp, c3fp);
+    collide_pair2<SCALED, 11>(h, m, om, omc, c3om, c9fp, c3fp);
+    collide_pair2<SCALED, 13>(h, m, om, omc, c3om, c9fp, c3fp);
+    collide_pair2<SCALED, 15>(h, m, om, omc, c3om, c9fp, c3fp);
+    collide_pair2<SCALED, 17>(h, m, om, omc, c3om, c9fp, c3fp);
+    const bool s0 = lk0 & 1u, s1 = lk1 & 1u;
+    if (!(s0 || s1)) {
+#define LBIBM_P2(I) IO::st2(dst + (size_t)(I) * (size_t)NT + gi0, h[I], seed * sr_k(I));
+        LBIBM_ALL_I(LBIBM_P2)
+#undef LBIBM_P2
+    } else {
+        // a solid node keeps its populations; the other one is stored alone
+        if (!s0) {
+#define LBIBM_P1(I) IO::st1(dst + (size_t)(I) * (size_t)NT + gi0, h[I].x, seed * sr_k(I));
+            LBIBM_ALL_I(LBIBM_P1)
+#undef LBIBM_P1
+        }
+        if (!s1) {
+#define LBIBM_P1(I) IO::st1(dst + (size_t)(I) * (size_t)NT + gi0 + 1, h[I].y, (seed * sr_k(I)) >> 16);
+            LBIBM_ALL_I(LBIBM_P1)
+#undef LBIBM_P1
+        }
+    }
+    if (forced) {
+        if (!s0) a.u[gi0] = make_float4(m.ux.x, m.uy.x, m.uz.x, m.rho.x);
+        if (!s1) a.u[gi0 + 1] = make_float4(m.ux.y, m.uy.y, m.uz.y, m.rho.y);
+    }
+    if (prevf) {
+        if (!s0) gprev[gi0] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (!s1) gprev[gi0 + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
+template <class S, bool ROW>
+__device__ __forceinline__ void sc_pair(const LatticeArgs& a, const ChannelDev& C, int p0, int xr, int yr, int zr) {
+    const int gi0 = (int)(C.base + p0);   // even; the padded node count of a context is below 2^31
+    const int grp = gi0 >> 5;
+    const int par = a.par;
+    uint8_t* fl_prev = par ? a.fl0 : a.fl1;
+    const bool inr = ROW ? true : p0 < C.n;
+    const uint8_t fslow = inr ? __ldg(a.slow + grp) : (uint8_t)0;
+    const S* src = (const S*)(par ? a.h1 : a.h0);
+    const long long NT = a.Ntot;
+    int x0, y, z;
+    if constexpr (ROW) {
+        x0 = xr; y = yr; z = zr;
+    } else {
+        const int r = fdiv(p0, C.dnx);
+        x0 = p0 - r * C.nx;
+        z = fdiv(r, C.dny);
+        y = r - z * C.ny;
+    }
+    PairNbr nb;
+    pair_neighbours(C, x0, y, z, nb);
+    // phase 1: every population load in flight at once
+    F2 h[Q];
+#define LBIBM_PP(I) h[I] = pair_pull<S, I>(src, NT, gi0, nb, inr);
+    LBIBM_ALL_I(LBIBM_PP)
+#undef LBIBM_PP
+    // the populations are the previous cycle's; flags and force densities come
+    // from the spreading kernel this launch may overlap
+    pdl_entry();
+    const uint8_t fcur = __ldg((par ? a.fl1 : a.fl0) + grp);
+    const uint8_t fprev = __ldg(fl_prev + grp);
+    const bool forced = fcur != 0;
+    const bool prevf = fprev != 0;
+    const bool wslow = __any_sync(FULL, fslow != 0);
+    uint32_t lk0 = 0u, lk1 = 0u;
+    if (wslow) {
+        if (inr && fslow) {
+            const uint2 l = __ldg(reinterpret_cast<const uint2*>(a.links + gi0));
+            lk0 = l.x;
+            lk1 = l.y;
+        }
+        if (lk0 & ~1u) {
+#define LBIBM_PB(I) if (I > 0) pair_bounce<S, I>(src, NT, gi0, lk0, C, y, h[I].x);
+            LBIBM_ALL_I(LBIBM_PB)
+#undef LBIBM_PB
+        }
+        if (lk1 & ~1u) {
+#define LBIBM_PB(I) if (I > 0) pair_bounce<S, I>(src, NT, gi0 + 1, lk1, C, y, h[I].y);
+            LBIBM_ALL_I(LBIBM_PB)
+#undef LBIBM_PB
+        }
+    }
+    if (inr) pair_collide_store<S>(a, C, gi0, h, lk0, lk1, forced, prevf);
+    // the lane holding the first node of each 32-node group clears the previous
+    // step's flag after every lane of the warp has consumed it
+    __syncwarp();
+    if (prevf && (gi0 & 31) == 0) fl_prev[grp] = 0;
+}
+
+// Resident threads per SM of the pair variant's register budget (512: the
+// kernel's 122 registers without spills).
+#ifndef LBIBM_K3_PAIR_THREADS
+#define LBIBM_K3_PAIR_THREADS 512
+#endif
+
+template <class S, int BS>
+__global__ void __launch_bounds__(BS, LBIBM_K3_PAIR_THREADS / BS) k_stream_collide_pair(const __grid_constant__ LatticeArgs a) {
+    // (sc_pair waits for the predecessor after its population loads)
+    const int b = blockIdx.x;
+    int c = 0;
+    for (int k = 1; k < a.n_ch; ++k)
+        if (b >= chan(a, k).blk0) c = k;
+    const ChannelDev C = chan(a, c);
+    const int pb = (b - C.blk0) * (2 * BS);                  // first channel-local node of the block
+    const int p0 = pb + 2 * (int)threadIdx.x;
+    if (C.nx % (2 * BS) == 0 && pb + 2 * BS <= C.n) {
+        // the block is a piece of one row: y and z are the block's
+        const int r = fdiv(pb, C.dnx);
+        const int z = fdiv(r, C.dny);
+        sc_pair<S, true>(a, C, p0, pb - r * C.nx + 2 * (int)threadIdx.x, r - z * C.ny, z);
+        return;
+    }
+    sc_pair<S, false>(a, C, p0, 0, 0, 0);
 }
 
 // Bulk of the overlapped schedule (one node per thread; a warp is one group).
@@ -705,8 +1126,9 @@ __device__ __forceinline__ void staged_compute(const LatticeArgs& a, const S* sr
                     gx += gg.x; gy += gg.y; gz += gg.z;
                 }
                 const Mac m = macro(h, gx, gy, gz);
+                const unsigned rb = sr_seed((unsigned)gp, m.drho, m.ux);
                 collide_all(h, m, om, fp);
-#define LBIBM_C1(I) Pop<S>::st(dst, (long long)(I) * NT + gp, h[I], I);
+#define LBIBM_C1(I) Pop<S>::st(dst, (long long)(I) * NT + gp, h[I], I, rb);
                 LBIBM_ALL_I(LBIBM_C1)
 #undef LBIBM_C1
                 if (forced) a.u[gp] = make_float4(m.ux, m.uy, m.uz, m.rho);
@@ -819,8 +1241,9 @@ __device__ __forceinline__ void pipe_process(const LatticeArgs& a, const S* src,
         }
         const Mac m = macro(h, gx, gy, gz);
         const float om = C.omega, fp = C.fpre;
+        const unsigned rb = sr_seed((unsigned)gp, m.drho, m.ux);
         collide_all(h, m, om, fp);
-#define LBIBM_C1(I) Pop<S>::st(dst, (long long)(I) * NT + gp, h[I], I);
+#define LBIBM_C1(I) Pop<S>::st(dst, (long long)(I) * NT + gp, h[I], I, rb);
         LBIBM_ALL_I(LBIBM_C1)
 #undef LBIBM_C1
         if (forced) a.u[gp] = make_float4(m.ux, m.uy, m.uz, m.rho);
@@ -1165,6 +1588,11 @@ static cudaError_t launch_sc_typed(const LatticeArgs& a, K3Config c, int blocks,
     if (c.npt == N && c.bs == B) {                         \
         return launch_ex(k_stream_collide<S, N, B>, blocks, B, 0, s, a.pdl, a); \
     }
+    if (c.npt == 2) {
+        if (c.bs == 128) return launch_ex(k_stream_collide_pair<S, 128>, blocks, 128, 0, s, a.pdl, a);
+        if (c.bs == 256) return launch_ex(k_stream_collide_pair<S, 256>, blocks, 256, 0, s, a.pdl, a);
+        return cudaErrorInvalidConfiguration;
+    }
     if (c.npt == 0) {
         return launch_ex(k_stream_collide_staged<S>, blocks, SG_THREADS, staged_smem<S>(), s, a.pdl, a);
     }
@@ -1173,11 +1601,9 @@ static cudaError_t launch_sc_typed(const LatticeArgs& a, K3Config c, int blocks,
         return launch_ex(k_stream_collide_pipe<S, 256>, blocks, 256, 0, s, a.pdl, a);
     }
     if constexpr (sizeof(S) == 4) {
-        LBIBM_CASE(1, 256) LBIBM_CASE(2, 256) LBIBM_CASE(4, 256) LBIBM_CASE(4, 128) LBIBM_CASE(2, 128)
-        LBIBM_CASE(1, 128)
+        LBIBM_CASE(1, 256) LBIBM_CASE(4, 256) LBIBM_CASE(4, 128) LBIBM_CASE(1, 128)
     } else {
-        LBIBM_CASE(2, 256) LBIBM_CASE(4, 256) LBIBM_CASE(4, 128) LBIBM_CASE(2, 128) LBIBM_CASE(1, 256)
-        LBIBM_CASE(1, 128)
+        LBIBM_CASE(4, 256) LBIBM_CASE(4, 128) LBIBM_CASE(1, 256) LBIBM_CASE(1, 128)
     }
 #undef LBIBM_CASE
     return cudaErrorInvalidConfiguration;

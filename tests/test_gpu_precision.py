@@ -1,11 +1,16 @@
 """Shifted 16-bit population storage at the 512x256x128 filter scale (404
 cells, 672 beads): error of FP32, FP16 and BF16 storage against the FP64
 oracle per field after 200 cycles (rho, u, node positions, per-cell volume
-change).  Measured on GB300: FP16 1.26e-3 in u (the 1e-3 target is met on
-the plain channel, tests/test_gpu_parity.py, but not at this scale, where the
-velocities are ~10x smaller and the storage rounding of every population in
-every cycle adds up), BF16 9.9e-3.  FP32 is held to the parity tolerance,
-FP16 and BF16 to regression bounds 2e-3 and 2e-2."""
+change).
+
+The 16-bit stores round stochastically (an unbiased rounding whose random bits
+are a hash of the node and its moments).  Rounding to nearest gave every node
+of a region of nearly uniform flow the same error, and those errors added up
+over the cycles into a velocity error that viscosity does not damp: on GB300
+FP16 reached 1.26e-3 and BF16 9.9e-3 in u with round-to-nearest, against
+2.0e-4 and 1.6e-3 with stochastic rounding.  FP32 is held to the parity
+tolerance, FP16 to the 1e-3 velocity target, BF16 (8-bit mantissa, reported,
+not a target) to a regression bound of 3e-3."""
 import numpy as np
 import pytest
 
@@ -56,5 +61,5 @@ def test_storage_precision_large_filter():
         print(st, errs[st])
         sim.close()
     assert errs["f32"]["u_rel_l2"] < 1e-5 and errs["f32"]["x_max"] < 1e-5
-    assert errs["f16"]["u_rel_l2"] <= 2e-3
-    assert errs["bf16"]["u_rel_l2"] <= 2e-2
+    assert errs["f16"]["u_rel_l2"] <= 1e-3
+    assert errs["bf16"]["u_rel_l2"] <= 3e-3
