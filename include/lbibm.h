@@ -231,11 +231,25 @@ lb_status lb_step(lb_ctx* ctx, int n_steps);
  * (not periodic) in y and z, nx in {32, 64, 128, 256} dividing block_size and
  * ny a multiple of block_size / nx.  A block that gives up waiting for its
  * copies makes lb_diagnostics return LB_ERR_TIMEOUT.  The default is 1 node per
- * thread, 128 threads.  LB_ERR_ARG for an unsupported pair.  Results depend
+ * thread, 128 threads, for FP32 storage, and for 16-bit storage 4 nodes per
+ * thread, 64 threads where every nx is a multiple of 4 (the 16-bit variant
+ * with 4 nodes per thread keeps each direction's four values packed in one
+ * 64-bit word until the node pairs are unpacked in turn).  LB_ERR_ARG for an unsupported pair.  Results depend
  * on the variant only through FP32 rounding (the two-node variant orders the
  * collision's operations differently). */
 lb_status lb_set_kernel_config(lb_ctx* ctx, int nodes_per_thread, int block_size);
 lb_status lb_get_kernel_config(lb_ctx* ctx, int* nodes_per_thread, int* block_size);
+
+/* L2 prefetch distance of the fused stream-collide kernel (one, two or four
+ * nodes per thread), in lattice nodes: each block asks L2 for the source
+ * populations (every direction's plane) of the nodes nodes_ahead past its
+ * own, so that blocks running later find their pulls in L2 rather than in
+ * HBM.  A performance setting only (Sec. 2.1's update is unchanged; results
+ * are bit-identical for every distance).  0 = off (the default); otherwise a
+ * multiple of 256 up to 2^24, else LB_ERR_ARG.  The bound on the useful
+ * distance is the L2 (19 x 4 bytes per node of distance for FP32 storage). */
+lb_status lb_set_prefetch(lb_ctx* ctx, int nodes_ahead);
+lb_status lb_get_prefetch(lb_ctx* ctx, int* nodes_ahead);
 
 /* Step schedule.  overlapped = 0 (default): the four kernels of the cycle
  * run one after another, each launched as a programmatic dependent of its
@@ -260,10 +274,12 @@ lb_status lb_set_schedule(lb_ctx* ctx, int overlapped);
 lb_status lb_get_schedule(lb_ctx* ctx, int* overlapped);
 
 /* Autotuner: times every supported stream-collide variant on this context's
- * lattice (`repeats` launches each, CUDA events), selects the fastest and
- * returns it with its mean time per launch in ms.  Only before the first
- * lb_step (LB_ERR_STATE otherwise): there, repeated launches leave the state
- * unchanged. */
+ * lattice (`repeats` launches each, CUDA events), selects the fastest, then
+ * times its L2 prefetch distances (0, 65536, 131072, 262144 nodes; variants
+ * with 1, 2 or 4 nodes per thread) and keeps the fastest (lb_get_prefetch
+ * reads it), and returns the variant with its mean time per launch in ms.
+ * Only before the first lb_step (LB_ERR_STATE otherwise): there, repeated
+ * launches leave the state unchanged. */
 lb_status lb_autotune(lb_ctx* ctx, int repeats, int* nodes_per_thread, int* block_size, double* ms);
 
 /* Wait for the context's stream and report any pending error. */

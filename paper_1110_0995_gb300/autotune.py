@@ -1,7 +1,8 @@
 """Autotuner cache for the stream-collide kernel variant.
 
 The library's ``lb_autotune`` times every (nodes per thread, block size)
-variant on a context's lattice; this module remembers the winner per
+variant on a context's lattice and then the L2 prefetch distance of the
+winner; this module remembers both per
 (device, storage, channel dimensions) in a JSON file outside the repository
 (``$LBIBM_CACHE`` or ``~/.cache/lbibm/autotune.json``) so later runs skip the
 timing.
@@ -36,12 +37,14 @@ def tune(sim, device: str, storage: str, repeats: int = 20, use_cache: bool = Tr
         npt, bs = table[key]["npt"], table[key]["bs"]
         try:
             sim.set_kernel_config(npt, bs)
-            return {"npt": npt, "bs": bs, "ms": table[key].get("ms"), "cached": True}
+            sim.set_prefetch(table[key].get("pf", 0))
+            return {"npt": npt, "bs": bs, "pf": sim.prefetch(), "ms": table[key].get("ms"), "cached": True}
         except RuntimeError:
             pass   # a variant this library no longer offers: time them again
     npt, bs, ms = sim.autotune(repeats)
+    pf = sim.prefetch()
     table = _load()
-    table[key] = {"npt": npt, "bs": bs, "ms": ms}
+    table[key] = {"npt": npt, "bs": bs, "pf": pf, "ms": ms}
     try:
         os.makedirs(os.path.dirname(cache_path()), exist_ok=True)
         tmp = cache_path() + f".tmp{os.getpid()}"
@@ -50,4 +53,4 @@ def tune(sim, device: str, storage: str, repeats: int = 20, use_cache: bool = Tr
         os.replace(tmp, cache_path())
     except OSError:
         pass
-    return {"npt": npt, "bs": bs, "ms": ms, "cached": False}
+    return {"npt": npt, "bs": bs, "pf": pf, "ms": ms, "cached": False}

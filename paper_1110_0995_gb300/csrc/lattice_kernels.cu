@@ -170,6 +170,25 @@ __device__ __forceinline__ const ChannelDev& chan(const LatticeArgs& a, int c) {
     return c < MAXCH_P ? a.chp[c] : a.ch[c];
 }
 
+// L2 prefetch ahead of the stream-collide blocks: threads 0..18 of a block
+// whose first node has global index g0 and that covers nb nodes each ask L2
+// (one bulk prefetch, no registers held, nothing returned) for the nb
+// populations of their direction starting pf_nodes further on, clipped to the
+// direction's plane.  Every address lies inside the population array: the
+// start is below the plane stride and the end at most at it.  Requires
+// g0 + pf_nodes and nb * sizeof(S) to be multiples of 16 bytes' worth of
+// populations (the block sizes and the distance are multiples of 256 nodes).
+template <class S>
+__device__ __forceinline__ void prefetch_ahead(const LatticeArgs& a, long long g0, int nb) {
+    if (a.pf_nodes <= 0 || threadIdx.x >= Q) return;
+    const long long g = g0 + a.pf_nodes;
+    if (g >= a.Ntot) return;
+    const long long n = a.Ntot - g < nb ? a.Ntot - g : nb;
+    const S* src = (const S*)(a.par ? a.h1 : a.h0) + (size_t)threadIdx.x * (size_t)a.Ntot + g;
+    const unsigned bytes = (unsigned)(n * (long long)sizeof(S)) & ~15u;
+    if (bytes) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 // Source offsets of the pull scheme for one node: for each axis the linear
 // offset to the neighbour at coordinate -1 ("m") and +1 ("p"), with periodic
 // wrap, and whether that neighbour exists.
@@ -600,6 +619,7 @@ __global__ void __launch_bounds__(BS, K3MinBlocks<S, NPT, BS>::value) k_stream_c
     const ChannelDev C = chan(a, c);   // registers: read once from the parameter bank
     const int lane = threadIdx.x & 31;
     const int p0 = ((b - C.blk0) * BS + (int)threadIdx.x) * NPT;   // first channel-local node of this thread
+    prefetch_ahead<S>(a, C.base + (long long)(b - C.blk0) * BS * NPT, BS * NPT);
     if constexpr (NPT == 1) {
         // (measured on GB300, 256x128x64 filter: FP32 62.4 -> 60.6 us with the
         // 56-register budget, 16-bit 59.6 -> 57.5 us)
@@ -700,8 +720,8 @@ __device__ __forceinline__ void pair_neighbours(const ChannelDev& C, int x0, int
     nb.dxp = x0 + 2 < C.nx ? 2 : (C.per[0] ? -x0 : 1);
 }
 
-template <int I>
-__device__ __forceinline__ int pair_row(const PairNbr& nb) {
+template <int I, class NB>
+__device__ __forceinline__ int pair_row(const NB& nb) {
     int o = 0;
     if (ey(I) == 1) o += nb.oym;
     if (ey(I) == -1) o += nb.oyp;
@@ -722,11 +742,12 @@ __device__ __forceinline__ F2 pair_pull(const S* src, long long NT, int gi0, con
 
 // Halfway bounce-back of node k of the pair: population I comes back as the
 // node's own opp(I) (in the storage's scaling), plus Ladd's moving-wall term.
-template <class S, int I>
-__device__ __forceinline__ void pair_bounce(const S* src, long long NT, int gi, uint32_t lk, const ChannelDev& C,
+template <class S, int I, class NTT>
+__device__ __forceinline__ void pair_bounce(const S* src, NTT NT, int gi, uint32_t lk, const ChannelDev& C,
                                             int y, float& v) {
     if (!((lk >> I) & 1u)) return;
-    float b = PairIO<S>::ld1(src + (size_t)opp(I) * (size_t)NT + gi);
+    float b = PairIO<S>::ld1(src + (sizeof(NTT) == 4 ? (size_t)((unsigned)opp(I) * (unsigned)NT + (unsigned)gi)
+                                                     : (size_t)opp(I) * (size_t)NT + gi));
     if (C.has_uw && !C.per[1]) {
         const int wall = (ey(I) == 1 && y == 0) ? 0 : ((ey(I) == -1 && y == C.ny - 1) ? 1 : -1);
         if (wall >= 0) {
@@ -783,24 +804,18 @@ __device__ __forceinline__ void collide_pair2(F2 h[Q], const Mac2& m, F2 om, F2 
     }
 }
 
-// Moments, collision and stores of one in-range node pair (h: the pulled
-// populations after bounce-back; lk0 / lk1: the nodes' link masks).
-template <class S>
-__device__ __forceinline__ void pair_collide_store(const LatticeArgs& a, const ChannelDev& C, int gi0, F2 h[Q],
-                                                   uint32_t lk0, uint32_t lk1, bool forced, bool prevf) {
-    using IO = PairIO<S>;
-    constexpr bool SCALED = IO::SCALED;
-    const int par = a.par;
-    S* dst = (S*)(par ? a.h0 : a.h1);
-    const long long NT = a.Ntot;
-    const float4* gcur = par ? a.g1 : a.g0;
-    float4* gprev = par ? a.g0 : a.g1;
-    Mac2 m;
+// Moments and collision of one in-range node pair in place (h: the pulled
+// populations after bounce-back, in the storage's scaling; g0, g1: the nodes'
+// force densities, added when the group is forced).  m returns the pair's
+// macroscopic state (velocity, density) for the velocity output and the
+// rounding seed.
+template <bool SCALED>
+__device__ __forceinline__ void pair_collide(const ChannelDev& C, float4 g0, float4 g1, bool forced, F2 h[Q],
+                                             Mac2& m) {
     m.gx = make_float2(C.G[0], C.G[0]);
     m.gy = make_float2(C.G[1], C.G[1]);
     m.gz = make_float2(C.G[2], C.G[2]);
     if (forced) {
-        const float4 g0 = gcur[gi0], g1 = gcur[gi0 + 1];
         m.gx = add2(m.gx, make_float2(g0.x, g1.x));
         m.gy = add2(m.gy, make_float2(g0.y, g1.y));
         m.gz = add2(m.gz, make_float2(g0.z, g1.z));
@@ -841,7 +856,6 @@ __device__ __forceinline__ void pair_collide_store(const LatticeArgs& a, const C
     const float om_s = C.omega, fp_s = C.fpre;
     m.A1 = fma2(mul2(f2s(-1.5f), m.rho), uu, m.drho);   // drho - 3/2 rho u.u
     m.mug = mul2(f2s(-3.0f * fp_s), ug);                // -3 fp u.g
-    const unsigned seed = sr_seed((unsigned)gi0, m.drho.x, m.ux.y);
     const F2 om = f2s(om_s), omc = f2s(1.0f - om_s), c3om = f2s(3.0f * om_s);
     const F2 c9fp = f2s(9.0f * fp_s), c3fp = f2s(3.0f * fp_s);
     // rest population: (1 - om) h0 + w0 [om A1 - 3 fp u.g]
@@ -859,6 +873,23 @@ __device__ __forceinline__ void pair_collide_store(const LatticeArgs& a, const C
     collide_pair2<SCALED, 13>(h, m, om, omc, c3om, c9fp, c3fp);
     collide_pair2<SCALED, 15>(h, m, om, omc, c3om, c9fp, c3fp);
     collide_pair2<SCALED, 17>(h, m, om, omc, c3om, c9fp, c3fp);
+}
+
+// Moments, collision and stores of one in-range node pair (h: the pulled
+// populations after bounce-back; lk0 / lk1: the nodes' link masks).
+template <class S>
+__device__ __forceinline__ void pair_collide_store(const LatticeArgs& a, const ChannelDev& C, int gi0, F2 h[Q],
+                                                   uint32_t lk0, uint32_t lk1, bool forced, bool prevf) {
+    using IO = PairIO<S>;
+    const int par = a.par;
+    S* dst = (S*)(par ? a.h0 : a.h1);
+    const long long NT = a.Ntot;
+    float4* gprev = par ? a.g0 : a.g1;
+    Mac2 m;
+    const float4* gcur = par ? a.g1 : a.g0;
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    pair_collide<IO::SCALED>(C, forced ? gcur[gi0] : z4, forced ? gcur[gi0 + 1] : z4, forced, h, m);
+    const unsigned seed = sr_seed((unsigned)gi0, m.drho.x, m.ux.y);
     const bool s0 = lk0 & 1u, s1 = lk1 & 1u;
     if (!(s0 || s1)) {
 #define LBIBM_P2(I) IO::st2(dst + (size_t)(I) * (size_t)NT + gi0, h[I], seed * sr_k(I));
@@ -962,6 +993,7 @@ __global__ void __launch_bounds__(BS, LBIBM_K3_PAIR_THREADS / BS) k_stream_colli
     const ChannelDev C = chan(a, c);
     const int pb = (b - C.blk0) * (2 * BS);                  // first channel-local node of the block
     const int p0 = pb + 2 * (int)threadIdx.x;
+    prefetch_ahead<S>(a, C.base + pb, 2 * BS);
     if (C.nx % (2 * BS) == 0 && pb + 2 * BS <= C.n) {
         // the block is a piece of one row: y and z are the block's
         const int r = fdiv(pb, C.dnx);
@@ -970,6 +1002,227 @@ __global__ void __launch_bounds__(BS, LBIBM_K3_PAIR_THREADS / BS) k_stream_colli
         return;
     }
     sc_pair<S, false>(a, C, p0, 0, 0, 0);
+}
+
+// ---------------------------------------------------------------------------
+// Quad variant for 16-bit storage (nodes_per_thread = 4): each thread takes
+// the consecutive x-nodes x0 .. x0 + 3 (x0 a multiple of 4) of one row and
+// pulls every direction as one aligned 64-bit word of four 16-bit values.  A
+// direction with an x component takes the value its first (+x) or last (-x)
+// node needs from the neighbouring lane's word by a shuffle, or, at a warp's
+// or a row's edge, from one extra aligned 32-bit word.  The words stay packed
+// (two registers per direction for four nodes) until the two node pairs are
+// unpacked in turn for the packed-FP32 moments and collision, and each
+// direction is stored as one 64-bit word.  The 16-bit kernel with one node per
+// thread holds too few population bytes in flight per register to cover HBM
+// latency; packed words hold four nodes' loads in the registers one node's
+// floats would take.
+// ---------------------------------------------------------------------------
+template <class S> struct QuadIO;
+template <> struct QuadIO<__half> {
+    // two packed halves (lo: first node) to floats
+    static __device__ __forceinline__ F2 unpack(unsigned w) {
+        return __half22float2(*reinterpret_cast<const __half2*>(&w));
+    }
+};
+template <> struct QuadIO<__nv_bfloat16> {
+    static __device__ __forceinline__ F2 unpack(unsigned w) {
+        return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+    }
+};
+
+// Row offsets of the pull sources (as PairNbr) and the element offsets, from
+// the thread's first node in the source row, of the aligned 32-bit words that
+// hold the x-neighbours x0 - 1 (hi half of the word at wxm) and x0 + 4 (lo
+// half of the word at wxp).  A missing neighbour (non-periodic x) maps to the
+// thread's own word; its link bounces back.
+struct QuadNbr {
+    int oym, oyp, ozm, ozp;
+    int wxm, wxp;
+};
+
+__device__ __forceinline__ void quad_neighbours(const ChannelDev& C, int x0, int y, int z, QuadNbr& nb) {
+    const int sy = C.nx, sz = C.nx * C.ny;
+    nb.oym = y > 0 ? -sy : (C.per[1] ? (C.ny - 1) * sy : 0);
+    nb.oyp = y < C.ny - 1 ? sy : (C.per[1] ? -(C.ny - 1) * sy : 0);
+    nb.ozm = z > 0 ? -sz : (C.per[2] ? (C.nz - 1) * sz : 0);
+    nb.ozp = z < C.nz - 1 ? sz : (C.per[2] ? -(C.nz - 1) * sz : 0);
+    nb.wxm = x0 > 0 ? -2 : (C.per[0] ? C.nx - 2 : 0);
+    nb.wxp = x0 + 4 < C.nx ? 4 : (C.per[0] ? -x0 : 0);
+}
+
+// Phase 1 of direction I: the thread's aligned word of the source row and,
+// on an edge lane of a direction with an x component, the extra word.
+template <class S, int I>
+__device__ __forceinline__ void quad_pull(const S* src, unsigned NT, int gi0, const QuadNbr& nb, bool inr,
+                                          bool edge_lo, bool edge_hi, uint2& w, unsigned& e) {
+    const S* pl = src + ((unsigned)I * NT + (unsigned)(gi0 + pair_row<I>(nb)));
+    w = inr ? __ldcs(reinterpret_cast<const uint2*>(pl)) : make_uint2(0u, 0u);
+    e = 0u;
+    if constexpr (ex(I) == 1) {
+        if (inr && edge_lo) e = __ldcs(reinterpret_cast<const unsigned*>(pl + nb.wxm));
+    } else if constexpr (ex(I) == -1) {
+        if (inr && edge_hi) e = __ldcs(reinterpret_cast<const unsigned*>(pl + nb.wxp));
+    }
+}
+
+// Phase 2 (converged warp): shift the word of a direction with an x component
+// by one node.  +x: nodes x0 .. x0 + 3 pull x0 - 1 .. x0 + 2; -x: x0 + 1 .. x0 + 4.
+template <int I>
+__device__ __forceinline__ void quad_shift(uint2& w, unsigned e, bool edge_lo, bool edge_hi) {
+    if constexpr (ex(I) == 1) {
+        unsigned prev = __shfl_up_sync(FULL, w.y, 1);   // hi half: element x0 - 1
+        if (edge_lo) prev = e;
+        w = make_uint2(__byte_perm(prev, w.x, 0x5432), __byte_perm(w.x, w.y, 0x5432));
+    } else if constexpr (ex(I) == -1) {
+        unsigned next = __shfl_down_sync(FULL, w.x, 1);  // lo half: element x0 + 4
+        if (edge_hi) next = e;
+        w = make_uint2(__byte_perm(w.x, w.y, 0x5432), __byte_perm(w.y, next, 0x5432));
+    }
+}
+
+// One node pair of the quad (k = 0: nodes x0, x0 + 1 from the words' lo
+// halves; k = 1: x0 + 2, x0 + 3): unpack, bounce-back, moments, collision and
+// the pair's stores (one 32-bit word per direction, rounded stochastically;
+// a solid node keeps its populations).
+template <class S>
+__device__ __forceinline__ void quad_half(const ChannelDev& C, const S* src, S* dst, unsigned NT, int gi, int y,
+                                          const uint2 w[Q], int k, uint32_t lk0, uint32_t lk1, bool forced,
+                                          float4 g0, float4 g1, Mac2& m) {
+    F2 h[Q];
+#define LBIBM_QU(I) h[I] = QuadIO<S>::unpack(k ? w[I].y : w[I].x);
+    LBIBM_ALL_I(LBIBM_QU)
+#undef LBIBM_QU
+    if (lk0 & ~1u) {
+#define LBIBM_PB(I) if (I > 0) pair_bounce<S, I>(src, NT, gi, lk0, C, y, h[I].x);
+        LBIBM_ALL_I(LBIBM_PB)
+#undef LBIBM_PB
+    }
+    if (lk1 & ~1u) {
+#define LBIBM_PB(I) if (I > 0) pair_bounce<S, I>(src, NT, gi + 1, lk1, C, y, h[I].y);
+        LBIBM_ALL_I(LBIBM_PB)
+#undef LBIBM_PB
+    }
+    pair_collide<true>(C, g0, g1, forced, h, m);
+    const unsigned seed = sr_seed((unsigned)gi, m.drho.x, m.ux.y);
+    using IO = PairIO<S>;
+    if (!((lk0 | lk1) & 1u)) {
+#define LBIBM_P2(I) IO::st2(dst + ((unsigned)(I) * NT + (unsigned)gi), h[I], seed * sr_k(I));
+        LBIBM_ALL_I(LBIBM_P2)
+#undef LBIBM_P2
+    } else {
+        if (!(lk0 & 1u)) {
+#define LBIBM_P1(I) IO::st1(dst + ((unsigned)(I) * NT + (unsigned)gi), h[I].x, seed * sr_k(I));
+            LBIBM_ALL_I(LBIBM_P1)
+#undef LBIBM_P1
+        }
+        if (!(lk1 & 1u)) {
+#define LBIBM_P1(I) IO::st1(dst + ((unsigned)(I) * NT + (unsigned)(gi + 1)), h[I].y, (seed * sr_k(I)) >> 16);
+            LBIBM_ALL_I(LBIBM_P1)
+#undef LBIBM_P1
+        }
+    }
+}
+
+template <class S, bool ROW>
+__device__ __forceinline__ void sc_quad(const LatticeArgs& a, const ChannelDev& C, int p0, int lane, int xr, int yr,
+                                        int zr) {
+    static_assert(sizeof(S) == 2, "the quad variant packs 16-bit populations");
+    const int gi0 = (int)(C.base + p0);   // a multiple of 4; the padded node count is below 2^31
+    const int grp = gi0 >> 5;
+    const int par = a.par;
+    uint8_t* fl_prev = par ? a.fl0 : a.fl1;
+    const bool inr = ROW ? true : p0 < C.n;
+    const uint8_t fslow = inr ? __ldg(a.slow + grp) : (uint8_t)0;
+    const S* src = (const S*)(par ? a.h1 : a.h0);
+    S* dst = (S*)(par ? a.h0 : a.h1);
+    const unsigned NT = (unsigned)a.Ntot;   // Q * plane stride < 2^32 (checked on the host)
+    int x0, y, z;
+    if constexpr (ROW) {
+        x0 = xr; y = yr; z = zr;
+    } else {
+        const int r = fdiv(p0, C.dnx);
+        x0 = p0 - r * C.nx;
+        z = fdiv(r, C.dny);
+        y = r - z * C.ny;
+    }
+    QuadNbr nb;
+    quad_neighbours(C, x0, y, z, nb);
+    const bool edge_lo = lane == 0 || x0 == 0;
+    const bool edge_hi = lane == 31 || x0 + 4 == C.nx;
+    // phase 1: every population word in flight at once
+    uint2 w[Q];
+    unsigned e[Q];
+#define LBIBM_QP(I) quad_pull<S, I>(src, NT, gi0, nb, inr, edge_lo, edge_hi, w[I], e[I]);
+    LBIBM_ALL_I(LBIBM_QP)
+#undef LBIBM_QP
+    // the populations are the previous cycle's; flags and force densities come
+    // from the spreading kernel this launch may overlap
+    pdl_entry();
+    const uint8_t fcur = __ldg((par ? a.fl1 : a.fl0) + grp);
+    const uint8_t fprev = __ldg(fl_prev + grp);
+    const bool forced = fcur != 0;
+    const bool prevf = fprev != 0;
+    const bool wslow = __any_sync(FULL, fslow != 0);
+#define LBIBM_QS(I) quad_shift<I>(w[I], e[I], edge_lo, edge_hi);
+    LBIBM_ALL_I(LBIBM_QS)
+#undef LBIBM_QS
+    uint4 lk = make_uint4(0u, 0u, 0u, 0u);
+    if (wslow && inr && fslow) lk = __ldg(reinterpret_cast<const uint4*>(a.links + gi0));
+    if (inr) {
+        Mac2 m0, m1;
+        const float4* gcur = par ? a.g1 : a.g0;
+        const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        quad_half<S>(C, src, dst, NT, gi0, y, w, 0, lk.x, lk.y, forced, forced ? gcur[gi0] : z4,
+                     forced ? gcur[gi0 + 1] : z4, m0);
+        quad_half<S>(C, src, dst, NT, gi0 + 2, y, w, 1, lk.z, lk.w, forced, forced ? gcur[gi0 + 2] : z4,
+                     forced ? gcur[gi0 + 3] : z4, m1);
+        float4* gprev = par ? a.g0 : a.g1;
+        if (forced) {
+            if (!(lk.x & 1u)) a.u[gi0] = make_float4(m0.ux.x, m0.uy.x, m0.uz.x, m0.rho.x);
+            if (!(lk.y & 1u)) a.u[gi0 + 1] = make_float4(m0.ux.y, m0.uy.y, m0.uz.y, m0.rho.y);
+            if (!(lk.z & 1u)) a.u[gi0 + 2] = make_float4(m1.ux.x, m1.uy.x, m1.uz.x, m1.rho.x);
+            if (!(lk.w & 1u)) a.u[gi0 + 3] = make_float4(m1.ux.y, m1.uy.y, m1.uz.y, m1.rho.y);
+        }
+        if (prevf) {
+            const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (!(lk.x & 1u)) gprev[gi0] = z4;
+            if (!(lk.y & 1u)) gprev[gi0 + 1] = z4;
+            if (!(lk.z & 1u)) gprev[gi0 + 2] = z4;
+            if (!(lk.w & 1u)) gprev[gi0 + 3] = z4;
+        }
+    }
+    // the lane holding the first node of each 32-node group clears the previous
+    // step's flag after every lane of the warp has consumed it
+    __syncwarp();
+    if (prevf && (gi0 & 31) == 0) fl_prev[grp] = 0;
+}
+
+// Resident threads per SM of the quad variant's register budget.
+#ifndef LBIBM_K3_QUAD_THREADS
+#define LBIBM_K3_QUAD_THREADS 640
+#endif
+
+template <class S, int BS, int MINB>
+__global__ void __launch_bounds__(BS, MINB) k_stream_collide_quad(const __grid_constant__ LatticeArgs a) {
+    // (sc_quad waits for the predecessor after its population loads)
+    const int b = blockIdx.x;
+    int c = 0;
+    for (int k = 1; k < a.n_ch; ++k)
+        if (b >= chan(a, k).blk0) c = k;
+    const ChannelDev C = chan(a, c);
+    const int lane = threadIdx.x & 31;
+    const int pb = (b - C.blk0) * (4 * BS);                  // first channel-local node of the block
+    const int p0 = pb + 4 * (int)threadIdx.x;
+    prefetch_ahead<S>(a, C.base + pb, 4 * BS);
+    if (C.nx % (4 * BS) == 0 && pb + 4 * BS <= C.n) {
+        // the block is a piece of one row: y and z are the block's
+        const int r = fdiv(pb, C.dnx);
+        const int z = fdiv(r, C.dny);
+        sc_quad<S, true>(a, C, p0, lane, pb - r * C.nx + 4 * (int)threadIdx.x, r - z * C.ny, z);
+        return;
+    }
+    sc_quad<S, false>(a, C, p0, lane, 0, 0, 0);
 }
 
 // Bulk of the overlapped schedule (one node per thread; a warp is one group).
@@ -1553,6 +1806,7 @@ cudaError_t launch_stream_collide_tma(const LatticeArgs& a, int tile, const CUte
     return cudaErrorInvalidConfiguration;
 }
 
+
 template <class S>
 static size_t staged_smem() { return 2 * (size_t)Q * SG_NODES * sizeof(S); }
 
@@ -1570,7 +1824,7 @@ cudaError_t prepare_staged(int storage) {
 // Supported (nodes per thread, block size) pairs per storage type; npt = 0 is
 // the staged variant, npt = -1 the pipelined one.
 static const K3Config CFG_F32[] = {{-2, 256}, {-2, 512}, {-1, 128}, {-1, 256}, {0, 256}, {1, 256}, {2, 256}, {4, 256}, {4, 128}, {2, 128}, {1, 128}};
-static const K3Config CFG_16[] = {{-1, 128}, {-1, 256}, {0, 256}, {2, 256}, {4, 256}, {4, 128}, {2, 128}, {1, 256}, {1, 128}};
+static const K3Config CFG_16[] = { {-1, 128}, {-1, 256}, {0, 256}, {2, 256}, {4, 128}, {4, 64}, {2, 128}, {1, 256}, {1, 128}};
 
 int k3_config_count(int storage) { return storage == 0 ? 11 : 9; }
 K3Config k3_config_at(int storage, int k) { return storage == 0 ? CFG_F32[k] : CFG_16[k]; }
@@ -1593,6 +1847,14 @@ static cudaError_t launch_sc_typed(const LatticeArgs& a, K3Config c, int blocks,
         if (c.bs == 256) return launch_ex(k_stream_collide_pair<S, 256>, blocks, 256, 0, s, a.pdl, a);
         return cudaErrorInvalidConfiguration;
     }
+    if constexpr (sizeof(S) == 2) {
+        if (c.npt == 4) {
+            if (c.bs == 64) return launch_ex(k_stream_collide_quad<S, 64, 512 / 64>, blocks, 64, 0, s, a.pdl, a);
+            if (c.bs == 128)
+                return launch_ex(k_stream_collide_quad<S, 128, LBIBM_K3_QUAD_THREADS / 128>, blocks, 128, 0, s, a.pdl, a);
+            return cudaErrorInvalidConfiguration;
+        }
+    }
     if (c.npt == 0) {
         return launch_ex(k_stream_collide_staged<S>, blocks, SG_THREADS, staged_smem<S>(), s, a.pdl, a);
     }
@@ -1603,7 +1865,7 @@ static cudaError_t launch_sc_typed(const LatticeArgs& a, K3Config c, int blocks,
     if constexpr (sizeof(S) == 4) {
         LBIBM_CASE(1, 256) LBIBM_CASE(4, 256) LBIBM_CASE(4, 128) LBIBM_CASE(1, 128)
     } else {
-        LBIBM_CASE(4, 256) LBIBM_CASE(4, 128) LBIBM_CASE(1, 256) LBIBM_CASE(1, 128)
+        LBIBM_CASE(1, 256) LBIBM_CASE(1, 128)
     }
 #undef LBIBM_CASE
     return cudaErrorInvalidConfiguration;

@@ -177,6 +177,10 @@ struct LatticeArgs {
     const float* phi;
     float alpha;
     int* tma_err;         // TMA variant: mbarrier waits that ran out
+    // stream-collide: L2 prefetch distance in lattice nodes (0: off).  A block
+    // asks L2 for the source rows of the nodes pf_nodes past its own, so the
+    // blocks that run a wave later find them there instead of in DRAM.
+    int pf_nodes;
     ChannelDev chp[MAXCH_P];   // copy of the first channels (constant bank)
 };
 

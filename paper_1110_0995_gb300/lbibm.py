@@ -25,7 +25,8 @@ EXPORTS = (
     "ibm_set_nodes", "lb_step", "lb_synchronize", "lb_get_fields", "lb_get_populations", "lb_set_populations",
     "ibm_get_nodes", "ibm_get_all_nodes", "ibm_get_forces", "ibm_get_area_volume", "lb_diagnostics", "lb_get_step", "lb_save_state",
     "lb_load_state", "lb_set_schedule", "lb_get_schedule", "lb_set_timing", "lb_kernel_times", "lb_last_error", "lb_version", "lb_get_mask",
-    "lb_set_kernel_config", "lb_get_kernel_config", "lb_autotune", "ibm_area_volume_noalloc",
+    "lb_set_kernel_config", "lb_get_kernel_config", "lb_set_prefetch", "lb_get_prefetch", "lb_autotune",
+    "ibm_area_volume_noalloc",
     "bead_forces", "bead_relax", "ibm_get_all_nodes_async", "lb_readback_wait", "ibm_check_mesh",
 )
 
@@ -105,6 +106,8 @@ def lib():
             "lb_get_mask": ([P, P], I),
             "lb_set_kernel_config": ([P, I, I], I),
             "lb_get_kernel_config": ([P, ctypes.POINTER(I), ctypes.POINTER(I)], I),
+            "lb_set_prefetch": ([P, I], I),
+            "lb_get_prefetch": ([P, ctypes.POINTER(I)], I),
             "lb_autotune": ([P, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(D)], I),
             "ibm_area_volume_noalloc": ([P, P, P, P, I, P, P, P], I),
             "bead_forces": ([P, P, I, P, P, P], I),
@@ -360,6 +363,15 @@ class Simulation:
         n, b = ctypes.c_int(), ctypes.c_int()
         self._check(self._L.lb_get_kernel_config(self._h, ctypes.byref(n), ctypes.byref(b)))
         return n.value, b.value
+
+    def set_prefetch(self, nodes_ahead: int):
+        """L2 prefetch distance of the stream-collide kernel in lattice nodes (0 = off)."""
+        self._check(self._L.lb_set_prefetch(self._h, int(nodes_ahead)))
+
+    def prefetch(self) -> int:
+        n = ctypes.c_int()
+        self._check(self._L.lb_get_prefetch(self._h, ctypes.byref(n)))
+        return n.value
 
     def autotune(self, repeats: int = 20):
         """Time every stream-collide variant (before the first step) and keep the fastest."""

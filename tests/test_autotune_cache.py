@@ -22,15 +22,24 @@ class FakeSim:
             raise lbibm.LbError(lbibm.LB_ERR_ARG, "no such variant")
         self.config = (npt, bs)
 
+    pf = 0
+
+    def set_prefetch(self, d):
+        self.pf = d
+
+    def prefetch(self):
+        return self.pf
+
 
 def test_cache_stores_reuses_and_retunes(tmp_path, monkeypatch):
     monkeypatch.setenv("LBIBM_CACHE", str(tmp_path / "at.json"))
     a = FakeSim([(256, 128, 64)])
+    a.pf = 65536                      # the distance the library's autotuner kept
     r = autotune.tune(a, "GB300", "f32")
-    assert not r["cached"] and a.timed == 1 and (r["npt"], r["bs"]) == (2, 256)
+    assert not r["cached"] and a.timed == 1 and (r["npt"], r["bs"], r["pf"]) == (2, 256, 65536)
     b = FakeSim([(256, 128, 64)])
     r = autotune.tune(b, "GB300", "f32")
-    assert r["cached"] and b.timed == 0 and b.config == (2, 256)
+    assert r["cached"] and b.timed == 0 and b.config == (2, 256) and b.pf == 65536
     # another lattice, storage or device is a separate entry
     for sim, dev, st in ((FakeSim([(128, 64, 64)]), "GB300", "f32"), (FakeSim([(256, 128, 64)]), "GB300", "f16"),
                          (FakeSim([(256, 128, 64)]), "other", "f32")):

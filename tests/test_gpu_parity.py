@@ -107,6 +107,56 @@ def test_lattice_parity_every_kernel_variant(npt, bs):
     np.testing.assert_allclose(sim.populations()[:, fluid], ref.get_f()[:, fluid], rtol=0, atol=2e-7)
 
 
+VARIANTS_16 = [(1, 128), (1, 256), (2, 128), (2, 256), (4, 64), (4, 128)]
+
+
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+@pytest.mark.parametrize("npt,bs", VARIANTS_16)
+def test_16bit_variants_one_step_within_one_rounding(storage, npt, bs):
+    """Every 16-bit stream-collide variant, one step from a random state against
+    the oracle started from the same (16-bit) populations: walls, a moving
+    wall, obstacles, periodic x and z, nx a multiple of 4 with rows breaking
+    inside warps.  Each population may differ by the one stochastic rounding
+    of its store, below one unit in the last place of h_i / w_i (2^-10 of the
+    value for FP16, 2^-7 for BF16), plus FP32 arithmetic; a wrong pull
+    source, bounce-back or halo would be off by the state's 1% variation."""
+    sc = _ragged_scene((1, 0, 1), ((0, 0, 0), (0.02, 0, 0.01)), dims=(36, 23, 19))
+    sim = _sim(sc, storage=storage)
+    sim.set_kernel_config(npt, bs)
+    ref = oracle.System.from_scene(sc)
+    f0 = ref.get_f() * (1 + 0.01 * scene.random_field(11, (19, ref.N)))
+    f0[:, ref.solid == 1] = ref.get_f()[:, ref.solid == 1]
+    sim.set_populations(f0)
+    ref.set_f(sim.populations().astype(np.float64))   # the rounded state both sides start from
+    sim.step(1)
+    ref.step(1)
+    fluid = ref.solid == 0
+    _, w, _ = oracle.constants()
+    fo = ref.get_f()[:, fluid]
+    s_ref = (fo - w[:, None]) / w[:, None]
+    ulp = 2.0 ** -10 if storage == "f16" else 2.0 ** -7
+    tol = w[:, None] * (ulp * np.abs(s_ref) + 2e-6)
+    err = np.abs(sim.populations()[:, fluid] - fo)
+    assert np.all(err <= tol), (float((err / tol).max()), np.unravel_index(np.argmax(err / tol), err.shape))
+
+
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+@pytest.mark.parametrize("npt,bs", [(2, 128), (4, 64)])
+def test_16bit_variants_plain_channel(storage, npt, bs):
+    """The two- and four-node 16-bit variants over 200 coupled cycles of the
+    plain channel (a cell's forces, flagged groups, velocity output): velocity
+    within the storage's error bound of the oracle."""
+    sc = scene.channel_plain(seed=1, steps=200)
+    sim = _sim(sc, storage=storage)
+    sim.set_kernel_config(npt, bs)
+    ref = oracle.System.from_scene(sc)
+    sim.step(sc.steps)
+    ref.step(sc.steps)
+    err = rel_l2(sim.fields()[1], ref.fields()[1])
+    print(f"{storage} {npt},{bs}: velocity rel L2 {err:.3e}")
+    assert err < (1e-3 if storage == "f16" else 3e-3)
+
+
 @pytest.mark.parametrize("dims,periodic,wall", [((64, 24, 19), (1, 0, 0), ((0, 0, 0), (0.02, 0, 0.01))),
                                                 ((32, 32, 7), (0, 0, 0), ((0.01, 0, 0), (0, 0, 0))),
                                                 ((256, 6, 5), (1, 0, 0), ((0, 0, 0), (0, 0, 0)))])
@@ -360,6 +410,52 @@ def test_deterministic_cycle_is_bit_reproducible():
         sim2 = _sim(sc)
         sim2.set_deterministic(True)
         sim2.set_repulsion(0.01, 1.0)
+
+
+def test_deterministic_checkpoint_resume_is_bit_identical():
+    """In the deterministic cycle every piece of the checkpointed state is
+    order-independent: a context that loads a checkpoint taken after 40 cycles
+    and runs 60 more matches the uninterrupted 100-cycle run bit for bit
+    (populations, node positions, velocity)."""
+    sc = scene.small_filter(seed=5, steps=0)
+    a = _sim(sc)
+    a.set_deterministic(True)
+    a.step(40)
+    state = a.save_state()
+    a.step(60)
+    b = _sim(sc)
+    b.set_deterministic(True)
+    b.load_state(state)
+    b.step(60)
+    assert np.array_equal(a.populations(), b.populations())
+    for m in range(len(sc.meshes)):
+        assert np.array_equal(a.nodes(m), b.nodes(m))
+    assert np.array_equal(a.fields()[1], b.fields()[1])
+
+
+@pytest.mark.parametrize("storage,variant", [("f32", (1, 128)), ("f16", (4, 64))])
+def test_l2_prefetch_leaves_results_bit_identical(storage, variant):
+    """The stream-collide's L2 prefetch distance is a performance setting
+    only: with fixed-point spreading, runs with the prefetch off and at two
+    distances give bit-identical populations and positions; invalid distances
+    are refused."""
+    from paper_1110_0995_gb300 import lbibm
+
+    sc = scene.small_filter(seed=5, steps=0)
+    runs = []
+    for d in (0, 65536, 262144):
+        sim = _sim(sc, storage=storage)
+        sim.set_kernel_config(*variant)
+        sim.set_deterministic(True)
+        sim.set_prefetch(d)
+        assert sim.prefetch() == d
+        sim.step(60)
+        runs.append((sim.populations(), np.concatenate([sim.nodes(m) for m in range(len(sc.meshes))])))
+    for r in runs[1:]:
+        assert np.array_equal(r[0], runs[0][0]) and np.array_equal(r[1], runs[0][1])
+    for bad in (-256, 100, (1 << 24) + 256):
+        with pytest.raises(lbibm.LbError):
+            sim.set_prefetch(bad)
 
 
 def test_api_edge_cases():
