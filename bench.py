@@ -9,7 +9,14 @@ the populations (2 x 159 MB) are larger than the 126 MB L2.
 After W warm-up steps the state is saved and K steps are timed twice from it:
 first as CUDA-graph replays (the reported `value`), then with CUDA events
 around every kernel launch (per-kernel durations and the roofline of the
-stream-collide kernel).
+stream-collide kernel).  `cycle_frac` is the whole cycle's MLUPS at 152 bytes
+per node against the measured HBM copy bandwidth.
+
+The same line carries short fixed windows of the other single-GPU workloads
+(`workloads`): the 512x256x128 filter with FP32, FP16 and BF16 population
+storage (cycle MLUPS, stream-collide fraction of the HBM bandwidth at 152 or
+76 bytes per fluid node, 16-bit over FP32 ratios) and the batched 24-channel
+gap sweep; the oracle's single-thread figure sits beside the all-core one.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
 
@@ -179,6 +186,19 @@ def cpu_baseline_line(target_seconds: float = 15.0):
                       f"({len(sc.meshes)} cells), FP64 oracle, {cpu_threads()} OpenMP threads"}
 
 
+def cpu_baseline_single_thread(target_seconds: float = 10.0):
+    """The same oracle timing with one OpenMP thread, in a fresh interpreter
+    (the thread count of an OpenMP runtime is fixed at its first use)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    try:
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-baseline-only",
+                            "--cpu-seconds", str(target_seconds)], env=env, capture_output=True, text=True,
+                           timeout=300)
+        return json.loads(r.stdout.strip().splitlines()[-1])
+    except (subprocess.SubprocessError, ValueError, IndexError) as e:
+        return {"unavailable": f"single-thread oracle run failed: {type(e).__name__}"}
+
+
 def adjoint_ratio(steps: int = 400, ckpt_every: int = 50):
     """Cost of the discrete adjoint on the 128x64x64 channel with 12 Brinkman
     beads and 9 cells: forward cycles alone vs lb_adjoint (forward with
@@ -214,6 +234,72 @@ def adjoint_ratio(steps: int = 400, ckpt_every: int = 50):
             "adjoint_us_per_step": 1e3 * (t_adj - t_fwd) / steps, "adjoint_over_forward": (t_adj - t_fwd) / t_fwd,
             "J": res["J"], "note": "adjoint step = recompute share + reverse sweep; gradients checked against the "
                                    "FP64 oracle's dual numbers in tests/test_gpu_adjoint.py"}
+
+
+def time_cycles(sim, stream, steps: int, warmup: int = 5):
+    """Mean CUDA-graph cycle time (ms) over `steps` cycles after `warmup`, and
+    the mean stream-collide launch time (ms) over a second, event-timed pass."""
+    import torch
+
+    sim.step(warmup)
+    sim.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        sim.step(steps)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    cyc = e0.elapsed_time(e1) / steps
+    sim.set_timing(4)
+    sim.kernel_times()
+    sim.step(steps)
+    sim.synchronize()
+    kms, kn = sim.kernel_times()
+    sim.set_timing(0)
+    return cyc, kms[2] / max(1, kn[2])
+
+
+def extra_workloads(stream, device_name: str, steps: int = 30):
+    """Short fixed windows of the other single-GPU workloads: the 512x256x128
+    filter (the largest, 16.8 M nodes, 404 cells) with FP32, FP16 and BF16
+    population storage, and the batched 24-channel gap sweep (FP32).  MLUPS
+    over all nodes from graph replays; the stream-collide's fraction of the
+    measured HBM copy bandwidth at its algorithmic bytes per fluid node."""
+    from paper_1110_0995_gb300 import autotune, lbibm
+
+    peak, _ = measured_peak()
+    out = {}
+    big = make_workload("micropost_filter_512x256x128")
+    n_nodes = big[0].n_nodes
+    res = {}
+    n_fluid = None
+    for st in ("f32", "f16", "bf16"):
+        sim = lbibm.Simulation.from_scenes(big, storage=st, stream=stream.cuda_stream)
+        tuned = autotune.tune(sim, device_name, st)
+        if n_fluid is None:
+            n_fluid = int((sim.solid_mask() == 0).sum())
+        cyc, k3 = time_cycles(sim, stream, steps)
+        fin = bool(sim.diagnostics()[4] == 0)
+        sim.close()
+        ach = BYTES_PER_NODE[st] * n_fluid / (k3 * 1e-3) / 1e9
+        res[st] = {"mlups": n_nodes / (cyc * 1e-3) / 1e6, "ms_per_step": cyc, "stream_collide_ms": k3,
+                   "stream_collide_frac": ach / peak, "cycle_frac": n_nodes / (cyc * 1e-3) * BYTES_PER_NODE[st] / (peak * 1e9),
+                   "variant": [tuned["npt"], tuned["bs"], tuned.get("pf", 0)], "finite": fin}
+    res["f16_over_f32_cycle"] = res["f16"]["mlups"] / res["f32"]["mlups"]
+    res["bf16_over_f32_cycle"] = res["bf16"]["mlups"] / res["f32"]["mlups"]
+    res["f16_over_f32_stream_collide"] = res["f32"]["stream_collide_ms"] / res["f16"]["stream_collide_ms"]
+    out["micropost_filter_512x256x128"] = dict(res, fluid_nodes=n_fluid, steps=steps)
+    sweep = make_workload("gap_sweep_24ch")
+    sim = lbibm.Simulation.from_scenes(sweep, storage="f32", stream=stream.cuda_stream)
+    tuned = autotune.tune(sim, device_name, "f32")
+    nodes = sum(sc.n_nodes for sc in sweep)
+    cyc, k3 = time_cycles(sim, stream, steps)
+    sim.close()
+    out["gap_sweep_24ch"] = {"mlups": nodes / (cyc * 1e-3) / 1e6, "ms_per_step": cyc, "stream_collide_ms": k3,
+                             "nodes": nodes, "channels": len(sweep), "cells": sum(len(sc.meshes) for sc in sweep),
+                             "variant": [tuned["npt"], tuned["bs"], tuned.get("pf", 0)], "steps": steps,
+                             "storage": "f32"}
+    return out
 
 
 def max_over_ranks(values, device="cuda"):
@@ -363,6 +449,9 @@ def run_ours(args):
         t0 = time.perf_counter()
         s2 = lbibm.Simulation.from_scenes(scenes, storage=args.storage, stream=stream.cuda_stream)
         s2.set_kernel_config(tuned["npt"], tuned["bs"])
+        s2.set_prefetch(tuned.get("pf", 0))
+        s2.synchronize()
+        t_setup = time.perf_counter() - t0
         h2d = sum(m.rest.nbytes + m.tris.nbytes for s in scenes for m in s.meshes) + sum(s.spheres.nbytes for s in scenes)
         d2h = 0
         # two page-locked slots: the readback of one chunk runs behind the next
@@ -394,12 +483,18 @@ def run_ours(args):
         s2.close()
         e2e = {"value": world * n_nodes * e2e_steps / dt / 1e6, "unit": "MLUPS",
                "h2d_bytes_per_step": h2d / e2e_steps, "d2h_bytes_per_step": d2h / e2e_steps,
+               "setup_ms": 1e3 * t_setup,
+               "steady_value": world * n_nodes * e2e_steps / (dt - t_setup) / 1e6,
                "includes": "context creation, scene upload, node positions read back every 10 steps "
-                           "(asynchronous, two page-locked slots), final fields"}
+                           "(asynchronous, two page-locked slots), final fields; steady_value leaves out "
+                           "the setup (context creation and scene upload, setup_ms)"}
 
     if rank == 0:
         cpu = None if (args.no_cpu_baseline or world > 1 or len(scenes) > 1) else cpu_baseline_line()
+        if cpu is not None:
+            cpu["single_thread"] = cpu_baseline_single_thread()
         adj = None if (args.no_adjoint or world > 1) else adjoint_ratio()
+        extra = None if (args.no_extra or world > 1) else extra_workloads(stream, torch.cuda.get_device_name(local_rank))
         line = {
             "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -411,11 +506,14 @@ def run_ours(args):
                        "storage": args.storage, "l2": "populations 2x%.0f MB > 126 MB L2" % (
                            19 * BYTES_PER_NODE[args.storage] / 38 * n_nodes / 1e6),
                        "parallelism": "replicas" if world > 1 else "single",
-                       "stream_collide_variant": {"nodes_per_thread": tuned["npt"], "block": tuned["bs"]}},
+                       "stream_collide_variant": {"nodes_per_thread": tuned["npt"], "block": tuned["bs"],
+                                                  "l2_prefetch_nodes": tuned.get("pf", 0)}},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                          "kernel": "k_stream_collide", "alg_bytes_per_launch": alg_bytes,
                          "avg_launch_ms": k3_ms},
+            "cycle_frac": value * 1e6 * BYTES_PER_NODE[args.storage] / (peak * 1e9) / world,
+            "cycle_frac_how": "value x algorithmic bytes per node / measured HBM copy bandwidth (per GPU)",
             "kernel_ms_per_step": {"elements": kms[0] / max(1, kn[0]), "forces_spread": kms[1] / max(1, kn[1]),
                                    "stream_collide": k3_ms, "interp_advance": kms[3] / max(1, kn[3])},
             "ib_node_updates_per_s": world * n_ib * args.steps / (ms * 1e-3),
@@ -428,6 +526,7 @@ def run_ours(args):
             "clocks": clk.summary(),
             "cpu_baseline": cpu,
             "adjoint": adj,
+            "workloads": extra,
             "e2e": e2e,
         }
         print(json.dumps(line), flush=True)
@@ -450,7 +549,14 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint / forward cost measurement")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the 512x256x128 storage comparison and the gap sweep")
+    ap.add_argument("--cpu-baseline-only", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help=argparse.SUPPRESS)
     args = ap.parse_args(argv)
+    if args.cpu_baseline_only:
+        print(json.dumps(cpu_baseline_line(args.cpu_seconds)), flush=True)
+        return 0
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":

@@ -571,6 +571,70 @@ def test_diagnostics_mass_and_momentum():
     assert d1[4] == 0 and 0 < d1[5] < 0.1
 
 
+def _post_collision_momentum_from_oracle_fields(ref, G):
+    """Sum over fluid nodes of sum_i e_i f*_i after the last collision, from
+    the oracle's fields of that collision: BGK conserves momentum and the Guo
+    source adds g, so it equals rho u + g / 2 per node (g = G without cells)."""
+    rho, u = ref.fields()
+    fluid = ref.solid == 0
+    return (rho[fluid] * u[:, fluid]).sum(axis=1) + 0.5 * np.asarray(G) * fluid.sum()
+
+
+def test_diagnostics_momentum_matches_oracle_with_walls_and_posts():
+    """lb_diagnostics' FP64 momentum sums (post-collision) against the oracle on
+    the small filter without cells (walls, posts, a body force in all three
+    directions), after 1 and 100 cycles; mass against the oracle's too."""
+    sc = scene.small_filter(seed=6, steps=0)
+    sc.meshes = []
+    sc.body_force = (2e-5, -6e-6, 4e-6)
+    sim = _sim(sc)
+    ref = oracle.System.from_scene(sc)
+    for n in (1, 99):
+        sim.step(n)
+        ref.step(n)
+        d = sim.diagnostics()
+        P = _post_collision_momentum_from_oracle_fields(ref, sc.body_force)
+        rho, _ = ref.fields()
+        assert abs(d[0] - rho[ref.solid == 0].sum()) < 1e-9 * d[0]
+        assert np.all(np.abs(d[1:4] - P) <= 1e-5 * np.abs(P).max()), (d[1:4], P)
+
+
+def test_diagnostics_momentum_matches_oracle_periodic_box_with_cells():
+    """A fully periodic box (streaming moves momentum without loss, so the
+    oracle's post-streaming populations carry the post-collision momentum)
+    with two red cells and a body force: lb_diagnostics' momentum sums equal
+    sum_x sum_i e_i f_i of the oracle's populations after 100 cycles, each
+    component within 1e-5 of the largest."""
+    sc = scene.channel_plain(seed=3, steps=100, dims=(32, 32, 32), n_rbc=2, moduli=scene.STABLE)
+    sc.periodic = (1, 1, 1)
+    sc.body_force = (1e-5, -4e-6, 3e-6)
+    sim = _sim(sc)
+    ref = oracle.System.from_scene(sc)
+    sim.step(sc.steps)
+    ref.step(sc.steps)
+    e, _, _ = oracle.constants()
+    P = e.T.astype(float) @ ref.get_f().sum(axis=1)
+    d = sim.diagnostics()
+    assert np.all(np.abs(d[1:4] - P) <= 1e-5 * np.abs(P).max()), (d[1:4], P)
+    assert abs(d[0] - ref.get_f().sum()) < 1e-9 * d[0]
+
+
+def test_cycle_advances_with_the_velocity_of_the_same_collision():
+    """The GPU cycle on the closed-form state of tests/test_oracle_cycle_order.py:
+    equilibrium populations of a linear velocity field u0, a cell at rest, a
+    body force G; after one cycle every node has moved by u0(X) + G/2."""
+    import test_oracle_cycle_order as co
+
+    sc = co.cycle_scene()
+    sim = _sim(sc)
+    sim.set_populations(co.linear_shear_state())
+    x0 = sim.nodes(0)
+    sim.step(1)
+    # FP32 velocities of ~1e-2 carry ~1e-9 of rounding; the alternative
+    # orderings are off by |G|/2 >= 2.5e-6 in some component
+    np.testing.assert_allclose(sim.nodes(0), co.expected_positions(x0), rtol=0, atol=5e-9)
+
+
 def test_batch_matches_single_channels():
     """Three channels of different sizes in one context = three separate contexts."""
     from paper_1110_0995_gb300 import lbibm
