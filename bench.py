@@ -159,8 +159,13 @@ def profiled_traffic(workload: str, storage: str, variant):
     text = open(path).read()
     m = re.search(r"^dram_bytes_per_launch: (\d+)$", text, re.M)
     h = re.search(r"^kernel_source_sha256: (.*)$", text, re.M)
-    v = re.search(r"k_stream_collide<\w+, (-?\d+), (\d+)>", text)
+    # the captured variant: explicit "variant: npt bs" line, else the name of a
+    # one-kernel-per-variant template k_stream_collide<S, NPT, BS>
+    v = re.search(r"^variant: (-?\d+) (\d+)$", text, re.M) or re.search(r"k_stream_collide<\w+, (-?\d+), (\d+)>", text)
     if not (m and h and v) or (int(v.group(1)), int(v.group(2))) != (variant["npt"], variant["bs"]):
+        return None
+    pf = re.search(r"^l2_prefetch_nodes: (\d+)$", text, re.M)
+    if pf and int(pf.group(1)) != variant.get("pf", 0):
         return None
     parts = h.group(1).split()
     for name, digest in zip(parts[0::2], parts[1::2]):
@@ -372,9 +377,11 @@ def run_ours(args):
     from paper_1110_0995_gb300 import autotune
 
     if args.variant:
-        npt, bs = (int(v) for v in args.variant.split(","))
+        vals = [int(v) for v in args.variant.split(",")]
+        npt, bs, pf = vals[0], vals[1], (vals[2] if len(vals) > 2 else 0)
         sim.set_kernel_config(npt, bs)
-        tuned = {"npt": npt, "bs": bs}
+        sim.set_prefetch(pf)
+        tuned = {"npt": npt, "bs": bs, "pf": pf}
     else:
         tuned = autotune.tune(sim, torch.cuda.get_device_name(local_rank), args.storage)
     n_nodes = sum(s.n_nodes for s in scenes)
@@ -545,7 +552,8 @@ def main(argv=None):
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="micropost_filter_256x128x64")
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
-    ap.add_argument("--variant", default="", help="stream-collide variant 'npt,bs' instead of the autotuner")
+    ap.add_argument("--variant", default="",
+                    help="stream-collide variant 'npt,bs[,l2_prefetch_nodes]' instead of the autotuner")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint / forward cost measurement")

@@ -1,7 +1,7 @@
 """Host logic of the bench line (no GPU).  `roofline.traffic`: the DRAM bytes
 of the committed ncu summary are reported only for the captured kernel
-variant and only while the kernel sources still match the digests recorded
-with the capture."""
+variant and L2 prefetch distance and only while the kernel sources still
+match the digests recorded with the capture."""
 import hashlib
 import os
 import shutil
@@ -39,9 +39,10 @@ def _recorded():
 def test_traffic_only_for_the_captured_kernel(tmp_path, monkeypatch):
     root = _tree(tmp_path)
     monkeypatch.setattr(bench, "ROOT", str(root))
-    wl, st, var = "micropost_filter_256x128x64", "f32", {"npt": 1, "bs": 128}
+    wl, st, var = "micropost_filter_256x128x64", "f32", {"npt": 1, "bs": 128, "pf": 65536}
     assert bench.profiled_traffic(wl, st, var) == _recorded()
-    assert bench.profiled_traffic(wl, st, {"npt": 2, "bs": 256}) is None       # another variant
+    assert bench.profiled_traffic(wl, st, {"npt": 2, "bs": 256, "pf": 65536}) is None   # another variant
+    assert bench.profiled_traffic(wl, st, {"npt": 1, "bs": 128, "pf": 0}) is None       # another prefetch distance
     assert bench.profiled_traffic(wl, "f16", var) is None                      # no summary for it
     src = root / "paper_1110_0995_gb300" / "csrc" / SRCS[1]
     src.write_text(src.read_text() + "\n")                                      # the kernel changed
