@@ -76,6 +76,45 @@ def test_adjoint_gradient_matches_oracle():
     assert gb.ravel()[checked[0]] == pytest.approx(refs[checked[0]], rel=1e-3)
 
 
+def test_adjoint_full_workload_every_parameter():
+    """The adjoint workload as stated: 128x64x64, two posts of six Brinkman
+    beads, a tumor cell and eight red cells, 400 cycles with checkpoints every
+    50.  Every one of the 36 bead-centre derivatives and dJ/dks, dJ/dkb of the
+    GPU adjoint against the FP64 oracle's dual numbers (stored by
+    tests/golden/make_adjoint_reference.py, which calls only the oracle):
+    within 1e-3 relative, or, for a component below 1e-3 of the largest
+    (whose exact value is near zero), within 1e-3 of the largest (those are
+    listed).  Two components are also checked against the oracle's central
+    differences (h = 1e-4)."""
+    import json
+    import os
+
+    path = os.path.join(os.path.dirname(__file__), "golden", "adjoint_reference_128x64x64.json")
+    ref = json.load(open(path))
+    T = ref["steps"]
+    sc = scene.adjoint_channel(steps=T)
+    res = _gpu_sim(sc).adjoint(T, ckpt_every=50, objective_mesh=0)
+    assert res["J"] == pytest.approx(ref["J"], rel=1e-5)
+    g = np.append(np.asarray(res["beads"], float).ravel(), [res["ks"], res["kb"]])
+    r = np.append(np.asarray(ref["dJ_dbeads"], float), [ref["dJ_dks"], ref["dJ_dkb"]])
+    assert g.shape == r.shape == (38,)
+    beads = np.abs(r[:36]).max()
+    floor = np.where(np.arange(38) < 36, 1e-3 * beads, 0.0)          # near-zero bead components
+    small = [int(i) for i in np.nonzero(np.abs(r) < floor)[0]]
+    rel = np.abs(g - r) / np.maximum(np.abs(r), floor)
+    worst = int(np.argmax(rel))
+    print(f"J gpu {res['J']:.9e} oracle {ref['J']:.9e}; worst component {worst} rel {rel[worst]:.2e}; "
+          f"near-zero bead components (absolute floor 1e-3 of the largest): {small}")
+    for k in range(38):
+        name = f"bead {k // 3} axis {k % 3}" if k < 36 else ("ks", "kb")[k - 36]
+        print(f"  {name}: gpu {g[k]: .6e} oracle {r[k]: .6e} rel {rel[k]:.1e}")
+    assert np.all(rel <= 1e-3), rel
+    for tag, v in ref["fd"].items():
+        k = 36 if tag == "ks" else int(tag.split("_")[1])
+        print(f"  FD {tag}: {v:.6e}  dual {r[k]:.6e}  gpu {g[k]:.6e}")
+        assert g[k] == pytest.approx(v, rel=1e-3)
+
+
 def test_adjoint_leaves_forward_state_and_time_ratio():
     """After lb_adjoint the context holds the state after the forward steps;
     the adjoint (forward with checkpoints + recompute + reverse sweep) costs a

@@ -666,26 +666,62 @@ def test_all_nodes_readback():
 
 
 def test_gap_sweep_batch_parity():
-    """The 24-channel gap sweep (uneven sizes 64-256 x 32-128 x 32-64, one post row each, 10-40 red cells) in
-    one context, every kernel one launch per step over all channels: 100 steps; the smallest, median and
-    largest channel against the oracle, every channel finite."""
+    """The 24-channel gap sweep (uneven sizes 64-256 x 32-128 x 32-64, one post
+    row each, 10-40 red cells) in one context, every kernel one launch per
+    step over all channels, with the one-node and the two-node stream-collide
+    (the latter is what the autotuner picks for this batch on GB300): after
+    100 steps every channel against the oracle (velocity rel L2 <= 1e-5, node
+    positions <= 1e-5 lu); the batch then runs to 1000 steps and its two
+    smallest channels are compared again: velocity within 1e-5, and node
+    positions within 1e-5 lu or 1e-5 of the largest node displacement over the
+    run, whichever is larger (a velocity error within the 1e-5 tolerance
+    integrates into that much position error; the oracle's own sensitivity to
+    a 1e-8 lu perturbation, printed, is far below it, so this is not
+    amplified rounding)."""
     from paper_1110_0995_gb300 import lbibm
 
-    scs = scene.gap_sweep(seed=21, steps=100)
+    T1, T2 = 100, 1000
+    scs = scene.gap_sweep(seed=21, steps=T1)
     assert len(scs) == 24
-    sim = lbibm.Simulation.from_scenes(scs)
-    sim.step(100)
-    for k in range(len(scs)):
-        sim.select(k)
-        assert sim.diagnostics()[4] == 0
-    order = np.argsort([s.n_nodes for s in scs])
-    for k in (order[0], order[len(order) // 2], order[-1]):
+    sims = []
+    for variant in ((1, 128), (2, 128)):
+        sim = lbibm.Simulation.from_scenes(scs)
+        sim.set_kernel_config(*variant)
+        sim.step(T1)
+        sims.append(sim)
+    worst_u, worst_x = 0.0, 0.0
+    for k, sc in enumerate(scs):
+        ref = oracle.System.from_scene(sc)
+        ref.step(T1)
+        uo = ref.fields()[1]
+        xo = [ref.nodes(m) for m in range(len(sc.meshes))]
+        for sim in sims:
+            sim.select(k)
+            assert sim.diagnostics()[4] == 0
+            worst_u = max(worst_u, rel_l2(sim.fields()[1], uo))
+            worst_x = max(worst_x, max(np.abs(sim.nodes(m) - xo[m]).max() for m in range(len(sc.meshes))))
+    print(f"24 channels, {T1} steps: worst velocity rel L2 {worst_u:.2e}, worst node error {worst_x:.2e} lu")
+    assert worst_u < 1e-5 and worst_x < 1e-5
+    sim = sims[1]
+    sim.step(T2 - T1)
+    for k in np.argsort([sc.n_nodes for sc in scs])[:2]:
         ref = oracle.System.from_scene(scs[k])
-        ref.step(100)
+        pert = oracle.System.from_scene(scs[k])
+        rng = np.random.default_rng(int(k))
+        for m, mesh in enumerate(scs[k].meshes):
+            pert.set_nodes(m, mesh.rest + 1e-8 * rng.standard_normal(mesh.rest.shape))
+        ref.step(T2)
+        pert.step(T2)
+        meshes = range(len(scs[k].meshes))
+        sens_u = rel_l2(pert.fields()[1], ref.fields()[1])
+        sens_x = max(np.abs(pert.nodes(m) - ref.nodes(m)).max() for m in meshes)
         sim.select(int(k))
-        assert rel_l2(sim.fields()[1], ref.fields()[1]) < 1e-5
-        for m in range(len(scs[k].meshes)):
-            assert np.abs(sim.nodes(m) - ref.nodes(m)).max() < 1e-5
+        err = rel_l2(sim.fields()[1], ref.fields()[1])
+        dx = max(np.abs(sim.nodes(m) - ref.nodes(m)).max() for m in meshes)
+        disp = max(np.linalg.norm(ref.nodes(m) - scs[k].meshes[m].rest, axis=1).max() for m in meshes)
+        print(f"channel {k} {scs[k].dims}, {T2} steps: velocity rel L2 {err:.2e} (oracle sensitivity {sens_u:.2e}), "
+              f"nodes {dx:.2e} lu (sensitivity {sens_x:.2e}, largest displacement {disp:.2f} lu)")
+        assert err < 1e-5 and dx < max(1e-5, 1e-5 * disp)
 
 
 @pytest.mark.parametrize("storage,tol", [("f16", 1e-3), ("bf16", None)])
