@@ -182,34 +182,9 @@ __device__ __forceinline__ double warp_sum_d(double v) {
     return v;
 }
 
-template <bool FORCES>
-__device__ __forceinline__ void tri_chunk(const IbmArgs& a, int chunk) {
-    const int4 ck = a.chunks[chunk];
-    double s = 0.0, v = 0.0;
-    for (int t = ck.y + (int)threadIdx.x; t < ck.z; t += CS_BLOCK) {
-        const int4 tr = a.tris[t];
-        const Q4* qc = cur_q(a);
-        const Pt R = load_pt(a, qc, a.cells[tr.w].ref);
-        const Pt P0 = load_pt(a, qc, tr.x), P1 = load_pt(a, qc, tr.y), P2 = load_pt(a, qc, tr.z);
-        const float3 e1 = edge(P0, P1), e2 = edge(P0, P2);
-        const float S0t = a.tri_S0[t];
-        const float dSt = tri_dS(e1, e2, ddisp(P0, P1), ddisp(P0, P2), S0t);
-        s += (double)dSt;
-        v += (double)tri_dV6(R, P0, P1, P2);
-        if constexpr (FORCES) {
-            const float St = S0t + dSt;
-            const float3 third = (1.0f / 3.0f) * (e1 + e2);
-            const float3 w0 = -third, w1 = e1 - third, w2 = e2 - third;
-            const float ww = dot(w0, w0) + dot(w1, w1) + dot(w2, w2);
-            const float c = -2.0f * St / ww;
-            const float sl = a.cells[tr.w].kal * dSt / S0t;
-            a.tA[3 * t] = make_float4(c * w0.x, c * w0.y, c * w0.z, sl);
-            a.tA[3 * t + 1] = make_float4(c * w1.x, c * w1.y, c * w1.z, sl);
-            a.tA[3 * t + 2] = make_float4(c * w2.x, c * w2.y, c * w2.z, sl);
-            const float3 n = cross(e1, e2);
-            a.tN[t] = make_float4(n.x, n.y, n.z, 0.f);
-        }
-    }
+// The cell's FP64 partial sums of one chunk: block reduction, then the last
+// block of the cell adds the cell's partials in chunk order (deterministic).
+__device__ __forceinline__ void chunk_sums(const IbmArgs& a, int chunk, const int4& ck, double s, double v) {
     __shared__ double sh[2][CS_BLOCK / 32];
     __shared__ bool last;
     s = warp_sum_d(s);
@@ -247,6 +222,58 @@ __device__ __forceinline__ void tri_chunk(const IbmArgs& a, int chunk) {
     }
 }
 
+// The static data of one triangle (indices, rest area, the cell's reference
+// node and local-area modulus), which the element pass loads before waiting
+// for the previous advance.
+struct TriStatic {
+    int4 tr;
+    float S0t, kal;
+    int ref;
+};
+
+__device__ __forceinline__ TriStatic tri_static(const IbmArgs& a, int t) {
+    TriStatic d;
+    d.tr = a.tris[t];
+    d.S0t = a.tri_S0[t];
+    d.ref = a.cells[d.tr.w].ref;
+    d.kal = a.cells[d.tr.w].kal;
+    return d;
+}
+
+// dS_t and dV_t (x 6) of one triangle; with FORCES also its area and volume
+// force terms.
+template <bool FORCES>
+__device__ __forceinline__ void tri_terms(const IbmArgs& a, int t, const TriStatic& d, double& s, double& v) {
+    const Q4* qc = cur_q(a);
+    const Pt R = load_pt(a, qc, d.ref);
+    const Pt P0 = load_pt(a, qc, d.tr.x), P1 = load_pt(a, qc, d.tr.y), P2 = load_pt(a, qc, d.tr.z);
+    const float3 e1 = edge(P0, P1), e2 = edge(P0, P2);
+    const float dSt = tri_dS(e1, e2, ddisp(P0, P1), ddisp(P0, P2), d.S0t);
+    s += (double)dSt;
+    v += (double)tri_dV6(R, P0, P1, P2);
+    if constexpr (FORCES) {
+        const float St = d.S0t + dSt;
+        const float3 third = (1.0f / 3.0f) * (e1 + e2);
+        const float3 w0 = -third, w1 = e1 - third, w2 = e2 - third;
+        const float ww = dot(w0, w0) + dot(w1, w1) + dot(w2, w2);
+        const float c = -2.0f * St / ww;
+        const float sl = d.kal * dSt / d.S0t;
+        a.tA[3 * t] = make_float4(c * w0.x, c * w0.y, c * w0.z, sl);
+        a.tA[3 * t + 1] = make_float4(c * w1.x, c * w1.y, c * w1.z, sl);
+        a.tA[3 * t + 2] = make_float4(c * w2.x, c * w2.y, c * w2.z, sl);
+        const float3 n = cross(e1, e2);
+        a.tN[t] = make_float4(n.x, n.y, n.z, 0.f);
+    }
+}
+
+template <bool FORCES>
+__device__ __forceinline__ void tri_chunk(const IbmArgs& a, int chunk) {
+    const int4 ck = a.chunks[chunk];
+    double s = 0.0, v = 0.0;
+    for (int t = ck.y + (int)threadIdx.x; t < ck.z; t += CS_BLOCK) tri_terms<FORCES>(a, t, tri_static(a, t), s, v);
+    chunk_sums(a, chunk, ck, s, v);
+}
+
 __global__ void __launch_bounds__(CS_BLOCK, 6) k_cell_sums(const __grid_constant__ IbmArgs a) {
     tri_chunk<false>(a, blockIdx.x);
 }
@@ -264,8 +291,17 @@ cudaError_t launch_cell_sums(const IbmArgs& a, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(CS_BLOCK, 6) k_elements(const __grid_constant__ IbmArgs a) {
     if ((int)blockIdx.x < a.n_chunks) {
+        // a chunk holds at most one triangle per thread: its static data
+        // before the previous advance has finished, then its positions
+        const int4 ck = a.chunks[blockIdx.x];
+        const int t = ck.y + (int)threadIdx.x;
+        const bool live = t < ck.z;
+        TriStatic d = {};
+        if (live) d = tri_static(a, t);
         pdl_entry();
-        tri_chunk<true>(a, blockIdx.x);
+        double s = 0.0, v = 0.0;
+        if (live) tri_terms<true>(a, t, d, s, v);
+        chunk_sums(a, blockIdx.x, ck, s, v);
         return;
     }
     // the edge's static data before the previous advance has finished
