@@ -529,6 +529,50 @@ def test_micropost_filter_runs_its_20000_steps():
         assert np.isfinite(sim.nodes(m)).all()
 
 
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
+def test_large_filter_runs_its_10000_steps(storage):
+    """The 512x256x128 filter (404 cells, 672 beads) over its stated horizon of
+    10000 cycles in every population storage: finite, mass conserved (16-bit:
+    within the stochastic rounding's random walk), velocities well below the
+    lattice sound speed, every cell's nodes finite."""
+    sc = scene.micropost_filter_large(seed=31)
+    sim = _sim(sc, storage=storage)
+    m0 = sim.diagnostics()[0]
+    for _ in range(20):
+        sim.step(500)
+        d = sim.diagnostics()
+        assert d[4] == 0
+    print(f"{storage}: mass drift {d[0] / m0 - 1.0:.2e}, max |u| {d[5]:.4f}")
+    assert abs(d[0] / m0 - 1.0) < (1e-6 if storage == "f32" else 1e-4)
+    assert d[5] < 0.1
+    x = np.zeros((sum(m.n_nodes for m in sc.meshes), 3))
+    sim.all_nodes_into(x)
+    assert np.isfinite(x).all()
+
+
+def test_gap_sweep_runs_its_5000_steps():
+    """The 24-channel sweep over its stated horizon of 5000 cycles with the
+    autotuned two-node kernel and L2 prefetch: every channel finite, its mass
+    conserved, velocities well below the sound speed."""
+    from paper_1110_0995_gb300 import lbibm
+
+    scs = scene.gap_sweep(seed=21)
+    sim = lbibm.Simulation.from_scenes(scs)
+    sim.set_kernel_config(2, 128)
+    sim.set_prefetch(65536)
+    m0 = []
+    for k in range(len(scs)):
+        sim.select(k)
+        m0.append(sim.diagnostics()[0])
+    sim.select(0)
+    sim.step(5000)
+    for k in range(len(scs)):
+        sim.select(k)
+        d = sim.diagnostics()
+        assert d[4] == 0 and d[5] < 0.1, (k, d)
+        assert abs(d[0] / m0[k] - 1.0) < 1e-6, (k, d[0], m0[k])
+
+
 def test_micropost_filter_full_size_parity():
     """Full 256x128x64 filter (62 cells, 120 beads): 200 steps against the oracle."""
     sc = scene.micropost_filter(seed=11)
