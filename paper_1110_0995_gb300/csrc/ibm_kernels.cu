@@ -564,10 +564,100 @@ __global__ void __launch_bounds__(FS_BLOCK, MASSIVE ? IB_MIN_BLOCKS : LBIBM_FS_M
     if (hit && (__ffs(same) - 1) == (int)(threadIdx.x & 31)) fl[grp] = 1;
 }
 
+// The massless node forces + spreading with four lanes per IB node (each
+// lane two ring slots and two stencil corners): half the threads of the
+// eight-lane kernel for the sequential schedule (the overlapped schedule's
+// stencil marking and points with mass keep eight lanes).
+constexpr int FS4 = 4;
+
+__global__ void __launch_bounds__(FS_BLOCK, 9) k_forces_spread4(const __grid_constant__ IbmArgs a) {
+    const int i = (blockIdx.x * FS_BLOCK + threadIdx.x) / FS4;
+    const int sl = threadIdx.x & (FS4 - 1);
+    const bool live = i < a.n_nodes;
+    // before the element pass has finished: the node's static data, its
+    // position (advanced in the previous cycle), this lane's two stencil
+    // corners with their obstacle bits and its first two ring slots
+    int4 inf = make_int4(0, 0, 0, 0);
+    int4 sr0 = make_int4(0, 0, 0, 0), sr1 = make_int4(0, 0, 0, 0);
+    long long g[2] = {0, 0};
+    float w[2] = {0.f, 0.f};
+    bool hit[2] = {false, false};
+    if (live) {
+        inf = a.info[i];
+        const int k = inf.w & 0xff;
+        if (sl < k) sr0 = a.slots[inf.z + sl];
+        if (sl + FS4 < k) sr1 = a.slots[inf.z + sl + FS4];
+        const Q4 qi = (a.par ? a.qb : a.qa)[i];
+        const ChannelDev& Ch = chan(a, inf.w >> 8);
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            hit[c] = corner(Ch, qi, sl + c * FS4, g[c], w[c]);
+            if (hit[c]) hit[c] = !((__ldg(a.mask + (g[c] >> 5)) >> (g[c] & 31)) & 1u);
+        }
+    }
+    pdl_entry();
+    if (!live) return;   // whole groups of four lanes leave together
+    const unsigned smask = 0xfu << (threadIdx.x & 28);
+    const int cid = inf.x, k0 = inf.z, k = inf.w & 0xff;
+    const CellDev& C = a.cells[cid];
+    const float2 rel = a.cell_rel[cid];
+    const float kag_dS = C.kag * rel.x;
+    const float kv_dV6 = C.kv * rel.y * (1.0f / 6.0f);
+    float3 F = make_float3(0.f, 0.f, 0.f);
+    for (int s = sl; s < k; s += FS4) {
+        const int4 sr = s == sl ? sr0 : (s == sl + FS4 ? sr1 : a.slots[k0 + s]);
+        const float4 ta = a.tA[sr.x];
+        const float4 tn = a.tN[sr.w];
+        const float4 es = a.eS[sr.y >> 2];
+        const float4 b1 = a.eB[sr.y];
+        const float4 b2 = a.eB[sr.z];
+        const float sg = (sr.y & 3) == 0 ? 1.0f : -1.0f;   // stretching acts on a, its negative on b
+        const float ca = ta.w + kag_dS;
+        F.x += ((ca * ta.x - kv_dV6 * tn.x) + sg * es.x) + (b1.x + b2.x);
+        F.y += ((ca * ta.y - kv_dV6 * tn.y) + sg * es.y) + (b1.y + b2.y);
+        F.z += ((ca * ta.z - kv_dV6 * tn.z) + sg * es.z) + (b1.z + b2.z);
+    }
+#pragma unroll
+    for (int o = FS4 / 2; o > 0; o >>= 1) {
+        F.x += __shfl_xor_sync(smask, F.x, o);
+        F.y += __shfl_xor_sync(smask, F.y, o);
+        F.z += __shfl_xor_sync(smask, F.z, o);
+    }
+    if (a.R) {
+        const float4 r = a.R[i];
+        F.x += r.x; F.y += r.y; F.z += r.z;
+    }
+    if (sl == 0) a.F[i] = make_float4(F.x, F.y, F.z, 0.f);
+    uint8_t* fl = a.par ? a.fl1 : a.fl0;
+    const unsigned active = __activemask();
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        if (hit[c]) {
+            if (a.gfix) {
+                const float cc[3] = {w[c] * F.x, w[c] * F.y, w[c] * F.z};
+#pragma unroll
+                for (int d = 0; d < 3; ++d)
+                    atomicAdd(a.gfix + d * a.gfix_stride + g[c],
+                              (unsigned long long)__float2ll_rn(cc[d] * FIX_SCALE_F));
+            } else {
+                atomicAdd((a.par ? a.g1 : a.g0) + g[c], make_float4(w[c] * F.x, w[c] * F.y, w[c] * F.z, 0.f));
+            }
+        }
+        // flag the 32-node groups that received force: one store per distinct group of this warp
+        const long long grp = hit[c] ? (g[c] >> 5) : -1;
+        const unsigned same = __match_any_sync(active, grp);
+        if (hit[c] && (__ffs(same) - 1) == (int)(threadIdx.x & 31)) fl[grp] = 1;
+    }
+}
+
 cudaError_t launch_forces_spread(const IbmArgs& a, cudaStream_t s) {
     if (a.n_nodes <= 0) return cudaSuccess;
     const long long threads = (long long)a.n_nodes * SUB;
     if (a.W) return launch_ex(k_forces_spread<true>, (unsigned)((threads + FS_BLOCK - 1) / FS_BLOCK), FS_BLOCK, 0, s, a.pdl, a);
+    if (!a.dcur) {
+        const long long t4 = (long long)a.n_nodes * FS4;
+        return launch_ex(k_forces_spread4, (unsigned)((t4 + FS_BLOCK - 1) / FS_BLOCK), FS_BLOCK, 0, s, a.pdl, a);
+    }
     return launch_ex(k_forces_spread<false>, (unsigned)((threads + FS_BLOCK - 1) / FS_BLOCK), FS_BLOCK, 0, s, a.pdl, a);
 }
 
