@@ -483,6 +483,47 @@ def test_api_edge_cases():
     assert np.abs(rho - 1.0).max() < 1e-6 and np.abs(u).max() < 1e-7   # no force, no meshes: at rest
 
 
+@pytest.mark.parametrize("storage,variants", [("f32", [(1, 128), (2, 128), (4, 128)]),
+                                              ("f16", [(1, 128), (2, 128), (4, 64)])])
+def test_smallest_lattice_every_variant(storage, variants):
+    """The smallest lattice the library takes (4 x 4 x 4, the whole lattice one
+    partial 32-node group), fully periodic and with walls, random state, 20
+    steps: every one-, two- and four-node variant against the oracle (FP32 at
+    the parity tolerance, 16-bit storage within its rounding)."""
+    for periodic in ((1, 1, 1), (0, 0, 0)):
+        sc = scene.Scene(name="tiny", dims=(4, 4, 4), tau=0.9, body_force=(1e-5, -2e-6, 3e-6), periodic=periodic,
+                         meshes=[], steps=0)
+        for v in variants:
+            sim = _sim(sc, storage=storage)
+            sim.set_kernel_config(*v)
+            ref = oracle.System.from_scene(sc)
+            f0 = ref.get_f() * (1 + 0.01 * scene.random_field(12, (19, ref.N)))
+            sim.set_populations(f0)
+            ref.set_f(sim.populations().astype(np.float64))
+            sim.step(20)
+            ref.step(20)
+            err = rel_l2(sim.fields()[1], ref.fields()[1])
+            assert err < (1e-5 if storage == "f32" else 2e-2), (periodic, v, err)
+
+
+def test_lattice_beyond_the_index_range_is_refused_before_allocating():
+    """Node indices are 32-bit inside the kernels: a batch of two 2^30-node
+    channels (each valid alone, refused one by one on the host otherwise) is
+    refused with LB_ERR_ARG and its reason once the padded total reaches 2^31,
+    before any device memory is taken."""
+    import ctypes
+
+    from paper_1110_0995_gb300 import lbibm
+
+    L = lbibm.lib()
+    p = lbibm.make_params((1024, 1024, 1024))
+    arr = (lbibm.LbParams * 2)(p, p)
+    h = ctypes.c_void_p()
+    st = L.lb_create_batch(arr, 2, None, ctypes.byref(h))
+    assert st == lbibm.LB_ERR_ARG and not h.value
+    assert b"too large" in L.lb_last_error(None)
+
+
 def test_mesh_validation():
     """ibm_add_mesh accepts a closed, outward, manifold mesh and refuses the
     rest with LB_ERR_ARG: a missing face, inward orientation, an edge used
