@@ -436,6 +436,20 @@ const char* lb_last_error(const lb_ctx* ctx);
 /* Library version: major * 10000 + minor * 100 + patch. */
 int lb_version(void);
 
+/* Debugging aid for out-of-bounds device writes (there is no memory checker
+ * to run): with bytes > 0, every device allocation of the contexts created
+ * afterwards gets `bytes` (rounded up to a multiple of 256) of a fixed byte
+ * pattern before and after it; 0 turns it off for later contexts.  Process-
+ * wide, host-only; LB_ERR_ARG above 1 GiB.  Not a paper operation. */
+lb_status lb_set_guard_zones(size_t bytes);
+
+/* Bytes of the context's guard zones that no longer hold the pattern (0 when
+ * no kernel wrote past either end of any of its allocations; 0 as well for a
+ * context created without guard zones).  Waits for the context's stream.
+ * self_test != 0 first changes one byte of every zone from the host, counts,
+ * and restores them: the count is then 2 per allocation plus any damage. */
+lb_status lb_check_guard_zones(lb_ctx* ctx, int self_test, int64_t* damaged_bytes);
+
 #ifdef __cplusplus
 }
 #endif

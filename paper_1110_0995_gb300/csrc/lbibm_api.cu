@@ -8,6 +8,7 @@
 #include "lbibm_internal.cuh"
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -171,6 +172,14 @@ struct lb_ctx {
     std::vector<EventPair> pending;
     std::vector<cudaEvent_t> free_events;
     std::vector<void*> allocations;
+    // debug guard zones (lb_set_guard_zones): bytes of pattern before and
+    // after every allocation of this context, and the guarded allocations
+    size_t guard = 0;
+    struct Guarded {
+        char* base;
+        size_t bytes, guard;
+    };
+    std::vector<Guarded> guarded;
 };
 
 namespace lbibm {
@@ -210,13 +219,31 @@ lb_status cuda_fail(lb_ctx* c, cudaError_t e, const char* where) {
         if ((ctx)->poisoned) return LB_ERR_CUDA;                              \
     } while (0)
 
+// Guard zones of the contexts created from now on (lb_set_guard_zones).
+std::atomic<size_t> g_guard_bytes{0};
+constexpr unsigned char GUARD_PATTERN = 0xA5;
+
+// Device allocation owned by the context.  With guard zones, `guard` bytes of
+// GUARD_PATTERN sit before and after the returned block (which keeps the
+// 256-byte alignment of cudaMalloc: guards are multiples of 256).
 template <class T>
 cudaError_t dalloc(lb_ctx* ctx, T** p, size_t count) {
     void* v = nullptr;
-    cudaError_t e = cudaMalloc(&v, std::max<size_t>(count, 1) * sizeof(T));
+    const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+    const size_t gz = ctx->guard;
+    cudaError_t e = cudaMalloc(&v, bytes + 2 * gz);
+    if (e == cudaSuccess && gz) {
+        e = cudaMemset(v, GUARD_PATTERN, gz);
+        if (e == cudaSuccess) e = cudaMemset((char*)v + gz + bytes, GUARD_PATTERN, gz);
+        if (e != cudaSuccess) {
+            cudaFree(v);
+            v = nullptr;
+        }
+    }
     if (e == cudaSuccess) {
-        *p = (T*)v;
+        *p = (T*)((char*)v + gz);
         ctx->allocations.push_back(v);
+        if (gz) ctx->guarded.push_back({(char*)v, bytes, gz});
     } else {
         *p = nullptr;
     }
@@ -225,9 +252,22 @@ cudaError_t dalloc(lb_ctx* ctx, T** p, size_t count) {
 
 void dfree(lb_ctx* ctx, void* p) {
     if (!p) return;
-    auto it = std::find(ctx->allocations.begin(), ctx->allocations.end(), p);
+    void* base = (char*)p - ctx->guard;
+    auto it = std::find(ctx->allocations.begin(), ctx->allocations.end(), base);
     if (it != ctx->allocations.end()) ctx->allocations.erase(it);
-    cudaFree(p);
+    ctx->guarded.erase(std::remove_if(ctx->guarded.begin(), ctx->guarded.end(),
+                                      [&](const lb_ctx::Guarded& g) { return g.base == base; }),
+                       ctx->guarded.end());
+    cudaFree(base);
+}
+
+// Bytes of [p, p + n) that differ from the guard pattern, added to *count.
+__global__ void k_guard_count(const unsigned char* __restrict__ p, size_t n, unsigned long long* count) {
+    unsigned long long c = 0;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        c += p[i] != GUARD_PATTERN;
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
 }
 
 size_t pop_bytes(lb_storage s) { return s == LB_F32 ? 4 : 2; }
@@ -812,6 +852,46 @@ extern "C" {
 
 int lb_version(void) { return 10000; }
 
+lb_status lb_set_guard_zones(size_t bytes) {
+    if (bytes > ((size_t)1 << 30)) return context_free_error(LB_ERR_ARG, "guard zone larger than 1 GiB");
+    g_guard_bytes.store((bytes + 255) / 256 * 256);
+    return LB_OK;
+}
+
+lb_status lb_check_guard_zones(lb_ctx* ctx, int self_test, int64_t* damaged_bytes) {
+    LB_GUARD(ctx);
+    if (!damaged_bytes) return fail(ctx, LB_ERR_ARG, "damaged_bytes is NULL");
+    *damaged_bytes = 0;
+    LB_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (ctx->guarded.empty()) return LB_OK;
+    unsigned long long* d_count = nullptr;
+    LB_CUDA(cudaMalloc(&d_count, sizeof(unsigned long long)));   // outside the guarded set
+    cudaError_t e = cudaMemset(d_count, 0, sizeof(unsigned long long));
+    // self test: one byte of every zone changed from the host first, then restored
+    for (const auto& g : ctx->guarded) {
+        if (e == cudaSuccess && self_test) e = cudaMemset(g.base + g.guard - 1, 0, 1);
+        if (e == cudaSuccess && self_test) e = cudaMemset(g.base + g.guard + g.bytes, 0, 1);
+        if (e == cudaSuccess) k_guard_count<<<8, 256, 0, ctx->stream>>>((const unsigned char*)g.base, g.guard, d_count);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e == cudaSuccess)
+            k_guard_count<<<8, 256, 0, ctx->stream>>>((const unsigned char*)g.base + g.guard + g.bytes, g.guard, d_count);
+        if (e == cudaSuccess) e = cudaGetLastError();
+    }
+    unsigned long long h = 0;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpy(&h, d_count, sizeof(h), cudaMemcpyDeviceToHost);
+    if (self_test) {
+        for (const auto& g : ctx->guarded) {
+            if (e == cudaSuccess) e = cudaMemset(g.base + g.guard - 1, GUARD_PATTERN, 1);
+            if (e == cudaSuccess) e = cudaMemset(g.base + g.guard + g.bytes, GUARD_PATTERN, 1);
+        }
+    }
+    cudaFree(d_count);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "lb_check_guard_zones");
+    *damaged_bytes = (int64_t)h;
+    return LB_OK;
+}
+
 const char* lb_last_error(const lb_ctx* ctx) { return ctx ? ctx->err.c_str() : context_free_err.c_str(); }
 
 lb_status lb_create_batch(const lb_params* params, int n_channels, void* cuda_stream, lb_ctx** out) {
@@ -827,6 +907,7 @@ lb_status lb_create_batch(const lb_params* params, int n_channels, void* cuda_st
             return context_free_error(LB_ERR_ARG, "every channel of a batch needs the same storage");
     }
     lb_ctx* ctx = new lb_ctx();
+    ctx->guard = g_guard_bytes.load();
     ctx->storage = params[0].storage;
     long long base = 0;
     for (int k = 0; k < n_channels; ++k) {

@@ -28,6 +28,7 @@ EXPORTS = (
     "lb_set_kernel_config", "lb_get_kernel_config", "lb_set_prefetch", "lb_get_prefetch", "lb_autotune",
     "ibm_area_volume_noalloc",
     "bead_forces", "bead_relax", "ibm_get_all_nodes_async", "lb_readback_wait", "ibm_check_mesh",
+    "lb_set_guard_zones", "lb_check_guard_zones",
 )
 
 
@@ -107,6 +108,8 @@ def lib():
             "lb_set_kernel_config": ([P, I, I], I),
             "lb_get_kernel_config": ([P, ctypes.POINTER(I), ctypes.POINTER(I)], I),
             "lb_set_prefetch": ([P, I], I),
+            "lb_set_guard_zones": ([ctypes.c_size_t], I),
+            "lb_check_guard_zones": ([P, I, ctypes.POINTER(ctypes.c_int64)], I),
             "lb_get_prefetch": ([P, ctypes.POINTER(I)], I),
             "lb_autotune": ([P, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(D)], I),
             "ibm_area_volume_noalloc": ([P, P, P, P, I, P, P, P], I),
@@ -373,6 +376,12 @@ class Simulation:
         self._check(self._L.lb_get_prefetch(self._h, ctypes.byref(n)))
         return n.value
 
+    def guard_damage(self, self_test: bool = False) -> int:
+        """Bytes of the debug guard zones a kernel overwrote (see set_guard_zones)."""
+        n = ctypes.c_int64()
+        self._check(self._L.lb_check_guard_zones(self._h, int(self_test), ctypes.byref(n)))
+        return n.value
+
     def autotune(self, repeats: int = 20):
         """Time every stream-collide variant (before the first step) and keep the fastest."""
         n, b, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
@@ -438,6 +447,16 @@ class Simulation:
         n = np.zeros(4, np.int64)
         self._check(self._L.lb_kernel_times(self._h, _ptr(ms), _ptr(n)))
         return ms, n
+
+
+def set_guard_zones(nbytes: int):
+    """Debug guard zones of nbytes around every device allocation of the
+    contexts created afterwards (0: off); Simulation.guard_damage counts the
+    bytes a kernel overwrote."""
+    L = lib()
+    st = L.lb_set_guard_zones(int(nbytes))
+    if st != LB_OK:
+        raise LbError(st, last_error())
 
 
 def check_mesh(rest: np.ndarray, tris: np.ndarray) -> str:

@@ -125,3 +125,11 @@ def test_batch_scenes_must_agree_on_context_settings(lbibm):
     for pair in ((a, b), (a, c)):
         with pytest.raises(ValueError, match="differ in"):
             lbibm.Simulation.from_scenes(list(pair))
+
+
+def test_guard_zone_size_is_checked_on_the_host(lbibm):
+    L = lbibm.lib()
+    assert L.lb_set_guard_zones(1 << 31) == lbibm.LB_ERR_ARG
+    assert "1 GiB" in lbibm.last_error()
+    assert L.lb_set_guard_zones(4096) == lbibm.LB_OK
+    assert L.lb_set_guard_zones(0) == lbibm.LB_OK
