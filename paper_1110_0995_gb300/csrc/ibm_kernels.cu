@@ -160,9 +160,13 @@ __device__ __forceinline__ float tri_dV6(const Pt& R, const Pt& P0, const Pt& P1
 }
 
 // ---------------------------------------------------------------------------
-// Per-cell dS, dV (FP64 accumulation), one block per chunk of one cell's
-// triangles, one triangle per thread; the last block of a cell adds the
-// cell's partials in chunk order (deterministic).  With FORCES the same pass
+// Per-cell dS, dV, one block per chunk of one cell's triangles, one triangle
+// per thread.  The per-triangle terms are added as 64-bit integers in 2^-40
+// units (each rounded once, far below its FP32 rounding; the sums are exact
+// and independent of their order, and run on the integer pipe: this GPU's
+// FP64 pipe retires about two operations per clock per SM).  The last block
+// of a cell adds the cell's partials and forms dS, dV in FP64 once.  With
+// FORCES the same pass
 // writes each triangle's area and volume force terms:
 //   area (local + global, homocentric): F_k = (kal dS_t/S0_t + kag dS/S0) a_k,
 //     a_k = -(2 S_t / sum_j |w_j|^2) w_k, w_k = x_k - centroid;
@@ -176,45 +180,45 @@ __device__ __forceinline__ float tri_dV6(const Pt& R, const Pt& P0, const Pt& P1
 constexpr int CS_BLOCK = 128;
 constexpr int IB_MIN_BLOCKS = 8;
 
-__device__ __forceinline__ double warp_sum_d(double v) {
+__device__ __forceinline__ long long warp_sum_ll(long long v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     return v;
 }
 
-// The cell's FP64 partial sums of one chunk: block reduction, then the last
-// block of the cell adds the cell's partials in chunk order (deterministic).
-__device__ __forceinline__ void chunk_sums(const IbmArgs& a, int chunk, const int4& ck, double s, double v) {
-    __shared__ double sh[2][CS_BLOCK / 32];
+// The cell's partial sums (dS, 6 dV in 2^-40 units) of one chunk: block
+// reduction, then the last block of the cell adds the cell's partials.
+__device__ __forceinline__ void chunk_sums(const IbmArgs& a, int chunk, const int4& ck, long long s, long long v) {
+    __shared__ long long sh[2][CS_BLOCK / 32];
     __shared__ bool last;
-    s = warp_sum_d(s);
-    v = warp_sum_d(v);
+    s = warp_sum_ll(s);
+    v = warp_sum_ll(v);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (lane == 0) { sh[0][wid] = s; sh[1][wid] = v; }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double S = 0.0, V = 0.0;
+        long long S = 0, V = 0;
         for (int w = 0; w < CS_BLOCK / 32; ++w) { S += sh[0][w]; V += sh[1][w]; }
-        a.partials[chunk] = make_double2(S, V / 6.0);
+        a.partials[chunk] = make_longlong2(S, V);
         __threadfence();
         const unsigned done = atomicAdd(a.counters + ck.x, 1u);
         last = (done + 1 == (unsigned)ck.w);
     }
     __syncthreads();
     if (last && threadIdx.x < 32) {
-        // the last block of the cell: one warp loads all partials at once and
-        // adds them in a fixed tree order (deterministic)
+        // the last block of the cell: one warp loads all partials at once
         __threadfence();
         const int c0 = a.cells[ck.x].chunk0, nc = ck.w;
-        double S = 0.0, V = 0.0;
+        long long Si = 0, Vi = 0;
         for (int k = threadIdx.x; k < nc; k += 32) {
-            const double2 pv = __ldcg(a.partials + c0 + k);
-            S += pv.x;
-            V += pv.y;
+            const longlong2 pv = __ldcg(a.partials + c0 + k);
+            Si += pv.x;
+            Vi += pv.y;
         }
-        S = warp_sum_d(S);
-        V = warp_sum_d(V);
+        Si = warp_sum_ll(Si);
+        Vi = warp_sum_ll(Vi);
         if (threadIdx.x == 0) {
+            const double S = (double)Si * (1.0 / FIX_SCALE), V = (double)Vi * (1.0 / (6.0 * FIX_SCALE));
             a.cell_sums[ck.x] = make_double2(S, V);
             a.cell_rel[ck.x] = make_float2((float)(S / a.cells[ck.x].S0), (float)(V / a.cells[ck.x].V0));
             a.counters[ck.x] = 0u;
@@ -243,14 +247,14 @@ __device__ __forceinline__ TriStatic tri_static(const IbmArgs& a, int t) {
 // dS_t and dV_t (x 6) of one triangle; with FORCES also its area and volume
 // force terms.
 template <bool FORCES>
-__device__ __forceinline__ void tri_terms(const IbmArgs& a, int t, const TriStatic& d, double& s, double& v) {
+__device__ __forceinline__ void tri_terms(const IbmArgs& a, int t, const TriStatic& d, long long& s, long long& v) {
     const Q4* qc = cur_q(a);
     const Pt R = load_pt(a, qc, d.ref);
     const Pt P0 = load_pt(a, qc, d.tr.x), P1 = load_pt(a, qc, d.tr.y), P2 = load_pt(a, qc, d.tr.z);
     const float3 e1 = edge(P0, P1), e2 = edge(P0, P2);
     const float dSt = tri_dS(e1, e2, ddisp(P0, P1), ddisp(P0, P2), d.S0t);
-    s += (double)dSt;
-    v += (double)tri_dV6(R, P0, P1, P2);
+    s += float_to_fixed(dSt);
+    v += float_to_fixed(tri_dV6(R, P0, P1, P2));
     if constexpr (FORCES) {
         const float St = d.S0t + dSt;
         const float3 third = (1.0f / 3.0f) * (e1 + e2);
@@ -269,7 +273,7 @@ __device__ __forceinline__ void tri_terms(const IbmArgs& a, int t, const TriStat
 template <bool FORCES>
 __device__ __forceinline__ void tri_chunk(const IbmArgs& a, int chunk) {
     const int4 ck = a.chunks[chunk];
-    double s = 0.0, v = 0.0;
+    long long s = 0, v = 0;
     for (int t = ck.y + (int)threadIdx.x; t < ck.z; t += CS_BLOCK) tri_terms<FORCES>(a, t, tri_static(a, t), s, v);
     chunk_sums(a, chunk, ck, s, v);
 }
@@ -299,7 +303,7 @@ __global__ void __launch_bounds__(CS_BLOCK, 6) k_elements(const __grid_constant_
         TriStatic d = {};
         if (live) d = tri_static(a, t);
         pdl_entry();
-        double s = 0.0, v = 0.0;
+        long long s = 0, v = 0;
         if (live) tri_terms<true>(a, t, d, s, v);
         chunk_sums(a, blockIdx.x, ck, s, v);
         return;

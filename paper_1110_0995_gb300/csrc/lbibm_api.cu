@@ -102,7 +102,7 @@ struct lb_ctx {
     int4* tris = nullptr;
     float* triS0 = nullptr;
     int4* chunks = nullptr;
-    double2* partials = nullptr;
+    longlong2* partials = nullptr;
     unsigned* counters = nullptr;
     double2* cell_sums = nullptr;
     float2* cell_rel = nullptr;

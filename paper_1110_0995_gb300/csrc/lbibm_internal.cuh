@@ -210,7 +210,7 @@ struct IbmArgs {
     const float* tri_S0;  // [T] rest area of each triangle
     const int4* chunks;   // [NCH] (cell, t_begin, t_end, chunks of that cell)
     int n_chunks;
-    double2* partials;    // [NCH]
+    longlong2* partials;  // [NCH] (dS, 6 dV) per chunk, 2^-40 units
     unsigned* counters;   // [C]
     double2* cell_sums;   // [C] (dS, dV)
     float2* cell_rel;     // [C] (dS / S0, dV / V0)
