@@ -232,7 +232,7 @@ __device__ __forceinline__ void edge_forces(const V3& xb, const V3& xc, const V3
 // lamF_v - lamF_a).
 __device__ __forceinline__ void adj_edges_block(const AdjArgs& a, int blk) {
     const int e = blk * blockDim.x + threadIdx.x;
-    double gks = 0.0, gkb = 0.0;
+    float gks = 0.f, gkb = 0.f;   // (FP32 within a warp, FP64 across warps and steps)
     if (e < a.n_edges) {
         const int4 ev = a.edges[e];
         const float4 er = a.edge_rest[e];   // (L0, theta0, ks, kb)
@@ -250,19 +250,19 @@ __device__ __forceinline__ void adj_edges_block(const AdjArgs& a, int blk) {
         atomic_add3(a.lamX_out + ev.w, fb[3].x.d, fb[3].y.d, fb[3].z.d);
         if (a.info[ev.x].x == a.obj_cell) {
             // parameter gradients (the forces are linear in ks and kb)
-            if (er.z != 0.f) gks = (double)((vdot(fs[0], la) + vdot(fs[1], lb)) / er.z);
-            if (er.w != 0.f)
-                gkb = (double)((vdot(fb[0], la) + vdot(fb[1], lb) + vdot(fb[2], lc) + vdot(fb[3], ld)) / er.w);
+            if (er.z != 0.f) gks = (vdot(fs[0], la) + vdot(fs[1], lb)) / er.z;
+            if (er.w != 0.f) gkb = (vdot(fb[0], la) + vdot(fb[1], lb) + vdot(fb[2], lc) + vdot(fb[3], ld)) / er.w;
         }
     }
+    if (!__any_sync(AFULL, gks != 0.f || gkb != 0.f)) return;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         gks += __shfl_down_sync(AFULL, gks, o);
         gkb += __shfl_down_sync(AFULL, gkb, o);
     }
-    if ((threadIdx.x & 31) == 0 && (gks != 0.0 || gkb != 0.0)) {
-        atomicAdd(a.grad + 0, gks);
-        atomicAdd(a.grad + 1, gkb);
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(a.grad + 0, (double)gks);
+        atomicAdd(a.grad + 1, (double)gkb);
     }
 }
 
@@ -331,15 +331,15 @@ __device__ __forceinline__ void adj_tris_block(const AdjArgs& a, int blk) {
         const int l0 = __ffs(rem) - 1;
         const int c = __shfl_sync(AFULL, cell, l0);
         const bool mine = has && cell == c;
-        double s1 = mine ? (double)lc1 : 0.0, s2 = mine ? (double)lc2 : 0.0;
+        float s1 = mine ? lc1 : 0.f, s2 = mine ? lc2 : 0.f;   // (FP32 within a warp)
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             s1 += __shfl_xor_sync(AFULL, s1, o);
             s2 += __shfl_xor_sync(AFULL, s2, o);
         }
         if (lane == l0) {
-            atomicAdd(a.lam_c + 2 * c, s1);
-            atomicAdd(a.lam_c + 2 * c + 1, s2);
+            atomicAdd(a.lam_c + 2 * c, (double)s1);
+            atomicAdd(a.lam_c + 2 * c + 1, (double)s2);
         }
         rem &= ~__ballot_sync(AFULL, mine);
     }
@@ -361,8 +361,8 @@ __global__ void k_adj_tris_global(const __grid_constant__ AdjArgs a) {
     if (t >= a.n_tris) return;
     const int4 tr = a.tris[t];
     const CellDev& C = a.cells[tr.w];
-    const float lS = (float)(a.lam_c[2 * tr.w] * (double)C.kag / C.S0);
-    const float lV = (float)(a.lam_c[2 * tr.w + 1] * (double)C.kv / (6.0 * C.V0));
+    const float lS = (float)a.lam_c[2 * tr.w] * C.kag_S0;
+    const float lV = (float)a.lam_c[2 * tr.w + 1] * C.kv_6V0;
     const float* ds = reinterpret_cast<const float*>(a.tri_dS) + 6 * t;
     const float3 db = make_float3(ds[0], ds[1], ds[2]), dc = make_float3(ds[3], ds[4], ds[5]);
     const float4 n = a.tri_n[t];
@@ -412,17 +412,18 @@ __global__ void k_adj_bead_grad(const __grid_constant__ AdjArgs a) {
             const float s = lp * others * 0.5f * (1.0f - t * t) / a.delta / d;
             gx = s * dx; gy = s * dy; gz = s * dz;
         }
-        double sx = gx, sy = gy, sz = gz;
+        float sx = gx, sy = gy, sz = gz;   // (FP32 within a warp)
+        if (!__any_sync(AFULL, sx != 0.f || sy != 0.f || sz != 0.f)) continue;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             sx += __shfl_down_sync(AFULL, sx, o);
             sy += __shfl_down_sync(AFULL, sy, o);
             sz += __shfl_down_sync(AFULL, sz, o);
         }
-        if ((threadIdx.x & 31) == 0 && (sx != 0.0 || sy != 0.0 || sz != 0.0)) {
-            atomicAdd(a.grad + 2 + 3 * k, sx);
-            atomicAdd(a.grad + 3 + 3 * k, sy);
-            atomicAdd(a.grad + 4 + 3 * k, sz);
+        if ((threadIdx.x & 31) == 0) {
+            atomicAdd(a.grad + 2 + 3 * k, (double)sx);
+            atomicAdd(a.grad + 3 + 3 * k, (double)sy);
+            atomicAdd(a.grad + 4 + 3 * k, (double)sz);
         }
     }
     (void)prod;

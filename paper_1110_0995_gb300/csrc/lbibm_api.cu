@@ -1750,6 +1750,8 @@ lb_status ibm_add_mesh(lb_ctx* ctx, const double* rest_xyz, int n, const int32_t
     cd.ks = (float)mod->ks; cd.kb = (float)mod->kb; cd.kal = (float)mod->kal; cd.kag = (float)mod->kag; cd.kv = (float)mod->kv;
     cd.S0 = S0;
     cd.V0 = V0;
+    cd.kag_S0 = (float)(mod->kag / S0);
+    cd.kv_6V0 = (float)(mod->kv / (6.0 * V0));
     ctx->hcells.push_back(cd);
     MeshHost mh;
     mh.ch = ctx->cur; mh.node0 = node0; mh.n = n; mh.tri0 = tri0; mh.nt = nt; mh.cell = cell; mh.S0 = S0; mh.V0 = V0;

@@ -144,6 +144,7 @@ struct CellDev {
     int node0, n_nodes;
     int chunk0, n_chunks; // triangle chunks of the area/volume reduction
     float ks, kb, kal, kag, kv;
+    float kag_S0, kv_6V0; // kag / S0 and kv / (6 V0) in FP32
     float pad;
     double S0, V0;        // rest area and volume (FP64)
 };
