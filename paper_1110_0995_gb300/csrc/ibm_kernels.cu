@@ -93,19 +93,25 @@ __device__ __forceinline__ const ChannelDev& chan(const IbmArgs& a, int c) {
 // element terms
 // ---------------------------------------------------------------------------
 
+// The element terms divide with __fdividef and take square roots as x
+// rsqrt(x) (a few ulp, against the ~10 instructions of a correctly rounded
+// division; every argument is positive for a non-degenerate element).
+__device__ __forceinline__ float sqrt_fast(float x) { return x * rsqrtf(x); }
+
 // Stretching (neo-Hookean bond, Dupin et al.): tension ks kappa(lambda)(lambda-1)
-// with kappa = (lambda^1/2 + lambda^-5/2)/(lambda + lambda^-3); returns the force
-// on a (the force on b is its negative).  a < b in global index.
+// with kappa = (lambda^1/2 + lambda^-5/2)/(lambda + lambda^-3)
+//            = lambda^1/2 (lambda^3 + 1)/(lambda^4 + 1);
+// returns the force on a (the force on b is its negative).  a < b in global index.
 __device__ __forceinline__ float3 stretch_on_a(const Pt& A, const Pt& B, float L0, float ks) {
     const float3 d = edge(A, B);
     const float3 de = ddisp(A, B);
     const float3 d0 = d - de;
     const float num = 2.0f * dot(d0, de) + dot(de, de);   // |d|^2 - |d0|^2
-    const float L = sqrtf(L0 * L0 + num);
-    const float lm1 = num / ((L + L0) * L0);               // lambda - 1
+    const float L = sqrt_fast(L0 * L0 + num);
+    const float lm1 = __fdividef(num, (L + L0) * L0);      // lambda - 1
     const float lam = 1.0f + lm1;
-    const float sl = sqrtf(lam);
-    const float kappa = (sl + 1.0f / (lam * lam * sl)) / (lam + 1.0f / (lam * lam * lam));
+    const float lam2 = lam * lam;
+    const float kappa = __fdividef(sqrt_fast(lam) * (lam2 * lam + 1.0f), lam2 * lam2 + 1.0f);
     const float T = ks * kappa * lm1;
     return (T * rsqrtf(dot(d, d))) * d;
 }
@@ -122,13 +128,15 @@ __device__ __forceinline__ void bend_all(const Pt& A, const Pt& B, const Pt& Cc,
     const float3 n1 = cross(e, ac);
     const float3 n2 = cross(-e, bd);
     const float l2 = dot(e, e);
-    const float l = sqrtf(l2);
-    const float theta = atan2f(dot(cross(n1, n2), e) / l, dot(n1, n2));
+    const float rl = rsqrtf(l2);
+    const float l = l2 * rl;
+    const float theta = atan2f(dot(cross(n1, n2), e) * rl, dot(n1, n2));
     const float coef = -kb * (theta - th0);
-    const float3 gc = (-l / dot(n1, n1)) * n1;
-    const float3 gd = (-l / dot(n2, n2)) * n2;
-    const float sc = dot(ac, e) / l2;
-    const float sd = dot(ad, e) / l2;
+    const float3 gc = __fdividef(-l, dot(n1, n1)) * n1;
+    const float3 gd = __fdividef(-l, dot(n2, n2)) * n2;
+    const float il2 = __fdividef(1.0f, l2);
+    const float sc = dot(ac, e) * il2;
+    const float sd = dot(ad, e) * il2;
     f[0] = coef * ((-(1.0f - sc)) * gc - (1.0f - sd) * gd);
     f[1] = coef * ((-sc) * gc - sd * gd);
     f[2] = coef * gc;
@@ -144,8 +152,8 @@ __device__ __forceinline__ float tri_dS(const float3& e1, const float3& e2, cons
     const float3 dn = cross(a1, b2) + cross(b1, a2) + cross(b1, b2);
     const float num = 2.0f * dot(n0, dn) + dot(dn, dn);
     const float nn0 = 2.0f * S0t;
-    const float nn = sqrtf(nn0 * nn0 + num);
-    return num / (2.0f * (nn + nn0));
+    const float nn = sqrt_fast(nn0 * nn0 + num);
+    return __fdividef(num, 2.0f * (nn + nn0));
 }
 
 // Volume change of the tetrahedron (reference node R, 0, 1, 2) from rest, times 6:
@@ -260,8 +268,8 @@ __device__ __forceinline__ void tri_terms(const IbmArgs& a, int t, const TriStat
         const float3 third = (1.0f / 3.0f) * (e1 + e2);
         const float3 w0 = -third, w1 = e1 - third, w2 = e2 - third;
         const float ww = dot(w0, w0) + dot(w1, w1) + dot(w2, w2);
-        const float c = -2.0f * St / ww;
-        const float sl = d.kal * dSt / d.S0t;
+        const float c = __fdividef(-2.0f * St, ww);
+        const float sl = __fdividef(d.kal * dSt, d.S0t);
         a.tA[3 * t] = make_float4(c * w0.x, c * w0.y, c * w0.z, sl);
         a.tA[3 * t + 1] = make_float4(c * w1.x, c * w1.y, c * w1.z, sl);
         a.tA[3 * t + 2] = make_float4(c * w2.x, c * w2.y, c * w2.z, sl);
