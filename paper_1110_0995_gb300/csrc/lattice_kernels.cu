@@ -1993,6 +1993,10 @@ __device__ __forceinline__ void adj_node(const AdjArgs& a, const ChannelDev& C, 
 #define LBIBM_AP(I) adj_pull<I, SLOW>(a, NT, gi, nb, lk, C, y, f, lh);
     LBIBM_ALL_I(LBIBM_AP)
 #undef LBIBM_AP
+    // The pulls above read the segment store and the adjoint written two kernels
+    // back, complete when this kernel starts; only the interpolation's adjoint
+    // lam_u comes from the kernel before it.
+    pdl_entry();
     float drho, jx, jy, jz;
     moments(f, drho, jx, jy, jz);
     const float rho = 1.0f + drho;
@@ -2064,7 +2068,7 @@ __device__ __forceinline__ void adj_node(const AdjArgs& a, const ChannelDev& C, 
 }
 
 __global__ void __launch_bounds__(128, 8) k_adj_collide(const __grid_constant__ AdjArgs a) {
-    pdl_entry();
+    // (adj_node waits for the predecessor after its pulls)
     const ChannelDev C = a.ch;
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     const bool inr = p < C.n;
