@@ -8,6 +8,7 @@
 #include "lbibm_internal.cuh"
 
 #include <algorithm>
+#include <thread>
 #include <atomic>
 #include <cmath>
 #include <cstdio>
@@ -39,6 +40,20 @@ struct MeshHost {
     int tri0 = 0, nt = 0;
     int cell = 0;
     double S0 = 0, V0 = 0;
+};
+
+// The connectivity-derived tables of a mesh, in its own node, triangle and
+// edge numbering: edges (a, b, c, d) with a < b in triangle order, and per
+// node its ring slots (3 t + position of the node in t, 4 e + role as a / b,
+// 4 e' + role as c / d, t).  They depend on the triangles only, so meshes
+// that share a template (every red cell of a scene) are checked and indexed
+// once per context.
+struct MeshConn {
+    int n = 0, nt = 0;
+    std::vector<int32_t> tris;   // the key
+    std::vector<int4> edges;
+    std::vector<int4> slots;
+    std::vector<int> ring_off, valence;
 };
 
 struct EventPair {
@@ -83,6 +98,8 @@ struct lb_ctx {
     std::vector<float> htriS0;
     std::vector<int4> hchunks;
     std::vector<CellDev> hcells;
+    std::vector<double> hrest;     // rest positions (x, y, z per node), for the rest dihedral angles
+    std::vector<std::unique_ptr<MeshConn>> conn_cache;   // connectivity per distinct triangle list
     std::vector<MeshHost> meshes;
     std::vector<std::vector<int>> ch_meshes;
     bool committed = false;
@@ -752,6 +769,28 @@ void apply_k3_config(lb_ctx* ctx, K3Config c) {
     ctx->total_blocks = blk;
 }
 
+// The rest dihedral angle of every edge (the bending's theta0, Sec. 2.3.1)
+// from the rest positions, on up to 16 host threads.
+void rest_dihedrals(lb_ctx* ctx) {
+    const int E = (int)ctx->hedges.size();
+    const double* x = ctx->hrest.data();
+    auto run = [ctx, x](int e0, int e1) {
+        for (int e = e0; e < e1; ++e) {
+            const int4 v = ctx->hedges[e];
+            ctx->hedge_rest[e].y = (float)dihedral_host(x + 3 * v.x, x + 3 * v.y, x + 3 * v.z, x + 3 * v.w);
+        }
+    };
+    const int nth = std::max(1, std::min({16, (int)std::thread::hardware_concurrency(), E / 8192}));
+    if (nth == 1) {
+        run(0, E);
+        return;
+    }
+    std::vector<std::thread> th;
+    const int per = (E + nth - 1) / nth;
+    for (int t = 0; t < nth; ++t) th.emplace_back(run, std::min(E, t * per), std::min(E, (t + 1) * per));
+    for (auto& t : th) t.join();
+}
+
 lb_status commit_ibm(lb_ctx* ctx) {
     if (ctx->committed) return LB_OK;
     ctx->committed = true;
@@ -804,6 +843,7 @@ lb_status commit_ibm(lb_ctx* ctx) {
             LB_CUDA(up(&ctx->rep_bead_ch, bc));
         }
     }
+    rest_dihedrals(ctx);
     LB_CUDA(up(&ctx->edges, ctx->hedges));
     LB_CUDA(up(&ctx->edge_rest, ctx->hedge_rest));
     LB_CUDA(dalloc(ctx, &ctx->eS, ctx->E));
@@ -1596,6 +1636,25 @@ struct MeshTopology {
 // node is a single fan of at most MAX_VALENCE triangles, and builds its
 // topology into *topo.  Returns nullptr, or why the mesh is refused.  Host
 // code only.
+// The rest area and volume (FP64) of a mesh whose connectivity is valid;
+// refuses non-finite positions and an inward orientation.
+const char* mesh_geometry(const double* x, int n, const int32_t* tris, int nt, double& S0, double& V0) {
+    for (int k = 0; k < 3 * n; ++k)
+        if (!std::isfinite(x[k]) || std::fabs(x[k]) > 4.0e6) return "node positions must be finite and |x| < 4e6";
+    S0 = 0.0;
+    V0 = 0.0;
+    for (int t = 0; t < nt; ++t) {
+        const double* a = x + 3 * tris[3 * t];
+        const double* b = x + 3 * tris[3 * t + 1];
+        const double* c = x + 3 * tris[3 * t + 2];
+        S0 += tri_area_host(a, b, c);
+        V0 += (a[0] * (b[1] * c[2] - b[2] * c[1]) + a[1] * (b[2] * c[0] - b[0] * c[2]) +
+               a[2] * (b[0] * c[1] - b[1] * c[0])) / 6.0;
+    }
+    if (!(V0 > 0.0)) return "mesh volume must be positive (outward orientation)";
+    return nullptr;
+}
+
 const char* mesh_topology(const double* x, int n, const int32_t* tris, int nt, std::unique_ptr<MeshTopology>& topo) {
     if (!x || !tris || n < 4 || nt < 4) return "mesh needs >= 4 nodes and triangles";
     for (int k = 0; k < 3 * n; ++k)
@@ -1627,6 +1686,7 @@ const char* mesh_topology(const double* x, int n, const int32_t* tris, int nt, s
         if (third.size(i) == 0) continue;
         int a = third.first(i);
         std::vector<int>& r = topo->ringv[i];
+        r.reserve((size_t)out_deg[i] + 1);
         for (int guard = 0; guard <= MAX_VALENCE; ++guard) {
             r.push_back(a);
             a = third.at(i, a);
@@ -1637,19 +1697,50 @@ const char* mesh_topology(const double* x, int n, const int32_t* tris, int nt, s
     }
     for (int i = 0; i < n; ++i)
         if (topo->ringv[i].empty()) return "mesh has an isolated node";
-    // rest area / volume (FP64)
-    double S0 = 0.0, V0 = 0.0;
+    return mesh_geometry(x, n, tris, nt, topo->S0, topo->V0);
+}
+}  // namespace
+
+namespace {
+const char* build_conn(const double* x, int n, const int32_t* tris, int nt, MeshConn& c, double& S0, double& V0) {
+    std::unique_ptr<MeshTopology> topo;
+    if (const char* err = mesh_topology(x, n, tris, nt, topo)) return err;
+    S0 = topo->S0;
+    V0 = topo->V0;
+    DirEdges& third = topo->third;
+    c.n = n;
+    c.nt = nt;
+    c.tris.assign(tris, tris + 3 * (size_t)nt);
+    DirEdges tri_of(n, tris, nt);    // directed edge -> 3 t + position
+    DirEdges edge_of(n, tris, nt);   // (a, b), a < b -> edge index
     for (int t = 0; t < nt; ++t) {
-        const double* a = x + 3 * tris[3 * t];
-        const double* b = x + 3 * tris[3 * t + 1];
-        const double* c = x + 3 * tris[3 * t + 2];
-        S0 += tri_area_host(a, b, c);
-        V0 += (a[0] * (b[1] * c[2] - b[2] * c[1]) + a[1] * (b[2] * c[0] - b[0] * c[2]) +
-               a[2] * (b[0] * c[1] - b[1] * c[0])) / 6.0;
+        const int v[3] = {tris[3 * t], tris[3 * t + 1], tris[3 * t + 2]};
+        for (int k = 0; k < 3; ++k) {
+            const int a = v[k], b = v[(k + 1) % 3];
+            tri_of.put(a, b, 3 * t + k);
+            if (a < b) {
+                edge_of.put(a, b, (int)c.edges.size());
+                c.edges.push_back(make_int4(a, b, third.at(a, b), third.at(b, a)));
+            }
+        }
     }
-    if (!(V0 > 0.0)) return "mesh volume must be positive (outward orientation)";
-    topo->S0 = S0;
-    topo->V0 = V0;
+    auto edge_id = [&](int u, int v) { return edge_of.at(std::min(u, v), std::max(u, v)); };
+    c.ring_off.resize(n);
+    c.valence.resize(n);
+    for (int i = 0; i < n; ++i) {
+        const std::vector<int>& r = topo->ringv[i];
+        const int k = (int)r.size();
+        c.ring_off[i] = (int)c.slots.size();
+        c.valence[i] = k;
+        for (int j = 0; j < k; ++j) {
+            // slot j: triangle (i, nb, nx), edge (i, nb), opposite edge (nb, nx)
+            const int nb = r[j], nx = r[(j + 1) % k];
+            const int tk = tri_of.at(i, nb);
+            const int role1 = i < nb ? 0 : 1;    // i is a or b of edge (i, nb)
+            const int role2 = nb < nx ? 2 : 3;   // i is c or d of edge (nb, nx)
+            c.slots.push_back(make_int4(tk, 4 * edge_id(i, nb) + role1, 4 * edge_id(nb, nx) + role2, tk / 3));
+        }
+    }
     return nullptr;
 }
 }  // namespace
@@ -1673,69 +1764,58 @@ lb_status ibm_add_mesh(lb_ctx* ctx, const double* rest_xyz, int n, const int32_t
     const double mv[5] = {mod->ks, mod->kb, mod->kal, mod->kag, mod->kv};
     for (double v : mv)
         if (!std::isfinite(v)) return fail(ctx, LB_ERR_ARG, "moduli must be finite");
-    std::unique_ptr<MeshTopology> topo;
-    if (const char* err = mesh_topology(rest_xyz, n, tris, nt, topo)) return fail(ctx, LB_ERR_ARG, err);
-    DirEdges& third = topo->third;
-    const std::vector<std::vector<int>>& ringv = topo->ringv;
-    const double S0 = topo->S0, V0 = topo->V0;
+    // the connectivity: from the context's cache when a mesh with the same
+    // triangles was added before (then only the positions are checked)
+    if (!rest_xyz || !tris || n < 4 || nt < 4) return fail(ctx, LB_ERR_ARG, "mesh needs >= 4 nodes and triangles");
+    const MeshConn* conn = nullptr;
+    for (const auto& c : ctx->conn_cache)
+        if (c->n == n && c->nt == nt && std::memcmp(c->tris.data(), tris, sizeof(int32_t) * 3 * (size_t)nt) == 0) {
+            conn = c.get();
+            break;
+        }
+    double S0 = 0.0, V0 = 0.0;
+    if (conn) {
+        if (const char* err = mesh_geometry(rest_xyz, n, tris, nt, S0, V0)) return fail(ctx, LB_ERR_ARG, err);
+    } else {
+        std::unique_ptr<MeshConn> c(new MeshConn);
+        if (const char* err = build_conn(rest_xyz, n, tris, nt, *c, S0, V0)) return fail(ctx, LB_ERR_ARG, err);
+        ctx->conn_cache.push_back(std::move(c));
+        conn = ctx->conn_cache.back().get();
+    }
     const double* x = rest_xyz;
-
-    auto theta0 = [&](int a, int b) {
-        if (a > b) std::swap(a, b);
-        const int c = third.at(a, b);
-        const int d = third.at(b, a);
-        return dihedral_host(x + 3 * a, x + 3 * b, x + 3 * c, x + 3 * d);
-    };
     const int node0 = (int)ctx->hq0.size();
     const int cell = (int)ctx->hcells.size();
-    // fixed-point rest positions
-    std::vector<Q4> q0(n);
-    for (int i = 0; i < n; ++i) {
-        q0[i].x = to_fixed(x[3 * i]);
-        q0[i].y = to_fixed(x[3 * i + 1]);
-        q0[i].z = to_fixed(x[3 * i + 2]);
-        q0[i].w = 0;
-    }
-    // triangles, and for each directed edge u -> v the triangle and position
-    // of u in it; edges (a, b) with a < b in triangle order
     const int tri0 = (int)ctx->htris.size();
-    DirEdges tri_of(n, tris, nt);    // directed edge -> 3 t + position
-    DirEdges edge_of(n, tris, nt);   // (a, b), a < b -> edge index
+    const int e0 = (int)ctx->hedges.size();
+    for (int i = 0; i < n; ++i) {
+        Q4 q;   // fixed-point rest position
+        q.x = to_fixed(x[3 * i]);
+        q.y = to_fixed(x[3 * i + 1]);
+        q.z = to_fixed(x[3 * i + 2]);
+        q.w = 0;
+        ctx->hq0.push_back(q);
+        ctx->hq.push_back(q);
+        ctx->hrest.insert(ctx->hrest.end(), x + 3 * i, x + 3 * i + 3);
+    }
     for (int t = 0; t < nt; ++t) {
         const int v[3] = {tris[3 * t], tris[3 * t + 1], tris[3 * t + 2]};
         ctx->htris.push_back(make_int4(node0 + v[0], node0 + v[1], node0 + v[2], cell));
         ctx->htriS0.push_back((float)tri_area_host(x + 3 * v[0], x + 3 * v[1], x + 3 * v[2]));
-        for (int k = 0; k < 3; ++k) {
-            const int a = v[k], b = v[(k + 1) % 3];
-            tri_of.put(a, b, 3 * (tri0 + t) + k);
-            if (a < b) {
-                const int c = third.at(a, b), d = third.at(b, a);
-                const double* xa = x + 3 * a;
-                const double* xb = x + 3 * b;
-                const double L0 = std::sqrt((xb[0] - xa[0]) * (xb[0] - xa[0]) + (xb[1] - xa[1]) * (xb[1] - xa[1]) +
-                                            (xb[2] - xa[2]) * (xb[2] - xa[2]));
-                edge_of.put(a, b, (int)ctx->hedges.size());
-                ctx->hedges.push_back(make_int4(node0 + a, node0 + b, node0 + c, node0 + d));
-                ctx->hedge_rest.push_back(make_float4((float)L0, (float)theta0(a, b), (float)mod->ks, (float)mod->kb));
-            }
-        }
     }
-    auto edge_id = [&](int u, int v) { return edge_of.at(std::min(u, v), std::max(u, v)); };
-    for (int i = 0; i < n; ++i) {
-        ctx->hq0.push_back(q0[i]);
-        ctx->hq.push_back(q0[i]);
-        const std::vector<int>& r = ringv[i];
-        const int k = (int)r.size();
-        ctx->hinfo.push_back(make_int4(cell, node0, (int)ctx->hslots.size(), k | (ctx->cur << 8)));
-        for (int j = 0; j < k; ++j) {
-            // slot j: triangle (i, nb, nx), edge (i, nb), opposite edge (nb, nx)
-            const int nb = r[j], nx = r[(j + 1) % k];
-            const int tk = tri_of.at(i, nb);
-            const int role1 = i < nb ? 0 : 1;    // i is a or b of edge (i, nb)
-            const int role2 = nb < nx ? 2 : 3;   // i is c or d of edge (nb, nx)
-            ctx->hslots.push_back(make_int4(tk, 4 * edge_id(i, nb) + role1, 4 * edge_id(nb, nx) + role2, tk / 3));
-        }
+    // edges: rest length now, rest dihedral angle when the context commits
+    for (const int4& e : conn->edges) {
+        const double* xa = x + 3 * e.x;
+        const double* xb = x + 3 * e.y;
+        const double L0 = std::sqrt((xb[0] - xa[0]) * (xb[0] - xa[0]) + (xb[1] - xa[1]) * (xb[1] - xa[1]) +
+                                    (xb[2] - xa[2]) * (xb[2] - xa[2]));
+        ctx->hedges.push_back(make_int4(node0 + e.x, node0 + e.y, node0 + e.z, node0 + e.w));
+        ctx->hedge_rest.push_back(make_float4((float)L0, 0.f, (float)mod->ks, (float)mod->kb));
     }
+    const int slot0 = (int)ctx->hslots.size();
+    for (int i = 0; i < n; ++i)
+        ctx->hinfo.push_back(make_int4(cell, node0, slot0 + conn->ring_off[i], conn->valence[i] | (ctx->cur << 8)));
+    for (const int4& sl : conn->slots)
+        ctx->hslots.push_back(make_int4(3 * tri0 + sl.x, 4 * e0 + sl.y, 4 * e0 + sl.z, tri0 + sl.w));
     CellDev cd;
     std::memset(&cd, 0, sizeof(cd));
     cd.ch = ctx->cur;
