@@ -1632,10 +1632,6 @@ struct MeshTopology {
     MeshTopology(int n, const int32_t* tris, int nt) : third(n, tris, nt), out_deg(n, 0), ringv(n) {}
 };
 
-// Checks that (x, tris) is a closed, outward, oriented 2-manifold whose every
-// node is a single fan of at most MAX_VALENCE triangles, and builds its
-// topology into *topo.  Returns nullptr, or why the mesh is refused.  Host
-// code only.
 // The rest area and volume (FP64) of a mesh whose connectivity is valid;
 // refuses non-finite positions and an inward orientation.
 const char* mesh_geometry(const double* x, int n, const int32_t* tris, int nt, double& S0, double& V0) {
@@ -1655,6 +1651,10 @@ const char* mesh_geometry(const double* x, int n, const int32_t* tris, int nt, d
     return nullptr;
 }
 
+// Checks that (x, tris) is a closed, outward, oriented 2-manifold whose every
+// node is a single fan of at most MAX_VALENCE triangles, and builds its
+// topology into *topo.  Returns nullptr, or why the mesh is refused.  Host
+// code only.
 const char* mesh_topology(const double* x, int n, const int32_t* tris, int nt, std::unique_ptr<MeshTopology>& topo) {
     if (!x || !tris || n < 4 || nt < 4) return "mesh needs >= 4 nodes and triangles";
     for (int k = 0; k < 3 * n; ++k)
@@ -1699,9 +1699,9 @@ const char* mesh_topology(const double* x, int n, const int32_t* tris, int nt, s
         if (topo->ringv[i].empty()) return "mesh has an isolated node";
     return mesh_geometry(x, n, tris, nt, topo->S0, topo->V0);
 }
-}  // namespace
 
-namespace {
+// Checks a mesh and builds its connectivity tables into c (and its rest area
+// and volume); nullptr, or why the mesh is refused.
 const char* build_conn(const double* x, int n, const int32_t* tris, int nt, MeshConn& c, double& S0, double& V0) {
     std::unique_ptr<MeshTopology> topo;
     if (const char* err = mesh_topology(x, n, tris, nt, topo)) return err;
