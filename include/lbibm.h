@@ -324,8 +324,10 @@ lb_status lb_readback_wait(lb_ctx* ctx, int slot);
 /* Node forces spread in the last step (n x 3, host). */
 lb_status ibm_get_forces(lb_ctx* ctx, int mesh_id, double* f);
 
-/* Per-cell surface area and volume at the current positions (FP64 sums),
- * for every mesh of the selected channel, in mesh order (host). */
+/* Per-cell surface area and volume at the current positions (the rest values
+ * plus the sums of the per-triangle changes, added exactly in 2^-40 fixed
+ * point; FP64 results), for every mesh of the selected channel, in mesh order
+ * (host). */
 lb_status ibm_get_area_volume(lb_ctx* ctx, double* area, double* volume);
 
 /* Surface area and enclosed volume of closed triangle meshes, allocating no

@@ -1,7 +1,7 @@
 // Immersed-boundary kernels (Gusenbauer et al., arXiv:1110.0995, Sec. 2.2-2.3):
 //   k_cell_sums      per-cell change of surface area and volume, FP32 per-triangle
-//                    terms accumulated in FP64 (Sec. 2.3.3: the global area and
-//                    volume constraints need every node of a cell)
+//                    terms added as exact 2^-40 fixed-point integers (Sec. 2.3.3:
+//                    the global area and volume constraints need every node of a cell)
 //   k_elements       the same per-triangle pass plus each triangle's area and
 //                    volume force terms, and per edge its stretching and
 //                    bending forces (Sec. 2.3.1), every element evaluated once
