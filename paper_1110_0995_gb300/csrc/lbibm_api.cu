@@ -56,6 +56,14 @@ struct MeshConn {
     std::vector<int> ring_off, valence;
 };
 
+// A mesh added to the context: its connectivity and where its nodes,
+// triangles, edges and ring slots go in the context's tables.
+struct PendingMesh {
+    const MeshConn* conn;
+    int node0, tri0, e0, slot0, cell, ch;
+    float ks, kb;
+};
+
 struct EventPair {
     cudaEvent_t a, b;
     int cls;
@@ -98,8 +106,11 @@ struct lb_ctx {
     std::vector<float> htriS0;
     std::vector<int4> hchunks;
     std::vector<CellDev> hcells;
-    std::vector<double> hrest;     // rest positions (x, y, z per node), for the rest dihedral angles
+    std::vector<double> hrest;     // rest positions (x, y, z per node)
     std::vector<std::unique_ptr<MeshConn>> conn_cache;   // connectivity per distinct triangle list
+    std::vector<PendingMesh> pending_meshes;             // meshes whose tables the commit writes
+    int n_tris_staged = 0, n_edges_staged = 0, n_slots_staged = 0;
+    float* fields_buf = nullptr;   // device scratch of lb_get_fields (4 floats per node of the largest channel)
     std::vector<MeshHost> meshes;
     std::vector<std::vector<int>> ch_meshes;
     bool committed = false;
@@ -769,31 +780,64 @@ void apply_k3_config(lb_ctx* ctx, K3Config c) {
     ctx->total_blocks = blk;
 }
 
-// The rest dihedral angle of every edge (the bending's theta0, Sec. 2.3.1)
-// from the rest positions, on up to 16 host threads.
-void rest_dihedrals(lb_ctx* ctx) {
-    const int E = (int)ctx->hedges.size();
+// The element and ring tables of every mesh (triangles with their rest
+// areas, edges with rest length and rest dihedral angle (the bending's
+// theta0, Sec. 2.3.1), each node's ring slots), written at the commit, the
+// meshes spread over up to 16 host threads (each writes only its own ranges).
+void build_tables(lb_ctx* ctx) {
+    ctx->htris.resize(ctx->n_tris_staged);
+    ctx->htriS0.resize(ctx->n_tris_staged);
+    ctx->hedges.resize(ctx->n_edges_staged);
+    ctx->hedge_rest.resize(ctx->n_edges_staged);
+    ctx->hslots.resize(ctx->n_slots_staged);
+    ctx->hinfo.resize(ctx->hq0.size());
     const double* x = ctx->hrest.data();
-    auto run = [ctx, x](int e0, int e1) {
-        for (int e = e0; e < e1; ++e) {
-            const int4 v = ctx->hedges[e];
-            ctx->hedge_rest[e].y = (float)dihedral_host(x + 3 * v.x, x + 3 * v.y, x + 3 * v.z, x + 3 * v.w);
+    auto one = [ctx, x](const PendingMesh& pm) {
+        const MeshConn& c = *pm.conn;
+        const int node0 = pm.node0;
+        for (int t = 0; t < c.nt; ++t) {
+            const int v[3] = {c.tris[3 * t], c.tris[3 * t + 1], c.tris[3 * t + 2]};
+            ctx->htris[pm.tri0 + t] = make_int4(node0 + v[0], node0 + v[1], node0 + v[2], pm.cell);
+            ctx->htriS0[pm.tri0 + t] =
+                (float)tri_area_host(x + 3 * (node0 + v[0]), x + 3 * (node0 + v[1]), x + 3 * (node0 + v[2]));
+        }
+        for (size_t k = 0; k < c.edges.size(); ++k) {
+            const int4 e = c.edges[k];
+            const int4 g = make_int4(node0 + e.x, node0 + e.y, node0 + e.z, node0 + e.w);
+            const double* xa = x + 3 * g.x;
+            const double* xb = x + 3 * g.y;
+            const double L0 = std::sqrt((xb[0] - xa[0]) * (xb[0] - xa[0]) + (xb[1] - xa[1]) * (xb[1] - xa[1]) +
+                                        (xb[2] - xa[2]) * (xb[2] - xa[2]));
+            const double th0 = dihedral_host(xa, xb, x + 3 * g.z, x + 3 * g.w);
+            ctx->hedges[pm.e0 + k] = g;
+            ctx->hedge_rest[pm.e0 + k] = make_float4((float)L0, (float)th0, pm.ks, pm.kb);
+        }
+        for (int i = 0; i < c.n; ++i)
+            ctx->hinfo[node0 + i] = make_int4(pm.cell, node0, pm.slot0 + c.ring_off[i], c.valence[i] | (pm.ch << 8));
+        for (size_t k = 0; k < c.slots.size(); ++k) {
+            const int4 sl = c.slots[k];
+            ctx->hslots[pm.slot0 + k] = make_int4(3 * pm.tri0 + sl.x, 4 * pm.e0 + sl.y, 4 * pm.e0 + sl.z, pm.tri0 + sl.w);
         }
     };
-    const int nth = std::max(1, std::min({16, (int)std::thread::hardware_concurrency(), E / 8192}));
+    const int nm = (int)ctx->pending_meshes.size();
+    const int nth = std::max(1, std::min({16, (int)std::thread::hardware_concurrency(), nm / 4}));
     if (nth == 1) {
-        run(0, E);
-        return;
+        for (const PendingMesh& pm : ctx->pending_meshes) one(pm);
+    } else {
+        std::vector<std::thread> th;
+        for (int t = 0; t < nth; ++t)
+            th.emplace_back([&, t] {
+                for (int m = t; m < nm; m += nth) one(ctx->pending_meshes[m]);
+            });
+        for (auto& t : th) t.join();
     }
-    std::vector<std::thread> th;
-    const int per = (E + nth - 1) / nth;
-    for (int t = 0; t < nth; ++t) th.emplace_back(run, std::min(E, t * per), std::min(E, (t + 1) * per));
-    for (auto& t : th) t.join();
+    ctx->pending_meshes.clear();
 }
 
 lb_status commit_ibm(lb_ctx* ctx) {
     if (ctx->committed) return LB_OK;
     ctx->committed = true;
+    build_tables(ctx);
     ctx->M = (int)ctx->hq0.size();
     ctx->C = (int)ctx->hcells.size();
     ctx->T = (int)ctx->htris.size();
@@ -843,7 +887,6 @@ lb_status commit_ibm(lb_ctx* ctx) {
             LB_CUDA(up(&ctx->rep_bead_ch, bc));
         }
     }
-    rest_dihedrals(ctx);
     LB_CUDA(up(&ctx->edges, ctx->hedges));
     LB_CUDA(up(&ctx->edge_rest, ctx->hedge_rest));
     LB_CUDA(dalloc(ctx, &ctx->eS, ctx->E));
@@ -1785,8 +1828,7 @@ lb_status ibm_add_mesh(lb_ctx* ctx, const double* rest_xyz, int n, const int32_t
     const double* x = rest_xyz;
     const int node0 = (int)ctx->hq0.size();
     const int cell = (int)ctx->hcells.size();
-    const int tri0 = (int)ctx->htris.size();
-    const int e0 = (int)ctx->hedges.size();
+    const int tri0 = ctx->n_tris_staged;
     for (int i = 0; i < n; ++i) {
         Q4 q;   // fixed-point rest position
         q.x = to_fixed(x[3 * i]);
@@ -1795,27 +1837,24 @@ lb_status ibm_add_mesh(lb_ctx* ctx, const double* rest_xyz, int n, const int32_t
         q.w = 0;
         ctx->hq0.push_back(q);
         ctx->hq.push_back(q);
-        ctx->hrest.insert(ctx->hrest.end(), x + 3 * i, x + 3 * i + 3);
     }
-    for (int t = 0; t < nt; ++t) {
-        const int v[3] = {tris[3 * t], tris[3 * t + 1], tris[3 * t + 2]};
-        ctx->htris.push_back(make_int4(node0 + v[0], node0 + v[1], node0 + v[2], cell));
-        ctx->htriS0.push_back((float)tri_area_host(x + 3 * v[0], x + 3 * v[1], x + 3 * v[2]));
-    }
-    // edges: rest length now, rest dihedral angle when the context commits
-    for (const int4& e : conn->edges) {
-        const double* xa = x + 3 * e.x;
-        const double* xb = x + 3 * e.y;
-        const double L0 = std::sqrt((xb[0] - xa[0]) * (xb[0] - xa[0]) + (xb[1] - xa[1]) * (xb[1] - xa[1]) +
-                                    (xb[2] - xa[2]) * (xb[2] - xa[2]));
-        ctx->hedges.push_back(make_int4(node0 + e.x, node0 + e.y, node0 + e.z, node0 + e.w));
-        ctx->hedge_rest.push_back(make_float4((float)L0, 0.f, (float)mod->ks, (float)mod->kb));
-    }
-    const int slot0 = (int)ctx->hslots.size();
-    for (int i = 0; i < n; ++i)
-        ctx->hinfo.push_back(make_int4(cell, node0, slot0 + conn->ring_off[i], conn->valence[i] | (ctx->cur << 8)));
-    for (const int4& sl : conn->slots)
-        ctx->hslots.push_back(make_int4(3 * tri0 + sl.x, 4 * e0 + sl.y, 4 * e0 + sl.z, tri0 + sl.w));
+    ctx->hrest.insert(ctx->hrest.end(), x, x + 3 * (size_t)n);
+    // the element and ring tables are written when the context commits
+    // (every mesh's ranges at once, on host threads)
+    PendingMesh pm;
+    pm.conn = conn;
+    pm.node0 = node0;
+    pm.tri0 = tri0;
+    pm.e0 = ctx->n_edges_staged;
+    pm.slot0 = ctx->n_slots_staged;
+    pm.cell = cell;
+    pm.ch = ctx->cur;
+    pm.ks = (float)mod->ks;
+    pm.kb = (float)mod->kb;
+    ctx->pending_meshes.push_back(pm);
+    ctx->n_tris_staged += nt;
+    ctx->n_edges_staged += (int)conn->edges.size();
+    ctx->n_slots_staged += (int)conn->slots.size();
     CellDev cd;
     std::memset(&cd, 0, sizeof(cd));
     cd.ch = ctx->cur;
@@ -2080,16 +2119,19 @@ lb_status lb_get_fields(lb_ctx* ctx, float* rho, float* u, int dst_is_device) {
         LB_CUDA(cudaStreamSynchronize(ctx->stream));
         return LB_OK;
     }
-    float* buf = nullptr;
-    LB_CUDA(dalloc(ctx, &buf, (size_t)4 * n));
-    lb_status st = LB_OK;
+    if (!ctx->fields_buf) {
+        // one device scratch for every later call: 4 floats per node of the largest channel
+        long long nmax = 0;
+        for (const ChannelHost& ch : ctx->ch) nmax = std::max<long long>(nmax, ch.d.n);
+        LB_CUDA(dalloc(ctx, &ctx->fields_buf, (size_t)4 * nmax));
+    }
+    float* buf = ctx->fields_buf;
     cudaError_t e = launch_fields(a, ctx->cur, rho ? buf : nullptr, u ? buf + n : nullptr, ctx->stream);
     if (e == cudaSuccess && rho) e = cudaMemcpyAsync(rho, buf, sizeof(float) * n, cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess && u) e = cudaMemcpyAsync(u, buf + n, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-    if (e != cudaSuccess) st = cuda_fail(ctx, e, "lb_get_fields");
-    dfree(ctx, buf);
-    return st;
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "lb_get_fields");
+    return LB_OK;
 }
 
 lb_status lb_get_populations(lb_ctx* ctx, double* f) {

@@ -288,10 +288,18 @@ class Simulation:
 
     # -- outputs -----------------------------------------------------------
     def fields(self):
-        rho = np.zeros(self.N, np.float32)
-        u = np.zeros((3, self.N), np.float32)
+        rho = np.empty(self.N, np.float32)
+        u = np.empty((3, self.N), np.float32)
         self._check(self._L.lb_get_fields(self._h, _ptr(rho), _ptr(u), 0))
         return rho, u
+
+    def fields_into(self, rho: np.ndarray, u: np.ndarray):
+        """The fields of the selected channel into caller buffers (float32,
+        contiguous, N and 3 x N values; page-locked buffers copy fastest)."""
+        for a, n in ((rho, self.N), (u, 3 * self.N)):
+            if a.dtype != np.float32 or not a.flags.c_contiguous or a.size != n:
+                raise ValueError(f"expected a contiguous float32 array of {n} values")
+        self._check(self._L.lb_get_fields(self._h, _ptr(rho), _ptr(u), 0))
 
     def fields_to_device(self, rho_ptr: int, u_ptr: int):
         self._check(self._L.lb_get_fields(self._h, ctypes.c_void_p(rho_ptr), ctypes.c_void_p(u_ptr), 1))
