@@ -193,7 +193,9 @@ lb_status lb_get_mask(lb_ctx* ctx, uint8_t* solid);
  * triangles.  The mesh must be a closed oriented 2-manifold with positive
  * volume and node valence <= 64 (LB_ERR_ARG otherwise). Positions are kept
  * in 64-bit fixed point with 2^-40 lu resolution.  Only before the first
- * lb_step.  *mesh_id receives the index of the mesh within the channel. */
+ * lb_step.  *mesh_id receives the index of the mesh within the channel.
+ * Meshes with the same triangle list share one connectivity check; the
+ * element tables are built by the first lb_step. */
 lb_status ibm_add_mesh(lb_ctx* ctx, const double* rest_xyz, int n_nodes, const int32_t* tris, int n_tris,
                        const ibm_moduli* moduli, int* mesh_id);
 
