@@ -821,16 +821,23 @@ void build_tables(lb_ctx* ctx) {
     };
     const int nm = (int)ctx->pending_meshes.size();
     const int nth = std::max(1, std::min({16, (int)std::thread::hardware_concurrency(), nm / 4}));
-    if (nth == 1) {
-        for (const PendingMesh& pm : ctx->pending_meshes) one(pm);
-    } else {
-        std::vector<std::thread> th;
-        for (int t = 0; t < nth; ++t)
+    // thread t takes meshes t, t + nth, ...; a thread that cannot be started
+    // leaves its meshes to this one (no exception leaves the library)
+    std::vector<std::thread> th;
+    std::vector<int> serial;
+    for (int t = 1; t < nth; ++t) {
+        try {
             th.emplace_back([&, t] {
                 for (int m = t; m < nm; m += nth) one(ctx->pending_meshes[m]);
             });
-        for (auto& t : th) t.join();
+        } catch (...) {
+            serial.push_back(t);
+        }
     }
+    for (int m = 0; m < nm; m += nth) one(ctx->pending_meshes[m]);
+    for (int t : serial)
+        for (int m = t; m < nm; m += nth) one(ctx->pending_meshes[m]);
+    for (auto& t : th) t.join();
     ctx->pending_meshes.clear();
 }
 
