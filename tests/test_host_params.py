@@ -133,3 +133,20 @@ def test_guard_zone_size_is_checked_on_the_host(lbibm):
     assert "1 GiB" in lbibm.last_error()
     assert L.lb_set_guard_zones(4096) == lbibm.LB_OK
     assert L.lb_set_guard_zones(0) == lbibm.LB_OK
+
+
+def test_fields_into_checks_its_buffers(lbibm):
+    """The caller's field buffers must be contiguous float32 arrays of N and
+    3 N values; anything else is refused in the binding, before the C ABI is
+    called (no context is needed to see it)."""
+    import numpy as np
+
+    sim = lbibm.Simulation.__new__(lbibm.Simulation)
+    sim.dims = [(4, 4, 4)]
+    sim.channel = 0
+    rho, u = np.empty(64, np.float32), np.empty(192, np.float32)
+    bad = [(np.empty(64, np.float64), u), (rho, np.empty(191, np.float32)),
+           (np.empty(128, np.float32)[::2], u), (rho, np.empty((3, 64), np.float32).T)]
+    for r, v in bad:
+        with pytest.raises(ValueError, match="contiguous float32"):
+            sim.fields_into(r, v)
