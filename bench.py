@@ -530,6 +530,7 @@ def run_ours(args):
             "kernel_ms_per_step": {"elements": kms[0] / max(1, kn[0]), "forces_spread": kms[1] / max(1, kn[1]),
                                    "stream_collide": k3_ms, "interp_advance": kms[3] / max(1, kn[3])},
             "ib_node_updates_per_s": world * n_ib * args.steps / (ms * 1e-3),
+            "mlups_fluid_nodes": value * n_fluid / n_nodes,
             "gpu_launches": int(sum(kn)),
             "kernel_timing": {"ms_per_step_with_events": ms_ev / args.steps, "clocks": clk_ev.summary(),
                               "how": "second pass over the same K steps from the same saved state, "
